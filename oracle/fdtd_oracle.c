@@ -1,0 +1,564 @@
+/*
+ * fdtd_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, FP64 CPU restatement of the hot path of Hassan & Cala Lesina,
+ * "Topology optimization of dispersive plasmonic nanostructures in the
+ * time-domain" (arXiv 2203.01462).  It exists to check the CUDA library: only
+ * the tests, the smoke check and the benchmark's CPU-baseline leg load it.  It
+ * shares no code, header, table or constant generator with the CUDA library,
+ * and the product path never calls it.
+ *
+ * Every quantity is in SI units.  The steps follow the paper in its order:
+ *
+ *   Sec. 2.1, Eq. (5a-c)  rho_i -> eps_inf_i, psi_i, sigma_i (linear in rho for
+ *                         eps_inf and psi = omega_p^2, parabolic sigma).
+ *   Sec. 3.1, Eq. (10)    eps0 eps_inf dE/dt + J + sigma E - curl H = -J_src
+ *                         dJ/dt + gamma J - eps0 psi E = 0
+ *                         mu0 dH/dt + curl E = 0
+ *   Sec. 3.2              Yee grid, E (and J) at integer steps, H at half
+ *                         steps.  The paper says it uses the ADE approach but
+ *                         prints no update; the reading taken here is a
+ *                         trapezoidal average of J and sigma E over the step,
+ *                         so that each node solves a 2x2 linear system.
+ *                         Open boundaries: CPML (Roden-Gedney recursive
+ *                         convolution), PEC walls behind it.
+ *   Eq. (24)              W~ = eps_g dt dx^d / 2 * sum_{n=0..N} sum_gap (E^n)^2
+ *                         (d = 2 in 2D, i.e. per unit length in z).
+ *   Eq. (20)              adjoint run: the same solver, started from rest,
+ *                         driven by eps_g E(T - tau) in the gap; its E*, J*
+ *                         live at half steps.
+ *   Eq. (25a-c)           pointwise sensitivities, sums over n = 0..N of
+ *                         E_i^{N-n} times half-step averages / differences of
+ *                         the adjoint fields (E*^{-1/2} = J*^{-1/2} = 0).
+ *   Eq. (26), (27)        filtered design rho~ = F(rho) and the chain rule.
+ *                         F is a normalised Gaussian; the chain rule applies
+ *                         F^T (the paper writes the diagonal d rho~_i/d rho_i).
+ *
+ * The oracle keeps whole arrays (no slabs), loops node by node and solves
+ * each node's 2x2 system by Cramer's rule.  Loops over nodes may run under
+ * OpenMP; every per-node result and every sum is formed in a fixed order, so
+ * results do not depend on the thread count.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* CODATA 2018 values. */
+#define OR_C0 299792458.0
+#define OR_MU0 1.25663706212e-6
+#define OR_PI 3.14159265358979323846
+
+typedef struct or_config {
+    int ndim;              /* 2: TM_z (Ez, Hx, Hy, Jz); 3: full Yee            */
+    int nx, ny, nz;        /* nodes (2D) / cells (3D) per axis                  */
+    double dx;             /* grid step, m                                      */
+    double courant;        /* S = c0 dt / dx                                    */
+    int npml;              /* CPML layers on each open side; 0 = PEC walls      */
+    double pml_m;          /* polynomial grading order                          */
+    double pml_sigma_factor; /* sigma_pml_max = factor (m+1) / (eta0 dx)         */
+    double pml_kappa_max;
+    double pml_alpha_max;  /* S/m, linear taper to 0 at the outer wall          */
+    int periodic_x;        /* 2D: x is periodic (no walls, no CPML in x)        */
+    double eps_inf, omega_p, gamma_p; /* Drude material, Eq. (1)                */
+    double eps_s;          /* background relative permittivity                  */
+    double psi_s_ratio;    /* psi_s = ratio * omega_p^2 (the paper uses 1/100)  */
+    double eps_g;          /* gap (observation region) permittivity             */
+    int design_lo[3], design_hi[3]; /* design box, half-open node/cell ranges   */
+    int gap_lo[3], gap_hi[3];       /* gap box (inside the design box)          */
+    int src_lo[3], src_hi[3];       /* soft current source box (Ez nodes/edges) */
+    int nbands;            /* 1 or 2 Gaussian-modulated carriers                */
+    double f0[2];          /* carrier frequencies, Hz                           */
+    double tau, t0;        /* Gaussian envelope exp(-((t-t0)/tau)^2), s         */
+    double src_amp;        /* J_src = src_amp * eps0 c0 / dx * g(t), A/m^2      */
+    int nsteps;            /* N: E^0 .. E^N                                     */
+    int filter_radius;     /* Gaussian filter half-width in cells; 0 = none     */
+    double filter_sigma;   /* Gaussian filter standard deviation in cells       */
+    int sigma_form;        /* 0: rho(1-rho) smax (Eq. 5c); 1: 4 rho(1-rho) smax */
+    double sub_eps;        /* 3D: background eps for cells with k < sub_hi      */
+    int sub_hi;
+} or_config;
+
+static int g_threads = 1;
+
+void or_set_threads(int n)
+{
+    g_threads = n < 1 ? 1 : n;
+#ifdef _OPENMP
+    omp_set_num_threads(g_threads);
+#endif
+}
+
+int or_get_threads(void) { return g_threads; }
+
+static double or_eps0(void) { return 1.0 / (OR_MU0 * OR_C0 * OR_C0); }
+static double or_dt(const or_config *c) { return c->courant * c->dx / OR_C0; }
+
+/* Excitation: Gaussian-modulated carrier(s).  The paper drives with a
+ * windowed sinc (Sec. 2); the workloads here use a Gaussian envelope. */
+static double or_signal(const or_config *c, double t)
+{
+    double env = exp(-((t - c->t0) / c->tau) * ((t - c->t0) / c->tau));
+    double s = 0.0;
+    for (int b = 0; b < c->nbands; ++b)
+        s += sin(2.0 * OR_PI * c->f0[b] * (t - c->t0));
+    return env * s;
+}
+
+/* Eq. (5a-c): material of one design node from its filtered density. */
+void or_material(const or_config *c, double rho, double sigma_max,
+                 double *eps_i, double *psi_i, double *sig_i)
+{
+    double psi = c->omega_p * c->omega_p;
+    double psi_s = c->psi_s_ratio * psi;
+    *eps_i = c->eps_s + rho * (c->eps_inf - c->eps_s);
+    *psi_i = psi_s + rho * (psi - psi_s);
+    *sig_i = rho * (1.0 - rho) * sigma_max * (c->sigma_form ? 4.0 : 1.0);
+}
+
+/* ---------------------------------------------------------------- boxes */
+
+static int in_box(const int *lo, const int *hi, int i, int j, int k)
+{
+    return i >= lo[0] && i < hi[0] && j >= lo[1] && j < hi[1] && k >= lo[2] && k < hi[2];
+}
+
+static long box_count(const int *lo, const int *hi, int ndim)
+{
+    long n = 1;
+    for (int a = 0; a < ndim; ++a) {
+        if (hi[a] <= lo[a]) return 0;
+        n *= hi[a] - lo[a];
+    }
+    return n;
+}
+
+int or_sizes(const or_config *c, long *n_design, long *n_gap)
+{
+    *n_design = box_count(c->design_lo, c->design_hi, c->ndim);
+    *n_gap = box_count(c->gap_lo, c->gap_hi, c->ndim);
+    return 0;
+}
+
+/* ------------------------------------------------------------- filter */
+
+/* Eq. (26): rho~ = F(rho), F a Gaussian window of half-width R cells,
+ * weights renormalised where the window leaves the design box.  Written as
+ * the plain double (2D) or triple (3D) sum. */
+static void filter_apply(const or_config *c, const double *in, double *out, int transpose)
+{
+    int w = c->design_hi[0] - c->design_lo[0];
+    int h = c->design_hi[1] - c->design_lo[1];
+    int d = c->ndim == 3 ? c->design_hi[2] - c->design_lo[2] : 1;
+    int R = c->filter_radius;
+    long M = (long)w * h * d;
+    if (R <= 0) {
+        memcpy(out, in, sizeof(double) * M);
+        return;
+    }
+    double s2 = 2.0 * c->filter_sigma * c->filter_sigma;
+    int Rz = c->ndim == 3 ? R : 0;
+    double *norm = (double *)malloc(sizeof(double) * M);
+    for (int z = 0; z < d; ++z)
+        for (int y = 0; y < h; ++y)
+            for (int x = 0; x < w; ++x) {
+                double s = 0.0;
+                for (int dz = -Rz; dz <= Rz; ++dz)
+                    for (int dy = -R; dy <= R; ++dy)
+                        for (int dx = -R; dx <= R; ++dx) {
+                            int xx = x + dx, yy = y + dy, zz = z + dz;
+                            if (xx < 0 || xx >= w || yy < 0 || yy >= h || zz < 0 || zz >= d) continue;
+                            s += exp(-(dx * dx + dy * dy + dz * dz) / s2);
+                        }
+                norm[((long)z * h + y) * w + x] = s;
+            }
+    for (long m = 0; m < M; ++m) out[m] = 0.0;
+    for (int z = 0; z < d; ++z)
+        for (int y = 0; y < h; ++y)
+            for (int x = 0; x < w; ++x) {
+                long i = ((long)z * h + y) * w + x;
+                double acc = 0.0;
+                for (int dz = -Rz; dz <= Rz; ++dz)
+                    for (int dy = -R; dy <= R; ++dy)
+                        for (int dx = -R; dx <= R; ++dx) {
+                            int xx = x + dx, yy = y + dy, zz = z + dz;
+                            if (xx < 0 || xx >= w || yy < 0 || yy >= h || zz < 0 || zz >= d) continue;
+                            long j = ((long)zz * h + yy) * w + xx;
+                            double wij = exp(-(dx * dx + dy * dy + dz * dz) / s2);
+                            if (!transpose)
+                                acc += wij * in[j];           /* row i of F times rho   */
+                            else
+                                out[j] += wij / norm[i] * in[i]; /* column i of F^T    */
+                        }
+                if (!transpose) out[i] = acc / norm[i];
+            }
+    free(norm);
+}
+
+void or_filter(const or_config *c, const double *in, double *out) { filter_apply(c, in, out, 0); }
+void or_filter_T(const or_config *c, const double *in, double *out) { filter_apply(c, in, out, 1); }
+
+/* --------------------------------------------------------------- CPML */
+
+/* Depth (in cells) of a position p (in cell units) inside the absorbing
+ * layer of an axis with n nodes; 0 in the interior. */
+static double pml_depth(const or_config *c, int n, double p)
+{
+    double L = c->npml;
+    if (c->npml <= 0) return 0.0;
+    if (p < L) return L - p;
+    if (p > (n - 1) - L) return p - ((n - 1) - L);
+    return 0.0;
+}
+
+typedef struct { double b, c, kappa; } pml_coef;
+
+/* Roden-Gedney CPML: sigma, kappa polynomially graded, alpha linear. */
+static pml_coef pml_at(const or_config *c, int n, double p)
+{
+    pml_coef r = {0.0, 0.0, 1.0};
+    double d = pml_depth(c, n, p);
+    if (d <= 0.0) return r;
+    double eps0 = or_eps0();
+    double eta0 = OR_MU0 * OR_C0;
+    double x = d / c->npml;
+    double xm = pow(x, c->pml_m);
+    double smax = c->pml_sigma_factor * (c->pml_m + 1.0) / (eta0 * c->dx);
+    double sig = smax * xm;
+    double kap = 1.0 + (c->pml_kappa_max - 1.0) * xm;
+    double alp = c->pml_alpha_max * (1.0 - x);
+    r.kappa = kap;
+    r.b = exp(-(sig / kap + alp) * or_dt(c) / eps0);
+    r.c = sig > 0.0 ? sig / (sig * kap + kap * kap * alp) * (r.b - 1.0) : 0.0;
+    return r;
+}
+
+/* ------------------------------------------------------- node solve */
+
+/* One node of Eq. (10a,b) over one step, trapezoidal in J and sigma E:
+ *   eps0 eps (E'-E)/dt + (J'+J)/2 + sig (E'+E)/2 = curl - jsrc
+ *   (J'-J)/dt + gam (J'+J)/2 = eps0 psi (E'+E)/2
+ * solved for (E', J') by Cramer's rule. */
+static void node_solve(double eps, double psi, double sig, double gam, double dt,
+                       double curl, double jsrc, double *E, double *J)
+{
+    double eps0 = or_eps0();
+    double a11 = eps0 * eps / dt + 0.5 * sig, a12 = 0.5;
+    double a21 = -0.5 * eps0 * psi, a22 = 1.0 / dt + 0.5 * gam;
+    double b1 = (eps0 * eps / dt - 0.5 * sig) * (*E) - 0.5 * (*J) + curl - jsrc;
+    double b2 = (1.0 / dt - 0.5 * gam) * (*J) + 0.5 * eps0 * psi * (*E);
+    double det = a11 * a22 - a12 * a21;
+    *E = (b1 * a22 - a12 * b2) / det;
+    *J = (a11 * b2 - a21 * b1) / det;
+}
+
+/* ================================================================ 2D */
+
+typedef struct {
+    int nx, ny;
+    double *Ez, *Jz, *Hx, *Hy;
+    double *pezx, *pezy, *phxy, *phyx;   /* CPML convolution terms */
+} st2;
+
+typedef struct {
+    double *eps, *psi, *sig;             /* per Ez node */
+    double gam;                          /* Drude collision rate (scaled) */
+    pml_coef *ex, *ey, *hx, *hy;         /* CPML at E / H positions per axis */
+} mat2;
+
+static void st2_alloc(st2 *s, int nx, int ny)
+{
+    size_t n = (size_t)nx * ny;
+    s->nx = nx; s->ny = ny;
+    s->Ez = calloc(n, sizeof(double)); s->Jz = calloc(n, sizeof(double));
+    s->Hx = calloc(n, sizeof(double)); s->Hy = calloc(n, sizeof(double));
+    s->pezx = calloc(n, sizeof(double)); s->pezy = calloc(n, sizeof(double));
+    s->phxy = calloc(n, sizeof(double)); s->phyx = calloc(n, sizeof(double));
+}
+
+static void st2_free(st2 *s)
+{
+    free(s->Ez); free(s->Jz); free(s->Hx); free(s->Hy);
+    free(s->pezx); free(s->pezy); free(s->phxy); free(s->phyx);
+}
+
+/* Material of every Ez node.  Outside the design box: background eps_s.
+ * Design box: Eq. (5a-c) from the filtered density.  Gap: eps_g, no Drude. */
+static void mat2_build(const or_config *c, const double *rho_t, double sigma_max,
+                       double gamma_scale, mat2 *m)
+{
+    int nx = c->nx, ny = c->ny;
+    size_t n = (size_t)nx * ny;
+    m->eps = malloc(n * sizeof(double));
+    m->psi = calloc(n, sizeof(double));
+    m->sig = calloc(n, sizeof(double));
+    m->gam = c->gamma_p * gamma_scale;
+    int w = c->design_hi[0] - c->design_lo[0];
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t q = (size_t)j * nx + i;
+            m->eps[q] = c->eps_s;
+            if (in_box(c->gap_lo, c->gap_hi, i, j, 0)) {
+                m->eps[q] = c->eps_g;
+            } else if (in_box(c->design_lo, c->design_hi, i, j, 0)) {
+                double r = rho_t[(size_t)(j - c->design_lo[1]) * w + (i - c->design_lo[0])];
+                or_material(c, r, sigma_max, &m->eps[q], &m->psi[q], &m->sig[q]);
+            }
+        }
+    m->ex = malloc(nx * sizeof(pml_coef)); m->hx = malloc(nx * sizeof(pml_coef));
+    m->ey = malloc(ny * sizeof(pml_coef)); m->hy = malloc(ny * sizeof(pml_coef));
+    or_config cx = *c;
+    if (c->periodic_x) cx.npml = 0;
+    for (int i = 0; i < nx; ++i) { m->ex[i] = pml_at(&cx, nx, i); m->hx[i] = pml_at(&cx, nx, i + 0.5); }
+    for (int j = 0; j < ny; ++j) { m->ey[j] = pml_at(c, ny, j); m->hy[j] = pml_at(c, ny, j + 0.5); }
+}
+
+static void mat2_free(mat2 *m)
+{
+    free(m->eps); free(m->psi); free(m->sig);
+    free(m->ex); free(m->ey); free(m->hx); free(m->hy);
+}
+
+
+/* H half of one leapfrog step (2D TM_z): mu0 dH/dt = -curl E, so
+ * H^{n-1/2} -> H^{n+1/2} from E^n, with the CPML terms of each derivative. */
+static void step2_h(const or_config *c, const mat2 *m, st2 *s)
+{
+    int nx = c->nx, ny = c->ny, per = c->periodic_x;
+    double dx = c->dx, ch = or_dt(c) / OR_MU0;
+    #pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            size_t q = (size_t)j * nx + i;
+            if (j + 1 < ny) {
+                double dEy = (s->Ez[q + nx] - s->Ez[q]) / dx;
+                s->phxy[q] = m->hy[j].b * s->phxy[q] + m->hy[j].c * dEy;
+                s->Hx[q] -= ch * (dEy / m->hy[j].kappa + s->phxy[q]);
+            }
+            int ip = i + 1;
+            if (ip == nx) {
+                if (!per) continue;
+                ip = 0;
+            }
+            double dEx = (s->Ez[(size_t)j * nx + ip] - s->Ez[q]) / dx;
+            s->phyx[q] = m->hx[i].b * s->phyx[q] + m->hx[i].c * dEx;
+            s->Hy[q] += ch * (dEx / m->hx[i].kappa + s->phyx[q]);
+        }
+    }
+}
+
+/* E, J half of one leapfrog step (2D TM_z): Eq. (10a,b) at every Ez node,
+ * driven by the current density jsrc (per node, taken at n+1/2).  With PEC
+ * walls the outermost Ez nodes stay zero; with periodic x every column is
+ * updated and indices wrap. */
+static void step2_e(const or_config *c, const mat2 *m, st2 *s, const double *jsrc)
+{
+    int nx = c->nx, ny = c->ny, per = c->periodic_x;
+    double dt = or_dt(c), dx = c->dx;
+    #pragma omp parallel for schedule(static)
+    for (int j = 1; j < ny - 1; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            if (!per && (i == 0 || i == nx - 1)) continue;
+            int im = i == 0 ? nx - 1 : i - 1;
+            size_t q = (size_t)j * nx + i;
+            double dHy = (s->Hy[q] - s->Hy[(size_t)j * nx + im]) / dx;
+            double dHx = (s->Hx[q] - s->Hx[q - nx]) / dx;
+            s->pezx[q] = m->ex[i].b * s->pezx[q] + m->ex[i].c * dHy;
+            s->pezy[q] = m->ey[j].b * s->pezy[q] + m->ey[j].c * dHx;
+            double curl = dHy / m->ex[i].kappa + s->pezx[q] - dHx / m->ey[j].kappa - s->pezy[q];
+            node_solve(m->eps[q], m->psi[q], m->sig[q], m->gam, dt, curl,
+                       jsrc[q], &s->Ez[q], &s->Jz[q]);
+        }
+    }
+}
+
+/* Discrete electromagnetic energy (per unit length in z) at step n from E^n
+ * and the H half steps on either side: sum eps0 eps (E^n)^2 / 2 +
+ * mu0 H^{n-1/2} . H^{n+1/2} / 2, times dx^2.  Lossless media conserve it. */
+static double energy2(const or_config *c, const mat2 *m, const st2 *s,
+                      const double *Hx_old, const double *Hy_old)
+{
+    double eps0 = or_eps0(), e = 0.0;
+    size_t n = (size_t)c->nx * c->ny;
+    for (size_t q = 0; q < n; ++q) {
+        e += 0.5 * eps0 * m->eps[q] * s->Ez[q] * s->Ez[q];
+        e += 0.5 * OR_MU0 * (Hx_old[q] * s->Hx[q] + Hy_old[q] * s->Hy[q]);
+    }
+    return e * c->dx * c->dx;
+}
+
+/* Forward solve (2D).  Records E^n, n = 0..N, in the gap and the design box,
+ * optional probes and an optional energy trace (entries 0..N-1), and returns
+ * W~ of Eq. (24). */
+static int forward2(const or_config *c, const double *rho, double sigma_max, double gamma_scale,
+                    double *W, double *gap_hist, double *design_hist,
+                    const int *probes, int nprobe, double *probe_hist, double *energy)
+{
+    int nx = c->nx, N = c->nsteps;
+    long M, G;
+    or_sizes(c, &M, &G);
+    double *rho_t = malloc(sizeof(double) * (M ? M : 1));
+    if (M) or_filter(c, rho, rho_t);
+    mat2 m;
+    mat2_build(c, rho_t, sigma_max, gamma_scale, &m);
+    st2 s;
+    st2_alloc(&s, nx, c->ny);
+    size_t n = (size_t)nx * c->ny;
+    double *jsrc = calloc(n, sizeof(double));
+    double *hxo = energy ? calloc(n, sizeof(double)) : NULL;
+    double *hyo = energy ? calloc(n, sizeof(double)) : NULL;
+    double dt = or_dt(c);
+    double J0 = c->src_amp * or_eps0() * OR_C0 / c->dx;
+    double sum = 0.0;
+    int gw = c->gap_hi[0] - c->gap_lo[0];
+    int dw = c->design_hi[0] - c->design_lo[0];
+
+    for (int t = 0; t <= N; ++t) {
+        for (int j = c->gap_lo[1]; j < c->gap_hi[1]; ++j)
+            for (int i = c->gap_lo[0]; i < c->gap_hi[0]; ++i) {
+                double e = s.Ez[(size_t)j * nx + i];
+                sum += e * e;
+                if (gap_hist)
+                    gap_hist[(size_t)t * G + (size_t)(j - c->gap_lo[1]) * gw + (i - c->gap_lo[0])] = e;
+            }
+        if (design_hist)
+            for (int j = c->design_lo[1]; j < c->design_hi[1]; ++j)
+                for (int i = c->design_lo[0]; i < c->design_hi[0]; ++i)
+                    design_hist[(size_t)t * M + (size_t)(j - c->design_lo[1]) * dw + (i - c->design_lo[0])] =
+                        s.Ez[(size_t)j * nx + i];
+        for (int p = 0; p < nprobe; ++p)
+            probe_hist[(size_t)t * nprobe + p] = s.Ez[(size_t)probes[2 * p + 1] * nx + probes[2 * p]];
+        if (t == N) break;
+        double js = J0 * or_signal(c, (t + 0.5) * dt);
+        for (int j = c->src_lo[1]; j < c->src_hi[1]; ++j)
+            for (int i = c->src_lo[0]; i < c->src_hi[0]; ++i)
+                jsrc[(size_t)j * nx + i] = js;
+        if (energy) {
+            memcpy(hxo, s.Hx, n * sizeof(double));
+            memcpy(hyo, s.Hy, n * sizeof(double));
+        }
+        step2_h(c, &m, &s);
+        if (energy) energy[t] = energy2(c, &m, &s, hxo, hyo);
+        step2_e(c, &m, &s, jsrc);
+    }
+    *W = 0.5 * c->eps_g * dt * c->dx * c->dx * sum;
+    free(jsrc); free(hxo); free(hyo); free(rho_t);
+    st2_free(&s);
+    mat2_free(&m);
+    return 0;
+}
+
+/* Forward, adjoint and gradient (2D).
+ *
+ * Adjoint (Eq. 20): the forward solver, from rest, with the source term
+ * eps_g E(T - tau) in the gap.  The forward solver takes its source as
+ * -J_src on the right of Ampere's law, so the adjoint passes
+ * J_src = -eps_g E^{N-n} at adjoint step n, n = 0..N; step n turns
+ * E*^{n-1/2} into E*^{n+1/2} (and J* likewise).
+ *
+ * Sensitivities (Eq. 25a-c), per design node i outside the gap:
+ *   dW/dpsi_i     = -(dt dx^2 / psi_i) sum_n E_i^{N-n} (J*^{n+1/2} + J*^{n-1/2}) / 2
+ *   dW/deps_inf_i = -eps0 dx^2        sum_n E_i^{N-n} (E*^{n+1/2} - E*^{n-1/2})
+ *   dW/dsigma_i   = -dt dx^2          sum_n E_i^{N-n} (E*^{n+1/2} + E*^{n-1/2}) / 2
+ * Chain rule (Eq. 27) with d psi_i/d rho~ = psi - psi_s,
+ * d eps_inf_i/d rho~ = eps_inf - eps_s, d sigma_i/d rho~ = smax (1 - 2 rho~)
+ * (times 4 for the peak-normalised form), zero in the gap, then F^T, then
+ * zero in the gap again (gap densities are not design variables). */
+static int gradient2(const or_config *c, const double *rho, double sigma_max, double gamma_scale,
+                     double *W, double *grad, double *g_psi, double *g_eps, double *g_sig)
+{
+    int nx = c->nx, N = c->nsteps;
+    long M, G;
+    or_sizes(c, &M, &G);
+    if (M == 0) return -1;
+    double *ghist = malloc(sizeof(double) * (size_t)(N + 1) * (G ? G : 1));
+    double *dhist = malloc(sizeof(double) * (size_t)(N + 1) * M);
+    forward2(c, rho, sigma_max, gamma_scale, W, ghist, dhist, NULL, 0, NULL, NULL);
+
+    double *rho_t = malloc(sizeof(double) * M);
+    or_filter(c, rho, rho_t);
+    mat2 m;
+    mat2_build(c, rho_t, sigma_max, gamma_scale, &m);
+    st2 a;
+    st2_alloc(&a, nx, c->ny);
+    size_t n = (size_t)nx * c->ny;
+    double *jsrc = calloc(n, sizeof(double));
+    double *sp = calloc(M, sizeof(double)), *se = calloc(M, sizeof(double)), *ss = calloc(M, sizeof(double));
+    double *Eold = malloc(sizeof(double) * M), *Jold = malloc(sizeof(double) * M);
+    int dw = c->design_hi[0] - c->design_lo[0];
+    int gw = c->gap_hi[0] - c->gap_lo[0];
+
+    for (int t = 0; t <= N; ++t) {
+        for (int j = c->gap_lo[1]; j < c->gap_hi[1]; ++j)
+            for (int i = c->gap_lo[0]; i < c->gap_hi[0]; ++i)
+                jsrc[(size_t)j * nx + i] =
+                    -c->eps_g * ghist[(size_t)(N - t) * G + (size_t)(j - c->gap_lo[1]) * gw + (i - c->gap_lo[0])];
+        for (int j = c->design_lo[1]; j < c->design_hi[1]; ++j)
+            for (int i = c->design_lo[0]; i < c->design_hi[0]; ++i) {
+                long d = (long)(j - c->design_lo[1]) * dw + (i - c->design_lo[0]);
+                Eold[d] = a.Ez[(size_t)j * nx + i];
+                Jold[d] = a.Jz[(size_t)j * nx + i];
+            }
+        step2_h(c, &m, &a);
+        step2_e(c, &m, &a, jsrc);
+        for (int j = c->design_lo[1]; j < c->design_hi[1]; ++j)
+            for (int i = c->design_lo[0]; i < c->design_hi[0]; ++i) {
+                long d = (long)(j - c->design_lo[1]) * dw + (i - c->design_lo[0]);
+                double Ef = dhist[(size_t)(N - t) * M + d];
+                double En = a.Ez[(size_t)j * nx + i], Jn = a.Jz[(size_t)j * nx + i];
+                sp[d] += Ef * 0.5 * (Jn + Jold[d]);
+                se[d] += Ef * (En - Eold[d]);
+                ss[d] += Ef * 0.5 * (En + Eold[d]);
+            }
+    }
+
+    double eps0 = or_eps0(), dt = or_dt(c), dx2 = c->dx * c->dx;
+    double psi = c->omega_p * c->omega_p, psi_s = c->psi_s_ratio * psi;
+    double *gt = malloc(sizeof(double) * M);
+    for (int j = c->design_lo[1]; j < c->design_hi[1]; ++j)
+        for (int i = c->design_lo[0]; i < c->design_hi[0]; ++i) {
+            long d = (long)(j - c->design_lo[1]) * dw + (i - c->design_lo[0]);
+            double ep, ps, sg;
+            or_material(c, rho_t[d], sigma_max, &ep, &ps, &sg);
+            double dpsi = -(dt * dx2 / ps) * sp[d];
+            double deps = -eps0 * dx2 * se[d];
+            double dsig = -dt * dx2 * ss[d];
+            if (in_box(c->gap_lo, c->gap_hi, i, j, 0)) dpsi = deps = dsig = 0.0;
+            if (g_psi) g_psi[d] = dpsi;
+            if (g_eps) g_eps[d] = deps;
+            if (g_sig) g_sig[d] = dsig;
+            double dsdr = sigma_max * (1.0 - 2.0 * rho_t[d]) * (c->sigma_form ? 4.0 : 1.0);
+            gt[d] = (psi - psi_s) * dpsi + (c->eps_inf - c->eps_s) * deps + dsdr * dsig;
+        }
+    or_filter_T(c, gt, grad);
+    for (int j = c->gap_lo[1]; j < c->gap_hi[1]; ++j)
+        for (int i = c->gap_lo[0]; i < c->gap_hi[0]; ++i)
+            grad[(long)(j - c->design_lo[1]) * dw + (i - c->design_lo[0])] = 0.0;
+
+    free(gt); free(Eold); free(Jold); free(sp); free(se); free(ss);
+    free(jsrc); free(rho_t); free(ghist); free(dhist);
+    st2_free(&a);
+    mat2_free(&m);
+    return 0;
+}
+
+/* ============================================================ public */
+
+int or_forward(const or_config *c, const double *rho, double sigma_max, double gamma_scale,
+               double *W, double *gap_hist, double *design_hist,
+               const int *probes, int nprobe, double *probe_hist, double *energy)
+{
+    if (c->ndim == 2)
+        return forward2(c, rho, sigma_max, gamma_scale, W, gap_hist, design_hist,
+                        probes, nprobe, probe_hist, energy);
+    return -1;
+}
+
+int or_gradient(const or_config *c, const double *rho, double sigma_max, double gamma_scale,
+                double *W, double *grad, double *g_psi, double *g_eps, double *g_sig)
+{
+    if (c->ndim == 2) return gradient2(c, rho, sigma_max, gamma_scale, W, grad, g_psi, g_eps, g_sig);
+    return -1;
+}

@@ -1,0 +1,180 @@
+"""ctypes front end of the FP64 CPU oracle (``fdtd_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg use it to check and time the CUDA path.  It
+imports nothing from the CUDA package; it takes the plain workload dicts of
+``paper_2203_01462_gb300.inputs`` and fills its own C struct.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fdtd_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class OrConfig(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("dx", C.c_double), ("courant", C.c_double),
+        ("npml", C.c_int), ("pml_m", C.c_double), ("pml_sigma_factor", C.c_double),
+        ("pml_kappa_max", C.c_double), ("pml_alpha_max", C.c_double),
+        ("periodic_x", C.c_int),
+        ("eps_inf", C.c_double), ("omega_p", C.c_double), ("gamma_p", C.c_double),
+        ("eps_s", C.c_double), ("psi_s_ratio", C.c_double), ("eps_g", C.c_double),
+        ("design_lo", C.c_int * 3), ("design_hi", C.c_int * 3),
+        ("gap_lo", C.c_int * 3), ("gap_hi", C.c_int * 3),
+        ("src_lo", C.c_int * 3), ("src_hi", C.c_int * 3),
+        ("nbands", C.c_int), ("f0", C.c_double * 2), ("tau", C.c_double), ("t0", C.c_double),
+        ("src_amp", C.c_double), ("nsteps", C.c_int),
+        ("filter_radius", C.c_int), ("filter_sigma", C.c_double),
+        ("sigma_form", C.c_int), ("sub_eps", C.c_double), ("sub_hi", C.c_int),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, -O2, OpenMP)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            dp = C.POINTER(C.c_double)
+            L.or_forward.argtypes = [C.POINTER(OrConfig), dp, C.c_double, C.c_double, dp, dp, dp,
+                                     C.POINTER(C.c_int), C.c_int, dp, dp]
+            L.or_gradient.argtypes = [C.POINTER(OrConfig), dp, C.c_double, C.c_double, dp, dp,
+                                      dp, dp, dp]
+            L.or_filter.argtypes = [C.POINTER(OrConfig), dp, dp]
+            L.or_filter_T.argtypes = [C.POINTER(OrConfig), dp, dp]
+            L.or_material.argtypes = [C.POINTER(OrConfig), C.c_double, C.c_double, dp, dp, dp]
+            L.or_set_threads.argtypes = [C.c_int]
+            L.or_get_threads.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def set_threads(n: int) -> None:
+    lib().or_set_threads(int(n))
+
+
+def threads() -> int:
+    return lib().or_get_threads()
+
+
+def config(w: dict) -> OrConfig:
+    c = OrConfig()
+    for name, ctype in OrConfig._fields_:
+        v = w[name]
+        if name == "f0":
+            c.f0[0], c.f0[1] = float(v[0]), float(v[1])
+        elif isinstance(getattr(c, name), C.Array):
+            arr = getattr(c, name)
+            for a in range(3):
+                arr[a] = int(v[a])
+        elif ctype is C.c_int:
+            setattr(c, name, int(v))
+        else:
+            setattr(c, name, float(v))
+    return c
+
+
+def _dptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _sizes(w: dict) -> tuple[int, int]:
+    def cnt(lo, hi):
+        n = 1
+        for a in range(w["ndim"]):
+            n *= max(0, hi[a] - lo[a])
+        return n
+    return cnt(w["design_lo"], w["design_hi"]), cnt(w["gap_lo"], w["gap_hi"])
+
+
+def forward(w: dict, rho: np.ndarray, sigma_max: float = 0.0, gamma_scale: float = 1.0,
+            record_gap: bool = False, record_design: bool = False, probes=None,
+            energy: bool = False) -> dict:
+    """Forward solve; returns W and whatever histories were asked for."""
+    M, G = _sizes(w)
+    N = int(w["nsteps"])
+    rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+    assert rho.size == M
+    cfg = config(w)
+    Wout = C.c_double(0.0)
+    gh = np.zeros((N + 1, G)) if record_gap else None
+    dh = np.zeros((N + 1, M)) if record_design else None
+    if probes is not None:
+        pr = np.ascontiguousarray(np.asarray(probes, dtype=np.int32).reshape(-1, 2))
+        ph = np.zeros((N + 1, pr.shape[0]))
+        pptr, npr = pr.ctypes.data_as(C.POINTER(C.c_int)), pr.shape[0]
+    else:
+        ph, pptr, npr = None, None, 0
+    en = np.zeros(N) if energy else None
+    rc = lib().or_forward(C.byref(cfg), _dptr(rho), float(sigma_max), float(gamma_scale),
+                          C.byref(Wout), _dptr(gh), _dptr(dh), pptr, npr, _dptr(ph), _dptr(en))
+    if rc != 0:
+        raise RuntimeError("oracle forward failed (%d)" % rc)
+    return dict(W=Wout.value, gap_hist=gh, design_hist=dh, probe_hist=ph, energy=en)
+
+
+def objective(w: dict, rho: np.ndarray, sigma_max: float = 0.0, gamma_scale: float = 1.0) -> float:
+    return forward(w, rho, sigma_max, gamma_scale)["W"]
+
+
+def gradient(w: dict, rho: np.ndarray, sigma_max: float = 0.0, gamma_scale: float = 1.0,
+             parts: bool = False) -> dict:
+    """W~ and dW~/drho via the adjoint run and Eq. (25)/(27)."""
+    M, _ = _sizes(w)
+    rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+    assert rho.size == M
+    cfg = config(w)
+    Wout = C.c_double(0.0)
+    g = np.zeros(M)
+    gp = np.zeros(M) if parts else None
+    ge = np.zeros(M) if parts else None
+    gs = np.zeros(M) if parts else None
+    rc = lib().or_gradient(C.byref(cfg), _dptr(rho), float(sigma_max), float(gamma_scale),
+                           C.byref(Wout), _dptr(g), _dptr(gp), _dptr(ge), _dptr(gs))
+    if rc != 0:
+        raise RuntimeError("oracle gradient failed (%d)" % rc)
+    out = dict(W=Wout.value, grad=g)
+    if parts:
+        out.update(g_psi=gp, g_eps=ge, g_sig=gs)
+    return out
+
+
+def filt(w: dict, x: np.ndarray, transpose: bool = False) -> np.ndarray:
+    M, _ = _sizes(w)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+    assert x.size == M
+    out = np.zeros(M)
+    cfg = config(w)
+    (lib().or_filter_T if transpose else lib().or_filter)(C.byref(cfg), _dptr(x), _dptr(out))
+    return out
+
+
+def material(w: dict, rho: float, sigma_max: float = 0.0) -> tuple[float, float, float]:
+    cfg = config(w)
+    e, p, s = C.c_double(), C.c_double(), C.c_double()
+    lib().or_material(C.byref(cfg), float(rho), float(sigma_max), C.byref(e), C.byref(p), C.byref(s))
+    return e.value, p.value, s.value

@@ -1,0 +1,159 @@
+"""Seeded synthetic workloads shared by the CUDA path, the oracle and the tests.
+
+This module only describes inputs: grid sizes, boxes, material constants,
+excitation parameters and seeded design densities.  It holds none of the
+method's arithmetic (no update coefficients, no CPML profiles, no source
+waveform samples); each implementation derives those itself.
+
+Workload shapes follow the nanoantenna problems of Sec. 4 of the paper (a
+square design box with a small observation gap at its centre, a soft current
+source on the incident side, absorbing layers around everything) at the
+sizes of the benchmark configurations:
+
+* ``cfg_2d_160``: 160 x 160 nodes, dx = 5 nm, S = 0.5, 10-cell CPML, 2000
+  steps, FP64; 60 x 60 centred design box, 3 x 3 gap.
+* ``cfg_2d_2048``: 2048 x 2048 nodes, dx = 2 nm, 20000 steps, FP32;
+  1024 x 1024 design box smoothed by a 5-cell Gaussian filter, snapshots
+  every 64 steps.
+
+Material: Drude gold, eps_inf = 1, omega_p = 1.37e16 rad/s, gamma = 1e14 1/s.
+Excitation: Gaussian-modulated carrier at 800 nm whose spectral amplitude
+falls to one half 100 THz either side of the carrier (600-1000 nm band).
+"""
+from __future__ import annotations
+
+import copy
+import math
+
+import numpy as np
+
+C0 = 299792458.0
+
+GOLD = dict(eps_inf=1.0, omega_p=1.37e16, gamma_p=1.0e14)
+SILVER = dict(eps_inf=4.469, omega_p=1.426e16, gamma_p=4.571e13)  # Sec. 2 fit
+
+
+def pulse(center_m: float = 800e-9, half_width_hz: float = 100e12, nbands: int = 1,
+          centers_m=None) -> dict:
+    """Gaussian envelope exp(-((t-t0)/tau)^2) on carrier(s) at c/center.
+
+    The envelope's spectrum exp(-(pi f tau)^2) drops to one half at
+    ``half_width_hz`` from the carrier; t0 = 4 tau starts the pulse from ~0.
+    """
+    tau = math.sqrt(math.log(2.0)) / (math.pi * half_width_hz)
+    cs = list(centers_m) if centers_m is not None else [center_m]
+    f0 = [C0 / c for c in cs] + [0.0] * (2 - len(cs))
+    return dict(nbands=len(cs), f0=f0, tau=tau, t0=4.0 * tau)
+
+
+def _centered_box(n: int, w: int) -> tuple[int, int]:
+    lo = (n - w) // 2
+    return lo, lo + w
+
+
+def workload_2d(nx: int, ny: int, *, dx: float, nsteps: int, npml: int = 10,
+                design: tuple[int, int] = (60, 60), gap: tuple[int, int] = (3, 3),
+                courant: float = 0.5, real: str = "f64", material: dict | None = None,
+                filter_radius: int = 0, filter_fwhm: float = 5.0,
+                snapshot_every: int = 0, snapshot_dtype: str = "f32",
+                accum: str = "f64", src_offset: int = 5, **over) -> dict:
+    """A 2D TM_z nanoantenna-shaped workload (E_z out of plane).
+
+    Design and gap boxes are centred; the line source is one row of E_z
+    ``src_offset`` nodes inside the lower CPML, spanning the non-CPML x range.
+    """
+    mat = dict(GOLD if material is None else material)
+    dlo_x, dhi_x = _centered_box(nx, design[0])
+    dlo_y, dhi_y = _centered_box(ny, design[1])
+    glo_x, ghi_x = _centered_box(nx, gap[0])
+    glo_y, ghi_y = _centered_box(ny, gap[1])
+    w = dict(
+        ndim=2, nx=nx, ny=ny, nz=1, dx=dx, courant=courant, npml=npml,
+        pml_m=3.0, pml_sigma_factor=0.8, pml_kappa_max=1.0, pml_alpha_max=0.0,
+        periodic_x=0,
+        eps_s=1.0, psi_s_ratio=0.01, eps_g=1.0,
+        design_lo=[dlo_x, dlo_y, 0], design_hi=[dhi_x, dhi_y, 1],
+        gap_lo=[glo_x, glo_y, 0], gap_hi=[ghi_x, ghi_y, 1],
+        src_lo=[npml, npml + src_offset, 0], src_hi=[nx - npml, npml + src_offset + 1, 1],
+        src_amp=1.0, nsteps=nsteps,
+        filter_radius=filter_radius,
+        filter_sigma=(filter_fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0)))) if filter_radius else 1.0,
+        sigma_form=0, sub_eps=1.0, sub_hi=0,
+        real=real, snapshot_every=snapshot_every, snapshot_dtype=snapshot_dtype, accum=accum,
+    )
+    w.update(mat)
+    w.update(pulse())
+    w.update(over)
+    return w
+
+
+def cfg_2d_160() -> dict:
+    """160^2 FP64 parity workload: full forward + adjoint + gradient."""
+    return workload_2d(160, 160, dx=5e-9, nsteps=2000, npml=10, design=(60, 60), gap=(3, 3),
+                       real="f64")
+
+
+def cfg_2d_2048(nsteps: int = 20000) -> dict:
+    """2048^2 FP32 workload with a 1024^2 filtered design box, snapshots every 64."""
+    return workload_2d(2048, 2048, dx=2e-9, nsteps=nsteps, npml=10, design=(1024, 1024),
+                       gap=(3, 3), real="f32", filter_radius=5, filter_fwhm=5.0,
+                       snapshot_every=64, snapshot_dtype="f32", accum="f64")
+
+
+def small_2d(nx: int = 40, ny: int = 36, nsteps: int = 300, real: str = "f64", **kw) -> dict:
+    """A small 2D case that spans several GPU tiles with ragged edges."""
+    d = kw.pop("design", (16, 14))
+    g = kw.pop("gap", (3, 3))
+    npml = kw.pop("npml", 6)
+    return workload_2d(nx, ny, dx=kw.pop("dx", 5e-9), nsteps=nsteps, npml=npml, design=d, gap=g,
+                       real=real, src_offset=kw.pop("src_offset", 2), **kw)
+
+
+def n_design(w: dict) -> int:
+    n = 1
+    for a in range(w["ndim"]):
+        n *= w["design_hi"][a] - w["design_lo"][a]
+    return n
+
+
+def design_shape(w: dict) -> tuple[int, ...]:
+    """Design-array shape, slowest axis first (x fastest)."""
+    s = [w["design_hi"][a] - w["design_lo"][a] for a in range(w["ndim"])]
+    return tuple(reversed(s))
+
+
+def rho_uniform(w: dict, seed: int) -> np.ndarray:
+    """rho ~ U[0,1] on the design box (PCG64(seed)), gap entries set to 0."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    r = rng.random(design_shape(w))
+    return zero_gap(w, r)
+
+
+def zero_gap(w: dict, r: np.ndarray) -> np.ndarray:
+    r = np.array(r, dtype=np.float64, copy=True)
+    sl = tuple(slice(w["gap_lo"][a] - w["design_lo"][a], w["gap_hi"][a] - w["design_lo"][a])
+               for a in reversed(range(w["ndim"])))
+    r[sl] = 0.0
+    return r
+
+
+def rho_bowtie(w: dict) -> np.ndarray:
+    """Binary bowtie: two triangles whose tips face each other across the gap."""
+    shape = design_shape(w)
+    h, wd = shape[-2], shape[-1]
+    y, x = np.mgrid[0:h, 0:wd]
+    cx = (w["gap_lo"][0] + w["gap_hi"][0]) / 2.0 - w["design_lo"][0] - 0.5
+    cy = (w["gap_lo"][1] + w["gap_hi"][1]) / 2.0 - w["design_lo"][1] - 0.5
+    gx = (w["gap_hi"][0] - w["gap_lo"][0]) / 2.0 + 0.5
+    ax = np.abs(y - cy)
+    tri = (np.abs(x - cx) >= gx) & (ax <= 0.6 * (np.abs(x - cx) - gx) + 1.0)
+    r = tri.astype(np.float64)
+    if len(shape) == 3:
+        r = np.broadcast_to(r, shape).copy()
+    return zero_gap(w, r)
+
+
+def with_(w: dict, **kw) -> dict:
+    v = copy.deepcopy(w)
+    v.update(kw)
+    return v

@@ -1,0 +1,233 @@
+"""Pins of the FP64 CPU oracle against physics and mathematics it must obey.
+
+None of these compares the oracle with itself: each checks it against a
+closed form (Fresnel coefficients of a Drude slab, radiation of a current
+sheet, the exact Yee dispersion of a PEC cavity), a conservation law, a
+library routine (scipy's Gaussian filter) or an independent differentiation
+(central finite differences of the forward solve).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2203_01462_gb300 import inputs as I
+
+C0 = 299792458.0
+MU0 = 1.25663706212e-6
+EPS0 = 1.0 / (MU0 * C0 * C0)
+
+
+def fast_case(npml=6, nsteps=400, **kw):
+    """Small grid, coarse dx and a broadband pulse so that 400 steps see it."""
+    w = I.small_2d(nx=40, ny=36, nsteps=nsteps, dx=20e-9, npml=npml, design=(16, 14), **kw)
+    w.update(I.pulse(800e-9, 300e12))
+    if npml == 0:
+        w["src_lo"] = [1, 3, 0]
+        w["src_hi"] = [39, 4, 1]
+    return w
+
+
+def slab(rho_val, smax=0.0, gscale=1.0, L=20, dx=1e-9):
+    """Normal-incidence Drude slab in a periodic-x strip; returns the FFT
+    reflection and transmission magnitudes and the analytic Fresnel ones."""
+    ny, npml = 1000, 20
+    js = npml + 5
+    pr, j0 = js + 60, 500
+    pt = j0 + L + 60
+    base = I.workload_2d(4, ny, dx=dx, nsteps=34000, npml=npml, design=(4, L), gap=(0, 0))
+    base.update(periodic_x=1, src_lo=[0, js, 0], src_hi=[4, js + 1, 1],
+                design_lo=[0, j0, 0], design_hi=[4, j0 + L, 1],
+                gap_lo=[0, 0, 0], gap_hi=[0, 0, 1])
+    ref = dict(base, design_lo=[0, 0, 0], design_hi=[0, 0, 1])
+    probes = [(1, pr), (1, pt)]
+    a = O.forward(base, np.full(4 * L, rho_val), smax, gscale, probes=probes)["probe_hist"]
+    b = O.forward(ref, np.zeros(0), probes=probes)["probe_hist"]
+    N = a.shape[0]
+    dt = base["courant"] * dx / C0
+    f = np.fft.rfftfreq(N, dt)
+    Fa, Fb = np.fft.rfft(a, axis=0), np.fft.rfft(b, axis=0)
+    R = np.abs(Fa[:, 0] - Fb[:, 0]) / np.abs(Fb[:, 0])
+    T = np.abs(Fa[:, 1]) / np.abs(Fb[:, 1])
+    lam = C0 / np.maximum(f, 1.0)
+    sel = (lam > 600e-9) & (lam < 1000e-9)
+    w = 2 * np.pi * f[sel]
+    # Eq. (4)/(5): interpolated Drude + artificial conductivity, e^{jwt}.
+    psi = base["omega_p"] ** 2
+    psis = base["psi_s_ratio"] * psi
+    e_inf = base["eps_s"] + rho_val * (base["eps_inf"] - base["eps_s"])
+    ps = psis + rho_val * (psi - psis)
+    sg = rho_val * (1 - rho_val) * smax
+    eps = e_inf - ps / (w ** 2 - 1j * w * base["gamma_p"] * gscale) - 1j * sg / (w * EPS0)
+    n = np.sqrt(eps)
+    n = np.where(n.imag > 0, -n, n)           # decaying into the slab
+    ph = np.exp(-1j * n * (w / C0) * L * dx)
+    r12 = (1 - n) / (1 + n)
+    den = 1 - r12 ** 2 * ph ** 2
+    return R[sel], T[sel], np.abs(r12 * (1 - ph ** 2) / den), np.abs((1 - r12 ** 2) * ph / den)
+
+
+@pytest.mark.parametrize("rho_val,smax,gscale", [
+    (1.0, 0.0, 1.0),      # Eq. (1): the Drude metal itself
+    (0.0, 0.0, 1.0),      # Eq. (5) at rho = 0: eps_s with psi_s = psi / 100
+    (0.5, 5e5, 1.0),      # Eq. (4)/(5c): halfway material plus sigma_max / 4
+    (1.0, 0.0, 10.0),     # damping level: gamma x 10
+])
+def test_drude_slab_matches_fresnel(rho_val, smax, gscale):
+    R, T, Ra, Ta = slab(rho_val, smax, gscale)
+    assert np.max(np.abs(R - Ra)) < 1e-3
+    assert np.max(np.abs(T - Ta)) < 1e-3
+
+
+def test_sheet_current_radiates_half_eta_K():
+    """A uniform current sheet K(t) in vacuum radiates E = -(eta0/2) K(t - d/c);
+    with K = J_src dx = src_amp eps0 c0 g(t) this is E = -src_amp g(t - d/c) / 2."""
+    dx, ny, npml = 5e-9, 800, 20
+    js, D = npml + 5, 300
+    w = I.workload_2d(4, ny, dx=dx, nsteps=9000, npml=npml, design=(0, 0), gap=(0, 0))
+    w.update(periodic_x=1, src_lo=[0, js, 0], src_hi=[4, js + 1, 1],
+             design_lo=[0, 0, 0], design_hi=[0, 0, 1], gap_lo=[0, 0, 0], gap_hi=[0, 0, 1],
+             src_amp=2.0)
+    e = O.forward(w, np.zeros(0), probes=[(2, js + D)])["probe_hist"][:, 0]
+    dt = w["courant"] * dx / C0
+    t = np.arange(e.size) * dt - D * dx / C0
+    g = np.exp(-((t - w["t0"]) / w["tau"]) ** 2) * np.sin(2 * np.pi * w["f0"][0] * (t - w["t0"]))
+    expect = -0.5 * w["src_amp"] * g
+    assert np.max(np.abs(expect)) > 0.9
+    assert np.max(np.abs(e - expect)) < 3e-3 * np.max(np.abs(expect))
+
+
+def test_pec_cavity_energy_conserved_and_yee_mode_frequency():
+    """Lossless PEC cavity: after the source has died out the discrete energy is
+    constant, and the lowest resonance sits at the exact Yee dispersion
+    sin(w dt/2)/(c dt) = sqrt(sum sin^2(k dx/2))/dx, k = pi/((n-1) dx)."""
+    n, dx = 24, 20e-9
+    w = I.workload_2d(n, n, dx=dx, nsteps=60000, npml=0, design=(0, 0), gap=(0, 0))
+    w.update(I.pulse(1600e-9, 200e12))
+    w.update(src_lo=[7, 9, 0], src_hi=[8, 10, 1], design_lo=[0, 0, 0], design_hi=[0, 0, 1],
+             gap_lo=[0, 0, 0], gap_hi=[0, 0, 1])
+    out = O.forward(w, np.zeros(0), probes=[(5, 6)], energy=True)
+    en = out["energy"]
+    dt = w["courant"] * dx / C0
+    quiet = int((w["t0"] + 7.0 * w["tau"]) / dt) + 1
+    tail = en[quiet:]
+    assert tail.max() > 0
+    assert (tail.max() - tail.min()) / tail.max() < 1e-11  # round-off over ~6e4 steps
+    p = out["probe_hist"][quiet:, 0]
+    pad = 1 << 22
+    F = np.abs(np.fft.rfft(p * np.hanning(p.size), pad))
+    f = np.fft.rfftfreq(pad, dt)
+    k = np.pi / ((n - 1) * dx)
+    s = np.sqrt(2.0) * np.sin(k * dx / 2) / dx
+    f_yee = 2.0 * np.arcsin(C0 * dt * s) / dt / (2 * np.pi)
+    f_cont = C0 * np.sqrt(2.0) * k / (2 * np.pi)
+    band = (f > 0.8 * f_yee) & (f < 1.1 * f_yee)
+    i = np.flatnonzero(band)[np.argmax(F[band])]
+    a, b, c = np.log(F[i - 1]), np.log(F[i]), np.log(F[i + 1])
+    f_pk = f[i] + 0.5 * (a - c) / (a - 2 * b + c) * (f[1] - f[0])
+    assert abs(f_pk - f_yee) < 0.1 * abs(f_yee - f_cont)
+
+
+def test_stable_at_courant_limit_with_drude_and_sigma():
+    """S = 0.99/sqrt(2) with Drude gold, sigma and CPML: no late-time growth."""
+    w = fast_case(npml=4, nsteps=40000, courant=0.99 / np.sqrt(2.0))
+    r = I.rho_uniform(w, 3)
+    out = O.forward(w, r, 5e5, 1.0, probes=[(20, 18), (12, 25)])
+    p = np.abs(out["probe_hist"])
+    peak = p.max()
+    assert np.isfinite(p).all() and peak > 1e-3
+    assert p[-2000:].max() < 1e-6 * peak
+
+
+@pytest.mark.parametrize("npml,material", [(0, "gold"), (6, "gold"), (6, "silver")])
+def test_adjoint_gradient_matches_central_differences(npml, material):
+    """Eq. (25)+(27) against central differences of the forward solve; the paper
+    reports agreement to more than 4 digits.  Silver (eps_inf = 4.469) exercises
+    the eps_inf term of Eq. (25b), which gold (eps_inf = eps_s = 1) leaves out."""
+    w = fast_case(npml=npml, material=I.SILVER if material == "silver" else I.GOLD)
+    r = I.zero_gap(w, I.rho_uniform(w, 1) * 0.8 + 0.1)
+    smax, gs = 5e5, 3.0
+    g = O.gradient(w, r, smax, gs)["grad"]
+    rf = r.reshape(-1)
+    rng = np.random.default_rng(0)
+    idx = rng.choice(np.flatnonzero(rf > 0), 8, replace=False)
+    for i in idx:
+        h = 1e-4
+        rp, rm = rf.copy(), rf.copy()
+        rp[i] += h
+        rm[i] -= h
+        fd = (O.objective(w, rp, smax, gs) - O.objective(w, rm, smax, gs)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-5 * abs(fd) + 1e-6 * np.abs(g).max()
+
+
+def test_adjoint_gradient_with_filter_matches_central_differences():
+    w = fast_case(filter_radius=2, filter_fwhm=2.5)
+    r = I.zero_gap(w, I.rho_uniform(w, 2))
+    g = O.gradient(w, r, 2e5, 1.0)["grad"]
+    rf = r.reshape(-1)
+    rng = np.random.default_rng(1)
+    gap = I.zero_gap(w, np.ones(I.design_shape(w))).reshape(-1) == 0
+    idx = rng.choice(np.flatnonzero(~gap), 6, replace=False)
+    for i in idx:
+        h = 1e-4
+        rp, rm = rf.copy(), rf.copy()
+        rp[i] += h
+        rm[i] -= h
+        fd = (O.objective(w, rp, 2e5) - O.objective(w, rm, 2e5)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-5 * abs(fd) + 1e-6 * np.abs(g).max()
+    assert np.all(g[gap] == 0.0)
+
+
+def test_linearity_source_scaling():
+    """Fields are linear in the source: doubling it multiplies W and dW by 4."""
+    w = fast_case()
+    r = I.rho_uniform(w, 4)
+    a = O.gradient(w, r, 1e5)
+    b = O.gradient(dict(w, src_amp=2.0), r, 1e5)
+    assert abs(b["W"] / a["W"] - 4.0) < 1e-12
+    np.testing.assert_allclose(b["grad"], 4.0 * a["grad"], rtol=1e-10, atol=1e-12 * np.abs(b["grad"]).max())
+
+
+def test_sigma_vanishes_at_binary_densities():
+    """Eq. (5c): sigma_i = 0 for rho in {0, 1}, so sigma_max cannot matter there."""
+    w = fast_case()
+    r = I.zero_gap(w, (I.rho_uniform(w, 5) > 0.5).astype(float))
+    assert O.objective(w, r, 0.0) == O.objective(w, r, 5e6)
+
+
+def test_gap_is_fixed_vacuum():
+    """The gap is not designable: its rho entries do not change W."""
+    w = fast_case()
+    r = I.rho_uniform(w, 6)
+    q = r.copy()
+    sl = tuple(slice(w["gap_lo"][a] - w["design_lo"][a], w["gap_hi"][a] - w["design_lo"][a])
+               for a in (1, 0))
+    q[sl] = 0.7
+    assert O.objective(w, r) == O.objective(w, q)
+
+
+def test_filter_against_scipy_and_transpose():
+    """Interior rows equal scipy's truncated Gaussian filter; F^T is the adjoint
+    of F; constants pass unchanged (edge renormalisation)."""
+    from scipy.ndimage import gaussian_filter
+    w = I.workload_2d(80, 80, dx=2e-9, nsteps=10, design=(40, 36), gap=(3, 3),
+                      filter_radius=5, filter_fwhm=5.0)
+    rng = np.random.default_rng(0)
+    x = rng.random(I.design_shape(w))
+    y = rng.random(I.design_shape(w))
+    Fx = O.filt(w, x).reshape(x.shape)
+    R, s = w["filter_radius"], w["filter_sigma"]
+    ref = gaussian_filter(x, s, truncate=R / s, mode="constant")
+    np.testing.assert_allclose(Fx[R:-R, R:-R], ref[R:-R, R:-R], rtol=1e-12)
+    FTy = O.filt(w, y, transpose=True).reshape(y.shape)
+    assert abs(np.sum(Fx * y) - np.sum(x * FTy)) < 1e-12 * np.sum(Fx * y)
+    np.testing.assert_allclose(O.filt(w, np.full(x.shape, 0.3)), 0.3, rtol=1e-14)
+
+
+def test_objective_literal_sum():
+    """Eq. (24) for 2D: eps_g dt dx^2 / 2 times the sum of recorded gap E^2."""
+    w = fast_case()
+    out = O.forward(w, I.rho_uniform(w, 7), record_gap=True)
+    dt = w["courant"] * w["dx"] / C0
+    assert abs(out["W"] - 0.5 * w["eps_g"] * dt * w["dx"] ** 2 * np.sum(out["gap_hist"] ** 2)) \
+        <= 1e-13 * out["W"]
+    assert np.all(out["gap_hist"][0] == 0.0)
