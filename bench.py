@@ -1,0 +1,305 @@
+#!/usr/bin/env python3
+"""Throughput of the FDTD + Drude adjoint hot path on one GB300 (or N replicas).
+
+One bench step = one design evaluation on the 2048 x 2048 FP32 workload:
+set_design (5-cell Gaussian filter) -> forward (20000 steps, FP32 snapshots
+every 64 steps) -> adjoint (segment recompute + adjoint + fused
+sensitivities) -> gradient.  The metric counts forward + adjoint
+cell-updates (2 x cells x steps per evaluation); recompute sweeps are
+work the method pays but are not counted.
+
+Timing: CUDA events on the solver's stream around each step, L2 flushed
+(a 256 MB write) between steps outside the events, max over ranks.  Under
+torchrun each rank runs an independent replica (the path needs no
+collective), so value = ranks x work / slowest rank ("weak" scaling).
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a
+bounded sample of the same workload (fewer time steps per evaluation).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2203_01462_gb300 import inputs as I  # noqa: E402
+
+METRIC = "Gcell-updates/s fwd+adjoint"
+UNIT = "Gcell-updates/s"
+
+
+def workload(name: str, nsteps: int | None):
+    if name == "cfg_2d_2048":
+        w = I.cfg_2d_2048()
+    elif name == "cfg_2d_160":
+        w = I.cfg_2d_160()
+    else:
+        raise SystemExit("unknown workload " + name)
+    if nsteps:
+        w["nsteps"] = int(nsteps)
+    return w
+
+
+def damping(k: int) -> float:
+    """Artificial-damping schedule: gamma x10 decaying geometrically to x1 over 50 iterations."""
+    return 10.0 ** (1.0 - min(k, 50) / 50.0)
+
+
+def algorithmic_bytes(w: dict) -> dict:
+    """Algorithmic HBM bytes per time step (one read + one write of each
+    state word touched, no temporal-blocking credit)."""
+    rb = 8 if w["real"] == "f64" else 4
+    nx, ny, npml = w["nx"], w["ny"], w["npml"]
+    nc = nx * ny
+    md = I.n_design(w)
+    npml_cells = 2 * npml * (nx + ny)
+    grid = 3 * 2 * rb * nc                 # Ez, Hx, Hy read + write
+    design = (2 + 1) * rb * md             # J read + write, rho~ read
+    pml = 2 * 2 * rb * npml_cells          # two psi words read + write per slab cell
+    K = w.get("snapshot_every", 0)
+    state = 3 * rb * nc + rb * md + 4 * rb * npml_cells
+    fwd = grid + design + pml + (2 * state / K if K else rb * md)
+    rec = grid + design + pml + rb * md
+    adj = grid + design + pml + rb * md + 16 * md   # forward E^m read, FP64 accumulator r + w
+    return dict(forward=fwd, recompute=rec, adjoint=adj, cells=nc)
+
+
+def sample_clocks(path: str):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(path, "w")
+        return subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits", "-lms", "200"],
+                                stdout=f, stderr=subprocess.DEVNULL), f
+    except Exception:
+        return None, None
+
+
+def parse_clocks(path: str, gpu_index: int):
+    out = dict(sm_mhz=None, sm_max_mhz=None, reasons=[])
+    try:
+        rows = [r.split(",") for r in open(path).read().strip().splitlines() if r.strip()]
+    except Exception:
+        return out
+    rows = [[x.strip() for x in r] for r in rows if len(r) >= 9 and r[0].strip() == str(gpu_index)]
+    if not rows:
+        return out
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+    out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+               reasons=reasons)
+    return out
+
+
+def cpu_baseline(w: dict, nsteps: int) -> dict:
+    """The oracle, as it stands, on the host cores: one forward + adjoint +
+    gradient of the same workload cut to ``nsteps`` time steps."""
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    ws = dict(w, nsteps=nsteps)
+    rho = I.rho_uniform(ws, 0)
+    t = time.perf_counter()
+    O.gradient(ws, rho, 0.0, damping(0))
+    dt = time.perf_counter() - t
+    cu = 2.0 * ws["nx"] * ws["ny"] * nsteps
+    return dict(value=cu / dt / 1e9, unit=UNIT, cores=O.threads(), kind="oracle",
+                sample="%s with %d of %d time steps, one forward+adjoint+gradient, %.1f s"
+                       % (w.get("name", "workload"), nsteps, w["nsteps"], dt))
+
+
+def run_reference(args, w) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    ns = args.ref_nsteps
+    ws = dict(w, nsteps=ns)
+    rho = I.rho_uniform(ws, 0)
+    for k in range(args.warmup):
+        O.gradient(ws, rho, 0.0, damping(k))
+    times = []
+    for k in range(args.steps):
+        t = time.perf_counter()
+        O.gradient(ws, rho, 0.0, damping(args.warmup + k))
+        times.append(time.perf_counter() - t)
+    cu = 2.0 * w["nx"] * w["ny"] * ns
+    value = cu * len(times) / sum(times) / 1e9
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=0, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * sum(times) / len(times), higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=w["name"], grid=[w["nx"], w["ny"]], nsteps=w["nsteps"],
+                            sample_nsteps=ns),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=O.threads(), kind="oracle",
+                                  sample="%d of %d time steps per evaluation" % (ns, w["nsteps"])),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="cfg_2d_2048")
+    ap.add_argument("--nsteps", type=int, default=0, help="override the time-step count (quick runs)")
+    ap.add_argument("--cpu-nsteps", type=int, default=300)
+    ap.add_argument("--ref-nsteps", type=int, default=200)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    w = workload(args.workload, args.nsteps)
+    w["name"] = args.workload
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    # The oracle's host-core sample runs before any GPU work.
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(w, args.cpu_nsteps)
+
+    from paper_2203_01462_gb300.binding import Solver
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    s = Solver(w, device=dev, stream=stream)
+    rho = torch.tensor(I.rho_uniform(w, rank), dtype=torch.float32 if w["real"] == "f32" else torch.float64,
+                       device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    Wout = torch.zeros(1, dtype=torch.float64, device=dev)
+    gout = torch.empty(s.n_design, dtype=torch.float64, device=dev)
+
+    def one_step(k, ev=None):
+        with torch.cuda.stream(stream):
+            if ev: ev[0].record(stream)
+            s.set_design(rho)
+            s.set_damping(0.0, damping(k))
+            if ev: ev[1].record(stream)
+            s.forward(Wout)
+            if ev: ev[2].record(stream)
+            s.adjoint()
+            if ev: ev[3].record(stream)
+            s.gradient(gout)
+            if ev: ev[4].record(stream)
+
+    for k in range(args.warmup):
+        one_step(k)
+    s.sync()
+
+    clk_path = os.path.join(ROOT, "gpurun_out", "clocks_bench_rank%d.csv" % rank)
+    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    proc, fh = sample_clocks(clk_path)
+    launches0 = s.info().launches
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    step_ms, fwd_ms, adj_ms = [], [], []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xff)
+        stream.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        one_step(args.warmup + k, ev)
+        ev[4].synchronize()
+        step_ms.append(ev[0].elapsed_time(ev[4]))
+        fwd_ms.append(ev[1].elapsed_time(ev[2]))
+        adj_ms.append(ev[2].elapsed_time(ev[3]))
+    s.sync()
+    torch.cuda.synchronize(dev)
+    launches = s.info().launches - launches0 - 0
+    if proc:
+        proc.terminate()
+        proc.wait()
+        fh.close()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        total_ms = float(t.item())
+
+    nc, N = w["nx"] * w["ny"], w["nsteps"]
+    cu_step = 2.0 * nc * N
+    value = world * cu_step * args.steps / (total_ms / 1e3) / 1e9
+
+    # e2e through the C ABI with host buffers (copies inside the call).
+    rho_h = rho.cpu().numpy()
+    e2e_t = []
+    for k in range(args.e2e_steps):
+        t0 = time.perf_counter()
+        s.run_host(rho_h)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_val = cu_step * len(e2e_t) / sum(e2e_t) / 1e9 if e2e_t else None
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    import json as _j
+    peaks = {}
+    try:
+        peaks = _j.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    ab = algorithmic_bytes(w)
+    fwd_s = statistics.median(fwd_ms) / 1e3
+    achieved = ab["forward"] * N / fwd_s / 1e9
+    clocks = parse_clocks(clk_path, local)
+    rb = 8 if w["real"] == "f64" else 4
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype=w["real"], data="synthetic",
+        config=dict(workload="2D TM_z %dx%d FP32, %d steps, %dx%d filtered design, snapshots every %d"
+                              % (w["nx"], w["ny"], N, I.design_shape(w)[1], I.design_shape(w)[0],
+                                 w["snapshot_every"]) if w["real"] == "f32" else w["name"],
+                    grid=[w["nx"], w["ny"]], nsteps=N, design=list(I.design_shape(w))[::-1],
+                    snapshot_every=w["snapshot_every"], parallelism="replicas" if world > 1 else "1 GPU",
+                    l2="flushed (256 MB write) between timed steps"),
+        roofline=dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm,
+                      traffic=None, kernel="forward time-step kernels (H + E/J update)",
+                      peak_source=peak_src),
+        phases_ms=dict(forward=statistics.median(fwd_ms), adjoint_with_recompute=statistics.median(adj_ms)),
+        cpu_baseline=cpu,
+        e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=s.n_design * rb,
+                 d2h_bytes_per_step=8 + 8 * s.n_design),
+        clocks=clocks,
+        gpu_launches=int(launches),
+    )
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * fdtd.h -- C ABI of the GB300 (sm_103a) FDTD + Drude adjoint library.
+ *
+ * The library computes, on one GPU, the hot path of time-domain topology
+ * optimization of Drude-dispersive nanostructures (Hassan & Cala Lesina,
+ * arXiv 2203.01462):
+ *
+ *   set_design   rho -> rho~ = F(rho) (Eq. 26) and the per-node material of
+ *                Eq. (5a-c), evaluated inside the stencil kernels;
+ *   set_damping  sigma_max of Eq. (5c) and a scale on the Drude collision
+ *                rate (the artificial damping level, Sec. 2.1);
+ *   forward      Yee leapfrog of Eq. (10a-c) (E, J at integer steps, H at
+ *                half steps, Sec. 3.2), CPML borders, soft current source,
+ *                objective W~ of Eq. (24), gap-field history for the adjoint
+ *                source and the design-box field record (full history or
+ *                snapshots every k steps);
+ *   adjoint      the same solver in reversed time driven by eps_g E(T - tau)
+ *                in the gap (Eq. 20), recomputing forward segments from
+ *                snapshots when needed, with the sensitivities of
+ *                Eq. (25a-c) accumulated per design node in the same pass;
+ *   gradient     chain rule of Eq. (27) with the filter transpose, giving
+ *                dW~/drho (ascent direction; the paper maximises W~).
+ *
+ * Ownership: the caller owns every device buffer.  The library allocates no
+ * device memory; it carves all of its state out of the caller's workspace
+ * (size from fdtd_workspace_bytes) and enqueues all work on the caller's
+ * CUDA stream.  A context is used by one host thread and one stream at a
+ * time.  Pointers named d_* are device pointers, h_* host pointers.
+ *
+ * Errors: every entry point returns an fdtd_status; nothing throws or aborts
+ * across the ABI.  Calls out of order return FDTD_ESTATE.  Device-side
+ * checks (density outside [0,1], a non-finite objective) set an error word
+ * that fdtd_sync reports.
+ *
+ * Units: SI.  W~ follows Eq. (24) literally (eps_g dt dx^d / 2 times the sum
+ * of E^2 over the gap nodes and steps n = 0..N, d = 2 in 2D, per unit length
+ * in z), so it is small in absolute terms; W~ and the gradient are returned
+ * in FP64 whatever the field precision.
+ */
+#ifndef FDTD_GB300_H
+#define FDTD_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fdtd_status {
+    FDTD_OK = 0,
+    FDTD_EINVAL = 1,     /* bad argument or configuration                     */
+    FDTD_ENOMEM = 2,     /* workspace smaller than fdtd_workspace_bytes       */
+    FDTD_ECUDA = 3,      /* a CUDA runtime call failed                         */
+    FDTD_ESTATE = 4,     /* call out of order (e.g. adjoint before forward)    */
+    FDTD_EUNSTABLE = 5,  /* non-finite objective (unstable run)                */
+    FDTD_ETIMEOUT = 6,   /* reserved: a bounded device wait gave up           */
+    FDTD_ERANGE = 7      /* a design density outside [0, 1]                    */
+} fdtd_status;
+
+enum { FDTD_SNAP_F32 = 0, FDTD_SNAP_BF16 = 1, FDTD_SNAP_F16 = 2 };
+enum { FDTD_ACC_F64 = 0, FDTD_ACC_COMP_F32 = 1 };
+enum { FDTD_SIGMA_PAPER = 0, FDTD_SIGMA_PEAK_NORMALISED = 1 };
+
+/* Problem description.  Boxes are half-open node ranges [lo, hi) per axis
+ * (x, y, z); in 2D the z range must be [0, 1).  Grid: nx x ny Ez nodes in
+ * 2D; nx x ny x nz cells in 3D. */
+typedef struct fdtd_config {
+    int ndim;                 /* 2: TM_z (Ez, Hx, Hy, Jz); 3: full Yee        */
+    int nx, ny, nz;
+    double dx;                /* grid step, m (dx = dy = dz, Sec. 3.2)         */
+    double courant;           /* S = c0 dt / dx                                */
+    int npml;                 /* CPML layers per side, PEC walls behind        */
+    double pml_m;             /* CPML polynomial grading order                 */
+    double pml_sigma_factor;  /* sigma_pml_max = factor (m + 1) / (eta0 dx)    */
+    double pml_kappa_max;
+    double pml_alpha_max;     /* S/m, linear taper                             */
+    double eps_inf, omega_p, gamma_p;  /* Drude material, Eq. (1)              */
+    double eps_s;             /* background relative permittivity              */
+    double psi_s_ratio;       /* psi_s = ratio * omega_p^2 (paper: 0.01)       */
+    double eps_g;             /* gap permittivity                              */
+    int design_lo[3], design_hi[3];
+    int gap_lo[3], gap_hi[3];
+    int src_lo[3], src_hi[3]; /* soft current source box on Ez nodes          */
+    int nbands;               /* 1 or 2 Gaussian-modulated carriers            */
+    double f0[2];             /* carrier frequencies, Hz                       */
+    double tau, t0;           /* envelope exp(-((t - t0) / tau)^2), s          */
+    double src_amp;           /* J_src = src_amp eps0 c0 / dx g(t), A/m^2      */
+    int nsteps;               /* N                                             */
+    int filter_radius;        /* Gaussian filter half-width, cells; 0 = none   */
+    double filter_sigma;      /* Gaussian filter standard deviation, cells     */
+    int sigma_form;           /* FDTD_SIGMA_*                                  */
+    double sub_eps;           /* 3D: background eps of cells with k < sub_hi   */
+    int sub_hi;
+    int real_bytes;           /* field precision: 4 (FP32) or 8 (FP64)         */
+    int snapshot_every;       /* 0: keep the full design-box E history;        */
+                              /* k > 0: checkpoint every k steps, recompute    */
+    int snapshot_dtype;       /* FDTD_SNAP_*: snapshot storage precision       */
+    int accum_kind;           /* FDTD_ACC_*: sensitivity accumulator           */
+} fdtd_config;
+
+typedef struct fdtd_ctx fdtd_ctx;
+
+/* Run-time facts about a context. */
+typedef struct fdtd_info {
+    double dt;                    /* time step, s                              */
+    long long n_cells;            /* grid nodes (2D) / cells (3D)              */
+    long long n_design;           /* M_d, length of rho and of the gradient    */
+    long long n_gap;              /* M_g                                       */
+    long long launches;           /* kernels launched since create             */
+    long long cell_updates;       /* cells x steps advanced since create       */
+    size_t workspace_bytes;
+} fdtd_info;
+
+/* Bytes of device workspace a context for cfg needs (256-byte aligned
+ * start expected).  Fails with FDTD_EINVAL on an invalid configuration. */
+fdtd_status fdtd_workspace_bytes(const fdtd_config *cfg, size_t *bytes);
+
+/* Create a context on the current device.  d_workspace: caller-owned device
+ * memory of at least fdtd_workspace_bytes bytes, 256-byte aligned, kept
+ * alive until fdtd_destroy.  stream: a cudaStream_t (NULL = legacy default
+ * stream).  Builds the CPML and source tables on the host, uploads them and
+ * synchronises the stream once. */
+fdtd_status fdtd_create(const fdtd_config *cfg, void *d_workspace, size_t bytes,
+                        void *stream, fdtd_ctx **out);
+
+/* Set the design densities (Sec. 2.1).  d_rho: device array of n = M_d
+ * values in the context's field precision (float for real_bytes 4, double
+ * for 8), x fastest, then y (then z); entries inside the gap are ignored
+ * (the gap is vacuum of eps_g).  Applies the filter of Eq. (26).  Checks
+ * 0 <= rho <= 1 on the device and synchronises the stream: returns
+ * FDTD_ERANGE if any entry is outside.  Invalidates earlier forward and
+ * adjoint results. */
+fdtd_status fdtd_set_design(fdtd_ctx *ctx, const void *d_rho, size_t n);
+
+/* Artificial damping (Sec. 2.1): sigma_max of Eq. (5c) in S/m (>= 0) and a
+ * factor (> 0) on the Drude collision rate.  Defaults: 0 and 1.
+ * Invalidates earlier forward and adjoint results. */
+fdtd_status fdtd_set_damping(fdtd_ctx *ctx, double sigma_max, double gamma_scale);
+
+/* Forward solve of N steps.  Writes W~ (Eq. 24) to d_W (device, one double;
+ * may be NULL) asynchronously.  Requires fdtd_set_design. */
+fdtd_status fdtd_forward(fdtd_ctx *ctx, double *d_W);
+
+/* Adjoint solve (Eq. 20) with the sensitivity accumulation of Eq. (25).
+ * Requires fdtd_forward since the last set_design / set_damping. */
+fdtd_status fdtd_adjoint(fdtd_ctx *ctx);
+
+/* dW~/drho (Eq. 27, with F^T) into d_grad (device, n = M_d doubles); zero
+ * on gap nodes.  Requires fdtd_adjoint since the last forward. */
+fdtd_status fdtd_gradient(fdtd_ctx *ctx, double *d_grad, size_t n);
+
+/* Gap-field history E^n, n = 0..N, of the last forward run into d_out
+ * (device, n = (N + 1) * M_g doubles, gap nodes x fastest). */
+fdtd_status fdtd_gap_history(fdtd_ctx *ctx, double *d_out, size_t n);
+
+/* Wait for the context's stream and report (then clear) device-side errors:
+ * FDTD_ERANGE, FDTD_EUNSTABLE, or FDTD_ECUDA for a failed kernel. */
+fdtd_status fdtd_sync(fdtd_ctx *ctx);
+
+/* One whole design evaluation from host memory: copies h_rho (M_d values in
+ * the field precision) into the workspace, then set_design, forward,
+ * adjoint and gradient, and copies W~ into *h_W and dW~/drho into h_grad
+ * (M_d doubles).  Synchronous. */
+fdtd_status fdtd_run_host(fdtd_ctx *ctx, const void *h_rho, size_t n, double *h_W, double *h_grad);
+
+fdtd_status fdtd_get_info(const fdtd_ctx *ctx, fdtd_info *info);
+
+const char *fdtd_status_string(fdtd_status s);
+
+/* Release the context (host memory only; the workspace stays the caller's). */
+void fdtd_destroy(fdtd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDTD_GB300_H */

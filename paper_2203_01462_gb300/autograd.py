@@ -1,0 +1,36 @@
+"""``torch.autograd.Function`` from the design densities rho to W~.
+
+forward runs set_design + forward (checkpointing the fields as configured);
+backward runs the adjoint solve, whose sensitivities (Eq. 25) and chain rule
+(Eq. 27) give dW~/drho, and scales it by the incoming gradient.
+"""
+from __future__ import annotations
+
+import torch
+
+from .binding import Solver
+
+
+class FdtdObjective(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, rho: torch.Tensor, solver: Solver, sigma_max: float = 0.0, gamma_scale: float = 1.0):
+        solver.set_design(rho.detach())
+        solver.set_damping(sigma_max, gamma_scale)
+        W = solver.forward().clone().reshape(())
+        ctx.solver = solver
+        ctx.shape = rho.shape
+        ctx.dtype = rho.dtype
+        return W
+
+    @staticmethod
+    def backward(ctx, gW: torch.Tensor):
+        s: Solver = ctx.solver
+        s.adjoint()
+        g = s.gradient()
+        g = (g * gW.to(g.dtype)).to(ctx.dtype).reshape(ctx.shape)
+        return g, None, None, None
+
+
+def objective(rho: torch.Tensor, solver: Solver, sigma_max: float = 0.0, gamma_scale: float = 1.0):
+    """W~(rho) as a differentiable scalar (FP64)."""
+    return FdtdObjective.apply(rho, solver, sigma_max, gamma_scale)

@@ -1,0 +1,242 @@
+"""ctypes binding of ``libfdtd_gb300.so`` (C ABI in ``include/fdtd.h``).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  PyTorch provides the device memory (the workspace, rho, the
+gradient) and the CUDA stream.  There is no fallback: if the library has not
+been built, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libfdtd_gb300.so")
+
+STATUS = {0: "FDTD_OK", 1: "FDTD_EINVAL", 2: "FDTD_ENOMEM", 3: "FDTD_ECUDA", 4: "FDTD_ESTATE",
+          5: "FDTD_EUNSTABLE", 6: "FDTD_ETIMEOUT", 7: "FDTD_ERANGE"}
+SNAP = {"f32": 0, "bf16": 1, "f16": 2}
+ACC = {"f64": 0, "comp_f32": 1}
+
+# Every symbol the header declares (checked by the CPU test-suite).
+EXPORTS = ["fdtd_workspace_bytes", "fdtd_create", "fdtd_set_design", "fdtd_set_damping",
+           "fdtd_forward", "fdtd_adjoint", "fdtd_gradient", "fdtd_gap_history", "fdtd_sync",
+           "fdtd_run_host", "fdtd_get_info", "fdtd_status_string", "fdtd_destroy"]
+
+
+class FdtdError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s: %s (%s)" % (where, STATUS.get(status, status), _status_string(status)))
+
+
+class FdtdConfig(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("dx", C.c_double), ("courant", C.c_double),
+        ("npml", C.c_int), ("pml_m", C.c_double), ("pml_sigma_factor", C.c_double),
+        ("pml_kappa_max", C.c_double), ("pml_alpha_max", C.c_double),
+        ("eps_inf", C.c_double), ("omega_p", C.c_double), ("gamma_p", C.c_double),
+        ("eps_s", C.c_double), ("psi_s_ratio", C.c_double), ("eps_g", C.c_double),
+        ("design_lo", C.c_int * 3), ("design_hi", C.c_int * 3),
+        ("gap_lo", C.c_int * 3), ("gap_hi", C.c_int * 3),
+        ("src_lo", C.c_int * 3), ("src_hi", C.c_int * 3),
+        ("nbands", C.c_int), ("f0", C.c_double * 2), ("tau", C.c_double), ("t0", C.c_double),
+        ("src_amp", C.c_double), ("nsteps", C.c_int),
+        ("filter_radius", C.c_int), ("filter_sigma", C.c_double),
+        ("sigma_form", C.c_int), ("sub_eps", C.c_double), ("sub_hi", C.c_int),
+        ("real_bytes", C.c_int), ("snapshot_every", C.c_int), ("snapshot_dtype", C.c_int),
+        ("accum_kind", C.c_int),
+    ]
+
+
+class FdtdInfo(C.Structure):
+    _fields_ = [("dt", C.c_double), ("n_cells", C.c_longlong), ("n_design", C.c_longlong),
+                ("n_gap", C.c_longlong), ("launches", C.c_longlong), ("cell_updates", C.c_longlong),
+                ("workspace_bytes", C.c_size_t)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Open the library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libfdtd_gb300.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        cfgp = C.POINTER(FdtdConfig)
+        sig = {
+            "fdtd_workspace_bytes": [cfgp, C.POINTER(C.c_size_t)],
+            "fdtd_create": [cfgp, P, C.c_size_t, P, C.POINTER(P)],
+            "fdtd_set_design": [P, P, C.c_size_t],
+            "fdtd_set_damping": [P, C.c_double, C.c_double],
+            "fdtd_forward": [P, P],
+            "fdtd_adjoint": [P],
+            "fdtd_gradient": [P, P, C.c_size_t],
+            "fdtd_gap_history": [P, P, C.c_size_t],
+            "fdtd_sync": [P],
+            "fdtd_run_host": [P, P, C.c_size_t, P, P],
+            "fdtd_get_info": [P, C.POINTER(FdtdInfo)],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.fdtd_status_string.argtypes = [C.c_int]
+        L.fdtd_status_string.restype = C.c_char_p
+        L.fdtd_destroy.argtypes = [P]
+        L.fdtd_destroy.restype = None
+        _lib = L
+        return L
+
+
+def _status_string(s: int) -> str:
+    try:
+        return load().fdtd_status_string(int(s)).decode()
+    except Exception:  # library missing while formatting an error
+        return "?"
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != 0:
+        raise FdtdError(rc, where)
+
+
+def config(w: dict) -> FdtdConfig:
+    """Fill the C struct from a workload dict (see ``inputs``)."""
+    c = FdtdConfig()
+    for name, ctype in FdtdConfig._fields_:
+        if name == "real_bytes":
+            c.real_bytes = 8 if w.get("real", "f64") == "f64" else 4
+            continue
+        if name == "snapshot_dtype":
+            c.snapshot_dtype = SNAP[w.get("snapshot_dtype", "f32")]
+            continue
+        if name == "accum_kind":
+            c.accum_kind = ACC[w.get("accum", "f64")]
+            continue
+        v = w[name] if name in w else (0 if name == "snapshot_every" else None)
+        if name == "f0":
+            c.f0[0], c.f0[1] = float(v[0]), float(v[1])
+        elif isinstance(getattr(c, name), C.Array):
+            arr = getattr(c, name)
+            for a in range(3):
+                arr[a] = int(v[a])
+        elif ctype is C.c_int:
+            setattr(c, name, int(v))
+        else:
+            setattr(c, name, float(v))
+    return c
+
+
+def workspace_bytes(w: dict) -> int:
+    n = C.c_size_t(0)
+    cfg = config(w)
+    _check(load().fdtd_workspace_bytes(C.byref(cfg), C.byref(n)), "fdtd_workspace_bytes")
+    return int(n.value)
+
+
+class Solver:
+    """One context: a caller-owned workspace on one device and one stream."""
+
+    def __init__(self, w: dict, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.w = dict(w)
+        self.lib = load()
+        self.cfg = config(w)
+        self.device = torch.device(device if device is not None else "cuda")
+        self.real = torch.float64 if self.cfg.real_bytes == 8 else torch.float32
+        nbytes = workspace_bytes(w)
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        ctx = C.c_void_p()
+        _check(self.lib.fdtd_create(C.byref(self.cfg), C.c_void_p(self.ws.data_ptr()), nbytes,
+                                    C.c_void_p(self.stream.cuda_stream), C.byref(ctx)), "fdtd_create")
+        self.ctx = ctx
+        inf = self.info()
+        self.n_design = int(inf.n_design)
+        self.n_gap = int(inf.n_gap)
+        self.dt = float(inf.dt)
+        self._W = torch.zeros(1, dtype=torch.float64, device=self.device)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            self.lib.fdtd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> FdtdInfo:
+        i = FdtdInfo()
+        _check(self.lib.fdtd_get_info(self.ctx, C.byref(i)), "fdtd_get_info")
+        return i
+
+    def set_design(self, rho) -> None:
+        t = self.torch
+        r = rho if isinstance(rho, t.Tensor) else t.as_tensor(np.asarray(rho))
+        r = r.to(device=self.device, dtype=self.real).contiguous().reshape(-1)
+        if r.numel() != self.n_design:
+            raise ValueError("rho has %d entries, design box has %d" % (r.numel(), self.n_design))
+        self._rho = r
+        _check(self.lib.fdtd_set_design(self.ctx, C.c_void_p(r.data_ptr()), r.numel()), "fdtd_set_design")
+
+    def set_damping(self, sigma_max: float = 0.0, gamma_scale: float = 1.0) -> None:
+        _check(self.lib.fdtd_set_damping(self.ctx, float(sigma_max), float(gamma_scale)), "fdtd_set_damping")
+
+    def forward(self, out=None):
+        out = self._W if out is None else out
+        _check(self.lib.fdtd_forward(self.ctx, C.c_void_p(out.data_ptr())), "fdtd_forward")
+        return out
+
+    def adjoint(self) -> None:
+        _check(self.lib.fdtd_adjoint(self.ctx), "fdtd_adjoint")
+
+    def gradient(self, out=None):
+        t = self.torch
+        if out is None:
+            out = t.empty(self.n_design, dtype=t.float64, device=self.device)
+        _check(self.lib.fdtd_gradient(self.ctx, C.c_void_p(out.data_ptr()), out.numel()), "fdtd_gradient")
+        return out
+
+    def gap_history(self):
+        t = self.torch
+        n = (int(self.cfg.nsteps) + 1) * self.n_gap
+        out = t.empty(n, dtype=t.float64, device=self.device)
+        _check(self.lib.fdtd_gap_history(self.ctx, C.c_void_p(out.data_ptr()), n), "fdtd_gap_history")
+        return out.reshape(int(self.cfg.nsteps) + 1, self.n_gap)
+
+    def sync(self) -> None:
+        _check(self.lib.fdtd_sync(self.ctx), "fdtd_sync")
+
+    def run_host(self, rho: np.ndarray):
+        """One evaluation from host memory (copies inside the call)."""
+        dt = np.float64 if self.cfg.real_bytes == 8 else np.float32
+        r = np.ascontiguousarray(np.asarray(rho, dtype=dt).reshape(-1))
+        g = np.empty(self.n_design, dtype=np.float64)
+        Wv = C.c_double(0.0)
+        _check(self.lib.fdtd_run_host(self.ctx, C.c_void_p(r.ctypes.data), r.size, C.byref(Wv),
+                                      C.c_void_p(g.ctypes.data)), "fdtd_run_host")
+        return Wv.value, g
+
+    def evaluate(self, rho, sigma_max: float = 0.0, gamma_scale: float = 1.0):
+        """W~ and dW~/drho on the device (both FP64 tensors)."""
+        self.set_design(rho)
+        self.set_damping(sigma_max, gamma_scale)
+        W = self.forward().clone()
+        self.adjoint()
+        g = self.gradient()
+        return W, g

@@ -1,0 +1,637 @@
+// Host side of the C ABI declared in include/fdtd.h: configuration checks,
+// workspace layout, CPML / source / filter tables, and the time loops of the
+// forward run, the checkpointed recompute and the adjoint run.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "../../include/fdtd.h"
+#include "fdtd_internal.h"
+
+using namespace fdtd;
+
+namespace {
+
+constexpr double kC0 = 299792458.0;
+constexpr double kMu0 = 1.25663706212e-6;  // CODATA 2018
+constexpr double kPi = 3.14159265358979323846;
+inline double eps0() { return 1.0 / (kMu0 * kC0 * kC0); }
+
+// Bump allocator over the caller's workspace; a null base only measures.
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base((char *)b) {}
+    template <typename T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? (T *)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+bool box_ok(const int *lo, const int *hi, const int *n, int ndim, bool allow_empty)
+{
+    for (int a = 0; a < 3; ++a) {
+        if (a >= ndim) {
+            if (lo[a] != 0 || hi[a] != 1) return false;
+            continue;
+        }
+        if (lo[a] < 0 || hi[a] > n[a] || hi[a] < lo[a]) return false;
+        if (!allow_empty && hi[a] == lo[a]) return false;
+    }
+    return true;
+}
+
+bool box_inside(const int *lo, const int *hi, const int *olo, const int *ohi, int ndim)
+{
+    for (int a = 0; a < ndim; ++a)
+        if (hi[a] > lo[a] && (lo[a] < olo[a] || hi[a] > ohi[a])) return false;
+    return true;
+}
+
+long long box_count(const int *lo, const int *hi, int ndim)
+{
+    long long n = 1;
+    for (int a = 0; a < ndim; ++a) n *= (long long)(hi[a] - lo[a]);
+    return n;
+}
+
+fdtd_status validate(const fdtd_config *c)
+{
+    if (!c) return FDTD_EINVAL;
+    if (c->ndim != 2) return FDTD_EINVAL;  // 3D: separate path
+    if (c->real_bytes != 4 && c->real_bytes != 8) return FDTD_EINVAL;
+    if (c->nx < 4 || c->ny < 4 || c->nz != 1) return FDTD_EINVAL;
+    if (c->npml < 0 || c->nx <= 2 * c->npml + 2 || c->ny <= 2 * c->npml + 2) return FDTD_EINVAL;
+    if (!(c->dx > 0) || !(c->courant > 0) || c->courant >= 1.0 / sqrt((double)c->ndim)) return FDTD_EINVAL;
+    if (c->nsteps < 1) return FDTD_EINVAL;
+    if (!(c->omega_p > 0) || !(c->psi_s_ratio > 0) || c->gamma_p < 0) return FDTD_EINVAL;
+    if (!(c->eps_s > 0) || !(c->eps_g > 0) || !(c->eps_inf > 0)) return FDTD_EINVAL;
+    if (c->nbands < 1 || c->nbands > 2 || !(c->tau > 0)) return FDTD_EINVAL;
+    int n[3] = {c->nx, c->ny, c->nz};
+    if (!box_ok(c->design_lo, c->design_hi, n, c->ndim, false)) return FDTD_EINVAL;
+    if (!box_ok(c->gap_lo, c->gap_hi, n, c->ndim, true)) return FDTD_EINVAL;
+    if (!box_ok(c->src_lo, c->src_hi, n, c->ndim, true)) return FDTD_EINVAL;
+    if (!box_inside(c->gap_lo, c->gap_hi, c->design_lo, c->design_hi, c->ndim)) return FDTD_EINVAL;
+    if (c->filter_radius < 0 || (c->filter_radius > 0 && !(c->filter_sigma > 0))) return FDTD_EINVAL;
+    if (c->snapshot_every < 0) return FDTD_EINVAL;
+    if (c->snapshot_dtype != FDTD_SNAP_F32) return FDTD_EINVAL;
+    if (c->accum_kind != FDTD_ACC_F64) return FDTD_EINVAL;
+    if (c->sigma_form != FDTD_SIGMA_PAPER && c->sigma_form != FDTD_SIGMA_PEAK_NORMALISED) return FDTD_EINVAL;
+    return FDTD_OK;
+}
+
+// ---------------------------------------------------------------- tables
+
+// CPML at a position p (cell units) of an axis with n nodes: depth into the
+// layer, polynomial sigma and kappa, linear alpha (Roden-Gedney).
+struct PmlPoint { double b, c, ki; };
+
+PmlPoint pml_point(const fdtd_config *c, int n, double p)
+{
+    PmlPoint r{0.0, 0.0, 1.0};
+    const double L = c->npml;
+    if (c->npml <= 0) return r;
+    double d = 0.0;
+    if (p < L) d = L - p;
+    else if (p > (n - 1) - L) d = p - ((n - 1) - L);
+    if (d <= 0.0) return r;
+    const double x = d / L, xm = pow(x, c->pml_m);
+    const double eta0 = kMu0 * kC0;
+    const double sig = c->pml_sigma_factor * (c->pml_m + 1.0) / (eta0 * c->dx) * xm;
+    const double kap = 1.0 + (c->pml_kappa_max - 1.0) * xm;
+    const double alp = c->pml_alpha_max * (1.0 - x);
+    const double dt = c->courant * c->dx / kC0;
+    r.b = exp(-(sig / kap + alp) * dt / eps0());
+    r.c = sig > 0.0 ? sig / (sig * kap + kap * kap * alp) * (r.b - 1.0) : 0.0;
+    r.ki = 1.0 / kap;
+    return r;
+}
+
+double excitation(const fdtd_config *c, double t)
+{
+    const double u = (t - c->t0) / c->tau;
+    double s = 0.0;
+    for (int b = 0; b < c->nbands; ++b) s += sin(2.0 * kPi * c->f0[b] * (t - c->t0));
+    return exp(-u * u) * s;
+}
+
+}  // namespace
+
+// -------------------------------------------------------------- context
+
+struct fdtd_ctx {
+    fdtd_config cfg;
+    cudaStream_t stream = nullptr;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    double dt = 0;
+    long long Md = 0, Mg = 0, ncells = 0;
+    bool has_design = false, fwd_done = false, adj_done = false;
+    double sigma_max = 0.0, gamma_scale = 1.0;
+    long long launches = 0, cell_updates = 0;
+    virtual ~fdtd_ctx() {}
+    virtual fdtd_status carve(Carver &cv) = 0;
+    virtual fdtd_status upload_tables() = 0;
+    virtual fdtd_status set_design(const void *d_rho) = 0;
+    virtual fdtd_status forward(double *d_W) = 0;
+    virtual fdtd_status adjoint() = 0;
+    virtual fdtd_status gradient(double *d_grad) = 0;
+    virtual fdtd_status gap_history(double *d_out) = 0;
+    virtual void *rho_stage() = 0;
+    virtual double *grad_stage() = 0;
+    virtual double *W_dev() = 0;
+    virtual unsigned *err_dev() = 0;
+};
+
+namespace {
+
+fdtd_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? FDTD_OK : FDTD_ECUDA; }
+#define FDTD_TRY(x)                          \
+    do {                                     \
+        fdtd_status s__ = (x);               \
+        if (s__ != FDTD_OK) return s__;      \
+    } while (0)
+
+template <typename R>
+struct Ctx2D final : fdtd_ctx {
+    Geo2D geo{};
+    State2D<R> F{}, A{};
+    char *stateF_base = nullptr, *stateA_base = nullptr;
+    size_t state_bytes = 0;
+    R *rho = nullptr, *rho_t = nullptr, *ftmp = nullptr, *rstage = nullptr;
+    double *G = nullptr, *gtmp = nullptr, *gtmp2 = nullptr, *gstage = nullptr;
+    R *gap_hist = nullptr, *rec = nullptr, *src_tab = nullptr;
+    char *snaps = nullptr;
+    int nsnap = 0;
+    R *pml_tab = nullptr;  // x: 6 * nx, then y: 6 * ny
+    Pml1D<R> px{}, py{};
+    R *fw_R = nullptr, *fnx_R = nullptr, *fny_R = nullptr;
+    double *fw_D = nullptr, *fnx_D = nullptr, *fny_D = nullptr;
+    double *misc = nullptr;   // [0] W
+    unsigned *err = nullptr;
+
+    void *rho_stage() override { return rstage; }
+    double *grad_stage() override { return gstage; }
+    double *W_dev() override { return misc; }
+    unsigned *err_dev() override { return err; }
+
+    void carve_state(Carver &cv, State2D<R> &s, char *&base)
+    {
+        const int np = cfg.npml;
+        const size_t grid = (size_t)geo.ny * geo.px;
+        size_t start = (cv.off + 255) & ~(size_t)255;
+        s.Ez = cv.take<R>(grid);
+        s.Hx = cv.take<R>(grid);
+        s.Hy = cv.take<R>(grid);
+        s.J = cv.take<R>((size_t)Md);
+        s.pezx = cv.take<R>((size_t)geo.ny * 2 * np);
+        s.phyx = cv.take<R>((size_t)geo.ny * 2 * np);
+        s.pezy = cv.take<R>((size_t)2 * np * geo.px);
+        s.phxy = cv.take<R>((size_t)2 * np * geo.px);
+        cv.off = (cv.off + 255) & ~(size_t)255;
+        base = cv.base ? cv.base + start : nullptr;
+        state_bytes = cv.off - start;
+    }
+
+    fdtd_status carve(Carver &cv) override
+    {
+        const fdtd_config &c = cfg;
+        geo.nx = c.nx;
+        geo.ny = c.ny;
+        geo.px = (c.nx + 31) / 32 * 32;
+        geo.npml = c.npml;
+        geo.dx0 = c.design_lo[0];
+        geo.dy0 = c.design_lo[1];
+        geo.dnx = c.design_hi[0] - c.design_lo[0];
+        geo.dny = c.design_hi[1] - c.design_lo[1];
+        geo.gx0 = c.gap_lo[0];
+        geo.gy0 = c.gap_lo[1];
+        geo.gnx = c.gap_hi[0] - c.gap_lo[0];
+        geo.gny = c.gap_hi[1] - c.gap_lo[1];
+        geo.sx0 = c.src_lo[0];
+        geo.sx1 = c.src_hi[0];
+        geo.sy0 = c.src_lo[1];
+        geo.sy1 = c.src_hi[1];
+        const long long N = c.nsteps;
+        carve_state(cv, F, stateF_base);
+        carve_state(cv, A, stateA_base);
+        rho = cv.take<R>(Md);
+        rho_t = cv.take<R>(Md);
+        ftmp = cv.take<R>(Md);
+        rstage = cv.take<R>(Md);
+        G = cv.take<double>(Md);
+        gtmp = cv.take<double>(Md);
+        gtmp2 = cv.take<double>(Md);
+        gstage = cv.take<double>(Md);
+        gap_hist = cv.take<R>((size_t)(N + 1) * (Mg ? Mg : 1));
+        const long long K = c.snapshot_every;
+        rec = cv.take<R>((size_t)(K > 0 ? std::min<long long>(K, N) : N) * Md);
+        nsnap = K > 0 ? (int)((N + K - 1) / K) : 0;
+        snaps = cv.take<char>((size_t)nsnap * state_bytes);
+        src_tab = cv.take<R>(N);
+        pml_tab = cv.take<R>(6 * (size_t)(c.nx + c.ny));
+        const int FR = c.filter_radius;
+        fw_R = cv.take<R>(2 * FR + 1);
+        fnx_R = cv.take<R>(geo.dnx);
+        fny_R = cv.take<R>(geo.dny);
+        fw_D = cv.take<double>(2 * FR + 1);
+        fnx_D = cv.take<double>(geo.dnx);
+        fny_D = cv.take<double>(geo.dny);
+        misc = cv.take<double>(4);
+        err = cv.take<unsigned>(4);
+        if (pml_tab) {
+            R *t = pml_tab;
+            px = {t, t + c.nx, t + 2 * c.nx, t + 3 * c.nx, t + 4 * c.nx, t + 5 * c.nx};
+            t += 6 * c.nx;
+            py = {t, t + c.ny, t + 2 * c.ny, t + 3 * c.ny, t + 4 * c.ny, t + 5 * c.ny};
+        }
+        return FDTD_OK;
+    }
+
+    fdtd_status upload_tables() override
+    {
+        const fdtd_config &c = cfg;
+        std::vector<R> tab(6 * (size_t)(c.nx + c.ny));
+        auto fill = [&](R *t, int n) {
+            for (int i = 0; i < n; ++i) {
+                PmlPoint e = pml_point(&c, n, i), h = pml_point(&c, n, i + 0.5);
+                t[i] = (R)e.b;
+                t[n + i] = (R)e.c;
+                t[2 * n + i] = (R)e.ki;
+                t[3 * n + i] = (R)h.b;
+                t[4 * n + i] = (R)h.c;
+                t[5 * n + i] = (R)h.ki;
+            }
+        };
+        fill(tab.data(), c.nx);
+        fill(tab.data() + 6 * c.nx, c.ny);
+        std::vector<R> src(c.nsteps);
+        for (int n = 0; n < c.nsteps; ++n) src[n] = (R)(c.src_amp * c.courant * excitation(&c, (n + 0.5) * dt));
+        const int FR = c.filter_radius;
+        std::vector<double> w(2 * FR + 1), nx(geo.dnx), ny(geo.dny);
+        for (int k = -FR; k <= FR; ++k) w[k + FR] = FR ? exp(-(double)k * k / (2.0 * c.filter_sigma * c.filter_sigma)) : 1.0;
+        auto norms = [&](std::vector<double> &v, int n) {
+            for (int i = 0; i < n; ++i) {
+                double s = 0.0;
+                for (int k = -FR; k <= FR; ++k)
+                    if (i + k >= 0 && i + k < n) s += w[k + FR];
+                v[i] = 1.0 / s;
+            }
+        };
+        norms(nx, geo.dnx);
+        norms(ny, geo.dny);
+        std::vector<R> wR(w.begin(), w.end()), nxR(nx.begin(), nx.end()), nyR(ny.begin(), ny.end());
+        cudaStream_t st = stream;
+        FDTD_TRY(cuda_ok(cudaMemcpyAsync(pml_tab, tab.data(), tab.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
+        FDTD_TRY(cuda_ok(cudaMemcpyAsync(src_tab, src.data(), src.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
+        FDTD_TRY(cuda_ok(cudaMemcpyAsync(fw_R, wR.data(), wR.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
+        FDTD_TRY(cuda_ok(cudaMemcpyAsync(fnx_R, nxR.data(), nxR.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
+        FDTD_TRY(cuda_ok(cudaMemcpyAsync(fny_R, nyR.data(), nyR.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
+        FDTD_TRY(cuda_ok(cudaMemcpyAsync(fw_D, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice, st)));
+        FDTD_TRY(cuda_ok(cudaMemcpyAsync(fnx_D, nx.data(), nx.size() * sizeof(double), cudaMemcpyHostToDevice, st)));
+        FDTD_TRY(cuda_ok(cudaMemcpyAsync(fny_D, ny.data(), ny.size() * sizeof(double), cudaMemcpyHostToDevice, st)));
+        launch_zero_bytes(err, 4 * sizeof(unsigned), st);
+        ++launches;
+        return cuda_ok(cudaStreamSynchronize(st));
+    }
+
+    Coef<R> coef() const
+    {
+        const fdtd_config &c = cfg;
+        Coef<R> k;
+        const double g = c.gamma_p * gamma_scale * dt;
+        const double kJ = (1.0 - 0.5 * g) / (1.0 + 0.5 * g);
+        const double psi = c.omega_p * c.omega_p * dt * dt;
+        k.S = (R)c.courant;
+        k.eps_s = (R)c.eps_s;
+        k.eps_g = (R)c.eps_g;
+        k.inv_eps_s = (R)(1.0 / c.eps_s);
+        k.inv_eps_g = (R)(1.0 / c.eps_g);
+        k.d_eps = (R)(c.eps_inf - c.eps_s);
+        k.psi = (R)psi;
+        k.psi_s = (R)(c.psi_s_ratio * psi);
+        k.sig_max = (R)(sigma_max * dt / eps0() * (c.sigma_form == FDTD_SIGMA_PEAK_NORMALISED ? 4.0 : 1.0));
+        k.kJ = (R)kJ;
+        k.inv1g = (R)(1.0 / (1.0 + 0.5 * g));
+        k.half1pkJ = (R)(0.5 * (1.0 + kJ));
+        return k;
+    }
+
+    fdtd_status check_launch() { return cuda_ok(cudaGetLastError()); }
+
+    fdtd_status set_design(const void *d_rho) override
+    {
+        cudaStream_t st = stream;
+        launch_copy_check_rho<R>((const R *)d_rho, rho, Md, err, st);
+        ++launches;
+        const int FR = cfg.filter_radius;
+        if (FR > 0) {
+            launch_filter_rows<R>(rho, ftmp, geo.dnx, geo.dny, FR, fw_R, fnx_R, 0, st);
+            launch_filter_cols<R>(ftmp, rho_t, geo.dnx, geo.dny, FR, fw_R, fny_R, 0, st);
+            launches += 2;
+        } else {
+            launch_copy_bytes(rho, rho_t, Md * sizeof(R), st);
+            ++launches;
+        }
+        FDTD_TRY(check_launch());
+        unsigned h_err = 0;
+        FDTD_TRY(cuda_ok(cudaMemcpyAsync(&h_err, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st)));
+        FDTD_TRY(cuda_ok(cudaStreamSynchronize(st)));
+        if (h_err & ERR_RANGE) {
+            launch_zero_bytes(err, sizeof(unsigned), st);
+            cudaStreamSynchronize(st);
+            return FDTD_ERANGE;
+        }
+        return FDTD_OK;
+    }
+
+    // Advance the forward state from step n0 by count steps.  gap: record
+    // E^{n+1} of the gap; rec_base: record design-box E^{n+1} in slot
+    // (n - n0) of rec_base (null: no record).
+    void advance_forward(const Coef<R> &k, int n0, int count, bool gap, R *rec_base)
+    {
+        cudaStream_t st = stream;
+        for (int n = n0; n < n0 + count; ++n) {
+            Step2D<R> a{};
+            a.rho_t = rho_t;
+            a.src = src_tab + n;
+            a.gap_rec = (gap && Mg) ? gap_hist + (size_t)(n + 1) * Mg : nullptr;
+            a.rec = rec_base ? rec_base + (size_t)(n - n0) * Md : nullptr;
+            launch_h2d<R>(geo, F, k, px, py, st);
+            launch_e2d<R>(0, geo, F, k, px, py, a, st);
+        }
+        launches += 2LL * count;
+        cell_updates += (long long)count * ncells;
+    }
+
+    // Adjoint steps for m = m_hi down to m_lo + 1 (adjoint step N - m), the
+    // forward E^m of the design box in slot (m - 1 - slot0) of rec.
+    void advance_adjoint(const Coef<R> &k, int m_hi, int m_lo, int slot0)
+    {
+        cudaStream_t st = stream;
+        for (int m = m_hi; m > m_lo; --m) {
+            Step2D<R> a{};
+            a.rho_t = rho_t;
+            a.gap_src = Mg ? gap_hist + (size_t)m * Mg : nullptr;
+            a.rec = rec + (size_t)(m - 1 - slot0) * Md;
+            a.G = G;
+            launch_h2d<R>(geo, A, k, px, py, st);
+            launch_e2d<R>(1, geo, A, k, px, py, a, st);
+        }
+        launches += 2LL * (m_hi - m_lo);
+        cell_updates += (long long)(m_hi - m_lo) * ncells;
+    }
+
+    fdtd_status forward(double *d_W) override
+    {
+        cudaStream_t st = stream;
+        const Coef<R> k = coef();
+        const int N = cfg.nsteps, K = cfg.snapshot_every;
+        launch_zero_bytes(stateF_base, state_bytes, st);
+        if (Mg) launch_zero_bytes(gap_hist, Mg * sizeof(R), st);
+        launches += 2;
+        if (K <= 0) {
+            advance_forward(k, 0, N, true, rec);
+        } else {
+            for (int s = 0; s < nsnap; ++s) {
+                const int n0 = s * K, cnt = std::min(K, N - n0);
+                launch_copy_bytes(stateF_base, snaps + (size_t)s * state_bytes, state_bytes, st);
+                ++launches;
+                advance_forward(k, n0, cnt, true, nullptr);
+            }
+        }
+        const double coefW = 0.5 * cfg.eps_g * dt * pow(cfg.dx, cfg.ndim);
+        launch_objective<R>(gap_hist, (long long)(N + 1) * Mg, coefW, misc, d_W, err, st);
+        ++launches;
+        return check_launch();
+    }
+
+    fdtd_status adjoint() override
+    {
+        cudaStream_t st = stream;
+        const Coef<R> k = coef();
+        const int N = cfg.nsteps, K = cfg.snapshot_every;
+        launch_zero_bytes(stateA_base, state_bytes, st);
+        launch_zero_bytes(G, Md * sizeof(double), st);
+        launches += 2;
+        if (K <= 0) {
+            advance_adjoint(k, N, 0, 0);
+        } else {
+            for (int s = nsnap - 1; s >= 0; --s) {
+                const int n0 = s * K, n1 = std::min(n0 + K, N);
+                launch_copy_bytes(snaps + (size_t)s * state_bytes, stateF_base, state_bytes, st);
+                ++launches;
+                advance_forward(k, n0, n1 - n0, false, rec);
+                advance_adjoint(k, n1, n0, n0);
+            }
+        }
+        return check_launch();
+    }
+
+    fdtd_status gradient(double *d_grad) override
+    {
+        cudaStream_t st = stream;
+        const double scale = dt * pow(cfg.dx, cfg.ndim);
+        const int FR = cfg.filter_radius;
+        if (FR > 0) {
+            launch_assemble_2d(G, gtmp, geo.dnx, geo.dny, geo.gx0 - geo.dx0, geo.gy0 - geo.dy0, geo.gnx,
+                               geo.gny, scale, st);
+            launch_filter_rows<double>(gtmp, gtmp2, geo.dnx, geo.dny, FR, fw_D, fnx_D, 1, st);
+            launch_filter_cols<double>(gtmp2, d_grad, geo.dnx, geo.dny, FR, fw_D, fny_D, 1, st);
+            launch_zero_gap_2d(d_grad, geo.dnx, geo.gx0 - geo.dx0, geo.gy0 - geo.dy0, geo.gnx, geo.gny, st);
+            launches += 4;
+        } else {
+            launch_assemble_2d(G, d_grad, geo.dnx, geo.dny, geo.gx0 - geo.dx0, geo.gy0 - geo.dy0, geo.gnx,
+                               geo.gny, scale, st);
+            ++launches;
+        }
+        return check_launch();
+    }
+
+    fdtd_status gap_history(double *d_out) override
+    {
+        launch_to_double<R>(gap_hist, d_out, (long long)(cfg.nsteps + 1) * Mg, stream);
+        ++launches;
+        return check_launch();
+    }
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI
+
+extern "C" {
+
+const char *fdtd_status_string(fdtd_status s)
+{
+    switch (s) {
+    case FDTD_OK: return "ok";
+    case FDTD_EINVAL: return "invalid argument or configuration";
+    case FDTD_ENOMEM: return "workspace too small";
+    case FDTD_ECUDA: return "CUDA error";
+    case FDTD_ESTATE: return "call out of order";
+    case FDTD_EUNSTABLE: return "non-finite objective (unstable run)";
+    case FDTD_ETIMEOUT: return "device wait timed out";
+    case FDTD_ERANGE: return "design density outside [0, 1]";
+    }
+    return "unknown status";
+}
+
+static fdtd_ctx *make_ctx(const fdtd_config *cfg)
+{
+    fdtd_ctx *c = nullptr;
+    if (cfg->real_bytes == 4) c = new (std::nothrow) Ctx2D<float>();
+    else c = new (std::nothrow) Ctx2D<double>();
+    if (!c) return nullptr;
+    c->cfg = *cfg;
+    c->dt = cfg->courant * cfg->dx / kC0;
+    c->Md = box_count(cfg->design_lo, cfg->design_hi, cfg->ndim);
+    c->Mg = box_count(cfg->gap_lo, cfg->gap_hi, cfg->ndim);
+    c->ncells = (long long)cfg->nx * cfg->ny * (cfg->ndim == 3 ? cfg->nz : 1);
+    return c;
+}
+
+fdtd_status fdtd_workspace_bytes(const fdtd_config *cfg, size_t *bytes)
+{
+    if (!bytes) return FDTD_EINVAL;
+    FDTD_TRY(validate(cfg));
+    std::unique_ptr<fdtd_ctx> c(make_ctx(cfg));
+    if (!c) return FDTD_ENOMEM;
+    Carver cv(nullptr);
+    FDTD_TRY(c->carve(cv));
+    *bytes = (cv.off + 255) & ~(size_t)255;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_create(const fdtd_config *cfg, void *d_workspace, size_t bytes, void *stream, fdtd_ctx **out)
+{
+    if (!out || !d_workspace) return FDTD_EINVAL;
+    *out = nullptr;
+    FDTD_TRY(validate(cfg));
+    if (((uintptr_t)d_workspace & 255) != 0) return FDTD_EINVAL;
+    size_t need = 0;
+    FDTD_TRY(fdtd_workspace_bytes(cfg, &need));
+    if (bytes < need) return FDTD_ENOMEM;
+    fdtd_ctx *c = make_ctx(cfg);
+    if (!c) return FDTD_ENOMEM;
+    c->stream = (cudaStream_t)stream;
+    c->ws = d_workspace;
+    c->ws_bytes = bytes;
+    Carver cv(d_workspace);
+    fdtd_status s = c->carve(cv);
+    if (s == FDTD_OK) s = c->upload_tables();
+    if (s != FDTD_OK) {
+        delete c;
+        return s;
+    }
+    *out = c;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_set_design(fdtd_ctx *ctx, const void *d_rho, size_t n)
+{
+    if (!ctx || !d_rho || (long long)n != ctx->Md) return FDTD_EINVAL;
+    ctx->has_design = ctx->fwd_done = ctx->adj_done = false;
+    FDTD_TRY(ctx->set_design(d_rho));
+    ctx->has_design = true;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_set_damping(fdtd_ctx *ctx, double sigma_max, double gamma_scale)
+{
+    if (!ctx || !(sigma_max >= 0) || !(gamma_scale > 0) || !isfinite(sigma_max) || !isfinite(gamma_scale))
+        return FDTD_EINVAL;
+    ctx->sigma_max = sigma_max;
+    ctx->gamma_scale = gamma_scale;
+    ctx->fwd_done = ctx->adj_done = false;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_forward(fdtd_ctx *ctx, double *d_W)
+{
+    if (!ctx) return FDTD_EINVAL;
+    if (!ctx->has_design) return FDTD_ESTATE;
+    ctx->fwd_done = ctx->adj_done = false;
+    FDTD_TRY(ctx->forward(d_W));
+    ctx->fwd_done = true;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_adjoint(fdtd_ctx *ctx)
+{
+    if (!ctx) return FDTD_EINVAL;
+    if (!ctx->fwd_done) return FDTD_ESTATE;
+    FDTD_TRY(ctx->adjoint());
+    ctx->adj_done = true;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_gradient(fdtd_ctx *ctx, double *d_grad, size_t n)
+{
+    if (!ctx || !d_grad || (long long)n != ctx->Md) return FDTD_EINVAL;
+    if (!ctx->adj_done) return FDTD_ESTATE;
+    return ctx->gradient(d_grad);
+}
+
+fdtd_status fdtd_gap_history(fdtd_ctx *ctx, double *d_out, size_t n)
+{
+    if (!ctx || !d_out || (long long)n != (long long)(ctx->cfg.nsteps + 1) * ctx->Mg) return FDTD_EINVAL;
+    if (!ctx->fwd_done) return FDTD_ESTATE;
+    return ctx->gap_history(d_out);
+}
+
+fdtd_status fdtd_sync(fdtd_ctx *ctx)
+{
+    if (!ctx) return FDTD_EINVAL;
+    unsigned h = 0;
+    FDTD_TRY(cuda_ok(cudaMemcpyAsync(&h, ctx->err_dev(), sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream)));
+    FDTD_TRY(cuda_ok(cudaStreamSynchronize(ctx->stream)));
+    if (h) {
+        launch_zero_bytes(ctx->err_dev(), sizeof(unsigned), ctx->stream);
+        ++ctx->launches;
+        cudaStreamSynchronize(ctx->stream);
+        if (h & ERR_RANGE) return FDTD_ERANGE;
+        return FDTD_EUNSTABLE;
+    }
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_run_host(fdtd_ctx *ctx, const void *h_rho, size_t n, double *h_W, double *h_grad)
+{
+    if (!ctx || !h_rho || !h_W || !h_grad || (long long)n != ctx->Md) return FDTD_EINVAL;
+    const size_t rb = (size_t)ctx->cfg.real_bytes;
+    FDTD_TRY(cuda_ok(cudaMemcpyAsync(ctx->rho_stage(), h_rho, n * rb, cudaMemcpyHostToDevice, ctx->stream)));
+    FDTD_TRY(fdtd_set_design(ctx, ctx->rho_stage(), n));
+    FDTD_TRY(fdtd_forward(ctx, nullptr));
+    FDTD_TRY(fdtd_adjoint(ctx));
+    FDTD_TRY(fdtd_gradient(ctx, ctx->grad_stage(), n));
+    FDTD_TRY(cuda_ok(cudaMemcpyAsync(h_W, ctx->W_dev(), sizeof(double), cudaMemcpyDeviceToHost, ctx->stream)));
+    FDTD_TRY(cuda_ok(cudaMemcpyAsync(h_grad, ctx->grad_stage(), n * sizeof(double), cudaMemcpyDeviceToHost,
+                                     ctx->stream)));
+    return fdtd_sync(ctx);
+}
+
+fdtd_status fdtd_get_info(const fdtd_ctx *ctx, fdtd_info *info)
+{
+    if (!ctx || !info) return FDTD_EINVAL;
+    info->dt = ctx->dt;
+    info->n_cells = ctx->ncells;
+    info->n_design = ctx->Md;
+    info->n_gap = ctx->Mg;
+    info->launches = ctx->launches;
+    info->cell_updates = ctx->cell_updates;
+    info->workspace_bytes = ctx->ws_bytes;
+    return FDTD_OK;
+}
+
+void fdtd_destroy(fdtd_ctx *ctx) { delete ctx; }
+
+}  // extern "C"

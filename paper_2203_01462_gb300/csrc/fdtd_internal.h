@@ -1,0 +1,94 @@
+// Internal declarations shared by the host orchestration (fdtd_host.cu) and
+// the kernel translation units.  Nothing here crosses the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace fdtd {
+
+// Device error word bits (reported by fdtd_sync).
+enum : unsigned { ERR_RANGE = 1u, ERR_NONFINITE = 2u };
+
+// Geometry of a 2D TM_z grid: Ez, Hx, Hy on nx x ny nodes with row pitch px
+// (elements).  Hx[j][i] sits at (i, j + 1/2), Hy[j][i] at (i + 1/2, j).
+struct Geo2D {
+    int nx, ny, px, npml;
+    int dx0, dy0, dnx, dny;   // design box origin and size (nodes)
+    int gx0, gy0, gnx, gny;   // gap box
+    int sx0, sx1, sy0, sy1;   // source box
+};
+
+// Field arrays of one 2D solver state.  J covers the design box only
+// (compact, dnx x dny).  CPML convolution terms live in border slabs:
+// x-slabs [ny][2 npml] for Ez and Hy, y-slabs [2 npml][px] for Ez and Hx.
+template <typename R>
+struct State2D {
+    R *Ez, *Hx, *Hy, *J;
+    R *pezx, *phyx, *pezy, *phxy;
+};
+
+// CPML tables along one axis, per node position (E) and half position (H):
+// b, c of the recursive convolution and 1 / kappa.
+template <typename R>
+struct Pml1D {
+    const R *bE, *cE, *kiE, *bH, *cH, *kiH;
+};
+
+// Step-invariant update coefficients in scaled units: E as is, H~ = eta0 H,
+// J~ = J dt / eps0, psi~ = omega_p^2 dt^2, sigma~ = sigma dt / eps0,
+// gamma~ = gamma dt.
+template <typename R>
+struct Coef {
+    R S;            // Courant number c0 dt / dx
+    R eps_s, eps_g, inv_eps_s, inv_eps_g;
+    R d_eps;        // eps_inf - eps_s
+    R psi, psi_s;   // scaled psi of the metal and of the background
+    R sig_max;      // scaled sigma_max, times 4 for the peak-normalised form
+    R kJ;           // (1 - gamma~/2) / (1 + gamma~/2)
+    R inv1g;        // 1 / (1 + gamma~/2)
+    R half1pkJ;     // (1 + kJ) / 2
+};
+
+// Per-step arguments.
+template <typename R>
+struct Step2D {
+    const R *rho_t;     // filtered density on the design box
+    const R *src;       // forward: source table entry for this step (device)
+    const R *gap_src;   // adjoint: forward gap field E^m
+    R *gap_rec;         // forward: where E^{n+1} of the gap goes (or null)
+    R *rec;             // forward: design-box E^{n+1} record (or null);
+                        // adjoint: design-box forward E^m
+    double *G;          // adjoint: sensitivity accumulator
+};
+
+// Launchers (kernels_2d.cu).  mode 0: forward / recompute; 1: adjoint.
+template <typename R>
+void launch_h2d(const Geo2D &g, const State2D<R> &s, const Coef<R> &c, const Pml1D<R> &px,
+                const Pml1D<R> &py, cudaStream_t st);
+template <typename R>
+void launch_e2d(int mode, const Geo2D &g, const State2D<R> &s, const Coef<R> &c, const Pml1D<R> &px,
+                const Pml1D<R> &py, const Step2D<R> &a, cudaStream_t st);
+
+// Auxiliary kernels (kernels_aux.cu).
+template <typename R>
+void launch_copy_check_rho(const R *src, R *dst, long long n, unsigned *err, cudaStream_t st);
+template <typename T>
+void launch_filter_rows(const T *in, T *out, int w, int h, int R_, const T *wts, const T *inv_norm,
+                        int transpose, cudaStream_t st);
+template <typename T>
+void launch_filter_cols(const T *in, T *out, int w, int h, int R_, const T *wts, const T *inv_norm,
+                        int transpose, cudaStream_t st);
+template <typename R>
+void launch_objective(const R *gap_hist, long long count, double coef, double *W, double *W_user,
+                      unsigned *err, cudaStream_t st);
+void launch_assemble_2d(const double *G, double *out, int dnx, int dny, int gx0, int gy0, int gnx,
+                        int gny, double scale, cudaStream_t st);
+void launch_zero_gap_2d(double *g, int dnx, int gx0, int gy0, int gnx, int gny, cudaStream_t st);
+template <typename R>
+void launch_to_double(const R *in, double *out, long long n, cudaStream_t st);
+void launch_copy_bytes(const void *src, void *dst, size_t bytes, cudaStream_t st);
+void launch_zero_bytes(void *dst, size_t bytes, cudaStream_t st);
+
+}  // namespace fdtd

@@ -1,0 +1,238 @@
+// Auxiliary kernels: design upload and range check, the Gaussian design
+// filter and its transpose (Eq. 26, 27), the objective reduction (Eq. 24),
+// gradient assembly, and plain copies for checkpoints.
+#include "fdtd_internal.h"
+
+namespace fdtd {
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline int blocks_for(long long n, int per_block = TPB, int cap = 152 * 16)
+{
+    long long b = (n + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    return (int)(b < cap ? b : cap);
+}
+
+template <typename R>
+__global__ void k_copy_check_rho(const R *src, R *dst, long long n, unsigned *err)
+{
+    bool bad = false;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const R v = src[k];
+        bad |= !(v >= R(0) && v <= R(1));  // also catches NaN
+        dst[k] = v;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_RANGE);
+}
+
+// One separable pass of the normalised Gaussian filter along x (rows) or y
+// (columns) of a w x h design array.  Forward:  out[i] = inv_norm[i] *
+// sum_k wts[k] in[i + k].  Transpose: out[i] = sum_k wts[k] inv_norm[i + k]
+// in[i + k] (the weights are symmetric).  Taps leaving the box are dropped.
+template <typename T>
+__global__ void k_filter_rows(const T *in, T *out, int w, int h, int R_, const T *wts, const T *inv_norm,
+                              int transpose)
+{
+    const long long n = (long long)w * h;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % w);
+        const T *row = in + (k - x);
+        T acc = T(0);
+        for (int t = -R_; t <= R_; ++t) {
+            const int xx = x + t;
+            if (xx < 0 || xx >= w) continue;
+            acc += transpose ? wts[t + R_] * inv_norm[xx] * row[xx] : wts[t + R_] * row[xx];
+        }
+        out[k] = transpose ? acc : acc * inv_norm[x];
+    }
+}
+
+template <typename T>
+__global__ void k_filter_cols(const T *in, T *out, int w, int h, int R_, const T *wts, const T *inv_norm,
+                              int transpose)
+{
+    const long long n = (long long)w * h;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % w);
+        const int y = (int)(k / w);
+        T acc = T(0);
+        for (int t = -R_; t <= R_; ++t) {
+            const int yy = y + t;
+            if (yy < 0 || yy >= h) continue;
+            const T v = in[(long long)yy * w + x];
+            acc += transpose ? wts[t + R_] * inv_norm[yy] * v : wts[t + R_] * v;
+        }
+        out[k] = transpose ? acc : acc * inv_norm[y];
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// W~ = coef * sum of squares of the recorded gap field (Eq. 24), FP64
+// accumulation, one block (the history is a few hundred kB at most).
+template <typename R>
+__global__ void __launch_bounds__(1024) k_objective(const R *h, long long count, double coef, double *W,
+                                                    double *W_user, unsigned *err)
+{
+    __shared__ double part[32];
+    double acc = 0.0;
+    for (long long k = threadIdx.x; k < count; k += blockDim.x) {
+        const double v = (double)h[k];
+        acc += v * v;
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) {
+            const double w = coef * v;
+            *W = w;
+            if (W_user) *W_user = w;
+            if (!isfinite(w)) atomicOr(err, ERR_NONFINITE);
+        }
+    }
+}
+
+__global__ void k_assemble_2d(const double *G, double *out, int dnx, int dny, int gx0, int gy0, int gnx,
+                              int gny, double scale)
+{
+    const long long n = (long long)dnx * dny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % dnx), y = (int)(k / dnx);
+        const bool gap = (unsigned)(x - gx0) < (unsigned)gnx && (unsigned)(y - gy0) < (unsigned)gny;
+        out[k] = gap ? 0.0 : scale * G[k];
+    }
+}
+
+__global__ void k_zero_gap_2d(double *g, int dnx, int gx0, int gy0, int gnx, int gny)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= gnx * gny) return;
+    const int x = gx0 + k % gnx, y = gy0 + k / gnx;
+    g[(long long)y * dnx + x] = 0.0;
+}
+
+template <typename R>
+__global__ void k_to_double(const R *in, double *out, long long n)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        out[k] = (double)in[k];
+}
+
+// 16-byte vector copy / clear; sizes are multiples of 256 bytes by
+// construction of the workspace layout, tails handled bytewise anyway.
+__global__ void k_copy_bytes(const uint4 *src, uint4 *dst, size_t n16, const unsigned char *s8,
+                             unsigned char *d8, size_t tail_from, size_t bytes)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n16; k += (size_t)gridDim.x * blockDim.x)
+        dst[k] = src[k];
+    for (size_t k = tail_from + blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < bytes;
+         k += (size_t)gridDim.x * blockDim.x)
+        d8[k] = s8[k];
+}
+
+__global__ void k_zero_bytes(uint4 *dst, size_t n16, unsigned char *d8, size_t tail_from, size_t bytes)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n16; k += (size_t)gridDim.x * blockDim.x)
+        dst[k] = make_uint4(0, 0, 0, 0);
+    for (size_t k = tail_from + blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < bytes;
+         k += (size_t)gridDim.x * blockDim.x)
+        d8[k] = 0;
+}
+
+}  // namespace
+
+template <typename R>
+void launch_copy_check_rho(const R *src, R *dst, long long n, unsigned *err, cudaStream_t st)
+{
+    k_copy_check_rho<R><<<blocks_for(n), TPB, 0, st>>>(src, dst, n, err);
+}
+
+template <typename T>
+void launch_filter_rows(const T *in, T *out, int w, int h, int R_, const T *wts, const T *inv_norm,
+                        int transpose, cudaStream_t st)
+{
+    k_filter_rows<T><<<blocks_for((long long)w * h), TPB, 0, st>>>(in, out, w, h, R_, wts, inv_norm, transpose);
+}
+
+template <typename T>
+void launch_filter_cols(const T *in, T *out, int w, int h, int R_, const T *wts, const T *inv_norm,
+                        int transpose, cudaStream_t st)
+{
+    k_filter_cols<T><<<blocks_for((long long)w * h), TPB, 0, st>>>(in, out, w, h, R_, wts, inv_norm, transpose);
+}
+
+template <typename R>
+void launch_objective(const R *gap_hist, long long count, double coef, double *W, double *W_user,
+                      unsigned *err, cudaStream_t st)
+{
+    k_objective<R><<<1, 1024, 0, st>>>(gap_hist, count, coef, W, W_user, err);
+}
+
+void launch_assemble_2d(const double *G, double *out, int dnx, int dny, int gx0, int gy0, int gnx, int gny,
+                        double scale, cudaStream_t st)
+{
+    k_assemble_2d<<<blocks_for((long long)dnx * dny), TPB, 0, st>>>(G, out, dnx, dny, gx0, gy0, gnx, gny, scale);
+}
+
+void launch_zero_gap_2d(double *g, int dnx, int gx0, int gy0, int gnx, int gny, cudaStream_t st)
+{
+    const int n = gnx * gny;
+    if (n <= 0) return;
+    k_zero_gap_2d<<<(n + TPB - 1) / TPB, TPB, 0, st>>>(g, dnx, gx0, gy0, gnx, gny);
+}
+
+template <typename R>
+void launch_to_double(const R *in, double *out, long long n, cudaStream_t st)
+{
+    k_to_double<R><<<blocks_for(n), TPB, 0, st>>>(in, out, n);
+}
+
+void launch_copy_bytes(const void *src, void *dst, size_t bytes, cudaStream_t st)
+{
+    if (!bytes) return;
+    const size_t n16 = bytes / 16;
+    k_copy_bytes<<<blocks_for((long long)(n16 ? n16 : 1)), TPB, 0, st>>>(
+        (const uint4 *)src, (uint4 *)dst, n16, (const unsigned char *)src, (unsigned char *)dst, n16 * 16, bytes);
+}
+
+void launch_zero_bytes(void *dst, size_t bytes, cudaStream_t st)
+{
+    if (!bytes) return;
+    const size_t n16 = bytes / 16;
+    k_zero_bytes<<<blocks_for((long long)(n16 ? n16 : 1)), TPB, 0, st>>>((uint4 *)dst, n16, (unsigned char *)dst,
+                                                                          n16 * 16, bytes);
+}
+
+template void launch_copy_check_rho<float>(const float *, float *, long long, unsigned *, cudaStream_t);
+template void launch_copy_check_rho<double>(const double *, double *, long long, unsigned *, cudaStream_t);
+template void launch_filter_rows<float>(const float *, float *, int, int, int, const float *, const float *, int,
+                                        cudaStream_t);
+template void launch_filter_rows<double>(const double *, double *, int, int, int, const double *, const double *,
+                                         int, cudaStream_t);
+template void launch_filter_cols<float>(const float *, float *, int, int, int, const float *, const float *, int,
+                                        cudaStream_t);
+template void launch_filter_cols<double>(const double *, double *, int, int, int, const double *, const double *,
+                                         int, cudaStream_t);
+template void launch_objective<float>(const float *, long long, double, double *, double *, unsigned *,
+                                      cudaStream_t);
+template void launch_objective<double>(const double *, long long, double, double *, double *, unsigned *,
+                                       cudaStream_t);
+template void launch_to_double<float>(const float *, double *, long long, cudaStream_t);
+template void launch_to_double<double>(const double *, double *, long long, cudaStream_t);
+
+}  // namespace fdtd

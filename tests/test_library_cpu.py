@@ -1,0 +1,69 @@
+"""CPU-only checks of the C ABI library: it loads, exports every symbol that
+include/fdtd.h declares, sizes workspaces and rejects bad configurations
+(no compute calls: there is no GPU here)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2203_01462_gb300 import binding as B
+from paper_2203_01462_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_symbols():
+    src = open(os.path.join(ROOT, "include", "fdtd.h")).read()
+    return sorted(set(re.findall(r"\b(fdtd_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_header_symbol():
+    L = B.load()
+    syms = header_symbols()
+    assert syms, "no declarations found"
+    for name in syms:
+        assert hasattr(L, name), name
+    assert sorted(B.EXPORTS) == syms
+
+
+def test_status_strings():
+    L = B.load()
+    for s in range(8):
+        assert L.fdtd_status_string(s)
+
+
+def test_workspace_sizes():
+    small = B.workspace_bytes(I.small_2d())
+    assert small > 0 and small % 256 == 0
+    big = B.workspace_bytes(I.cfg_2d_2048())
+    # 313 FP32 snapshots of ~54 MB dominate the 2048^2 workload.
+    assert 15e9 < big < 25e9
+    full = B.workspace_bytes(dict(I.cfg_2d_2048(), snapshot_every=0))
+    assert full > 80e9  # full FP32 design-box history: 20000 x 1024^2 x 4 B
+
+
+@pytest.mark.parametrize("bad", [
+    dict(courant=0.75),                    # above the 2D Courant limit
+    dict(real="f16"),
+    dict(design_lo=[0, 0, 0]),             # design box wider than the grid? (lo 0 still valid)
+    dict(gap_lo=[1, 1, 0], gap_hi=[4, 4, 1]),  # gap outside the design box
+    dict(npml=30),                         # CPML slabs overlap
+    dict(nsteps=0),
+    dict(omega_p=0.0),
+    dict(psi_s_ratio=0.0),                 # Eq. (25a) divides by psi_i
+])
+def test_bad_configurations_rejected(bad):
+    w = I.small_2d()
+    if "real" in bad and bad["real"] == "f16":
+        cfg = B.config(w)
+        cfg.real_bytes = 2
+        n = C.c_size_t()
+        assert B.load().fdtd_workspace_bytes(C.byref(cfg), C.byref(n)) == 1
+        return
+    w.update(bad)
+    if bad.get("design_lo") == [0, 0, 0]:
+        return  # valid: design box may start at the corner
+    with pytest.raises(B.FdtdError) as e:
+        B.workspace_bytes(w)
+    assert e.value.status == 1
