@@ -2,6 +2,7 @@
 // workspace layout, CPML / source / filter tables, and the time loops of the
 // forward run, the checkpointed recompute and the adjoint run.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -149,6 +150,7 @@ struct fdtd_ctx {
     virtual double *grad_stage() = 0;
     virtual double *W_dev() = 0;
     virtual unsigned *err_dev() = 0;
+    virtual void set_chunk(int rows) = 0;
 };
 
 namespace {
@@ -163,8 +165,9 @@ fdtd_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? FDTD_OK : FDTD_EC
 template <typename R>
 struct Ctx2D final : fdtd_ctx {
     Geo2D geo{};
-    State2D<R> F{}, A{};
-    char *stateF_base = nullptr, *stateA_base = nullptr;
+    State2D<R> F[2]{}, A[2]{};  // ping-pong pairs: forward and adjoint
+    char *F_base[2] = {nullptr, nullptr}, *A_base[2] = {nullptr, nullptr};
+    int curF = 0, curA = 0;
     size_t state_bytes = 0;
     R *rho = nullptr, *rho_t = nullptr, *ftmp = nullptr, *rstage = nullptr;
     double *G = nullptr, *gtmp = nullptr, *gtmp2 = nullptr, *gstage = nullptr;
@@ -177,11 +180,13 @@ struct Ctx2D final : fdtd_ctx {
     double *fw_D = nullptr, *fnx_D = nullptr, *fny_D = nullptr;
     double *misc = nullptr;   // [0] W
     unsigned *err = nullptr;
+    int chunk = 16;  // rows per thread block of the step kernel
 
     void *rho_stage() override { return rstage; }
     double *grad_stage() override { return gstage; }
     double *W_dev() override { return misc; }
     unsigned *err_dev() override { return err; }
+    void set_chunk(int rows) override { chunk = rows; }
 
     void carve_state(Carver &cv, State2D<R> &s, char *&base)
     {
@@ -221,8 +226,8 @@ struct Ctx2D final : fdtd_ctx {
         geo.sy0 = c.src_lo[1];
         geo.sy1 = c.src_hi[1];
         const long long N = c.nsteps;
-        carve_state(cv, F, stateF_base);
-        carve_state(cv, A, stateA_base);
+        for (int b = 0; b < 2; ++b) carve_state(cv, F[b], F_base[b]);
+        for (int b = 0; b < 2; ++b) carve_state(cv, A[b], A_base[b]);
         rho = cv.take<R>(Md);
         rho_t = cv.take<R>(Md);
         ftmp = cv.take<R>(Md);
@@ -358,17 +363,18 @@ struct Ctx2D final : fdtd_ctx {
     // (n - n0) of rec_base (null: no record).
     void advance_forward(const Coef<R> &k, int n0, int count, bool gap, R *rec_base)
     {
-        cudaStream_t st = stream;
+        TB2D<R> a{};
+        a.rho_t = rho_t;
+        a.src_tab = src_tab;
+        a.gap_rec = (gap && Mg) ? gap_hist : nullptr;
+        a.Md = Md;
+        a.Mg = (int)Mg;
         for (int n = n0; n < n0 + count; ++n) {
-            Step2D<R> a{};
-            a.rho_t = rho_t;
-            a.src = src_tab + n;
-            a.gap_rec = (gap && Mg) ? gap_hist + (size_t)(n + 1) * Mg : nullptr;
+            a.n0 = n;
             a.rec = rec_base ? rec_base + (size_t)(n - n0) * Md : nullptr;
-            launch_h2d<R>(geo, F, k, px, py, st);
-            launch_e2d<R>(0, geo, F, k, px, py, a, st);
+            launches += launch_step2d<R>(0, chunk, geo, F[curF], F[curF ^ 1], k, px, py, a, stream);
+            curF ^= 1;
         }
-        launches += 2LL * count;
         cell_updates += (long long)count * ncells;
     }
 
@@ -376,17 +382,19 @@ struct Ctx2D final : fdtd_ctx {
     // forward E^m of the design box in slot (m - 1 - slot0) of rec.
     void advance_adjoint(const Coef<R> &k, int m_hi, int m_lo, int slot0)
     {
-        cudaStream_t st = stream;
+        TB2D<R> a{};
+        a.rho_t = rho_t;
+        a.gap_hist = gap_hist;
+        a.rec = rec;
+        a.G = G;
+        a.slot0 = slot0;
+        a.Md = Md;
+        a.Mg = (int)Mg;
         for (int m = m_hi; m > m_lo; --m) {
-            Step2D<R> a{};
-            a.rho_t = rho_t;
-            a.gap_src = Mg ? gap_hist + (size_t)m * Mg : nullptr;
-            a.rec = rec + (size_t)(m - 1 - slot0) * Md;
-            a.G = G;
-            launch_h2d<R>(geo, A, k, px, py, st);
-            launch_e2d<R>(1, geo, A, k, px, py, a, st);
+            a.n0 = m;
+            launches += launch_step2d<R>(1, chunk, geo, A[curA], A[curA ^ 1], k, px, py, a, stream);
+            curA ^= 1;
         }
-        launches += 2LL * (m_hi - m_lo);
         cell_updates += (long long)(m_hi - m_lo) * ncells;
     }
 
@@ -395,7 +403,8 @@ struct Ctx2D final : fdtd_ctx {
         cudaStream_t st = stream;
         const Coef<R> k = coef();
         const int N = cfg.nsteps, K = cfg.snapshot_every;
-        launch_zero_bytes(stateF_base, state_bytes, st);
+        curF = 0;
+        launch_zero_bytes(F_base[0], state_bytes, st);
         if (Mg) launch_zero_bytes(gap_hist, Mg * sizeof(R), st);
         launches += 2;
         if (K <= 0) {
@@ -403,7 +412,7 @@ struct Ctx2D final : fdtd_ctx {
         } else {
             for (int s = 0; s < nsnap; ++s) {
                 const int n0 = s * K, cnt = std::min(K, N - n0);
-                launch_copy_bytes(stateF_base, snaps + (size_t)s * state_bytes, state_bytes, st);
+                launch_copy_bytes(F_base[curF], snaps + (size_t)s * state_bytes, state_bytes, st);
                 ++launches;
                 advance_forward(k, n0, cnt, true, nullptr);
             }
@@ -419,7 +428,8 @@ struct Ctx2D final : fdtd_ctx {
         cudaStream_t st = stream;
         const Coef<R> k = coef();
         const int N = cfg.nsteps, K = cfg.snapshot_every;
-        launch_zero_bytes(stateA_base, state_bytes, st);
+        curA = 0;
+        launch_zero_bytes(A_base[0], state_bytes, st);
         launch_zero_bytes(G, Md * sizeof(double), st);
         launches += 2;
         if (K <= 0) {
@@ -427,7 +437,7 @@ struct Ctx2D final : fdtd_ctx {
         } else {
             for (int s = nsnap - 1; s >= 0; --s) {
                 const int n0 = s * K, n1 = std::min(n0 + K, N);
-                launch_copy_bytes(snaps + (size_t)s * state_bytes, stateF_base, state_bytes, st);
+                launch_copy_bytes(snaps + (size_t)s * state_bytes, F_base[curF], state_bytes, st);
                 ++launches;
                 advance_forward(k, n0, n1 - n0, false, rec);
                 advance_adjoint(k, n1, n0, n0);
@@ -524,6 +534,11 @@ fdtd_status fdtd_create(const fdtd_config *cfg, void *d_workspace, size_t bytes,
     if (!c) return FDTD_ENOMEM;
     c->stream = (cudaStream_t)stream;
     c->ws = d_workspace;
+    // Tuning knob: rows marched per thread block by the step kernels.
+    if (const char *e = getenv("FDTD_STEP_CHUNK")) {
+        const int v = atoi(e);
+        if (v >= 1 && v <= 4096) c->set_chunk(v);
+    }
     c->ws_bytes = bytes;
     Carver cv(d_workspace);
     fdtd_status s = c->carve(cv);

@@ -51,25 +51,28 @@ struct Coef {
     R half1pkJ;     // (1 + kJ) / 2
 };
 
-// Per-step arguments.
+// Arguments of the fused step kernel (kernels_2d.cu) that change per step.
 template <typename R>
-struct Step2D {
-    const R *rho_t;     // filtered density on the design box
-    const R *src;       // forward: source table entry for this step (device)
-    const R *gap_src;   // adjoint: forward gap field E^m
-    R *gap_rec;         // forward: where E^{n+1} of the gap goes (or null)
-    R *rec;             // forward: design-box E^{n+1} record (or null);
-                        // adjoint: design-box forward E^m
-    double *G;          // adjoint: sensitivity accumulator
+struct TB2D {
+    const R *rho_t;
+    const R *src_tab;    // forward: source table, indexed by step n
+    const R *gap_hist;   // adjoint: gap history, row m = E^m
+    R *gap_rec;          // forward: gap history base (row n + 1 written), or null
+    R *rec;              // forward: design-box record of E^{n+1} (or null);
+                         // adjoint: forward E^m at rec + (m - 1 - slot0) Md
+    double *G;           // adjoint: sensitivity accumulator
+    int n0;              // forward: step n; adjoint: m
+    int slot0;
+    long long Md;
+    int Mg;
 };
 
-// Launchers (kernels_2d.cu).  mode 0: forward / recompute; 1: adjoint.
+// One fused time step of the whole grid, reading state `in`, writing `out`.
+// mode 0: forward / recompute (step a.n0); 1: adjoint (forward index m = a.n0).
+// chunk: rows marched by each thread block.
 template <typename R>
-void launch_h2d(const Geo2D &g, const State2D<R> &s, const Coef<R> &c, const Pml1D<R> &px,
-                const Pml1D<R> &py, cudaStream_t st);
-template <typename R>
-void launch_e2d(int mode, const Geo2D &g, const State2D<R> &s, const Coef<R> &c, const Pml1D<R> &px,
-                const Pml1D<R> &py, const Step2D<R> &a, cudaStream_t st);
+int launch_step2d(int mode, int chunk, const Geo2D &g, const State2D<R> &in, const State2D<R> &out, const Coef<R> &c,
+                  const Pml1D<R> &px, const Pml1D<R> &py, const TB2D<R> &a, cudaStream_t st);
 
 // Auxiliary kernels (kernels_aux.cu).
 template <typename R>
