@@ -86,6 +86,9 @@ fdtd_status validate(const fdtd_config *c)
     if (c->snapshot_dtype != FDTD_SNAP_F32) return FDTD_EINVAL;
     if (c->accum_kind != FDTD_ACC_F64) return FDTD_EINVAL;
     if (c->sigma_form != FDTD_SIGMA_PAPER && c->sigma_form != FDTD_SIGMA_PEAK_NORMALISED) return FDTD_EINVAL;
+    // The step kernels index one array with 32-bit integers.
+    const long long px = (c->nx + 31) / 32 * 32;
+    if (px * (long long)c->ny >= (1LL << 31)) return FDTD_EINVAL;
     return FDTD_OK;
 }
 
@@ -150,7 +153,6 @@ struct fdtd_ctx {
     virtual double *grad_stage() = 0;
     virtual double *W_dev() = 0;
     virtual unsigned *err_dev() = 0;
-    virtual void set_chunk(int rows) = 0;
 };
 
 namespace {
@@ -169,7 +171,8 @@ struct Ctx2D final : fdtd_ctx {
     char *F_base[2] = {nullptr, nullptr}, *A_base[2] = {nullptr, nullptr};
     int curF = 0, curA = 0;
     size_t state_bytes = 0;
-    R *rho = nullptr, *rho_t = nullptr, *ftmp = nullptr, *rstage = nullptr;
+    long long Mdi = 0;  // pitched design-box elements (dny x dp)
+    R *rho = nullptr, *rhof = nullptr, *rho_t = nullptr, *ftmp = nullptr, *rstage = nullptr;
     double *G = nullptr, *gtmp = nullptr, *gtmp2 = nullptr, *gstage = nullptr;
     R *gap_hist = nullptr, *rec = nullptr, *src_tab = nullptr;
     char *snaps = nullptr;
@@ -180,13 +183,10 @@ struct Ctx2D final : fdtd_ctx {
     double *fw_D = nullptr, *fnx_D = nullptr, *fny_D = nullptr;
     double *misc = nullptr;   // [0] W
     unsigned *err = nullptr;
-    int chunk = 16;  // rows per thread block of the step kernel
-
     void *rho_stage() override { return rstage; }
     double *grad_stage() override { return gstage; }
     double *W_dev() override { return misc; }
     unsigned *err_dev() override { return err; }
-    void set_chunk(int rows) override { chunk = rows; }
 
     void carve_state(Carver &cv, State2D<R> &s, char *&base)
     {
@@ -196,7 +196,7 @@ struct Ctx2D final : fdtd_ctx {
         s.Ez = cv.take<R>(grid);
         s.Hx = cv.take<R>(grid);
         s.Hy = cv.take<R>(grid);
-        s.J = cv.take<R>((size_t)Md);
+        s.J = cv.take<R>((size_t)Mdi);
         s.pezx = cv.take<R>((size_t)geo.ny * 2 * np);
         s.phyx = cv.take<R>((size_t)geo.ny * 2 * np);
         s.pezy = cv.take<R>((size_t)2 * np * geo.px);
@@ -217,6 +217,9 @@ struct Ctx2D final : fdtd_ctx {
         geo.dy0 = c.design_lo[1];
         geo.dnx = c.design_hi[0] - c.design_lo[0];
         geo.dny = c.design_hi[1] - c.design_lo[1];
+        geo.dxa = geo.dx0 & ~3;
+        geo.dp = (geo.dx0 + geo.dnx - geo.dxa + 3) & ~3;
+        Mdi = (long long)geo.dny * geo.dp;
         geo.gx0 = c.gap_lo[0];
         geo.gy0 = c.gap_lo[1];
         geo.gnx = c.gap_hi[0] - c.gap_lo[0];
@@ -229,16 +232,17 @@ struct Ctx2D final : fdtd_ctx {
         for (int b = 0; b < 2; ++b) carve_state(cv, F[b], F_base[b]);
         for (int b = 0; b < 2; ++b) carve_state(cv, A[b], A_base[b]);
         rho = cv.take<R>(Md);
-        rho_t = cv.take<R>(Md);
+        rhof = cv.take<R>(Md);
+        rho_t = cv.take<R>(Mdi);
         ftmp = cv.take<R>(Md);
         rstage = cv.take<R>(Md);
-        G = cv.take<double>(Md);
+        G = cv.take<double>(Mdi);
         gtmp = cv.take<double>(Md);
         gtmp2 = cv.take<double>(Md);
         gstage = cv.take<double>(Md);
         gap_hist = cv.take<R>((size_t)(N + 1) * (Mg ? Mg : 1));
         const long long K = c.snapshot_every;
-        rec = cv.take<R>((size_t)(K > 0 ? std::min<long long>(K, N) : N) * Md);
+        rec = cv.take<R>((size_t)(K > 0 ? std::min<long long>(K, N) : N) * Mdi);
         nsnap = K > 0 ? (int)((N + K - 1) / K) : 0;
         snaps = cv.take<char>((size_t)nsnap * state_bytes);
         src_tab = cv.take<R>(N);
@@ -340,10 +344,11 @@ struct Ctx2D final : fdtd_ctx {
         const int FR = cfg.filter_radius;
         if (FR > 0) {
             launch_filter_rows<R>(rho, ftmp, geo.dnx, geo.dny, FR, fw_R, fnx_R, 0, st);
-            launch_filter_cols<R>(ftmp, rho_t, geo.dnx, geo.dny, FR, fw_R, fny_R, 0, st);
-            launches += 2;
+            launch_filter_cols<R>(ftmp, rhof, geo.dnx, geo.dny, FR, fw_R, fny_R, 0, st);
+            launch_pitch2d<R>(rhof, rho_t, geo.dnx, geo.dny, geo.dx0 - geo.dxa, geo.dp, st);
+            launches += 3;
         } else {
-            launch_copy_bytes(rho, rho_t, Md * sizeof(R), st);
+            launch_pitch2d<R>(rho, rho_t, geo.dnx, geo.dny, geo.dx0 - geo.dxa, geo.dp, st);
             ++launches;
         }
         FDTD_TRY(check_launch());
@@ -363,16 +368,13 @@ struct Ctx2D final : fdtd_ctx {
     // (n - n0) of rec_base (null: no record).
     void advance_forward(const Coef<R> &k, int n0, int count, bool gap, R *rec_base)
     {
-        TB2D<R> a{};
+        Step2D<R> a{};
         a.rho_t = rho_t;
-        a.src_tab = src_tab;
-        a.gap_rec = (gap && Mg) ? gap_hist : nullptr;
-        a.Md = Md;
-        a.Mg = (int)Mg;
         for (int n = n0; n < n0 + count; ++n) {
-            a.n0 = n;
-            a.rec = rec_base ? rec_base + (size_t)(n - n0) * Md : nullptr;
-            launches += launch_step2d<R>(0, chunk, geo, F[curF], F[curF ^ 1], k, px, py, a, stream);
+            a.src = src_tab + n;
+            a.gap_rec = (gap && Mg) ? gap_hist + (size_t)(n + 1) * Mg : nullptr;
+            a.rec = rec_base ? rec_base + (size_t)(n - n0) * Mdi : nullptr;
+            launches += launch_step2d<R>(0, geo, F[curF], F[curF ^ 1], k, px, py, a, stream);
             curF ^= 1;
         }
         cell_updates += (long long)count * ncells;
@@ -382,17 +384,13 @@ struct Ctx2D final : fdtd_ctx {
     // forward E^m of the design box in slot (m - 1 - slot0) of rec.
     void advance_adjoint(const Coef<R> &k, int m_hi, int m_lo, int slot0)
     {
-        TB2D<R> a{};
+        Step2D<R> a{};
         a.rho_t = rho_t;
-        a.gap_hist = gap_hist;
-        a.rec = rec;
         a.G = G;
-        a.slot0 = slot0;
-        a.Md = Md;
-        a.Mg = (int)Mg;
         for (int m = m_hi; m > m_lo; --m) {
-            a.n0 = m;
-            launches += launch_step2d<R>(1, chunk, geo, A[curA], A[curA ^ 1], k, px, py, a, stream);
+            a.gap_src = Mg ? gap_hist + (size_t)m * Mg : nullptr;
+            a.rec = rec + (size_t)(m - 1 - slot0) * Mdi;
+            launches += launch_step2d<R>(1, geo, A[curA], A[curA ^ 1], k, px, py, a, stream);
             curA ^= 1;
         }
         cell_updates += (long long)(m_hi - m_lo) * ncells;
@@ -430,7 +428,7 @@ struct Ctx2D final : fdtd_ctx {
         const int N = cfg.nsteps, K = cfg.snapshot_every;
         curA = 0;
         launch_zero_bytes(A_base[0], state_bytes, st);
-        launch_zero_bytes(G, Md * sizeof(double), st);
+        launch_zero_bytes(G, Mdi * sizeof(double), st);
         launches += 2;
         if (K <= 0) {
             advance_adjoint(k, N, 0, 0);
@@ -452,15 +450,15 @@ struct Ctx2D final : fdtd_ctx {
         const double scale = dt * pow(cfg.dx, cfg.ndim);
         const int FR = cfg.filter_radius;
         if (FR > 0) {
-            launch_assemble_2d(G, gtmp, geo.dnx, geo.dny, geo.gx0 - geo.dx0, geo.gy0 - geo.dy0, geo.gnx,
-                               geo.gny, scale, st);
+            launch_assemble_2d(G, gtmp, geo.dnx, geo.dny, geo.dx0 - geo.dxa, geo.dp, geo.gx0 - geo.dx0,
+                               geo.gy0 - geo.dy0, geo.gnx, geo.gny, scale, st);
             launch_filter_rows<double>(gtmp, gtmp2, geo.dnx, geo.dny, FR, fw_D, fnx_D, 1, st);
             launch_filter_cols<double>(gtmp2, d_grad, geo.dnx, geo.dny, FR, fw_D, fny_D, 1, st);
             launch_zero_gap_2d(d_grad, geo.dnx, geo.gx0 - geo.dx0, geo.gy0 - geo.dy0, geo.gnx, geo.gny, st);
             launches += 4;
         } else {
-            launch_assemble_2d(G, d_grad, geo.dnx, geo.dny, geo.gx0 - geo.dx0, geo.gy0 - geo.dy0, geo.gnx,
-                               geo.gny, scale, st);
+            launch_assemble_2d(G, d_grad, geo.dnx, geo.dny, geo.dx0 - geo.dxa, geo.dp, geo.gx0 - geo.dx0,
+                               geo.gy0 - geo.dy0, geo.gnx, geo.gny, scale, st);
             ++launches;
         }
         return check_launch();
@@ -534,11 +532,7 @@ fdtd_status fdtd_create(const fdtd_config *cfg, void *d_workspace, size_t bytes,
     if (!c) return FDTD_ENOMEM;
     c->stream = (cudaStream_t)stream;
     c->ws = d_workspace;
-    // Tuning knob: rows marched per thread block by the step kernels.
-    if (const char *e = getenv("FDTD_STEP_CHUNK")) {
-        const int v = atoi(e);
-        if (v >= 1 && v <= 4096) c->set_chunk(v);
-    }
+
     c->ws_bytes = bytes;
     Carver cv(d_workspace);
     fdtd_status s = c->carve(cv);

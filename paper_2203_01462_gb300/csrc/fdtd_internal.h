@@ -16,12 +16,16 @@ enum : unsigned { ERR_RANGE = 1u, ERR_NONFINITE = 2u };
 struct Geo2D {
     int nx, ny, px, npml;
     int dx0, dy0, dnx, dny;   // design box origin and size (nodes)
+    int dxa, dp;              // pitched design arrays: column origin (dx0
+                              // rounded down to a multiple of 4) and row
+                              // pitch (a multiple of 4); node (i, j) of the
+                              // box is element (j - dy0) * dp + (i - dxa)
     int gx0, gy0, gnx, gny;   // gap box
     int sx0, sx1, sy0, sy1;   // source box
 };
 
 // Field arrays of one 2D solver state.  J covers the design box only
-// (compact, dnx x dny).  CPML convolution terms live in border slabs:
+// (pitched layout, see Geo2D).  CPML convolution terms live in border slabs:
 // x-slabs [ny][2 npml] for Ez and Hy, y-slabs [2 npml][px] for Ez and Hx.
 template <typename R>
 struct State2D {
@@ -51,28 +55,24 @@ struct Coef {
     R half1pkJ;     // (1 + kJ) / 2
 };
 
-// Arguments of the fused step kernel (kernels_2d.cu) that change per step.
+// Per-step arguments of the fused step kernel (kernels_2d.cu); the host
+// resolves every per-step offset into a base pointer.
 template <typename R>
-struct TB2D {
-    const R *rho_t;
-    const R *src_tab;    // forward: source table, indexed by step n
-    const R *gap_hist;   // adjoint: gap history, row m = E^m
-    R *gap_rec;          // forward: gap history base (row n + 1 written), or null
-    R *rec;              // forward: design-box record of E^{n+1} (or null);
-                         // adjoint: forward E^m at rec + (m - 1 - slot0) Md
+struct Step2D {
+    const R *rho_t;      // filtered density on the design box
+    const R *src;        // forward: source table entry of this step
+    const R *gap_src;    // adjoint: forward gap field E^m (row m of the history)
+    R *gap_rec;          // forward: gap-history row receiving E^{n+1} (or null)
+    R *rec;              // forward: design-box slot receiving E^{n+1} (or null);
+                         // adjoint: design-box forward E^m
     double *G;           // adjoint: sensitivity accumulator
-    int n0;              // forward: step n; adjoint: m
-    int slot0;
-    long long Md;
-    int Mg;
 };
 
 // One fused time step of the whole grid, reading state `in`, writing `out`.
-// mode 0: forward / recompute (step a.n0); 1: adjoint (forward index m = a.n0).
-// chunk: rows marched by each thread block.
+// mode 0: forward / recompute; 1: adjoint.
 template <typename R>
-int launch_step2d(int mode, int chunk, const Geo2D &g, const State2D<R> &in, const State2D<R> &out, const Coef<R> &c,
-                  const Pml1D<R> &px, const Pml1D<R> &py, const TB2D<R> &a, cudaStream_t st);
+int launch_step2d(int mode, const Geo2D &g, const State2D<R> &in, const State2D<R> &out, const Coef<R> &c,
+                  const Pml1D<R> &px, const Pml1D<R> &py, const Step2D<R> &a, cudaStream_t st);
 
 // Auxiliary kernels (kernels_aux.cu).
 template <typename R>
@@ -86,8 +86,13 @@ void launch_filter_cols(const T *in, T *out, int w, int h, int R_, const T *wts,
 template <typename R>
 void launch_objective(const R *gap_hist, long long count, double coef, double *W, double *W_user,
                       unsigned *err, cudaStream_t st);
-void launch_assemble_2d(const double *G, double *out, int dnx, int dny, int gx0, int gy0, int gnx,
-                        int gny, double scale, cudaStream_t st);
+// Compact (dnx x dny) <-> pitched (dny rows of dp, box at column off).
+template <typename T>
+void launch_pitch2d(const T *compact, T *pitched, int dnx, int dny, int off, int dp, cudaStream_t st);
+// out (compact) = scale * G (pitched), zero on gap nodes (gap box relative
+// to the design box).
+void launch_assemble_2d(const double *G, double *out, int dnx, int dny, int off, int dp, int gx0, int gy0,
+                        int gnx, int gny, double scale, cudaStream_t st);
 void launch_zero_gap_2d(double *g, int dnx, int gx0, int gy0, int gnx, int gny, cudaStream_t st);
 template <typename R>
 void launch_to_double(const R *in, double *out, long long n, cudaStream_t st);

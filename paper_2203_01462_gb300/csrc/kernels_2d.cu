@@ -4,273 +4,305 @@
 // step of mu0 dH/dt = -curl E and the E half step of Eq. (10a,b) (J and
 // sigma E averaged over the step, scaled units, see Coef).  State is read
 // from one buffer of a ping-pong pair and written to the other, so every
-// word crosses HBM once per step (24 B per vacuum node).
+// state word crosses HBM once per step (24 B per vacuum node).
 //
-// Work layout: each thread owns one grid column and marches up a chunk of
-// rows.  Values along y stay in registers (Ez of the next row, the new Hx of
-// the previous row); x neighbours come from the adjacent lanes by warp
-// shuffles.  A warp covers 32 columns but writes 31: lane 0 is a halo lane
-// that recomputes the new Hy of the column left of the warp's first output
-// column, and lane 31 loads Ez of the column to its right.  All region
-// logic (CPML slabs, design box, gap, source row) is per column (fixed for
-// the thread) or per row (uniform across the warp).
+// Each thread owns four adjacent nodes of one row (16-byte vector loads and
+// stores; rows are padded to 32 nodes), 32 x 8 threads per block, i.e. a
+// 128 x 8 node tile.  A thread computes the new Hx and Hy of its nodes and,
+// in registers, the new Hy left of its first node and the new Hx below its
+// nodes, which its E updates need: 6 vector and 3 scalar loads per 4 nodes,
+// neighbour rows served by L1, no exchange between threads and no barrier.
+//
+// Paths are chosen per block (uniform): blocks whose nodes and neighbours
+// are clear of walls and CPML slabs run vector code, with per-node design /
+// gap / source logic only when the tile touches those boxes; border blocks
+// run a scalar path with CPML.  The design-box arrays (J, rho~, records, G) use the library's
+// pitched layout: column origin dxa (a multiple of 4) and row pitch dp (a
+// multiple of 4), so that they load as vectors too.  Indices are 32-bit.
 #include "fdtd_internal.h"
 
 namespace fdtd {
 
 namespace {
 
-constexpr int WARPS = 4;
-constexpr int NTH = 32 * WARPS;
-constexpr int OUT_PER_WARP = 31;
-constexpr int U = 4;  // rows loaded ahead per group
+constexpr int BX = 32, BY = 8, VX = 4;
+constexpr int TILE_X = BX * VX;
 
 __device__ __forceinline__ bool in_range(int v, int lo, int n) { return (unsigned)(v - lo) < (unsigned)n; }
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+
+__device__ __forceinline__ void ld4(const float *__restrict__ p, float (&o)[4])
+{
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double *__restrict__ p, double (&o)[4])
+{
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void st4(float *p, const float (&o)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ void st4(double *p, const double (&o)[4])
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(o[0], o[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(o[2], o[3]);
+}
+
+// Drude node of Eq. (10a,b): new E and J from old E, J, the scaled curl and
+// the source; term = the Eq. (25a-c) bracket folded through Eq. (27).
+template <typename R, int MODE>
+__device__ __forceinline__ void drude(const Coef<R> &c, R rt, R ez, R jo, R curl, R src, R &en, R &jn, R &term)
+{
+    const R eps = c.eps_s + rt * c.d_eps;
+    const R psi = c.psi_s + rt * (c.psi - c.psi_s);
+    const R sig = c.sig_max * rt * (R(1) - rt);
+    const R bJ = R(0.5) * psi * c.inv1g;
+    const R hs = R(0.5) * (sig + bJ);
+    const R cb = rcp(eps + hs);
+    const R ca = (eps - hs) * cb;
+    en = ca * ez + cb * (curl - c.half1pkJ * jo - src);
+    jn = c.kJ * jo + bJ * (en + ez);
+    if (MODE == 1)
+        term = -c.d_eps * (en - ez) - c.sig_max * (R(1) - R(2) * rt) * R(0.5) * (en + ez) -
+               (c.psi - c.psi_s) * rcp(psi) * R(0.5) * (jn + jo);
+}
+
+// Scalar E update of one node (border blocks): design, gap and source
+// logic, records and sensitivity.
+template <typename R, int MODE>
+__device__ __forceinline__ R e_update(const Geo2D &g, const State2D<R> &in, const State2D<R> &out, const Coef<R> &c,
+                                      const Step2D<R> &a, int i, int j, R ez, R curl)
+{
+    const bool gap = in_range(i, g.gx0, g.gnx) && in_range(j, g.gy0, g.gny);
+    const int gidx = (j - g.gy0) * g.gnx + (i - g.gx0);
+    R src = R(0);
+    if (MODE == 0) {
+        if (in_range(i, g.sx0, g.sx1 - g.sx0) && in_range(j, g.sy0, g.sy1 - g.sy0)) src = *a.src;
+    } else if (gap) {
+        src = -c.eps_g * a.gap_src[gidx];
+    }
+    const bool des = in_range(i, g.dx0, g.dnx) && in_range(j, g.dy0, g.dny);
+    const int d = (j - g.dy0) * g.dp + (i - g.dxa);
+    R en;
+    if (des && !gap) {
+        R jn, term = R(0);
+        drude<R, MODE>(c, a.rho_t[d], ez, in.J[d], curl, src, en, jn, term);
+        out.J[d] = jn;
+        if (MODE == 0) {
+            if (a.rec) a.rec[d] = en;
+        } else {
+            a.G[d] += (double)a.rec[d] * (double)term;
+        }
+    } else {
+        en = ez + (curl - src) * (gap ? c.inv_eps_g : c.inv_eps_s);
+        if (MODE == 0 && des && a.rec) a.rec[d] = en;
+    }
+    if (MODE == 0 && gap && a.gap_rec) a.gap_rec[gidx] = en;
+    return en;
+}
+
+// Scalar step of the four nodes i0 .. i0+3 of row j in a border block.
+template <typename R, int MODE>
+__device__ __forceinline__ void border_step(const Geo2D &g, const State2D<R> &in, const State2D<R> &out,
+                                         const Coef<R> &c, const Pml1D<R> &px, const Pml1D<R> &py,
+                                         const Step2D<R> &a, int i0, int j)
+{
+    const int nx = g.nx, ny = g.ny, np = g.npml, P = g.px;
+    const R S = c.S;
+    if (j >= ny) return;
+    // New Hx at (ii, jj + 1/2); psi written only for the own node.
+    auto hx_new = [&](int ii, int jj, bool own) -> R {
+        if ((unsigned)ii >= (unsigned)nx || (unsigned)jj >= (unsigned)ny) return R(0);
+        const int qq = jj * P + ii;
+        const R h = in.Hx[qq];
+        if (jj + 1 >= ny) return h;
+        const R dd = in.Ez[qq + P] - in.Ez[qq];
+        R t = dd;
+        if (np > 0 && (jj < np || jj >= ny - 1 - np)) {
+            const int qs = (jj < np ? jj : np + jj - (ny - 1 - np)) * P + ii;
+            const R p = py.bH[jj] * in.phxy[qs] + py.cH[jj] * dd;
+            if (own) out.phxy[qs] = p;
+            t = dd * py.kiH[jj] + p;
+        }
+        return h - S * t;
+    };
+    // New Hy at (ii + 1/2, jj).
+    auto hy_new = [&](int ii, int jj, bool own) -> R {
+        if ((unsigned)ii >= (unsigned)nx || (unsigned)jj >= (unsigned)ny) return R(0);
+        const int qq = jj * P + ii;
+        const R h = in.Hy[qq];
+        if (ii + 1 >= nx) return h;
+        const R dd = in.Ez[qq + 1] - in.Ez[qq];
+        R t = dd;
+        if (np > 0 && (ii < np || ii >= nx - 1 - np)) {
+            const int qs = jj * 2 * np + (ii < np ? ii : np + ii - (nx - 1 - np));
+            const R p = px.bH[ii] * in.phyx[qs] + px.cH[ii] * dd;
+            if (own) out.phyx[qs] = p;
+            t = dd * px.kiH[ii] + p;
+        }
+        return h + S * t;
+    };
+    for (int k = 0; k < VX; ++k) {
+        const int i = i0 + k;
+        if (i >= nx) return;
+        const int q = j * P + i;
+        const R ez = in.Ez[q];
+        const R hxn = hx_new(i, j, true);
+        const R hyn = hy_new(i, j, true);
+        R en = ez;
+        if (i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2) {
+            const R dHy = hyn - hy_new(i - 1, j, false);
+            const R dHx = hxn - hx_new(i, j - 1, false);
+            R cx = dHy, cy = dHx;
+            if (np > 0 && (i < np || i >= nx - np)) {
+                const int qs = j * 2 * np + (i < np ? i : i - (nx - 2 * np));
+                const R p = px.bE[i] * in.pezx[qs] + px.cE[i] * dHy;
+                out.pezx[qs] = p;
+                cx = dHy * px.kiE[i] + p;
+            }
+            if (np > 0 && (j < np || j >= ny - np)) {
+                const int qs = (j < np ? j : j - (ny - 2 * np)) * P + i;
+                const R p = py.bE[j] * in.pezy[qs] + py.cE[j] * dHx;
+                out.pezy[qs] = p;
+                cy = dHx * py.kiE[j] + p;
+            }
+            en = e_update<R, MODE>(g, in, out, c, a, i, j, ez, S * (cx - cy));
+        }
+        out.Ez[q] = en;
+        out.Hx[q] = hxn;
+        out.Hy[q] = hyn;
+    }
+}
 
 template <typename R, int MODE>
-__global__ void __launch_bounds__(NTH, 6) k_step2d(Geo2D g, State2D<R> in, State2D<R> out, Coef<R> c, Pml1D<R> px,
-                                                 Pml1D<R> py, TB2D<R> a, int chunk)
+__global__ void __launch_bounds__(BX *BY, 5)
+    k_step2d(const __grid_constant__ Geo2D g, const __grid_constant__ State2D<R> in,
+             const __grid_constant__ State2D<R> out, const __grid_constant__ Coef<R> c,
+             const __grid_constant__ Pml1D<R> px, const __grid_constant__ Pml1D<R> py,
+             const __grid_constant__ Step2D<R> a)
 {
-    const int lane = threadIdx.x & 31;
-    const int warp = blockIdx.x * WARPS + (threadIdx.x >> 5);
-    const int i = warp * OUT_PER_WARP - 1 + lane;  // this thread's column
-    const int y0 = blockIdx.y * chunk;
-    const int y1 = min(y0 + chunk, g.ny);
-    const int nx = g.nx, ny = g.ny, np = g.npml;
-    const size_t P = (size_t)g.px;
+    const int x0 = blockIdx.x * TILE_X, y0 = blockIdx.y * BY;
+    const int i0 = x0 + threadIdx.x * VX, j = y0 + threadIdx.y;
+    const int nx = g.nx, ny = g.ny, np = g.npml, P = g.px;
+    const R S = c.S;
 
-    const bool col = (unsigned)i < (unsigned)nx;
-    const bool store = col && lane > 0;
-    const bool colE = i >= 1 && i <= nx - 2;
-    const bool hy_upd = col && i + 1 < nx;
-    const bool xpE = col && np > 0 && (i < np || i >= nx - np);
-    const bool xpH = col && np > 0 && (i < np || (i >= nx - 1 - np && i < nx - 1));
-    const int slE = i < np ? i : i - (nx - 2 * np);
-    const int slH = i < np ? i : np + i - (nx - 1 - np);
-    const bool desx = in_range(i, g.dx0, g.dnx);
-    const bool gapx = in_range(i, g.gx0, g.gnx);
-    const bool srcx = in_range(i, g.sx0, g.sx1 - g.sx0);
-    R kiEx = R(1), bEx = R(0), cEx = R(0), kiHx = R(1), bHx = R(0), cHx = R(0);
-    if (xpE) { kiEx = px.kiE[i]; bEx = px.bE[i]; cEx = px.cE[i]; }
-    if (xpH) { kiHx = px.kiH[i]; bHx = px.bH[i]; cHx = px.cH[i]; }
-    const int n = a.n0;  // forward: step n; adjoint: m
-    R src_val = R(0);
-    if (MODE == 0 && srcx) src_val = a.src_tab[n];
+    // Vector path for blocks none of whose read nodes (x0-1 .. x0+TILE_X,
+    // y0-1 .. y0+BY) is a wall or CPML node (uniform across the block).
+    const bool interior =
+        x0 - 1 >= np + 1 && x0 + TILE_X <= nx - np - 2 && y0 - 1 >= np + 1 && y0 + BY <= ny - np - 2;
 
-    const R *__restrict__ iEz = in.Ez;
-    const R *__restrict__ iHx = in.Hx;
-    const R *__restrict__ iHy = in.Hy;
-    auto ld = [&](const R *__restrict__ p, int j) -> R {
-        return (col && (unsigned)j < (unsigned)ny) ? p[(size_t)j * P + i] : R(0);
-    };
-
-    // New Hx of row j from old Hx, Ez(j), Ez(j+1) and (in a y-slab) the old
-    // CPML term psi_old; the new term goes to *psi_new.
-    auto hx_new = [&](int j, R hx, R ez, R ezn, R psi_old, R *psi_new) -> R {
-        if (j + 1 >= ny || !col) return hx;
-        const R d = ezn - ez;
-        R t = d;
-        if (np > 0 && (j < np || j >= ny - 1 - np)) {
-            const R p = py.bH[j] * psi_old + py.cH[j] * d;
-            *psi_new = p;
-            t = d * py.kiH[j] + p;
+    if (interior) {
+        const int q = j * P + i0;
+        R e[4], eN[4], eS[4], hx[4], hxS[4], hy[4];
+        ld4(in.Ez + q, e);
+        ld4(in.Ez + q + P, eN);
+        ld4(in.Ez + q - P, eS);
+        ld4(in.Hx + q, hx);
+        ld4(in.Hx + q - P, hxS);
+        ld4(in.Hy + q, hy);
+        const R ezW = in.Ez[q - 1], ezE = in.Ez[q + VX], hyW = in.Hy[q - 1];
+        R hxn[4], yn[5], curlS[4];
+        yn[0] = hyW + S * (e[0] - ezW);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            hxn[k] = hx[k] - S * (eN[k] - e[k]);
+            const R hxsn = hxS[k] - S * (e[k] - eS[k]);
+            yn[k + 1] = hy[k] + S * ((k < 3 ? e[k + 1] : ezE) - e[k]);
+            curlS[k] = -(hxn[k] - hxsn);
         }
-        return hx - c.S * t;
-    };
-    auto yslabH = [&](int j) { return np > 0 && j + 1 < ny && (j < np || j >= ny - 1 - np); };
-    auto yslabE = [&](int j) { return np > 0 && (j < np || j >= ny - np); };
-    auto slabH = [&](int j) { return j < np ? j : np + j - (ny - 1 - np); };
-    auto slabE = [&](int j) { return j < np ? j : j - (ny - 2 * np); };
-
-    // Prologue: Ez of the first row and the new Hx of the row below it.
-    R ez = ld(iEz, y0);
-    R hxp = R(0);
-    if (y0 >= 1) {
-        R dummy;
-        const R po = (col && yslabH(y0 - 1)) ? in.phxy[(size_t)slabH(y0 - 1) * P + i] : R(0);
-        hxp = hx_new(y0 - 1, ld(iHx, y0 - 1), ld(iEz, y0 - 1), ez, po, &dummy);
-    }
-
-    // Warp-uniform classification of the warp's columns: a row group takes
-    // the fast path when no column of the warp and no row of the group
-    // touches a wall, a CPML slab, the design box, the gap or the source.
-    const unsigned FULL = 0xffffffffu;
-    // Lane 0 only supplies the new Hy of its column, so it needs a plain H
-    // update there; the other lanes need a plain E update too.
-    const bool plain_col = col && (lane == 0 ? (hy_upd && !xpH) : (colE && !xpE && !xpH));
-    const bool wx_edge = !__all_sync(FULL, plain_col);
-    const bool wx_des = __any_sync(FULL, desx && lane > 0);
-    const bool wx_src = __any_sync(FULL, srcx && lane > 0);
-
-    for (int jb = y0; jb < y1; jb += U) {
-        const int je = min(jb + U, y1);
-        const bool rows_ok = jb >= 1 && je + 1 <= ny - 1 && !(np > 0 && (jb < np + 1 || je > ny - 2 - np));
-        const bool rows_des = in_range(jb, g.dy0 - U + 1, g.dny + U - 1);
-        const bool rows_src = jb < g.sy1 && je > g.sy0;
-        const bool fast = !wx_edge && rows_ok && !(wx_des && rows_des) && !(wx_src && rows_src) && je - jb == U;
-        if (fast) {
-            R ezn_[U], hx_[U], hy_[U], ezr_[U];
+        R en[4];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const size_t q = (size_t)(jb + u) * P + i;
-                ezn_[u] = iEz[q + P];
-                hx_[u] = iHx[q];
-                hy_[u] = iHy[q];
-                ezr_[u] = lane == 31 ? iEz[q + 1] : R(0);
+        for (int k = 0; k < 4; ++k) curlS[k] += yn[k + 1] - yn[k];
+
+        const bool touches = (x0 < g.dx0 + g.dnx && x0 + TILE_X > g.dx0 && y0 < g.dy0 + g.dny && y0 + BY > g.dy0) ||
+                             (MODE == 0 && x0 < g.sx1 && x0 + TILE_X > g.sx0 && y0 < g.sy1 && y0 + BY > g.sy0);
+        if (!touches) {
+            const R Se = S * c.inv_eps_s;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) en[k] = e[k] + Se * curlS[k];
+        } else {
+            // Design / gap / source tile: vector loads of the design arrays
+            // when this thread's four nodes lie in the pitched design rows.
+            const bool rdes = in_range(j, g.dy0, g.dny);
+            const bool vdes = rdes && in_range(i0, g.dxa, g.dp);
+            const int d0 = (j - g.dy0) * g.dp + (i0 - g.dxa);
+            R J4[4] = {R(0), R(0), R(0), R(0)}, rt4[4] = {R(0), R(0), R(0), R(0)}, em4[4] = {R(0), R(0), R(0), R(0)};
+            if (vdes) {
+                ld4(in.J + d0, J4);
+                ld4(a.rho_t + d0, rt4);
+                if (MODE == 1) ld4(a.rec + d0, em4);
             }
+            const bool rgap = in_range(j, g.gy0, g.gny);
+            const bool rsrc = MODE == 0 && in_range(j, g.sy0, g.sy1 - g.sy0);
+            R jn4[4];
+            double gadd[4];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const size_t q = (size_t)(jb + u) * P + i;
-                R ezr = __shfl_down_sync(FULL, ez, 1);
-                if (lane == 31) ezr = ezr_[u];
-                const R hxn = hx_[u] - c.S * (ezn_[u] - ez);
-                const R hyn = hy_[u] + c.S * (ezr - ez);
-                const R hyl = __shfl_up_sync(FULL, hyn, 1);
-                const R en = ez + c.S * c.inv_eps_s * ((hyn - hyl) - (hxn - hxp));
-                if (lane > 0) {
-                    out.Ez[q] = en;
-                    out.Hx[q] = hxn;
-                    out.Hy[q] = hyn;
-                }
-                ez = ezn_[u];
-                hxp = hxn;
-            }
-            continue;
-        }
-
-        // ---- general path: loads of the group first, CPML terms on demand
-        R ezn_[U], hx_[U], hy_[U], ezr_[U], J_[U], rt_[U], em_[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int j = jb + u;
-            ezn_[u] = ld(iEz, j + 1);
-            hx_[u] = ld(iHx, j);
-            hy_[u] = ld(iHy, j);
-            ezr_[u] = (lane == 31 && col && i + 1 < nx && j < ny) ? iEz[(size_t)j * P + i + 1] : R(0);
-            const bool des = desx && in_range(j, g.dy0, g.dny) && j < y1;
-            const size_t d = (size_t)(j - g.dy0) * g.dnx + (i - g.dx0);
-            J_[u] = des ? in.J[d] : R(0);
-            rt_[u] = des ? a.rho_t[d] : R(0);
-            em_[u] = (MODE == 1 && des) ? a.rec[(size_t)(n - 1 - a.slot0) * a.Md + d] : R(0);
-        }
-
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int j = jb + u;
-            if (j >= y1) break;
-            const size_t q = (size_t)j * P + i;
-            const R ezn = ezn_[u];
-            R ezr = __shfl_down_sync(FULL, ez, 1);
-            if (lane == 31) ezr = ezr_[u];
-
-            // ---- H half step
-            R psn = R(0);
-            const R pho = (col && yslabH(j)) ? in.phxy[(size_t)slabH(j) * P + i] : R(0);
-            const R hxn = hx_new(j, hx_[u], ez, ezn, pho, &psn);
-            if (store && yslabH(j)) out.phxy[(size_t)slabH(j) * P + i] = psn;
-            R hyn = hy_[u];
-            if (hy_upd) {
-                const R dd = ezr - ez;
-                R t = dd;
-                if (xpH) {
-                    const size_t qs = (size_t)j * 2 * np + slH;
-                    const R p = bHx * in.phyx[qs] + cHx * dd;
-                    if (store) out.phyx[qs] = p;
-                    t = dd * kiHx + p;
-                }
-                hyn = hy_[u] + c.S * t;
-            }
-            const R hyl = __shfl_up_sync(FULL, hyn, 1);
-
-            // ---- E (and J) half step
-            R en = ez;
-            const bool rowE = j >= 1 && j <= ny - 2;
-            if (colE && rowE) {
-                const R dHy = hyn - hyl;
-                const R dHx = hxn - hxp;
-                R cx = dHy, cy = dHx;
-                if (xpE) {
-                    const size_t qs = (size_t)j * 2 * np + slE;
-                    const R p = bEx * in.pezx[qs] + cEx * dHy;
-                    if (store) out.pezx[qs] = p;
-                    cx = dHy * kiEx + p;
-                }
-                if (yslabE(j)) {
-                    const size_t qs = (size_t)slabE(j) * P + i;
-                    const R p = py.bE[j] * in.pezy[qs] + py.cE[j] * dHx;
-                    if (store) out.pezy[qs] = p;
-                    cy = dHx * py.kiE[j] + p;
-                }
-                const R curl = c.S * (cx - cy);
-                const bool gap = gapx && in_range(j, g.gy0, g.gny);
+            for (int k = 0; k < 4; ++k) {
+                const int i = i0 + k;
+                const R curl = S * curlS[k];
+                const bool gap = rgap && in_range(i, g.gx0, g.gnx);
                 const int gidx = (j - g.gy0) * g.gnx + (i - g.gx0);
                 R src = R(0);
                 if (MODE == 0) {
-                    if (srcx && in_range(j, g.sy0, g.sy1 - g.sy0)) src = src_val;
+                    if (rsrc && in_range(i, g.sx0, g.sx1 - g.sx0)) src = *a.src;
                 } else if (gap) {
-                    src = -c.eps_g * a.gap_hist[(size_t)n * a.Mg + gidx];
+                    src = -c.eps_g * a.gap_src[gidx];
                 }
-                const bool des = desx && in_range(j, g.dy0, g.dny);
-                const size_t d = (size_t)(j - g.dy0) * g.dnx + (i - g.dx0);
-                if (des && !gap) {
-                    const R rt = rt_[u];
-                    const R eps = c.eps_s + rt * c.d_eps;
-                    const R psi = c.psi_s + rt * (c.psi - c.psi_s);
-                    const R sig = c.sig_max * rt * (R(1) - rt);
-                    const R bJ = R(0.5) * psi * c.inv1g;
-                    const R hs = R(0.5) * (sig + bJ);
-                    const R cb = R(1) / (eps + hs);
-                    const R ca = (eps - hs) * cb;
-                    const R jo = J_[u];
-                    en = ca * ez + cb * (curl - c.half1pkJ * jo - src);
-                    const R jn = c.kJ * jo + bJ * (en + ez);
-                    if (store) {
-                        out.J[d] = jn;
-                        if (MODE == 0) {
-                            if (a.rec) a.rec[d] = en;
-                        } else {
-                            // Eq. (25a-c) folded through the chain rule of Eq. (27).
-                            const R term = -c.d_eps * (en - ez) -
-                                           c.sig_max * (R(1) - R(2) * rt) * R(0.5) * (en + ez) -
-                                           ((c.psi - c.psi_s) / psi) * R(0.5) * (jn + jo);
-                            a.G[d] += (double)em_[u] * (double)term;
-                        }
-                    }
+                jn4[k] = J4[k];
+                gadd[k] = 0.0;
+                if (vdes && in_range(i, g.dx0, g.dnx) && !gap) {
+                    R term = R(0);
+                    drude<R, MODE>(c, rt4[k], e[k], J4[k], curl, src, en[k], jn4[k], term);
+                    if (MODE == 1) gadd[k] = (double)em4[k] * (double)term;
                 } else {
-                    en = ez + (curl - src) * (gap ? c.inv_eps_g : c.inv_eps_s);
-                    if (MODE == 0 && store && des && a.rec) a.rec[d] = en;
+                    en[k] = e[k] + (curl - src) * (gap ? c.inv_eps_g : c.inv_eps_s);
                 }
-                if (MODE == 0 && store && gap && a.gap_rec) a.gap_rec[(size_t)(n + 1) * a.Mg + gidx] = en;
+                if (MODE == 0 && gap && a.gap_rec) a.gap_rec[gidx] = en[k];
             }
-            if (store) {
-                out.Ez[q] = en;
-                out.Hx[q] = hxn;
-                out.Hy[q] = hyn;
+            if (vdes) {
+                st4(out.J + d0, jn4);
+                if (MODE == 0) {
+                    if (a.rec) st4(a.rec + d0, en);
+                } else {
+                    double G4[4];
+                    ld4(a.G + d0, G4);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) G4[k] += gadd[k];
+                    st4(a.G + d0, G4);
+                }
             }
-            ez = ezn;
-            hxp = hxn;
         }
+        st4(out.Ez + q, en);
+        st4(out.Hx + q, hxn);
+        const R hy4[4] = {yn[1], yn[2], yn[3], yn[4]};
+        st4(out.Hy + q, hy4);
+        return;
     }
+
+    border_step<R, MODE>(g, in, out, c, px, py, a, i0, j);
 }
 
 }  // namespace
 
 template <typename R>
-int launch_step2d(int mode, int chunk, const Geo2D &g, const State2D<R> &in, const State2D<R> &out, const Coef<R> &c,
-                  const Pml1D<R> &px, const Pml1D<R> &py, const TB2D<R> &a, cudaStream_t st)
+int launch_step2d(int mode, const Geo2D &g, const State2D<R> &in, const State2D<R> &out, const Coef<R> &c,
+                  const Pml1D<R> &px, const Pml1D<R> &py, const Step2D<R> &a, cudaStream_t st)
 {
-    const int warps = (g.nx + 1 + OUT_PER_WARP - 1) / OUT_PER_WARP;
-    dim3 grid((warps + WARPS - 1) / WARPS, (g.ny + chunk - 1) / chunk);
-    if (mode == 0) k_step2d<R, 0><<<grid, NTH, 0, st>>>(g, in, out, c, px, py, a, chunk);
-    else k_step2d<R, 1><<<grid, NTH, 0, st>>>(g, in, out, c, px, py, a, chunk);
+    dim3 grid((g.nx + TILE_X - 1) / TILE_X, (g.ny + BY - 1) / BY), block(BX, BY);
+    if (mode == 0) k_step2d<R, 0><<<grid, block, 0, st>>>(g, in, out, c, px, py, a);
+    else k_step2d<R, 1><<<grid, block, 0, st>>>(g, in, out, c, px, py, a);
     return 1;
 }
 
-template int launch_step2d<float>(int, int, const Geo2D &, const State2D<float> &, const State2D<float> &,
+template int launch_step2d<float>(int, const Geo2D &, const State2D<float> &, const State2D<float> &,
                                   const Coef<float> &, const Pml1D<float> &, const Pml1D<float> &,
-                                  const TB2D<float> &, cudaStream_t);
-template int launch_step2d<double>(int, int, const Geo2D &, const State2D<double> &, const State2D<double> &,
+                                  const Step2D<float> &, cudaStream_t);
+template int launch_step2d<double>(int, const Geo2D &, const State2D<double> &, const State2D<double> &,
                                    const Coef<double> &, const Pml1D<double> &, const Pml1D<double> &,
-                                   const TB2D<double> &, cudaStream_t);
+                                   const Step2D<double> &, cudaStream_t);
 
 }  // namespace fdtd

@@ -105,15 +105,27 @@ __global__ void __launch_bounds__(1024) k_objective(const R *h, long long count,
     }
 }
 
-__global__ void k_assemble_2d(const double *G, double *out, int dnx, int dny, int gx0, int gy0, int gnx,
-                              int gny, double scale)
+__global__ void k_assemble_2d(const double *G, double *out, int dnx, int dny, int off, int dp, int gx0, int gy0,
+                              int gnx, int gny, double scale)
 {
     const long long n = (long long)dnx * dny;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(k % dnx), y = (int)(k / dnx);
         const bool gap = (unsigned)(x - gx0) < (unsigned)gnx && (unsigned)(y - gy0) < (unsigned)gny;
-        out[k] = gap ? 0.0 : scale * G[k];
+        out[k] = gap ? 0.0 : scale * G[(long long)y * dp + off + x];
+    }
+}
+
+template <typename T>
+__global__ void k_pitch2d(const T *compact, T *pitched, int dnx, int dny, int off, int dp)
+{
+    const long long n = (long long)dp * dny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int xp = (int)(k % dp), y = (int)(k / dp);
+        const int x = xp - off;
+        pitched[k] = (x >= 0 && x < dnx) ? compact[(long long)y * dnx + x] : T(0);
     }
 }
 
@@ -183,10 +195,17 @@ void launch_objective(const R *gap_hist, long long count, double coef, double *W
     k_objective<R><<<1, 1024, 0, st>>>(gap_hist, count, coef, W, W_user, err);
 }
 
-void launch_assemble_2d(const double *G, double *out, int dnx, int dny, int gx0, int gy0, int gnx, int gny,
-                        double scale, cudaStream_t st)
+void launch_assemble_2d(const double *G, double *out, int dnx, int dny, int off, int dp, int gx0, int gy0,
+                        int gnx, int gny, double scale, cudaStream_t st)
 {
-    k_assemble_2d<<<blocks_for((long long)dnx * dny), TPB, 0, st>>>(G, out, dnx, dny, gx0, gy0, gnx, gny, scale);
+    k_assemble_2d<<<blocks_for((long long)dnx * dny), TPB, 0, st>>>(G, out, dnx, dny, off, dp, gx0, gy0, gnx, gny,
+                                                                   scale);
+}
+
+template <typename T>
+void launch_pitch2d(const T *compact, T *pitched, int dnx, int dny, int off, int dp, cudaStream_t st)
+{
+    k_pitch2d<T><<<blocks_for((long long)dp * dny), TPB, 0, st>>>(compact, pitched, dnx, dny, off, dp);
 }
 
 void launch_zero_gap_2d(double *g, int dnx, int gx0, int gy0, int gnx, int gny, cudaStream_t st)
@@ -232,6 +251,8 @@ template void launch_objective<float>(const float *, long long, double, double *
                                       cudaStream_t);
 template void launch_objective<double>(const double *, long long, double, double *, double *, unsigned *,
                                        cudaStream_t);
+template void launch_pitch2d<float>(const float *, float *, int, int, int, int, cudaStream_t);
+template void launch_pitch2d<double>(const double *, double *, int, int, int, int, cudaStream_t);
 template void launch_to_double<float>(const float *, double *, long long, cudaStream_t);
 template void launch_to_double<double>(const double *, double *, long long, cudaStream_t);
 
