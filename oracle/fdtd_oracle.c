@@ -79,6 +79,7 @@ typedef struct or_config {
     int sigma_form;        /* 0: rho(1-rho) smax (Eq. 5c); 1: 4 rho(1-rho) smax */
     double sub_eps;        /* 3D: background eps for cells with k < sub_hi      */
     int sub_hi;
+    int src_comp;          /* 3D: component driven by the source (0 x, 1 y, 2 z) */
 } or_config;
 
 static int g_threads = 1;
@@ -544,6 +545,358 @@ static int gradient2(const or_config *c, const double *rho, double sigma_max, do
     return 0;
 }
 
+/* ================================================================ 3D */
+
+/* Full Yee grid of nx x ny x nz nodes: Ex(i,j,k) at (i+1/2, j, k), Ey at
+ * (i, j+1/2, k), Ez at (i, j, k+1/2), Hx at (i, j+1/2, k+1/2), Hy at
+ * (i+1/2, j, k+1/2), Hz at (i+1/2, j+1/2, k).  Tangential E vanishes on the
+ * outer faces (PEC walls behind the CPML).  Every component of index
+ * (i, j, k) in the design box takes the material of rho(i, j, k); J is kept
+ * per E component.  All arrays are whole [nz][ny][nx]. */
+
+enum { X = 0, Y = 1, Z = 2 };
+
+typedef struct {
+    double *E[3], *J[3], *H[3];
+    double *pe[3][3], *ph[3][3];   /* CPML term of component c along axis a */
+} st3;
+
+typedef struct {
+    double *eps[3], *psi[3], *sig[3];  /* per E component */
+    double gam;
+    pml_coef *e[3], *h[3];             /* per axis, at node / half positions */
+} mat3;
+
+static size_t n3(const or_config *c) { return (size_t)c->nx * c->ny * c->nz; }
+static size_t id3(const or_config *c, int i, int j, int k) { return ((size_t)k * c->ny + j) * c->nx + i; }
+
+static void st3_alloc(const or_config *c, st3 *s)
+{
+    size_t n = n3(c);
+    for (int a = 0; a < 3; ++a) {
+        s->E[a] = calloc(n, sizeof(double));
+        s->J[a] = calloc(n, sizeof(double));
+        s->H[a] = calloc(n, sizeof(double));
+        for (int b = 0; b < 3; ++b) {
+            s->pe[a][b] = calloc(n, sizeof(double));
+            s->ph[a][b] = calloc(n, sizeof(double));
+        }
+    }
+}
+
+static void st3_free(st3 *s)
+{
+    for (int a = 0; a < 3; ++a) {
+        free(s->E[a]); free(s->J[a]); free(s->H[a]);
+        for (int b = 0; b < 3; ++b) { free(s->pe[a][b]); free(s->ph[a][b]); }
+    }
+}
+
+static void mat3_build(const or_config *c, const double *rho_t, double sigma_max, double gamma_scale, mat3 *m)
+{
+    size_t n = n3(c);
+    int dw = c->design_hi[0] - c->design_lo[0], dh = c->design_hi[1] - c->design_lo[1];
+    m->gam = c->gamma_p * gamma_scale;
+    for (int a = 0; a < 3; ++a) {
+        m->eps[a] = malloc(n * sizeof(double));
+        m->psi[a] = calloc(n, sizeof(double));
+        m->sig[a] = calloc(n, sizeof(double));
+    }
+    for (int k = 0; k < c->nz; ++k)
+        for (int j = 0; j < c->ny; ++j)
+            for (int i = 0; i < c->nx; ++i) {
+                size_t q = id3(c, i, j, k);
+                double eb = k < c->sub_hi ? c->sub_eps : c->eps_s;
+                double e = eb, p = 0.0, sg = 0.0;
+                if (in_box(c->gap_lo, c->gap_hi, i, j, k)) {
+                    e = c->eps_g;
+                } else if (in_box(c->design_lo, c->design_hi, i, j, k)) {
+                    double r = rho_t[((size_t)(k - c->design_lo[2]) * dh + (j - c->design_lo[1])) * dw +
+                                     (i - c->design_lo[0])];
+                    or_material(c, r, sigma_max, &e, &p, &sg);
+                }
+                for (int a = 0; a < 3; ++a) { m->eps[a][q] = e; m->psi[a][q] = p; m->sig[a][q] = sg; }
+            }
+    int nn[3] = {c->nx, c->ny, c->nz};
+    for (int a = 0; a < 3; ++a) {
+        m->e[a] = malloc(nn[a] * sizeof(pml_coef));
+        m->h[a] = malloc(nn[a] * sizeof(pml_coef));
+        for (int i = 0; i < nn[a]; ++i) {
+            m->e[a][i] = pml_at(c, nn[a], i);
+            m->h[a][i] = pml_at(c, nn[a], i + 0.5);
+        }
+    }
+}
+
+static void mat3_free(mat3 *m)
+{
+    for (int a = 0; a < 3; ++a) {
+        free(m->eps[a]); free(m->psi[a]); free(m->sig[a]); free(m->e[a]); free(m->h[a]);
+    }
+}
+
+/* d/d(axis) of field F at node (i, j, k), forward difference (for H from E)
+ * or backward difference (for E from H), divided by dx; 0 where the
+ * neighbour is outside the grid. */
+static double dfwd(const or_config *c, const double *F, int ax, int i, int j, int k)
+{
+    int ii = i + (ax == X), jj = j + (ax == Y), kk = k + (ax == Z);
+    if (ii >= c->nx || jj >= c->ny || kk >= c->nz) return 0.0;
+    return (F[id3(c, ii, jj, kk)] - F[id3(c, i, j, k)]) / c->dx;
+}
+
+static double dbwd(const or_config *c, const double *F, int ax, int i, int j, int k)
+{
+    int ii = i - (ax == X), jj = j - (ax == Y), kk = k - (ax == Z);
+    if (ii < 0 || jj < 0 || kk < 0) return 0.0;
+    return (F[id3(c, i, j, k)] - F[id3(c, ii, jj, kk)]) / c->dx;
+}
+
+/* Is component comp of E (or H) at index (i, j, k) inside the grid and, for
+ * E, away from the PEC walls (tangential E = 0 on the outer faces)? */
+static int e_active(const or_config *c, int comp, int i, int j, int k)
+{
+    int n[3] = {c->nx, c->ny, c->nz}, p[3] = {i, j, k};
+    for (int a = 0; a < 3; ++a) {
+        if (a == comp) { if (p[a] > n[a] - 2) return 0; }
+        else if (p[a] < 1 || p[a] > n[a] - 2) return 0;
+    }
+    return 1;
+}
+
+static int h_active(const or_config *c, int comp, int i, int j, int k)
+{
+    int n[3] = {c->nx, c->ny, c->nz}, p[3] = {i, j, k};
+    for (int a = 0; a < 3; ++a)
+        if (a != comp && p[a] > n[a] - 2) return 0;
+    return 1;
+}
+
+/* The two (axis, sign) terms of curl component comp: curl_c = d_a F_b - d_b F_a
+ * with (c, a, b) cyclic. */
+static void curl_axes(int comp, int *a, int *b) { *a = (comp + 1) % 3; *b = (comp + 2) % 3; }
+
+/* H half step: mu0 dH/dt = -curl E with CPML on each derivative. */
+static void step3_h(const or_config *c, const mat3 *m, st3 *s)
+{
+    double ch = or_dt(c) / OR_MU0;
+    #pragma omp parallel for schedule(static)
+    for (int k = 0; k < c->nz; ++k)
+        for (int j = 0; j < c->ny; ++j)
+            for (int i = 0; i < c->nx; ++i) {
+                int p[3] = {i, j, k};
+                size_t q = id3(c, i, j, k);
+                for (int comp = 0; comp < 3; ++comp) {
+                    if (!h_active(c, comp, i, j, k)) continue;
+                    int a, b;
+                    curl_axes(comp, &a, &b);
+                    /* curl_comp E = d_a E_b - d_b E_a */
+                    double da = dfwd(c, s->E[b], a, i, j, k);
+                    double db = dfwd(c, s->E[a], b, i, j, k);
+                    pml_coef pa = m->h[a][p[a]], pb = m->h[b][p[b]];
+                    s->ph[comp][a][q] = pa.b * s->ph[comp][a][q] + pa.c * da;
+                    s->ph[comp][b][q] = pb.b * s->ph[comp][b][q] + pb.c * db;
+                    double curl = da / pa.kappa + s->ph[comp][a][q] - db / pb.kappa - s->ph[comp][b][q];
+                    s->H[comp][q] -= ch * curl;
+                }
+            }
+}
+
+/* E, J half step: Eq. (10a,b) for every active E component; jsrc[comp] is a
+ * per-node current density (or NULL). */
+static void step3_e(const or_config *c, const mat3 *m, st3 *s, double *const *jsrc)
+{
+    double dt = or_dt(c);
+    #pragma omp parallel for schedule(static)
+    for (int k = 0; k < c->nz; ++k)
+        for (int j = 0; j < c->ny; ++j)
+            for (int i = 0; i < c->nx; ++i) {
+                int p[3] = {i, j, k};
+                size_t q = id3(c, i, j, k);
+                for (int comp = 0; comp < 3; ++comp) {
+                    if (!e_active(c, comp, i, j, k)) continue;
+                    int a, b;
+                    curl_axes(comp, &a, &b);
+                    double da = dbwd(c, s->H[b], a, i, j, k);
+                    double db = dbwd(c, s->H[a], b, i, j, k);
+                    pml_coef pa = m->e[a][p[a]], pb = m->e[b][p[b]];
+                    s->pe[comp][a][q] = pa.b * s->pe[comp][a][q] + pa.c * da;
+                    s->pe[comp][b][q] = pb.b * s->pe[comp][b][q] + pb.c * db;
+                    double curl = da / pa.kappa + s->pe[comp][a][q] - db / pb.kappa - s->pe[comp][b][q];
+                    node_solve(m->eps[comp][q], m->psi[comp][q], m->sig[comp][q], m->gam, dt, curl,
+                               jsrc && jsrc[comp] ? jsrc[comp][q] : 0.0, &s->E[comp][q], &s->J[comp][q]);
+                }
+            }
+}
+
+static double energy3(const or_config *c, const mat3 *m, const st3 *s, double *const *Hold)
+{
+    double eps0 = or_eps0(), e = 0.0;
+    size_t n = n3(c);
+    for (int a = 0; a < 3; ++a)
+        for (size_t q = 0; q < n; ++q) {
+            e += 0.5 * eps0 * m->eps[a][q] * s->E[a][q] * s->E[a][q];
+            e += 0.5 * OR_MU0 * Hold[a][q] * s->H[a][q];
+        }
+    return e * c->dx * c->dx * c->dx;
+}
+
+/* Gap / design boxes hold 3 components per index: history layout
+ * [t][comp][box index]. */
+static int forward3(const or_config *c, const double *rho, double sigma_max, double gamma_scale, double *W,
+                    double *gap_hist, double *design_hist, const int *probes, int nprobe, double *probe_hist,
+                    double *energy)
+{
+    int N = c->nsteps;
+    long M, G;
+    or_sizes(c, &M, &G);
+    double *rho_t = malloc(sizeof(double) * (M ? M : 1));
+    if (M) or_filter(c, rho, rho_t);
+    mat3 m;
+    mat3_build(c, rho_t, sigma_max, gamma_scale, &m);
+    st3 s;
+    st3_alloc(c, &s);
+    size_t n = n3(c);
+    double *js[3] = {NULL, NULL, NULL};
+    js[c->src_comp] = calloc(n, sizeof(double));
+    double *Hold[3] = {NULL, NULL, NULL};
+    if (energy)
+        for (int a = 0; a < 3; ++a) Hold[a] = calloc(n, sizeof(double));
+    double dt = or_dt(c);
+    double J0 = c->src_amp * or_eps0() * OR_C0 / c->dx;
+    double sum = 0.0;
+    int gw = c->gap_hi[0] - c->gap_lo[0], gh = c->gap_hi[1] - c->gap_lo[1];
+    int dw = c->design_hi[0] - c->design_lo[0], dh = c->design_hi[1] - c->design_lo[1];
+    for (int t = 0; t <= N; ++t) {
+        for (int a = 0; a < 3; ++a) {
+            for (int k = c->gap_lo[2]; k < c->gap_hi[2]; ++k)
+                for (int j = c->gap_lo[1]; j < c->gap_hi[1]; ++j)
+                    for (int i = c->gap_lo[0]; i < c->gap_hi[0]; ++i) {
+                        double e = s.E[a][id3(c, i, j, k)];
+                        sum += e * e;
+                        if (gap_hist)
+                            gap_hist[((size_t)t * 3 + a) * G +
+                                     ((size_t)(k - c->gap_lo[2]) * gh + (j - c->gap_lo[1])) * gw + (i - c->gap_lo[0])] = e;
+                    }
+            if (design_hist)
+                for (int k = c->design_lo[2]; k < c->design_hi[2]; ++k)
+                    for (int j = c->design_lo[1]; j < c->design_hi[1]; ++j)
+                        for (int i = c->design_lo[0]; i < c->design_hi[0]; ++i)
+                            design_hist[((size_t)t * 3 + a) * M +
+                                        ((size_t)(k - c->design_lo[2]) * dh + (j - c->design_lo[1])) * dw +
+                                        (i - c->design_lo[0])] = s.E[a][id3(c, i, j, k)];
+        }
+        for (int pi = 0; pi < nprobe; ++pi)
+            probe_hist[(size_t)t * nprobe + pi] =
+                s.E[probes[4 * pi + 3]][id3(c, probes[4 * pi], probes[4 * pi + 1], probes[4 * pi + 2])];
+        if (t == N) break;
+        double v = J0 * or_signal(c, (t + 0.5) * dt);
+        for (int k = c->src_lo[2]; k < c->src_hi[2]; ++k)
+            for (int j = c->src_lo[1]; j < c->src_hi[1]; ++j)
+                for (int i = c->src_lo[0]; i < c->src_hi[0]; ++i) js[c->src_comp][id3(c, i, j, k)] = v;
+        if (energy)
+            for (int a = 0; a < 3; ++a) memcpy(Hold[a], s.H[a], n * sizeof(double));
+        step3_h(c, &m, &s);
+        if (energy) energy[t] = energy3(c, &m, &s, Hold);
+        step3_e(c, &m, &s, js);
+    }
+    *W = 0.5 * c->eps_g * dt * c->dx * c->dx * c->dx * sum;
+    free(js[c->src_comp]);
+    for (int a = 0; a < 3; ++a) free(Hold[a]);
+    free(rho_t);
+    st3_free(&s);
+    mat3_free(&m);
+    return 0;
+}
+
+/* Adjoint (Eq. 20) and sensitivities (Eq. 25) per E component, summed over
+ * the three components of each design index, then Eq. (27). */
+static int gradient3(const or_config *c, const double *rho, double sigma_max, double gamma_scale, double *W,
+                     double *grad, double *g_psi, double *g_eps, double *g_sig)
+{
+    int N = c->nsteps;
+    long M, G;
+    or_sizes(c, &M, &G);
+    if (M == 0) return -1;
+    double *ghist = malloc(sizeof(double) * (size_t)(N + 1) * 3 * (G ? G : 1));
+    double *dhist = malloc(sizeof(double) * (size_t)(N + 1) * 3 * M);
+    forward3(c, rho, sigma_max, gamma_scale, W, ghist, dhist, NULL, 0, NULL, NULL);
+    double *rho_t = malloc(sizeof(double) * M);
+    or_filter(c, rho, rho_t);
+    mat3 m;
+    mat3_build(c, rho_t, sigma_max, gamma_scale, &m);
+    st3 s;
+    st3_alloc(c, &s);
+    size_t n = n3(c);
+    double *js[3];
+    for (int a = 0; a < 3; ++a) js[a] = calloc(n, sizeof(double));
+    double *sp = calloc(M, sizeof(double)), *se = calloc(M, sizeof(double)), *ss = calloc(M, sizeof(double));
+    double *Eo = malloc(sizeof(double) * 3 * M), *Jo = malloc(sizeof(double) * 3 * M);
+    int gw = c->gap_hi[0] - c->gap_lo[0], gh = c->gap_hi[1] - c->gap_lo[1];
+    int dw = c->design_hi[0] - c->design_lo[0], dh = c->design_hi[1] - c->design_lo[1];
+    for (int t = 0; t <= N; ++t) {
+        for (int a = 0; a < 3; ++a)
+            for (int k = c->gap_lo[2]; k < c->gap_hi[2]; ++k)
+                for (int j = c->gap_lo[1]; j < c->gap_hi[1]; ++j)
+                    for (int i = c->gap_lo[0]; i < c->gap_hi[0]; ++i)
+                        js[a][id3(c, i, j, k)] =
+                            -c->eps_g * ghist[((size_t)(N - t) * 3 + a) * G +
+                                              ((size_t)(k - c->gap_lo[2]) * gh + (j - c->gap_lo[1])) * gw +
+                                              (i - c->gap_lo[0])];
+        for (int a = 0; a < 3; ++a)
+            for (int k = c->design_lo[2]; k < c->design_hi[2]; ++k)
+                for (int j = c->design_lo[1]; j < c->design_hi[1]; ++j)
+                    for (int i = c->design_lo[0]; i < c->design_hi[0]; ++i) {
+                        long d = ((long)(k - c->design_lo[2]) * dh + (j - c->design_lo[1])) * dw + (i - c->design_lo[0]);
+                        Eo[a * M + d] = s.E[a][id3(c, i, j, k)];
+                        Jo[a * M + d] = s.J[a][id3(c, i, j, k)];
+                    }
+        step3_h(c, &m, &s);
+        step3_e(c, &m, &s, js);
+        for (int a = 0; a < 3; ++a)
+            for (int k = c->design_lo[2]; k < c->design_hi[2]; ++k)
+                for (int j = c->design_lo[1]; j < c->design_hi[1]; ++j)
+                    for (int i = c->design_lo[0]; i < c->design_hi[0]; ++i) {
+                        long d = ((long)(k - c->design_lo[2]) * dh + (j - c->design_lo[1])) * dw + (i - c->design_lo[0]);
+                        size_t q = id3(c, i, j, k);
+                        double Ef = dhist[((size_t)(N - t) * 3 + a) * M + d];
+                        sp[d] += Ef * 0.5 * (s.J[a][q] + Jo[a * M + d]);
+                        se[d] += Ef * (s.E[a][q] - Eo[a * M + d]);
+                        ss[d] += Ef * 0.5 * (s.E[a][q] + Eo[a * M + d]);
+                    }
+    }
+    double eps0 = or_eps0(), dt = or_dt(c), dx3 = c->dx * c->dx * c->dx;
+    double psi = c->omega_p * c->omega_p, psi_s = c->psi_s_ratio * psi;
+    double *gt = malloc(sizeof(double) * M);
+    for (int k = c->design_lo[2]; k < c->design_hi[2]; ++k)
+        for (int j = c->design_lo[1]; j < c->design_hi[1]; ++j)
+            for (int i = c->design_lo[0]; i < c->design_hi[0]; ++i) {
+                long d = ((long)(k - c->design_lo[2]) * dh + (j - c->design_lo[1])) * dw + (i - c->design_lo[0]);
+                double ep, ps, sg;
+                or_material(c, rho_t[d], sigma_max, &ep, &ps, &sg);
+                double dpsi = -(dt * dx3 / ps) * sp[d];
+                double deps = -eps0 * dx3 * se[d];
+                double dsig = -dt * dx3 * ss[d];
+                if (in_box(c->gap_lo, c->gap_hi, i, j, k)) dpsi = deps = dsig = 0.0;
+                if (g_psi) g_psi[d] = dpsi;
+                if (g_eps) g_eps[d] = deps;
+                if (g_sig) g_sig[d] = dsig;
+                double dsdr = sigma_max * (1.0 - 2.0 * rho_t[d]) * (c->sigma_form ? 4.0 : 1.0);
+                gt[d] = (psi - psi_s) * dpsi + (c->eps_inf - c->eps_s) * deps + dsdr * dsig;
+            }
+    or_filter_T(c, gt, grad);
+    for (int k = c->gap_lo[2]; k < c->gap_hi[2]; ++k)
+        for (int j = c->gap_lo[1]; j < c->gap_hi[1]; ++j)
+            for (int i = c->gap_lo[0]; i < c->gap_hi[0]; ++i)
+                grad[((long)(k - c->design_lo[2]) * dh + (j - c->design_lo[1])) * dw + (i - c->design_lo[0])] = 0.0;
+    free(gt); free(Eo); free(Jo); free(sp); free(se); free(ss);
+    for (int a = 0; a < 3; ++a) free(js[a]);
+    free(rho_t); free(ghist); free(dhist);
+    st3_free(&s);
+    mat3_free(&m);
+    return 0;
+}
+
 /* ============================================================ public */
 
 int or_forward(const or_config *c, const double *rho, double sigma_max, double gamma_scale,
@@ -553,6 +906,9 @@ int or_forward(const or_config *c, const double *rho, double sigma_max, double g
     if (c->ndim == 2)
         return forward2(c, rho, sigma_max, gamma_scale, W, gap_hist, design_hist,
                         probes, nprobe, probe_hist, energy);
+    if (c->ndim == 3)
+        return forward3(c, rho, sigma_max, gamma_scale, W, gap_hist, design_hist,
+                        probes, nprobe, probe_hist, energy);
     return -1;
 }
 
@@ -560,5 +916,6 @@ int or_gradient(const or_config *c, const double *rho, double sigma_max, double 
                 double *W, double *grad, double *g_psi, double *g_eps, double *g_sig)
 {
     if (c->ndim == 2) return gradient2(c, rho, sigma_max, gamma_scale, W, grad, g_psi, g_eps, g_sig);
+    if (c->ndim == 3) return gradient3(c, rho, sigma_max, gamma_scale, W, grad, g_psi, g_eps, g_sig);
     return -1;
 }

@@ -37,6 +37,7 @@ class OrConfig(C.Structure):
         ("src_amp", C.c_double), ("nsteps", C.c_int),
         ("filter_radius", C.c_int), ("filter_sigma", C.c_double),
         ("sigma_form", C.c_int), ("sub_eps", C.c_double), ("sub_hi", C.c_int),
+        ("src_comp", C.c_int),
     ]
 
 
@@ -81,7 +82,7 @@ def threads() -> int:
 def config(w: dict) -> OrConfig:
     c = OrConfig()
     for name, ctype in OrConfig._fields_:
-        v = w[name]
+        v = w.get(name, 2 if name == "src_comp" else None)
         if name == "f0":
             c.f0[0], c.f0[1] = float(v[0]), float(v[1])
         elif isinstance(getattr(c, name), C.Array):
@@ -114,17 +115,24 @@ def _sizes(w: dict) -> tuple[int, int]:
 def forward(w: dict, rho: np.ndarray, sigma_max: float = 0.0, gamma_scale: float = 1.0,
             record_gap: bool = False, record_design: bool = False, probes=None,
             energy: bool = False) -> dict:
-    """Forward solve; returns W and whatever histories were asked for."""
+    """Forward solve; returns W and whatever histories were asked for.
+
+    2D: gap_hist (N+1, M_g), design_hist (N+1, M_d), probes (i, j) of Ez.
+    3D: gap_hist (N+1, 3, M_g), design_hist (N+1, 3, M_d) with components
+    x, y, z, probes (i, j, k, component)."""
     M, G = _sizes(w)
     N = int(w["nsteps"])
+    nc = 3 if w["ndim"] == 3 else 1
     rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
     assert rho.size == M
     cfg = config(w)
     Wout = C.c_double(0.0)
-    gh = np.zeros((N + 1, G)) if record_gap else None
-    dh = np.zeros((N + 1, M)) if record_design else None
+    gshape = (N + 1, 3, G) if nc == 3 else (N + 1, G)
+    dshape = (N + 1, 3, M) if nc == 3 else (N + 1, M)
+    gh = np.zeros(gshape) if record_gap else None
+    dh = np.zeros(dshape) if record_design else None
     if probes is not None:
-        pr = np.ascontiguousarray(np.asarray(probes, dtype=np.int32).reshape(-1, 2))
+        pr = np.ascontiguousarray(np.asarray(probes, dtype=np.int32).reshape(-1, 4 if nc == 3 else 2))
         ph = np.zeros((N + 1, pr.shape[0]))
         pptr, npr = pr.ctypes.data_as(C.POINTER(C.c_int)), pr.shape[0]
     else:

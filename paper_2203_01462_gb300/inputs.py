@@ -78,7 +78,7 @@ def workload_2d(nx: int, ny: int, *, dx: float, nsteps: int, npml: int = 10,
         src_amp=1.0, nsteps=nsteps,
         filter_radius=filter_radius,
         filter_sigma=(filter_fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0)))) if filter_radius else 1.0,
-        sigma_form=0, sub_eps=1.0, sub_hi=0,
+        sigma_form=0, sub_eps=1.0, sub_hi=0, src_comp=2,
         real=real, snapshot_every=snapshot_every, snapshot_dtype=snapshot_dtype, accum=accum,
     )
     w.update(mat)
@@ -107,6 +107,59 @@ def small_2d(nx: int = 40, ny: int = 36, nsteps: int = 300, real: str = "f64", *
     npml = kw.pop("npml", 6)
     return workload_2d(nx, ny, dx=kw.pop("dx", 5e-9), nsteps=nsteps, npml=npml, design=d, gap=g,
                        real=real, src_offset=kw.pop("src_offset", 2), **kw)
+
+
+def workload_3d(nx: int, ny: int, nz: int, *, dx: float, nsteps: int, npml: int = 12,
+                design: tuple[int, int, int] = (32, 32, 16), gap: tuple[int, int, int] = (4, 4, 4),
+                courant: float = 0.5, real: str = "f32", material: dict | None = None,
+                source: str = "sheet", src_offset: int = 5, substrate: bool = False,
+                snapshot_every: int = 0, snapshot_dtype: str = "f32", accum: str = "f64",
+                pulse_kw: dict | None = None, **over) -> dict:
+    """A 3D nanoantenna-shaped workload: centred design slab and gap.
+
+    source="sheet": a soft E_x current sheet on the plane z = npml + src_offset
+    over the non-CPML x-y range (a plane wave along +z, x-polarised).
+    source="dipole": a soft E_z current at the centre node of the gap.
+    substrate=True: background eps 2.25 below the design slab.
+    """
+    mat = dict(GOLD if material is None else material)
+    d_lo = [(n - w_) // 2 for n, w_ in zip((nx, ny, nz), design)]
+    g_lo = [(n - w_) // 2 for n, w_ in zip((nx, ny, nz), gap)]
+    w = dict(
+        ndim=3, nx=nx, ny=ny, nz=nz, dx=dx, courant=courant, npml=npml,
+        pml_m=3.0, pml_sigma_factor=0.8, pml_kappa_max=1.0, pml_alpha_max=0.0,
+        periodic_x=0, eps_s=1.0, psi_s_ratio=0.01, eps_g=1.0,
+        design_lo=d_lo, design_hi=[l + w_ for l, w_ in zip(d_lo, design)],
+        gap_lo=g_lo, gap_hi=[l + w_ for l, w_ in zip(g_lo, gap)],
+        src_amp=1.0, nsteps=nsteps, filter_radius=0, filter_sigma=1.0, sigma_form=0,
+        sub_eps=2.25 if substrate else 1.0, sub_hi=d_lo[2] if substrate else 0,
+        real=real, snapshot_every=snapshot_every, snapshot_dtype=snapshot_dtype, accum=accum,
+    )
+    if source == "sheet":
+        zs = npml + src_offset
+        w.update(src_lo=[npml, npml, zs], src_hi=[nx - npml, ny - npml, zs + 1], src_comp=0)
+    else:
+        c = [(l + h) // 2 for l, h in zip(w["gap_lo"], w["gap_hi"])]
+        w.update(src_lo=c, src_hi=[x + 1 for x in c], src_comp=2)
+    w.update(mat)
+    w.update(pulse(**(pulse_kw or {})))
+    w.update(over)
+    return w
+
+
+def cfg_3d_256(nsteps: int = 10000) -> dict:
+    """256^3 FP32: 128 x 128 x 64 design slab on an eps 2.25 substrate, 4^3 gap,
+    x-polarised plane wave along +z (current sheet), BF16 snapshots every 32."""
+    return workload_3d(256, 256, 256, dx=5e-9, nsteps=nsteps, npml=12, design=(128, 128, 64), gap=(4, 4, 4),
+                       source="sheet", substrate=True, snapshot_every=32, snapshot_dtype="bf16")
+
+
+def cfg_3d_512(nsteps: int = 16000) -> dict:
+    """512 x 512 x 384 FP32: 256 x 256 x 96 design region, z-dipole in the gap,
+    two bands (650-750 nm and 850-950 nm), FP16 snapshots."""
+    return workload_3d(512, 512, 384, dx=5e-9, nsteps=nsteps, npml=12, design=(256, 256, 96), gap=(4, 4, 4),
+                       source="dipole", snapshot_every=500, snapshot_dtype="f16",
+                       pulse_kw=dict(centers_m=[700e-9, 900e-9], half_width_hz=C0 / 650e-9 - C0 / 700e-9))
 
 
 def n_design(w: dict) -> int:

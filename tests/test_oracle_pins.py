@@ -231,3 +231,90 @@ def test_objective_literal_sum():
     assert abs(out["W"] - 0.5 * w["eps_g"] * dt * w["dx"] ** 2 * np.sum(out["gap_hist"] ** 2)) \
         <= 1e-13 * out["W"]
     assert np.all(out["gap_hist"][0] == 0.0)
+
+
+# ------------------------------------------------------------------ 3D
+
+def fast_case_3d(npml=4, source="dipole", material=None, nsteps=200):
+    w = I.workload_3d(20, 18, 22, dx=20e-9, nsteps=nsteps, npml=npml, design=(8, 6, 6), gap=(2, 2, 2),
+                      source=source, material=material, real="f64")
+    w.update(I.pulse(800e-9, 300e12))
+    if npml == 0 and source == "sheet":
+        w["src_lo"] = [1, 1, 3]
+        w["src_hi"] = [19, 17, 4]
+    return w
+
+
+def test_3d_dipole_field_matches_hertzian_dipole():
+    """A soft E_z current on one edge is a current element I l = J dx^3; in the
+    equatorial plane its field is E_z = -(p/r^3 + p'/(c r^2) + p''/(c^2 r)) / (4 pi eps0)
+    at the retarded time (near, intermediate and far terms)."""
+    n, dx, D = 52, 5e-9, 13
+    c = n // 2
+    w = I.workload_3d(n, n, n, dx=dx, nsteps=2400, npml=8, design=(0, 0, 0), gap=(0, 0, 0), source="dipole",
+                      real="f64")
+    w.update(I.pulse(800e-9, 300e12))
+    w.update(design_lo=[0, 0, 0], design_hi=[0, 0, 0], gap_lo=[0, 0, 0], gap_hi=[0, 0, 0],
+             src_lo=[c, c, c], src_hi=[c + 1, c + 1, c + 1], src_comp=2)
+    O.set_threads(8)
+    e = O.forward(w, np.zeros(0), probes=[(c + D, c, c, 2), (c, c - D, c, 2)])["probe_hist"]
+    O.set_threads(1)
+    dt = w["courant"] * dx / C0
+    r = D * dx
+    tr = np.arange(e.shape[0]) * dt - r / C0
+
+    def g(t):
+        return np.exp(-((t - w["t0"]) / w["tau"]) ** 2) * np.sin(2 * np.pi * w["f0"][0] * (t - w["t0"]))
+
+    J0 = w["src_amp"] * EPS0 * C0 / dx
+    fine = np.linspace(tr.min() - 1e-15, tr.max(), 200001)
+    p = dx ** 3 * J0 * np.interp(tr, fine, np.cumsum(g(fine)) * (fine[1] - fine[0]))
+    pd = dx ** 3 * J0 * g(tr)
+    h = 1e-20
+    pdd = dx ** 3 * J0 * (g(tr + h) - g(tr - h)) / (2 * h)
+    Ez = -(p / r ** 3 + pd / (C0 * r ** 2) + pdd / (C0 ** 2 * r)) / (4 * np.pi * EPS0)
+    for k in range(2):
+        assert np.max(np.abs(e[:, k] - Ez)) < 3e-2 * np.max(np.abs(Ez))
+
+
+def test_3d_pec_cavity_energy_conserved():
+    n, dx = 12, 20e-9
+    w = I.workload_3d(n, n + 1, n + 2, dx=dx, nsteps=6000, npml=0, design=(0, 0, 0), gap=(0, 0, 0),
+                      source="dipole", real="f64")
+    w.update(I.pulse(1600e-9, 200e12))
+    w.update(design_lo=[0, 0, 0], design_hi=[0, 0, 0], gap_lo=[0, 0, 0], gap_hi=[0, 0, 0],
+             src_lo=[4, 5, 6], src_hi=[5, 6, 7], src_comp=1)
+    en = O.forward(w, np.zeros(0), energy=True)["energy"]
+    dt = w["courant"] * dx / C0
+    quiet = int((w["t0"] + 7.0 * w["tau"]) / dt) + 1
+    tail = en[quiet:]
+    assert tail.max() > 0
+    assert (tail.max() - tail.min()) / tail.max() < 1e-11
+
+
+@pytest.mark.parametrize("npml,source,material", [(0, "dipole", "gold"), (4, "dipole", "silver"),
+                                                  (4, "sheet", "gold"), (0, "sheet", "silver")])
+def test_3d_adjoint_gradient_matches_central_differences(npml, source, material):
+    """Eq. (25) summed over the three E components of each design cell, then
+    Eq. (27), against central differences of the 3D forward solve."""
+    w = fast_case_3d(npml, source, I.SILVER if material == "silver" else I.GOLD)
+    r = I.zero_gap(w, I.rho_uniform(w, 8) * 0.8 + 0.1)
+    smax, gs = 5e5, 2.0
+    g = O.gradient(w, r, smax, gs)["grad"]
+    rf = r.reshape(-1)
+    rng = np.random.default_rng(2)
+    for i in rng.choice(np.flatnonzero(rf > 0), 5, replace=False):
+        h = 1e-4
+        rp, rm = rf.copy(), rf.copy()
+        rp[i] += h
+        rm[i] -= h
+        fd = (O.objective(w, rp, smax, gs) - O.objective(w, rm, smax, gs)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-5 * abs(fd) + 1e-6 * np.abs(g).max()
+
+
+def test_3d_objective_literal_sum():
+    """Eq. (24) in 3D: eps_g dt dx^3 / 2 times the sum over the gap of |E|^2."""
+    w = fast_case_3d()
+    out = O.forward(w, I.rho_uniform(w, 9), record_gap=True)
+    dt = w["courant"] * w["dx"] / C0
+    assert abs(out["W"] - 0.5 * w["eps_g"] * dt * w["dx"] ** 3 * np.sum(out["gap_hist"] ** 2)) <= 1e-13 * out["W"]
