@@ -33,9 +33,14 @@
  * that fdtd_sync reports.
  *
  * Units: SI.  W~ follows Eq. (24) literally (eps_g dt dx^d / 2 times the sum
- * of E^2 over the gap nodes and steps n = 0..N, d = 2 in 2D, per unit length
- * in z), so it is small in absolute terms; W~ and the gradient are returned
- * in FP64 whatever the field precision.
+ * of |E|^2 over the gap nodes and steps n = 0..N; d = 2 in 2D, per unit
+ * length in z; d = 3 in 3D), so it is small in absolute terms; W~ and the
+ * gradient are returned in FP64 whatever the field precision.
+ *
+ * 2D: TM_z (Ez, Hx, Hy, Jz) on nx x ny nodes.  3D: full Yee grid on
+ * nx x ny x nz nodes, Ex at (i+1/2, j, k), Ey at (i, j+1/2, k), Ez at
+ * (i, j, k+1/2); the three E components of node (i, j, k) share rho(i, j, k)
+ * and the gradient sums their sensitivities.  3D takes no design filter.
  */
 #ifndef FDTD_GB300_H
 #define FDTD_GB300_H
@@ -63,7 +68,7 @@ enum { FDTD_SIGMA_PAPER = 0, FDTD_SIGMA_PEAK_NORMALISED = 1 };
 
 /* Problem description.  Boxes are half-open node ranges [lo, hi) per axis
  * (x, y, z); in 2D the z range must be [0, 1).  Grid: nx x ny Ez nodes in
- * 2D; nx x ny x nz cells in 3D. */
+ * 2D; nx x ny x nz Yee nodes in 3D. */
 typedef struct fdtd_config {
     int ndim;                 /* 2: TM_z (Ez, Hx, Hy, Jz); 3: full Yee        */
     int nx, ny, nz;
@@ -80,7 +85,8 @@ typedef struct fdtd_config {
     double eps_g;             /* gap permittivity                              */
     int design_lo[3], design_hi[3];
     int gap_lo[3], gap_hi[3];
-    int src_lo[3], src_hi[3]; /* soft current source box on Ez nodes          */
+    int src_lo[3], src_hi[3]; /* soft current source box (Ez in 2D, src_comp   */
+                              /* edges in 3D)                                 */
     int nbands;               /* 1 or 2 Gaussian-modulated carriers            */
     double f0[2];             /* carrier frequencies, Hz                       */
     double tau, t0;           /* envelope exp(-((t - t0) / tau)^2), s          */
@@ -96,6 +102,8 @@ typedef struct fdtd_config {
                               /* k > 0: checkpoint every k steps, recompute    */
     int snapshot_dtype;       /* FDTD_SNAP_*: snapshot storage precision       */
     int accum_kind;           /* FDTD_ACC_*: sensitivity accumulator           */
+    int src_comp;             /* 3D: E component the source drives (0 x, 1 y, */
+                              /* 2 z); the source box holds those edges      */
 } fdtd_config;
 
 typedef struct fdtd_ctx fdtd_ctx;
@@ -150,7 +158,8 @@ fdtd_status fdtd_adjoint(fdtd_ctx *ctx);
 fdtd_status fdtd_gradient(fdtd_ctx *ctx, double *d_grad, size_t n);
 
 /* Gap-field history E^n, n = 0..N, of the last forward run into d_out
- * (device, n = (N + 1) * M_g doubles, gap nodes x fastest). */
+ * (device doubles, gap nodes x fastest): 2D n = (N + 1) * M_g; 3D
+ * n = (N + 1) * 3 * M_g, layout [step][component x, y, z][gap node]. */
 fdtd_status fdtd_gap_history(fdtd_ctx *ctx, double *d_out, size_t n);
 
 /* Wait for the context's stream and report (then clear) device-side errors:

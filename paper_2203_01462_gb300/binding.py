@@ -49,7 +49,7 @@ class FdtdConfig(C.Structure):
         ("filter_radius", C.c_int), ("filter_sigma", C.c_double),
         ("sigma_form", C.c_int), ("sub_eps", C.c_double), ("sub_hi", C.c_int),
         ("real_bytes", C.c_int), ("snapshot_every", C.c_int), ("snapshot_dtype", C.c_int),
-        ("accum_kind", C.c_int),
+        ("accum_kind", C.c_int), ("src_comp", C.c_int),
     ]
 
 
@@ -124,7 +124,7 @@ def config(w: dict) -> FdtdConfig:
         if name == "accum_kind":
             c.accum_kind = ACC[w.get("accum", "f64")]
             continue
-        v = w[name] if name in w else (0 if name == "snapshot_every" else None)
+        v = w[name] if name in w else {"snapshot_every": 0, "src_comp": 2}.get(name)
         if name == "f0":
             c.f0[0], c.f0[1] = float(v[0]), float(v[1])
         elif isinstance(getattr(c, name), C.Array):
@@ -213,11 +213,14 @@ class Solver:
         return out
 
     def gap_history(self):
+        """(N+1, M_g) in 2D; (N+1, 3, M_g) in 3D."""
         t = self.torch
-        n = (int(self.cfg.nsteps) + 1) * self.n_gap
+        nc = 3 if self.cfg.ndim == 3 else 1
+        n = (int(self.cfg.nsteps) + 1) * nc * self.n_gap
         out = t.empty(n, dtype=t.float64, device=self.device)
         _check(self.lib.fdtd_gap_history(self.ctx, C.c_void_p(out.data_ptr()), n), "fdtd_gap_history")
-        return out.reshape(int(self.cfg.nsteps) + 1, self.n_gap)
+        shape = (int(self.cfg.nsteps) + 1, 3, self.n_gap) if nc == 3 else (int(self.cfg.nsteps) + 1, self.n_gap)
+        return out.reshape(shape)
 
     def sync(self) -> None:
         _check(self.lib.fdtd_sync(self.ctx), "fdtd_sync")

@@ -67,10 +67,13 @@ long long box_count(const int *lo, const int *hi, int ndim)
 fdtd_status validate(const fdtd_config *c)
 {
     if (!c) return FDTD_EINVAL;
-    if (c->ndim != 2) return FDTD_EINVAL;  // 3D: separate path
+    if (c->ndim != 2 && c->ndim != 3) return FDTD_EINVAL;
     if (c->real_bytes != 4 && c->real_bytes != 8) return FDTD_EINVAL;
-    if (c->nx < 4 || c->ny < 4 || c->nz != 1) return FDTD_EINVAL;
-    if (c->npml < 0 || c->nx <= 2 * c->npml + 2 || c->ny <= 2 * c->npml + 2) return FDTD_EINVAL;
+    if (c->nx < 4 || c->ny < 4 || (c->ndim == 2 ? c->nz != 1 : c->nz < 4)) return FDTD_EINVAL;
+    if (c->npml < 0 || c->nx <= 2 * c->npml + 2 || c->ny <= 2 * c->npml + 2 ||
+        (c->ndim == 3 && c->nz <= 2 * c->npml + 2))
+        return FDTD_EINVAL;
+    if (c->ndim == 3 && (c->filter_radius != 0 || c->src_comp < 0 || c->src_comp > 2)) return FDTD_EINVAL;
     if (!(c->dx > 0) || !(c->courant > 0) || c->courant >= 1.0 / sqrt((double)c->ndim)) return FDTD_EINVAL;
     if (c->nsteps < 1) return FDTD_EINVAL;
     if (!(c->omega_p > 0) || !(c->psi_s_ratio > 0) || c->gamma_p < 0) return FDTD_EINVAL;
@@ -88,7 +91,7 @@ fdtd_status validate(const fdtd_config *c)
     if (c->sigma_form != FDTD_SIGMA_PAPER && c->sigma_form != FDTD_SIGMA_PEAK_NORMALISED) return FDTD_EINVAL;
     // The step kernels index one array with 32-bit integers.
     const long long px = (c->nx + 31) / 32 * 32;
-    if (px * (long long)c->ny >= (1LL << 31)) return FDTD_EINVAL;
+    if (c->ndim == 2 && px * (long long)c->ny >= (1LL << 31)) return FDTD_EINVAL;
     return FDTD_OK;
 }
 
@@ -163,6 +166,55 @@ fdtd_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? FDTD_OK : FDTD_EC
         fdtd_status s__ = (x);               \
         if (s__ != FDTD_OK) return s__;      \
     } while (0)
+
+// Step-invariant coefficients in the scaled units of Coef.
+template <typename R>
+Coef<R> make_coef(const fdtd_config &c, double dt, double sigma_max, double gamma_scale)
+{
+    Coef<R> k;
+    const double g = c.gamma_p * gamma_scale * dt;
+    const double kJ = (1.0 - 0.5 * g) / (1.0 + 0.5 * g);
+    const double psi = c.omega_p * c.omega_p * dt * dt;
+    k.S = (R)c.courant;
+    k.eps_s = (R)c.eps_s;
+    k.eps_g = (R)c.eps_g;
+    k.eps_sub = (R)c.sub_eps;
+    k.inv_eps_s = (R)(1.0 / c.eps_s);
+    k.inv_eps_g = (R)(1.0 / c.eps_g);
+    k.d_eps = (R)(c.eps_inf - c.eps_s);
+    k.psi = (R)psi;
+    k.psi_s = (R)(c.psi_s_ratio * psi);
+    k.sig_max = (R)(sigma_max * dt / eps0() * (c.sigma_form == FDTD_SIGMA_PEAK_NORMALISED ? 4.0 : 1.0));
+    k.kJ = (R)kJ;
+    k.inv1g = (R)(1.0 / (1.0 + 0.5 * g));
+    k.half1pkJ = (R)(0.5 * (1.0 + kJ));
+    return k;
+}
+
+// CPML tables of one axis of n nodes: b, c, 1/kappa at node positions, then
+// at half positions (6 n values).
+template <typename R>
+void fill_pml(const fdtd_config &c, int n, R *t)
+{
+    for (int i = 0; i < n; ++i) {
+        PmlPoint e = pml_point(&c, n, i), h = pml_point(&c, n, i + 0.5);
+        t[i] = (R)e.b;
+        t[n + i] = (R)e.c;
+        t[2 * n + i] = (R)e.ki;
+        t[3 * n + i] = (R)h.b;
+        t[4 * n + i] = (R)h.c;
+        t[5 * n + i] = (R)h.ki;
+    }
+}
+
+// Source samples J_src dt / eps0 at t = (n + 1/2) dt, n = 0 .. N-1.
+template <typename R>
+std::vector<R> source_table(const fdtd_config &c, double dt)
+{
+    std::vector<R> v(c.nsteps);
+    for (int n = 0; n < c.nsteps; ++n) v[n] = (R)(c.src_amp * c.courant * excitation(&c, (n + 0.5) * dt));
+    return v;
+}
 
 template <typename R>
 struct Ctx2D final : fdtd_ctx {
@@ -269,21 +321,9 @@ struct Ctx2D final : fdtd_ctx {
     {
         const fdtd_config &c = cfg;
         std::vector<R> tab(6 * (size_t)(c.nx + c.ny));
-        auto fill = [&](R *t, int n) {
-            for (int i = 0; i < n; ++i) {
-                PmlPoint e = pml_point(&c, n, i), h = pml_point(&c, n, i + 0.5);
-                t[i] = (R)e.b;
-                t[n + i] = (R)e.c;
-                t[2 * n + i] = (R)e.ki;
-                t[3 * n + i] = (R)h.b;
-                t[4 * n + i] = (R)h.c;
-                t[5 * n + i] = (R)h.ki;
-            }
-        };
-        fill(tab.data(), c.nx);
-        fill(tab.data() + 6 * c.nx, c.ny);
-        std::vector<R> src(c.nsteps);
-        for (int n = 0; n < c.nsteps; ++n) src[n] = (R)(c.src_amp * c.courant * excitation(&c, (n + 0.5) * dt));
+        fill_pml<R>(c, c.nx, tab.data());
+        fill_pml<R>(c, c.ny, tab.data() + 6 * c.nx);
+        std::vector<R> src = source_table<R>(c, dt);
         const int FR = c.filter_radius;
         std::vector<double> w(2 * FR + 1), nx(geo.dnx), ny(geo.dny);
         for (int k = -FR; k <= FR; ++k) w[k + FR] = FR ? exp(-(double)k * k / (2.0 * c.filter_sigma * c.filter_sigma)) : 1.0;
@@ -312,27 +352,7 @@ struct Ctx2D final : fdtd_ctx {
         return cuda_ok(cudaStreamSynchronize(st));
     }
 
-    Coef<R> coef() const
-    {
-        const fdtd_config &c = cfg;
-        Coef<R> k;
-        const double g = c.gamma_p * gamma_scale * dt;
-        const double kJ = (1.0 - 0.5 * g) / (1.0 + 0.5 * g);
-        const double psi = c.omega_p * c.omega_p * dt * dt;
-        k.S = (R)c.courant;
-        k.eps_s = (R)c.eps_s;
-        k.eps_g = (R)c.eps_g;
-        k.inv_eps_s = (R)(1.0 / c.eps_s);
-        k.inv_eps_g = (R)(1.0 / c.eps_g);
-        k.d_eps = (R)(c.eps_inf - c.eps_s);
-        k.psi = (R)psi;
-        k.psi_s = (R)(c.psi_s_ratio * psi);
-        k.sig_max = (R)(sigma_max * dt / eps0() * (c.sigma_form == FDTD_SIGMA_PEAK_NORMALISED ? 4.0 : 1.0));
-        k.kJ = (R)kJ;
-        k.inv1g = (R)(1.0 / (1.0 + 0.5 * g));
-        k.half1pkJ = (R)(0.5 * (1.0 + kJ));
-        return k;
-    }
+    Coef<R> coef() const { return make_coef<R>(cfg, dt, sigma_max, gamma_scale); }
 
     fdtd_status check_launch() { return cuda_ok(cudaGetLastError()); }
 
@@ -472,6 +492,236 @@ struct Ctx2D final : fdtd_ctx {
     }
 };
 
+// ------------------------------------------------------------------ 3D
+
+template <typename R>
+struct Ctx3D final : fdtd_ctx {
+    Geo3D geo{};
+    State3D<R> F{}, A{};  // updated in place (split H and E launches)
+    char *F_base = nullptr, *A_base = nullptr;
+    size_t state_bytes = 0;
+    long long Mdi = 0;
+    R *rho = nullptr, *rho_t = nullptr, *rstage = nullptr;
+    double *G = nullptr, *gstage = nullptr;
+    R *gap_hist = nullptr, *rec = nullptr, *src_tab = nullptr;
+    char *snaps = nullptr;
+    int nsnap = 0;
+    R *pml_tab = nullptr;
+    Pml3D<R> pm{};
+    double *misc = nullptr;
+    unsigned *err = nullptr;
+
+    void *rho_stage() override { return rstage; }
+    double *grad_stage() override { return gstage; }
+    double *W_dev() override { return misc; }
+    unsigned *err_dev() override { return err; }
+
+    size_t slab_elems(int ax) const
+    {
+        const int np2 = 2 * cfg.npml;
+        if (ax == 0) return (size_t)geo.n[2] * geo.n[1] * np2;
+        if (ax == 1) return (size_t)geo.n[2] * np2 * geo.px;
+        return (size_t)np2 * geo.n[1] * geo.px;
+    }
+
+    void carve_state(Carver &cv, State3D<R> &s, char *&base)
+    {
+        const size_t grid = (size_t)geo.PP * geo.n[2];
+        size_t start = (cv.off + 255) & ~(size_t)255;
+        for (int c = 0; c < 3; ++c) s.E[c] = cv.take<R>(grid);
+        for (int c = 0; c < 3; ++c) s.H[c] = cv.take<R>(grid);
+        for (int c = 0; c < 3; ++c) s.J[c] = cv.take<R>((size_t)Mdi);
+        for (int c = 0; c < 3; ++c)
+            for (int t = 0; t < 2; ++t) {
+                const int ax = (c + 1 + t) % 3;
+                s.pe[c][t] = cv.take<R>(slab_elems(ax));
+                s.ph[c][t] = cv.take<R>(slab_elems(ax));
+            }
+        cv.off = (cv.off + 255) & ~(size_t)255;
+        base = cv.base ? cv.base + start : nullptr;
+        state_bytes = cv.off - start;
+    }
+
+    fdtd_status carve(Carver &cv) override
+    {
+        const fdtd_config &c = cfg;
+        geo.n[0] = c.nx;
+        geo.n[1] = c.ny;
+        geo.n[2] = c.nz;
+        geo.px = (c.nx + 31) / 32 * 32;
+        geo.PP = (long long)geo.px * c.ny;
+        geo.npml = c.npml;
+        for (int a = 0; a < 3; ++a) {
+            geo.d0[a] = c.design_lo[a];
+            geo.dn[a] = c.design_hi[a] - c.design_lo[a];
+            geo.g0[a] = c.gap_lo[a];
+            geo.gn[a] = c.gap_hi[a] - c.gap_lo[a];
+            geo.s0[a] = c.src_lo[a];
+            geo.s1[a] = c.src_hi[a];
+        }
+        geo.dxa = geo.d0[0] & ~3;
+        geo.dp = (geo.d0[0] + geo.dn[0] - geo.dxa + 3) & ~3;
+        Mdi = (long long)geo.dn[2] * geo.dn[1] * geo.dp;
+        geo.Mdi = Mdi;
+        geo.Mg = (int)Mg;
+        geo.src_comp = c.src_comp;
+        geo.sub_hi = c.sub_hi;
+        const long long N = c.nsteps;
+        carve_state(cv, F, F_base);
+        carve_state(cv, A, A_base);
+        rho = cv.take<R>(Md);
+        rho_t = cv.take<R>(Mdi);
+        rstage = cv.take<R>(Md);
+        G = cv.take<double>(Mdi);
+        gstage = cv.take<double>(Md);
+        gap_hist = cv.take<R>((size_t)(N + 1) * 3 * (Mg ? Mg : 1));
+        const long long K = c.snapshot_every;
+        rec = cv.take<R>((size_t)(K > 0 ? std::min<long long>(K, N) : N) * 3 * Mdi);
+        nsnap = K > 0 ? (int)((N + K - 1) / K) : 0;
+        snaps = cv.take<char>((size_t)nsnap * state_bytes);
+        src_tab = cv.take<R>(N);
+        pml_tab = cv.take<R>(6 * (size_t)(c.nx + c.ny + c.nz));
+        misc = cv.take<double>(4);
+        err = cv.take<unsigned>(4);
+        if (pml_tab) {
+            R *t = pml_tab;
+            for (int a = 0; a < 3; ++a) {
+                const int n = geo.n[a];
+                pm.bE[a] = t; pm.cE[a] = t + n; pm.kiE[a] = t + 2 * n;
+                pm.bH[a] = t + 3 * n; pm.cH[a] = t + 4 * n; pm.kiH[a] = t + 5 * n;
+                t += 6 * n;
+            }
+        }
+        return FDTD_OK;
+    }
+
+    fdtd_status upload_tables() override
+    {
+        const fdtd_config &c = cfg;
+        std::vector<R> tab(6 * (size_t)(c.nx + c.ny + c.nz));
+        fill_pml<R>(c, c.nx, tab.data());
+        fill_pml<R>(c, c.ny, tab.data() + 6 * c.nx);
+        fill_pml<R>(c, c.nz, tab.data() + 6 * (c.nx + c.ny));
+        std::vector<R> src = source_table<R>(c, dt);
+        cudaStream_t st = stream;
+        FDTD_TRY(cuda_ok(cudaMemcpyAsync(pml_tab, tab.data(), tab.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
+        FDTD_TRY(cuda_ok(cudaMemcpyAsync(src_tab, src.data(), src.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
+        launch_zero_bytes(err, 4 * sizeof(unsigned), st);
+        ++launches;
+        return cuda_ok(cudaStreamSynchronize(st));
+    }
+
+    Coef<R> coef() const { return make_coef<R>(cfg, dt, sigma_max, gamma_scale); }
+    fdtd_status check_launch() { return cuda_ok(cudaGetLastError()); }
+
+    fdtd_status set_design(const void *d_rho) override
+    {
+        cudaStream_t st = stream;
+        launch_copy_check_rho<R>((const R *)d_rho, rho, Md, err, st);
+        launch_pitch2d<R>(rho, rho_t, geo.dn[0], geo.dn[1] * geo.dn[2], geo.d0[0] - geo.dxa, geo.dp, st);
+        launches += 2;
+        FDTD_TRY(check_launch());
+        unsigned h_err = 0;
+        FDTD_TRY(cuda_ok(cudaMemcpyAsync(&h_err, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st)));
+        FDTD_TRY(cuda_ok(cudaStreamSynchronize(st)));
+        if (h_err & ERR_RANGE) {
+            launch_zero_bytes(err, sizeof(unsigned), st);
+            cudaStreamSynchronize(st);
+            return FDTD_ERANGE;
+        }
+        return FDTD_OK;
+    }
+
+    void advance_forward(const Coef<R> &k, int n0, int count, bool gap, R *rec_base)
+    {
+        Step3D<R> a{};
+        a.rho_t = rho_t;
+        for (int n = n0; n < n0 + count; ++n) {
+            a.src = src_tab + n;
+            a.gap_rec = (gap && Mg) ? gap_hist + (size_t)(n + 1) * 3 * Mg : nullptr;
+            a.rec = rec_base ? rec_base + (size_t)(n - n0) * 3 * Mdi : nullptr;
+            launches += launch_step3d<R>(0, geo, F, k, pm, a, stream);
+        }
+        cell_updates += (long long)count * ncells;
+    }
+
+    void advance_adjoint(const Coef<R> &k, int m_hi, int m_lo, int slot0)
+    {
+        Step3D<R> a{};
+        a.rho_t = rho_t;
+        a.G = G;
+        for (int m = m_hi; m > m_lo; --m) {
+            a.gap_src = Mg ? gap_hist + (size_t)m * 3 * Mg : nullptr;
+            a.rec = rec + (size_t)(m - 1 - slot0) * 3 * Mdi;
+            launches += launch_step3d<R>(1, geo, A, k, pm, a, stream);
+        }
+        cell_updates += (long long)(m_hi - m_lo) * ncells;
+    }
+
+    fdtd_status forward(double *d_W) override
+    {
+        cudaStream_t st = stream;
+        const Coef<R> k = coef();
+        const int N = cfg.nsteps, K = cfg.snapshot_every;
+        launch_zero_bytes(F_base, state_bytes, st);
+        if (Mg) launch_zero_bytes(gap_hist, 3 * Mg * sizeof(R), st);
+        launches += 2;
+        if (K <= 0) {
+            advance_forward(k, 0, N, true, rec);
+        } else {
+            for (int s = 0; s < nsnap; ++s) {
+                const int n0 = s * K, cnt = std::min(K, N - n0);
+                launch_copy_bytes(F_base, snaps + (size_t)s * state_bytes, state_bytes, st);
+                ++launches;
+                advance_forward(k, n0, cnt, true, nullptr);
+            }
+        }
+        const double coefW = 0.5 * cfg.eps_g * dt * pow(cfg.dx, 3);
+        launch_objective<R>(gap_hist, (long long)(N + 1) * 3 * Mg, coefW, misc, d_W, err, st);
+        ++launches;
+        return check_launch();
+    }
+
+    fdtd_status adjoint() override
+    {
+        cudaStream_t st = stream;
+        const Coef<R> k = coef();
+        const int N = cfg.nsteps, K = cfg.snapshot_every;
+        launch_zero_bytes(A_base, state_bytes, st);
+        launch_zero_bytes(G, Mdi * sizeof(double), st);
+        launches += 2;
+        if (K <= 0) {
+            advance_adjoint(k, N, 0, 0);
+        } else {
+            for (int s = nsnap - 1; s >= 0; --s) {
+                const int n0 = s * K, n1 = std::min(n0 + K, N);
+                launch_copy_bytes(snaps + (size_t)s * state_bytes, F_base, state_bytes, st);
+                ++launches;
+                advance_forward(k, n0, n1 - n0, false, rec);
+                advance_adjoint(k, n1, n0, n0);
+            }
+        }
+        return check_launch();
+    }
+
+    fdtd_status gradient(double *d_grad) override
+    {
+        const double scale = dt * pow(cfg.dx, 3);
+        launch_assemble_3d(G, d_grad, geo.dn[0], geo.dn[1], geo.dn[2], geo.d0[0] - geo.dxa, geo.dp,
+                           geo.g0[0] - geo.d0[0], geo.g0[1] - geo.d0[1], geo.g0[2] - geo.d0[2], geo.gn[0], geo.gn[1],
+                           geo.gn[2], scale, stream);
+        ++launches;
+        return check_launch();
+    }
+
+    fdtd_status gap_history(double *d_out) override
+    {
+        launch_to_double<R>(gap_hist, d_out, (long long)(cfg.nsteps + 1) * 3 * Mg, stream);
+        ++launches;
+        return check_launch();
+    }
+};
+
 }  // namespace
 
 // ------------------------------------------------------------------ ABI
@@ -496,8 +746,13 @@ const char *fdtd_status_string(fdtd_status s)
 static fdtd_ctx *make_ctx(const fdtd_config *cfg)
 {
     fdtd_ctx *c = nullptr;
-    if (cfg->real_bytes == 4) c = new (std::nothrow) Ctx2D<float>();
-    else c = new (std::nothrow) Ctx2D<double>();
+    if (cfg->ndim == 3) {
+        if (cfg->real_bytes == 4) c = new (std::nothrow) Ctx3D<float>();
+        else c = new (std::nothrow) Ctx3D<double>();
+    } else {
+        if (cfg->real_bytes == 4) c = new (std::nothrow) Ctx2D<float>();
+        else c = new (std::nothrow) Ctx2D<double>();
+    }
     if (!c) return nullptr;
     c->cfg = *cfg;
     c->dt = cfg->courant * cfg->dx / kC0;
@@ -592,7 +847,8 @@ fdtd_status fdtd_gradient(fdtd_ctx *ctx, double *d_grad, size_t n)
 
 fdtd_status fdtd_gap_history(fdtd_ctx *ctx, double *d_out, size_t n)
 {
-    if (!ctx || !d_out || (long long)n != (long long)(ctx->cfg.nsteps + 1) * ctx->Mg) return FDTD_EINVAL;
+    if (!ctx || !d_out || (long long)n != (long long)(ctx->cfg.nsteps + 1) * ctx->Mg * (ctx->cfg.ndim == 3 ? 3 : 1))
+        return FDTD_EINVAL;
     if (!ctx->fwd_done) return FDTD_ESTATE;
     return ctx->gap_history(d_out);
 }

@@ -47,6 +47,7 @@ template <typename R>
 struct Coef {
     R S;            // Courant number c0 dt / dx
     R eps_s, eps_g, inv_eps_s, inv_eps_g;
+    R eps_sub;      // 3D: background below the substrate plane
     R d_eps;        // eps_inf - eps_s
     R psi, psi_s;   // scaled psi of the metal and of the background
     R sig_max;      // scaled sigma_max, times 4 for the peak-normalised form
@@ -86,6 +87,55 @@ void launch_filter_cols(const T *in, T *out, int w, int h, int R_, const T *wts,
 template <typename R>
 void launch_objective(const R *gap_hist, long long count, double coef, double *W, double *W_user,
                       unsigned *err, cudaStream_t st);
+// ------------------------------------------------------------------ 3D
+
+// Geometry of a 3D Yee grid of n[0] x n[1] x n[2] nodes; rows padded to px
+// nodes, planes of PP = px * n[1] nodes.  Boxes are half-open node ranges.
+// Design-box arrays are pitched: dn[2] x dn[1] rows of dp elements starting
+// at column dxa; Mdi = dn[2] * dn[1] * dp elements per component.
+struct Geo3D {
+    int n[3];
+    int px;
+    long long PP;
+    int npml;
+    int d0[3], dn[3], dxa, dp;
+    long long Mdi;
+    int g0[3], gn[3];
+    int Mg;
+    int s0[3], s1[3], src_comp;
+    int sub_hi;
+};
+
+// One 3D solver state: three E, H and J components (J over the pitched
+// design box), and the CPML terms of component c for its two derivative
+// axes (c+1, c+2 cyclic), each stored in the slabs of that axis.
+template <typename R>
+struct State3D {
+    R *E[3], *H[3], *J[3];
+    R *pe[3][2], *ph[3][2];
+};
+
+template <typename R>
+struct Pml3D {
+    const R *bE[3], *cE[3], *kiE[3], *bH[3], *cH[3], *kiH[3];
+};
+
+template <typename R>
+struct Step3D {
+    const R *rho_t;
+    const R *src;        // forward: source table entry of this step
+    const R *gap_src;    // adjoint: gap rows E^m, [component][M_g]
+    R *gap_rec;          // forward: gap rows receiving E^{n+1} (or null)
+    R *rec;              // forward: design record slot [component][Mdi] (or null);
+                         // adjoint: forward E^m, same layout
+    double *G;           // adjoint: sensitivity accumulator [Mdi]
+};
+
+// H then E half steps of the whole grid, in place (two launches).
+template <typename R>
+int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, const Coef<R> &c, const Pml3D<R> &pm,
+                  const Step3D<R> &a, cudaStream_t st);
+
 // Compact (dnx x dny) <-> pitched (dny rows of dp, box at column off).
 template <typename T>
 void launch_pitch2d(const T *compact, T *pitched, int dnx, int dny, int off, int dp, cudaStream_t st);
@@ -93,6 +143,8 @@ void launch_pitch2d(const T *compact, T *pitched, int dnx, int dny, int off, int
 // to the design box).
 void launch_assemble_2d(const double *G, double *out, int dnx, int dny, int off, int dp, int gx0, int gy0,
                         int gnx, int gny, double scale, cudaStream_t st);
+void launch_assemble_3d(const double *G, double *out, int dx, int dy, int dz, int off, int dp, int gx0, int gy0,
+                        int gz0, int gnx, int gny, int gnz, double scale, cudaStream_t st);
 void launch_zero_gap_2d(double *g, int dnx, int gx0, int gy0, int gnx, int gny, cudaStream_t st);
 template <typename R>
 void launch_to_double(const R *in, double *out, long long n, cudaStream_t st);

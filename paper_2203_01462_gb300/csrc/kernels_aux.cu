@@ -117,6 +117,23 @@ __global__ void k_assemble_2d(const double *G, double *out, int dnx, int dny, in
     }
 }
 
+// 3D: out (compact dx x dy x dz) = scale * G (pitched rows of dp from column
+// off), zero inside the gap box (relative to the design box).
+__global__ void k_assemble_3d(const double *G, double *out, int dx, int dy, int dz, int off, int dp, int gx0, int gy0,
+                              int gz0, int gnx, int gny, int gnz, double scale)
+{
+    const long long n = (long long)dx * dy * dz;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % dx);
+        const long long r = k / dx;  // row index (y + z * dy)
+        const int y = (int)(r % dy), z = (int)(r / dy);
+        const bool gap = (unsigned)(x - gx0) < (unsigned)gnx && (unsigned)(y - gy0) < (unsigned)gny &&
+                         (unsigned)(z - gz0) < (unsigned)gnz;
+        out[k] = gap ? 0.0 : scale * G[r * dp + off + x];
+    }
+}
+
 template <typename T>
 __global__ void k_pitch2d(const T *compact, T *pitched, int dnx, int dny, int off, int dp)
 {
@@ -200,6 +217,13 @@ void launch_assemble_2d(const double *G, double *out, int dnx, int dny, int off,
 {
     k_assemble_2d<<<blocks_for((long long)dnx * dny), TPB, 0, st>>>(G, out, dnx, dny, off, dp, gx0, gy0, gnx, gny,
                                                                    scale);
+}
+
+void launch_assemble_3d(const double *G, double *out, int dx, int dy, int dz, int off, int dp, int gx0, int gy0,
+                        int gz0, int gnx, int gny, int gnz, double scale, cudaStream_t st)
+{
+    k_assemble_3d<<<blocks_for((long long)dx * dy * dz), TPB, 0, st>>>(G, out, dx, dy, dz, off, dp, gx0, gy0, gz0,
+                                                                       gnx, gny, gnz, scale);
 }
 
 template <typename T>
