@@ -62,6 +62,10 @@ typedef enum fdtd_status {
     FDTD_ERANGE = 7      /* a design density outside [0, 1]                    */
 } fdtd_status;
 
+/* Checkpoint storage: FDTD_SNAP_F32 keeps the field precision (lossless);
+ * BF16 / F16 store 16-bit words with one scale per slab of 2048 state words
+ * (lossy: the recomputed forward fields, hence the gradient, carry the
+ * rounding of the restart). */
 enum { FDTD_SNAP_F32 = 0, FDTD_SNAP_BF16 = 1, FDTD_SNAP_F16 = 2 };
 enum { FDTD_ACC_F64 = 0, FDTD_ACC_COMP_F32 = 1 };
 enum { FDTD_SIGMA_PAPER = 0, FDTD_SIGMA_PEAK_NORMALISED = 1 };

@@ -86,7 +86,7 @@ fdtd_status validate(const fdtd_config *c)
     if (!box_inside(c->gap_lo, c->gap_hi, c->design_lo, c->design_hi, c->ndim)) return FDTD_EINVAL;
     if (c->filter_radius < 0 || (c->filter_radius > 0 && !(c->filter_sigma > 0))) return FDTD_EINVAL;
     if (c->snapshot_every < 0) return FDTD_EINVAL;
-    if (c->snapshot_dtype != FDTD_SNAP_F32) return FDTD_EINVAL;
+    if (c->snapshot_dtype < FDTD_SNAP_F32 || c->snapshot_dtype > FDTD_SNAP_F16) return FDTD_EINVAL;
     if (c->accum_kind != FDTD_ACC_F64) return FDTD_EINVAL;
     if (c->sigma_form != FDTD_SIGMA_PAPER && c->sigma_form != FDTD_SIGMA_PEAK_NORMALISED) return FDTD_EINVAL;
     // The step kernels index one array with 32-bit integers.
@@ -167,6 +167,43 @@ fdtd_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? FDTD_OK : FDTD_EC
         if (s__ != FDTD_OK) return s__;      \
     } while (0)
 
+// Bytes of one checkpoint of a state block of `state_bytes` bytes of R
+// words: a plain copy, or 16-bit words plus one float scale per slab (each
+// part 256-byte aligned).
+template <typename R>
+size_t snapshot_bytes(int dtype, size_t state_bytes)
+{
+    if (dtype == FDTD_SNAP_F32) return state_bytes;
+    const long long n = (long long)(state_bytes / sizeof(R));
+    const size_t words = ((size_t)n * 2 + 255) & ~(size_t)255;
+    const size_t scales = ((size_t)((n + SNAP_SLAB - 1) / SNAP_SLAB) * 4 + 255) & ~(size_t)255;
+    return words + scales;
+}
+
+template <typename R>
+void snapshot_save(int dtype, const char *state, size_t state_bytes, char *snap, cudaStream_t st)
+{
+    if (dtype == FDTD_SNAP_F32) {
+        launch_copy_bytes(state, snap, state_bytes, st);
+        return;
+    }
+    const long long n = (long long)(state_bytes / sizeof(R));
+    const size_t words = ((size_t)n * 2 + 255) & ~(size_t)255;
+    launch_snap_pack<R>(dtype, (const R *)state, snap, (float *)(snap + words), n, st);
+}
+
+template <typename R>
+void snapshot_load(int dtype, const char *snap, char *state, size_t state_bytes, cudaStream_t st)
+{
+    if (dtype == FDTD_SNAP_F32) {
+        launch_copy_bytes(snap, state, state_bytes, st);
+        return;
+    }
+    const long long n = (long long)(state_bytes / sizeof(R));
+    const size_t words = ((size_t)n * 2 + 255) & ~(size_t)255;
+    launch_snap_unpack<R>(dtype, snap, (const float *)(snap + words), (R *)state, n, st);
+}
+
 // Step-invariant coefficients in the scaled units of Coef.
 template <typename R>
 Coef<R> make_coef(const fdtd_config &c, double dt, double sigma_max, double gamma_scale)
@@ -228,6 +265,7 @@ struct Ctx2D final : fdtd_ctx {
     double *G = nullptr, *gtmp = nullptr, *gtmp2 = nullptr, *gstage = nullptr;
     R *gap_hist = nullptr, *rec = nullptr, *src_tab = nullptr;
     char *snaps = nullptr;
+    size_t snap_stride = 0;
     int nsnap = 0;
     R *pml_tab = nullptr;  // x: 6 * nx, then y: 6 * ny
     Pml1D<R> px{}, py{};
@@ -296,7 +334,8 @@ struct Ctx2D final : fdtd_ctx {
         const long long K = c.snapshot_every;
         rec = cv.take<R>((size_t)(K > 0 ? std::min<long long>(K, N) : N) * Mdi);
         nsnap = K > 0 ? (int)((N + K - 1) / K) : 0;
-        snaps = cv.take<char>((size_t)nsnap * state_bytes);
+        snap_stride = snapshot_bytes<R>(c.snapshot_dtype, state_bytes);
+        snaps = cv.take<char>((size_t)nsnap * snap_stride);
         src_tab = cv.take<R>(N);
         pml_tab = cv.take<R>(6 * (size_t)(c.nx + c.ny));
         const int FR = c.filter_radius;
@@ -422,15 +461,18 @@ struct Ctx2D final : fdtd_ctx {
         const Coef<R> k = coef();
         const int N = cfg.nsteps, K = cfg.snapshot_every;
         curF = 0;
+        // Both buffers of the pair: padding words are never written by the
+        // step kernel, and 16-bit checkpoints scale by the slab maximum.
         launch_zero_bytes(F_base[0], state_bytes, st);
+        launch_zero_bytes(F_base[1], state_bytes, st);
         if (Mg) launch_zero_bytes(gap_hist, Mg * sizeof(R), st);
-        launches += 2;
+        launches += 3;
         if (K <= 0) {
             advance_forward(k, 0, N, true, rec);
         } else {
             for (int s = 0; s < nsnap; ++s) {
                 const int n0 = s * K, cnt = std::min(K, N - n0);
-                launch_copy_bytes(F_base[curF], snaps + (size_t)s * state_bytes, state_bytes, st);
+                snapshot_save<R>(cfg.snapshot_dtype, F_base[curF], state_bytes, snaps + (size_t)s * snap_stride, st);
                 ++launches;
                 advance_forward(k, n0, cnt, true, nullptr);
             }
@@ -448,6 +490,7 @@ struct Ctx2D final : fdtd_ctx {
         const int N = cfg.nsteps, K = cfg.snapshot_every;
         curA = 0;
         launch_zero_bytes(A_base[0], state_bytes, st);
+        launch_zero_bytes(A_base[1], state_bytes, st);
         launch_zero_bytes(G, Mdi * sizeof(double), st);
         launches += 2;
         if (K <= 0) {
@@ -455,7 +498,7 @@ struct Ctx2D final : fdtd_ctx {
         } else {
             for (int s = nsnap - 1; s >= 0; --s) {
                 const int n0 = s * K, n1 = std::min(n0 + K, N);
-                launch_copy_bytes(snaps + (size_t)s * state_bytes, F_base[curF], state_bytes, st);
+                snapshot_load<R>(cfg.snapshot_dtype, snaps + (size_t)s * snap_stride, F_base[curF], state_bytes, st);
                 ++launches;
                 advance_forward(k, n0, n1 - n0, false, rec);
                 advance_adjoint(k, n1, n0, n0);
@@ -505,6 +548,7 @@ struct Ctx3D final : fdtd_ctx {
     double *G = nullptr, *gstage = nullptr;
     R *gap_hist = nullptr, *rec = nullptr, *src_tab = nullptr;
     char *snaps = nullptr;
+    size_t snap_stride = 0;
     int nsnap = 0;
     R *pml_tab = nullptr;
     Pml3D<R> pm{};
@@ -578,7 +622,8 @@ struct Ctx3D final : fdtd_ctx {
         const long long K = c.snapshot_every;
         rec = cv.take<R>((size_t)(K > 0 ? std::min<long long>(K, N) : N) * 3 * Mdi);
         nsnap = K > 0 ? (int)((N + K - 1) / K) : 0;
-        snaps = cv.take<char>((size_t)nsnap * state_bytes);
+        snap_stride = snapshot_bytes<R>(c.snapshot_dtype, state_bytes);
+        snaps = cv.take<char>((size_t)nsnap * snap_stride);
         src_tab = cv.take<R>(N);
         pml_tab = cv.take<R>(6 * (size_t)(c.nx + c.ny + c.nz));
         misc = cv.take<double>(4);
@@ -671,7 +716,7 @@ struct Ctx3D final : fdtd_ctx {
         } else {
             for (int s = 0; s < nsnap; ++s) {
                 const int n0 = s * K, cnt = std::min(K, N - n0);
-                launch_copy_bytes(F_base, snaps + (size_t)s * state_bytes, state_bytes, st);
+                snapshot_save<R>(cfg.snapshot_dtype, F_base, state_bytes, snaps + (size_t)s * snap_stride, st);
                 ++launches;
                 advance_forward(k, n0, cnt, true, nullptr);
             }
@@ -695,7 +740,7 @@ struct Ctx3D final : fdtd_ctx {
         } else {
             for (int s = nsnap - 1; s >= 0; --s) {
                 const int n0 = s * K, n1 = std::min(n0 + K, N);
-                launch_copy_bytes(snaps + (size_t)s * state_bytes, F_base, state_bytes, st);
+                snapshot_load<R>(cfg.snapshot_dtype, snaps + (size_t)s * snap_stride, F_base, state_bytes, st);
                 ++launches;
                 advance_forward(k, n0, n1 - n0, false, rec);
                 advance_adjoint(k, n1, n0, n0);

@@ -149,6 +149,14 @@ void launch_zero_gap_2d(double *g, int dnx, int gx0, int gy0, int gnx, int gny, 
 template <typename R>
 void launch_to_double(const R *in, double *out, long long n, cudaStream_t st);
 void launch_copy_bytes(const void *src, void *dst, size_t bytes, cudaStream_t st);
+
+// 16-bit checkpoints (kind 1: BF16, 2: FP16) with one float scale per slab
+// of SNAP_SLAB consecutive words of the state block.
+constexpr long long SNAP_SLAB = 2048;
+template <typename R>
+void launch_snap_pack(int kind, const R *src, void *dst, float *scales, long long n, cudaStream_t st);
+template <typename R>
+void launch_snap_unpack(int kind, const void *src, const float *scales, R *dst, long long n, cudaStream_t st);
 void launch_zero_bytes(void *dst, size_t bytes, cudaStream_t st);
 
 }  // namespace fdtd

@@ -1,6 +1,9 @@
 // Auxiliary kernels: design upload and range check, the Gaussian design
 // filter and its transpose (Eq. 26, 27), the objective reduction (Eq. 24),
 // gradient assembly, and plain copies for checkpoints.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "fdtd_internal.h"
 
 namespace fdtd {
@@ -183,7 +186,68 @@ __global__ void k_zero_bytes(uint4 *dst, size_t n16, unsigned char *d8, size_t t
         d8[k] = 0;
 }
 
+// 16-bit checkpoint of a state block: slabs of SLAB consecutive words, one
+// warp per slab.  The warp finds max |x| (shuffle reduction), picks a scale
+// (FP16: the maximum maps to 2^15, keeping small values out of the subnormal
+// range; BF16: the maximum maps to 1) and stores x * scale.  Restoring
+// divides by the scale.
+template <typename T> __device__ __forceinline__ T to16(float v);
+template <> __device__ __forceinline__ __half to16<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ float from16(__half v) { return __half2float(v); }
+__device__ __forceinline__ float from16(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename T> __device__ __forceinline__ float target_max();
+template <> __device__ __forceinline__ float target_max<__half>() { return 32768.0f; }
+template <> __device__ __forceinline__ float target_max<__nv_bfloat16>() { return 1.0f; }
+
+template <typename R, typename T>
+__global__ void k_snap_pack(const R *src, T *dst, float *scales, long long n)
+{
+    const long long nslab = (n + SNAP_SLAB - 1) / SNAP_SLAB;
+    const int lane = threadIdx.x & 31;
+    for (long long sl = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; sl < nslab;
+         sl += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const long long b = sl * SNAP_SLAB, e = min(b + SNAP_SLAB, n);
+        float m = 0.0f;
+        for (long long k = b + lane; k < e; k += 32) m = fmaxf(m, fabsf((float)src[k]));
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        // A slab whose largest word is below 1e-30 keeps scale 1 (its words
+        // round to zero) so that the scale cannot overflow.
+        const float sc = m > 1e-30f ? target_max<T>() / m : 1.0f;
+        if (lane == 0) scales[sl] = sc;
+        for (long long k = b + lane; k < e; k += 32) dst[k] = to16<T>((float)src[k] * sc);
+    }
+}
+
+template <typename R, typename T>
+__global__ void k_snap_unpack(const T *src, const float *scales, R *dst, long long n)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        dst[k] = (R)(from16(src[k]) / scales[k / SNAP_SLAB]);
+}
+
 }  // namespace
+
+template <typename R>
+void launch_snap_pack(int kind, const R *src, void *dst, float *scales, long long n, cudaStream_t st)
+{
+    const int blocks = blocks_for(((n + SNAP_SLAB - 1) / SNAP_SLAB) * 32);
+    if (kind == 2) k_snap_pack<R, __half><<<blocks, TPB, 0, st>>>(src, (__half *)dst, scales, n);
+    else k_snap_pack<R, __nv_bfloat16><<<blocks, TPB, 0, st>>>(src, (__nv_bfloat16 *)dst, scales, n);
+}
+
+template <typename R>
+void launch_snap_unpack(int kind, const void *src, const float *scales, R *dst, long long n, cudaStream_t st)
+{
+    if (kind == 2) k_snap_unpack<R, __half><<<blocks_for(n), TPB, 0, st>>>((const __half *)src, scales, dst, n);
+    else k_snap_unpack<R, __nv_bfloat16><<<blocks_for(n), TPB, 0, st>>>((const __nv_bfloat16 *)src, scales, dst, n);
+}
+
+template void launch_snap_pack<float>(int, const float *, void *, float *, long long, cudaStream_t);
+template void launch_snap_pack<double>(int, const double *, void *, float *, long long, cudaStream_t);
+template void launch_snap_unpack<float>(int, const void *, const float *, float *, long long, cudaStream_t);
+template void launch_snap_unpack<double>(int, const void *, const float *, double *, long long, cudaStream_t);
 
 template <typename R>
 void launch_copy_check_rho(const R *src, R *dst, long long n, unsigned *err, cudaStream_t st)
