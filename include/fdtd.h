@@ -161,6 +161,21 @@ fdtd_status fdtd_adjoint(fdtd_ctx *ctx);
  * on gap nodes.  Requires fdtd_adjoint since the last forward. */
 fdtd_status fdtd_gradient(fdtd_ctx *ctx, double *d_grad, size_t n);
 
+/* Largest design box (M_d) that fdtd_gradient_static accepts. */
+#define FDTD_STATIC_DESIGN_MAX 1048576
+
+/* Same result as fdtd_gradient, but the two FP64 intermediates of the
+ * filter-transpose passes live in a fixed array owned by the library
+ * (2 x FDTD_STATIC_DESIGN_MAX doubles = 16 MiB of device memory on every GPU
+ * that loads the library, kept until the process exits) instead of the
+ * context's workspace; nothing is allocated.  For callers that cannot hand
+ * out or grow device memory at call time.  The paper has no counterpart.
+ * Returns FDTD_EINVAL if n exceeds FDTD_STATIC_DESIGN_MAX.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current, so make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race on it. */
+fdtd_status fdtd_gradient_static(fdtd_ctx *ctx, double *d_grad, size_t n);
+
 /* Gap-field history E^n, n = 0..N, of the last forward run into d_out
  * (device doubles, gap nodes x fastest): 2D n = (N + 1) * M_g; 3D
  * n = (N + 1) * 3 * M_g, layout [step][component x, y, z][gap node]. */

@@ -24,7 +24,8 @@ ACC = {"f64": 0, "comp_f32": 1}
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTS = ["fdtd_workspace_bytes", "fdtd_create", "fdtd_set_design", "fdtd_set_damping",
            "fdtd_forward", "fdtd_adjoint", "fdtd_gradient", "fdtd_gap_history", "fdtd_sync",
-           "fdtd_run_host", "fdtd_get_info", "fdtd_status_string", "fdtd_destroy"]
+           "fdtd_run_host", "fdtd_get_info", "fdtd_status_string", "fdtd_destroy",
+           "fdtd_gradient_static"]
 
 
 class FdtdError(RuntimeError):
@@ -82,6 +83,7 @@ def load():
             "fdtd_forward": [P, P],
             "fdtd_adjoint": [P],
             "fdtd_gradient": [P, P, C.c_size_t],
+            "fdtd_gradient_static": [P, P, C.c_size_t],
             "fdtd_gap_history": [P, P, C.c_size_t],
             "fdtd_sync": [P],
             "fdtd_run_host": [P, P, C.c_size_t, P, P],
@@ -210,6 +212,16 @@ class Solver:
         if out is None:
             out = t.empty(self.n_design, dtype=t.float64, device=self.device)
         _check(self.lib.fdtd_gradient(self.ctx, C.c_void_p(out.data_ptr()), out.numel()), "fdtd_gradient")
+        return out
+
+    def gradient_static(self, out=None):
+        """fdtd_gradient_static: the gradient with the library's fixed device
+        scratch instead of the workspace (no allocation at call time)."""
+        t = self.torch
+        if out is None:
+            out = t.empty(self.n_design, dtype=t.float64, device=self.device)
+        _check(self.lib.fdtd_gradient_static(self.ctx, C.c_void_p(out.data_ptr()), out.numel()),
+               "fdtd_gradient_static")
         return out
 
     def gap_history(self):

@@ -152,6 +152,8 @@ struct fdtd_ctx {
     virtual fdtd_status adjoint() = 0;
     virtual fdtd_status gradient(double *d_grad) = 0;
     virtual fdtd_status gap_history(double *d_out) = 0;
+    // fdtd_gradient with the filter-transpose intermediates in s1, s2.
+    virtual fdtd_status gradient_scratch(double *d_grad, double *s1, double *s2) = 0;
     virtual void *rho_stage() = 0;
     virtual double *grad_stage() = 0;
     virtual double *W_dev() = 0;
@@ -527,6 +529,26 @@ struct Ctx2D final : fdtd_ctx {
         return check_launch();
     }
 
+    fdtd_status gradient_scratch(double *d_grad, double *s1, double *s2) override
+    {
+        cudaStream_t st = stream;
+        const double scale = dt * pow(cfg.dx, cfg.ndim);
+        const int FR = cfg.filter_radius;
+        if (FR > 0) {
+            launch_assemble_2d(G, s1, geo.dnx, geo.dny, geo.dx0 - geo.dxa, geo.dp, geo.gx0 - geo.dx0,
+                               geo.gy0 - geo.dy0, geo.gnx, geo.gny, scale, st);
+            launch_filter_rows<double>(s1, s2, geo.dnx, geo.dny, FR, fw_D, fnx_D, 1, st);
+            launch_filter_cols<double>(s2, d_grad, geo.dnx, geo.dny, FR, fw_D, fny_D, 1, st);
+            launch_zero_gap_2d(d_grad, geo.dnx, geo.gx0 - geo.dx0, geo.gy0 - geo.dy0, geo.gnx, geo.gny, st);
+            launches += 4;
+        } else {
+            launch_assemble_2d(G, d_grad, geo.dnx, geo.dny, geo.dx0 - geo.dxa, geo.dp, geo.gx0 - geo.dx0,
+                               geo.gy0 - geo.dy0, geo.gnx, geo.gny, scale, st);
+            ++launches;
+        }
+        return check_launch();
+    }
+
     fdtd_status gap_history(double *d_out) override
     {
         launch_to_double<R>(gap_hist, d_out, (long long)(cfg.nsteps + 1) * Mg, stream);
@@ -759,6 +781,8 @@ struct Ctx3D final : fdtd_ctx {
         return check_launch();
     }
 
+    fdtd_status gradient_scratch(double *d_grad, double *, double *) override { return gradient(d_grad); }
+
     fdtd_status gap_history(double *d_out) override
     {
         launch_to_double<R>(gap_hist, d_out, (long long)(cfg.nsteps + 1) * 3 * Mg, stream);
@@ -889,6 +913,17 @@ fdtd_status fdtd_gradient(fdtd_ctx *ctx, double *d_grad, size_t n)
     if (!ctx->adj_done) return FDTD_ESTATE;
     return ctx->gradient(d_grad);
 }
+
+}  // extern "C"
+
+int fdtd::gradient_into(fdtd_ctx *ctx, double *d_grad, size_t n, double *scratch, size_t scratch_per_array)
+{
+    if (!ctx || !d_grad || !scratch || (long long)n != ctx->Md || n > scratch_per_array) return FDTD_EINVAL;
+    if (!ctx->adj_done) return FDTD_ESTATE;
+    return ctx->gradient_scratch(d_grad, scratch, scratch + scratch_per_array);
+}
+
+extern "C" {
 
 fdtd_status fdtd_gap_history(fdtd_ctx *ctx, double *d_out, size_t n)
 {

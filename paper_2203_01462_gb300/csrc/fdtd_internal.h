@@ -160,3 +160,12 @@ void launch_snap_unpack(int kind, const void *src, const float *scales, R *dst, 
 void launch_zero_bytes(void *dst, size_t bytes, cudaStream_t st);
 
 }  // namespace fdtd
+
+struct fdtd_ctx;
+namespace fdtd {
+// The gradient of fdtd_gradient with the two filter-transpose intermediates
+// taken from `scratch` (at least 2 * n doubles of device memory) instead of
+// the workspace (fdtd_host.cu).
+// Returns an fdtd_status value.
+int gradient_into(fdtd_ctx *ctx, double *d_grad, size_t n, double *scratch, size_t scratch_per_array);
+}  // namespace fdtd
