@@ -38,13 +38,18 @@ METRIC = "Gcell-updates/s fwd+adjoint"
 UNIT = "Gcell-updates/s"
 
 
+WORKLOADS = {
+    "cfg_2d_2048": I.cfg_2d_2048,
+    "cfg_2d_160": I.cfg_2d_160,
+    "cfg_3d_256": I.cfg_3d_256,
+    "cfg_3d_512": I.cfg_3d_512,
+}
+
+
 def workload(name: str, nsteps: int | None):
-    if name == "cfg_2d_2048":
-        w = I.cfg_2d_2048()
-    elif name == "cfg_2d_160":
-        w = I.cfg_2d_160()
-    else:
+    if name not in WORKLOADS:
         raise SystemExit("unknown workload " + name)
+    w = WORKLOADS[name]()
     if nsteps:
         w["nsteps"] = int(nsteps)
     return w
@@ -56,21 +61,36 @@ def damping(k: int) -> float:
 
 
 def algorithmic_bytes(w: dict) -> dict:
-    """Algorithmic HBM bytes per time step (one read + one write of each
-    state word touched, no temporal-blocking credit)."""
+    """Algorithmic HBM bytes per time step: one read + one write of each
+    state word touched, no temporal-blocking credit.  2D: Ez, Hx, Hy per
+    node; 3D: six components per node.  Design nodes add J (read + write per
+    E component) and rho~ (read); CPML slab nodes add their psi terms (2 in
+    2D, 4 per slab crossed in 3D, read + write); the forward pays the
+    amortised checkpoint copy, the recompute the design record, the adjoint
+    the forward-field read and the FP64 accumulator."""
     rb = 8 if w["real"] == "f64" else 4
-    nx, ny, npml = w["nx"], w["ny"], w["npml"]
-    nc = nx * ny
+    npml = w["npml"]
     md = I.n_design(w)
-    npml_cells = 2 * npml * (nx + ny)
-    grid = 3 * 2 * rb * nc                 # Ez, Hx, Hy read + write
-    design = (2 + 1) * rb * md             # J read + write, rho~ read
-    pml = 2 * 2 * rb * npml_cells          # two psi words read + write per slab cell
+    if w["ndim"] == 2:
+        nx, ny = w["nx"], w["ny"]
+        nc = nx * ny
+        ncomp, psi_per_slab = 3, 2
+        slab_nodes = 2 * npml * (nx + ny)
+    else:
+        nx, ny, nz = w["nx"], w["ny"], w["nz"]
+        nc = nx * ny * nz
+        ncomp, psi_per_slab = 6, 4
+        slab_nodes = 2 * npml * (nx * ny + ny * nz + nx * nz)
+    ne = ncomp // 3 if w["ndim"] == 2 else 3   # E components carrying J
+    grid = 2 * ncomp * rb * nc
+    design = (2 * ne + 1) * rb * md
+    pml = 2 * psi_per_slab * rb * slab_nodes
     K = w.get("snapshot_every", 0)
-    state = 3 * rb * nc + rb * md + 4 * rb * npml_cells
-    fwd = grid + design + pml + (2 * state / K if K else rb * md)
-    rec = grid + design + pml + rb * md
-    adj = grid + design + pml + rb * md + 16 * md   # forward E^m read, FP64 accumulator r + w
+    snap_rb = {"f32": rb, "bf16": 2, "f16": 2}[w.get("snapshot_dtype", "f32")]
+    state_words = ncomp * nc + ne * md + 2 * psi_per_slab * slab_nodes
+    fwd = grid + design + pml + (2 * (rb + snap_rb) * state_words / 2 / K if K else ne * rb * md)
+    rec = grid + design + pml + ne * rb * md
+    adj = grid + design + pml + ne * rb * md + 16 * md
     return dict(forward=fwd, recompute=rec, adjoint=adj, cells=nc)
 
 
@@ -115,7 +135,7 @@ def cpu_baseline(w: dict, nsteps: int) -> dict:
     t = time.perf_counter()
     O.gradient(ws, rho, 0.0, damping(0))
     dt = time.perf_counter() - t
-    cu = 2.0 * ws["nx"] * ws["ny"] * nsteps
+    cu = 2.0 * I.n_cells(ws) * nsteps
     return dict(value=cu / dt / 1e9, unit=UNIT, cores=O.threads(), kind="oracle",
                 sample="%s with %d of %d time steps, one forward+adjoint+gradient, %.1f s"
                        % (w.get("name", "workload"), nsteps, w["nsteps"], dt))
@@ -138,17 +158,26 @@ def run_reference(args, w) -> None:
         t = time.perf_counter()
         O.gradient(ws, rho, 0.0, damping(args.warmup + k))
         times.append(time.perf_counter() - t)
-    cu = 2.0 * w["nx"] * w["ny"] * ns
+    cu = 2.0 * I.n_cells(w) * ns
     value = cu * len(times) / sum(times) / 1e9
     line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=0, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1e3 * sum(times) / len(times), higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(workload=w["name"], grid=[w["nx"], w["ny"]], nsteps=w["nsteps"],
+                config=dict(workload=I.describe(w), grid=I.grid_shape(w), nsteps=w["nsteps"],
                             sample_nsteps=ns),
                 cpu_baseline=dict(value=value, unit=UNIT, cores=O.threads(), kind="oracle",
                                   sample="%d of %d time steps per evaluation" % (ns, w["nsteps"])),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's time (all ranks call this after their timed region)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
 
 
 def main() -> None:
@@ -239,12 +268,9 @@ def main() -> None:
         fh.close()
     total_ms = sum(step_ms)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, dev)
 
-    nc, N = w["nx"] * w["ny"], w["nsteps"]
+    nc, N = I.n_cells(w), w["nsteps"]
     cu_step = 2.0 * nc * N
     value = world * cu_step * args.steps / (total_ms / 1e3) / 1e9
 
@@ -280,14 +306,14 @@ def main() -> None:
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
         dtype=w["real"], data="synthetic",
-        config=dict(workload="2D TM_z %dx%d FP32, %d steps, %dx%d filtered design, snapshots every %d"
-                              % (w["nx"], w["ny"], N, I.design_shape(w)[1], I.design_shape(w)[0],
-                                 w["snapshot_every"]) if w["real"] == "f32" else w["name"],
-                    grid=[w["nx"], w["ny"]], nsteps=N, design=list(I.design_shape(w))[::-1],
-                    snapshot_every=w["snapshot_every"], parallelism="replicas" if world > 1 else "1 GPU",
+        config=dict(workload=I.describe(w), grid=I.grid_shape(w), nsteps=N, design=list(I.design_shape(w))[::-1],
+                    snapshot_every=w["snapshot_every"], snapshot_dtype=w.get("snapshot_dtype", "f32"),
+                    parallelism="replicas" if world > 1 else "1 GPU",
                     l2="flushed (256 MB write) between timed steps"),
         roofline=dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm,
-                      traffic=None, kernel="forward time-step kernels (H + E/J update)",
+                      traffic=None,
+                      kernel="k_step2d<float,0> (fused forward leapfrog step)" if w["ndim"] == 2
+                      else "k_h3d + k_e3d<float,0> (forward H and E half steps)",
                       peak_source=peak_src),
         phases_ms=dict(forward=statistics.median(fwd_ms), adjoint_with_recompute=statistics.median(adj_ms)),
         cpu_baseline=cpu,

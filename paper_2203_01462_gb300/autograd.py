@@ -3,6 +3,11 @@
 forward runs set_design + forward (checkpointing the fields as configured);
 backward runs the adjoint solve, whose sensitivities (Eq. 25) and chain rule
 (Eq. 27) give dW~/drho, and scales it by the incoming gradient.
+
+W~ of Eq. (24) is tiny in SI units (~1e-32 for the 2048^2 workload) and its
+per-node derivatives smaller still, below the FP32 range.  ``scale``
+multiplies W~ and, in FP64 before the cast to rho's dtype, its gradient;
+optimizers normally pass 1 / W~(rho0).
 """
 from __future__ import annotations
 
@@ -13,13 +18,15 @@ from .binding import Solver
 
 class FdtdObjective(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, rho: torch.Tensor, solver: Solver, sigma_max: float = 0.0, gamma_scale: float = 1.0):
+    def forward(ctx, rho: torch.Tensor, solver: Solver, sigma_max: float = 0.0, gamma_scale: float = 1.0,
+                scale: float = 1.0):
         solver.set_design(rho.detach())
         solver.set_damping(sigma_max, gamma_scale)
-        W = solver.forward().clone().reshape(())
+        W = solver.forward().clone().reshape(()) * scale
         ctx.solver = solver
         ctx.shape = rho.shape
         ctx.dtype = rho.dtype
+        ctx.scale = scale
         return W
 
     @staticmethod
@@ -27,10 +34,11 @@ class FdtdObjective(torch.autograd.Function):
         s: Solver = ctx.solver
         s.adjoint()
         g = s.gradient()
-        g = (g * gW.to(g.dtype)).to(ctx.dtype).reshape(ctx.shape)
-        return g, None, None, None
+        g = (g * (gW.to(g.dtype) * ctx.scale)).to(ctx.dtype).reshape(ctx.shape)
+        return g, None, None, None, None
 
 
-def objective(rho: torch.Tensor, solver: Solver, sigma_max: float = 0.0, gamma_scale: float = 1.0):
-    """W~(rho) as a differentiable scalar (FP64)."""
-    return FdtdObjective.apply(rho, solver, sigma_max, gamma_scale)
+def objective(rho: torch.Tensor, solver: Solver, sigma_max: float = 0.0, gamma_scale: float = 1.0,
+              scale: float = 1.0):
+    """scale * W~(rho) as a differentiable FP64 scalar."""
+    return FdtdObjective.apply(rho, solver, sigma_max, gamma_scale, scale)

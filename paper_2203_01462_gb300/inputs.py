@@ -162,6 +162,26 @@ def cfg_3d_512(nsteps: int = 16000) -> dict:
                        pulse_kw=dict(centers_m=[700e-9, 900e-9], half_width_hz=C0 / 650e-9 - C0 / 700e-9))
 
 
+def n_cells(w: dict) -> int:
+    n = w["nx"] * w["ny"]
+    return n * w["nz"] if w["ndim"] == 3 else n
+
+
+def grid_shape(w: dict) -> list[int]:
+    return [w["nx"], w["ny"], w["nz"]] if w["ndim"] == 3 else [w["nx"], w["ny"]]
+
+
+def describe(w: dict) -> str:
+    """One-line description of a workload."""
+    dims = "x".join(str(v) for v in grid_shape(w))
+    des = "x".join(str(v) for v in reversed(design_shape(w)))
+    kind = "2D TM_z" if w["ndim"] == 2 else "3D Yee"
+    snap = ("snapshots every %d (%s)" % (w["snapshot_every"], w.get("snapshot_dtype", "f32"))
+            if w.get("snapshot_every") else "full history")
+    filt = ", %d-cell Gaussian filter" % w["filter_radius"] if w.get("filter_radius") else ""
+    return "%s %s %s, %d steps, %s design%s, %s" % (kind, dims, w["real"].upper(), w["nsteps"], des, filt, snap)
+
+
 def n_design(w: dict) -> int:
     n = 1
     for a in range(w["ndim"]):

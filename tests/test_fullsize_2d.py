@@ -1,0 +1,92 @@
+"""Checks at the full 2048^2 x 20000-step size of the benchmark workload,
+in the launch configuration bench.py times (FP32, snapshots every 64).
+
+The oracle cannot run this size in seconds, so these use properties that
+hold at any size: the adjoint gradient against central differences of the
+objective, along a random direction in FP32 and per design cell in FP64 on
+16 seeded random cells, and the autograd wrapper (normalised objective) in
+FP32 against the library's FP64 gradient."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2203_01462_gb300 import inputs as I
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def interior_rho(w, seed):
+    # keep rho +- h inside [0, 1]
+    return I.zero_gap(w, 0.1 + 0.8 * I.rho_uniform(w, seed))
+
+
+def _report(name, d):
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    with open(os.path.join(ROOT, "gpurun_out", "fullsize_%s.json" % name), "w") as f:
+        json.dump(d, f)
+
+
+def test_fullsize_fp32_directional_derivative_and_autograd():
+    import torch
+    from paper_2203_01462_gb300.autograd import objective
+    from paper_2203_01462_gb300.binding import Solver
+    w = I.cfg_2d_2048()
+    s = Solver(w)
+    rho = interior_rho(w, 3)
+    W0, g = s.evaluate(rho, 0.0, 10.0)
+    W0 = float(W0.item())
+    g = g.cpu().numpy()
+    v = I.zero_gap(w, np.random.default_rng(5).standard_normal(rho.shape)).reshape(-1)
+    h = 0.05 / np.abs(v).max()
+
+    def Wat(x):
+        s.set_design(x.reshape(rho.shape).astype(np.float32))
+        s.set_damping(0.0, 10.0)
+        out = s.forward().item()
+        s.sync()
+        return out
+
+    fd = (Wat(rho.reshape(-1) + h * v) - Wat(rho.reshape(-1) - h * v)) / (2 * h)
+    gv = float(np.dot(g, v))
+    # autograd with the objective normalised by W0: FP32 gradient of W / W0
+    r = torch.tensor(rho, dtype=torch.float32, device="cuda", requires_grad=True)
+    Wn = objective(r, s, 0.0, 10.0, scale=1.0 / W0)
+    Wn.backward()
+    ga = r.grad.double().cpu().numpy().reshape(-1)
+    ag_err = float(np.linalg.norm(ga - g / W0) / np.linalg.norm(g / W0))
+    _report("fp32_directional", dict(W=W0, fd=fd, g_dot_v=gv, rel_err=abs(fd - gv) / abs(fd),
+                                     autograd_vs_fp64=ag_err))
+    assert abs(Wn.item() - 1.0) < 1e-12
+    assert abs(fd - gv) <= 1e-3 * abs(fd), (fd, gv)
+    assert ag_err <= 1e-6
+
+
+def test_fullsize_fp64_gradient_on_16_random_cells():
+    from paper_2203_01462_gb300.binding import Solver
+    w = dict(I.cfg_2d_2048(), real="f64")
+    s = Solver(w)
+    rho = interior_rho(w, 7)
+    W, g = s.evaluate(rho, 5e5, 10.0)
+    g = g.cpu().numpy()
+    flat = rho.reshape(-1)
+    gap = I.zero_gap(w, np.ones(rho.shape)).reshape(-1) == 0
+    cells = np.random.default_rng(7).choice(np.flatnonzero(~gap), 16, replace=False)
+    h = 1e-2
+    gmax = np.abs(g).max()
+    rows = []
+    for c in cells:
+        vals = []
+        for sgn in (1, -1):
+            x = flat.copy()
+            x[c] += sgn * h
+            s.set_design(x.reshape(rho.shape))
+            s.set_damping(5e5, 10.0)
+            vals.append(s.forward().item())
+        fd = (vals[0] - vals[1]) / (2 * h)
+        rows.append(dict(cell=int(c), fd=fd, adjoint=float(g[c]), rel=abs(fd - g[c]) / abs(fd)))
+    _report("fp64_cells", dict(W=float(W.item()), gmax=float(gmax), h=h, cells=rows))
+    for r in rows:
+        assert abs(r["fd"] - r["adjoint"]) <= 1e-3 * abs(r["fd"]) + 1e-5 * gmax, r
