@@ -8,7 +8,9 @@
 // Eq. (10a,b) per component (J and sigma E averaged over the step, scaled
 // units, see Coef).  Curl component c uses the cyclic axes a = c+1, b = c+2:
 // curl_c = d_a F_b - d_b F_a, each derivative with its own CPML term in the
-// slab of its axis.  One thread per node, threads consecutive along x.
+// slab of its axis.  Tiles of 32 x 8 x 4 nodes clear of walls and CPML
+// (halo included) run vector kernels with the curls written out; the other
+// nodes run generic one-node-per-thread kernels with CPML.
 //
 // Every E component of a node inside the design box takes the material of
 // rho~ at that node (Eq. 5); the adjoint sums the Eq. (25) brackets of the
@@ -19,11 +21,45 @@ namespace fdtd {
 
 namespace {
 
+// Generic (border) kernels: one node per thread.
 constexpr int BX = 32, BY = 4, BZ = 2;
+// Interior tiles: 8 x 8 x 4 threads, four x-adjacent nodes each, i.e.
+// 32 x 8 x 4 nodes (a warp reads 128 contiguous bytes per row).
+constexpr int VX = 4, TBX = 8, TBY = 8, TBZ = 4;
+constexpr int TX = TBX * VX;
 
 __device__ __forceinline__ bool in_range(int v, int lo, int n) { return (unsigned)(v - lo) < (unsigned)n; }
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+
+__device__ __forceinline__ void ld4(const float *__restrict__ p, float (&o)[4])
+{
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double *__restrict__ p, double (&o)[4])
+{
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void st4(float *p, const float (&o)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ void st4(double *p, const double (&o)[4])
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(o[0], o[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(o[2], o[3]);
+}
+
+// Is the interior tile at (x0, y0, z0) clear of walls and CPML slabs, its
+// one-node halo included?
+__device__ __forceinline__ bool tile_interior(const Geo3D &g, int x0, int y0, int z0)
+{
+    const int np = g.npml;
+    return x0 - 1 >= np + 1 && x0 + TX <= g.n[0] - np - 2 && y0 - 1 >= np + 1 && y0 + TBY <= g.n[1] - np - 2 &&
+           z0 - 1 >= np + 1 && z0 + TBZ <= g.n[2] - np - 2;
+}
 
 // Slab index of position p along an axis of n nodes (E: node positions,
 // H: half positions), or -1 outside the absorbing layer.
@@ -42,6 +78,12 @@ __device__ __forceinline__ long long pidx(const Geo3D &g, int ax, int s, int i, 
     return ((long long)s * g.n[1] + j) * g.px + i;
 }
 
+// Node (i, j, k) lies in an interior tile (updated by the vector kernels)?
+__device__ __forceinline__ bool in_interior_tile(const Geo3D &g, int i, int j, int k)
+{
+    return tile_interior(g, i / TX * TX, j / TBY * TBY, k / TBZ * TBZ);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(BX *BY *BZ) k_h3d(Geo3D g, State3D<R> s, Coef<R> c, Pml3D<R> pm)
 {
@@ -49,6 +91,7 @@ __global__ void __launch_bounds__(BX *BY *BZ) k_h3d(Geo3D g, State3D<R> s, Coef<
     const int j = blockIdx.y * BY + threadIdx.y;
     const int k = blockIdx.z * BZ + threadIdx.z;
     if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
+    if (in_interior_tile(g, i, j, k)) return;
     const int p[3] = {i, j, k};
     const long long st[3] = {1, g.px, g.PP};
     const long long q = k * g.PP + (long long)j * g.px + i;
@@ -82,6 +125,7 @@ __global__ void __launch_bounds__(BX *BY *BZ) k_e3d(Geo3D g, State3D<R> s, Coef<
     const int j = blockIdx.y * BY + threadIdx.y;
     const int k = blockIdx.z * BZ + threadIdx.z;
     if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
+    if (in_interior_tile(g, i, j, k)) return;
     const int p[3] = {i, j, k};
     const long long st[3] = {1, g.px, g.PP};
     const long long q = k * g.PP + (long long)j * g.px + i;
@@ -154,6 +198,153 @@ __global__ void __launch_bounds__(BX *BY *BZ) k_e3d(Geo3D g, State3D<R> s, Coef<
     if (MODE == 1 && des && !gap) a3.G[d] += gsum;
 }
 
+// Interior H half step: curl E with forward differences, no CPML.
+//   Hx -= S (dy Ez - dz Ey),  Hy -= S (dz Ex - dx Ez),  Hz -= S (dx Ey - dy Ex)
+template <typename R>
+__global__ void __launch_bounds__(TBX *TBY *TBZ) k_h3d_in(Geo3D g, State3D<R> s, Coef<R> c)
+{
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TBY, z0 = blockIdx.z * TBZ;
+    if (!tile_interior(g, x0, y0, z0)) return;  // handled by the border kernel
+    const int i0 = x0 + threadIdx.x * VX, j = y0 + threadIdx.y, k = z0 + threadIdx.z;
+    const long long q = k * g.PP + (long long)j * g.px + i0;
+    const long long P = g.px, PP = g.PP;
+    R ex[4], exN[4], exU[4], ey[4], eyU[4], ez[4], ezN[4], hx[4], hy[4], hz[4];
+    ld4(s.E[0] + q, ex);
+    ld4(s.E[0] + q + P, exN);
+    ld4(s.E[0] + q + PP, exU);
+    ld4(s.E[1] + q, ey);
+    ld4(s.E[1] + q + PP, eyU);
+    ld4(s.E[2] + q, ez);
+    ld4(s.E[2] + q + P, ezN);
+    ld4(s.H[0] + q, hx);
+    ld4(s.H[1] + q, hy);
+    ld4(s.H[2] + q, hz);
+    const R eyE = s.E[1][q + VX], ezE = s.E[2][q + VX];
+    const R S = c.S;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const R ezx = v < 3 ? ez[v + 1] : ezE, eyx = v < 3 ? ey[v + 1] : eyE;
+        hx[v] -= S * ((ezN[v] - ez[v]) - (eyU[v] - ey[v]));
+        hy[v] -= S * ((exU[v] - ex[v]) - (ezx - ez[v]));
+        hz[v] -= S * ((eyx - ey[v]) - (exN[v] - ex[v]));
+    }
+    st4(s.H[0] + q, hx);
+    st4(s.H[1] + q, hy);
+    st4(s.H[2] + q, hz);
+}
+
+// Interior E half step: curl H with backward differences, no CPML; per
+// component the Drude update of Eq. (10a,b) in the design box.
+//   curl_x = dy Hz - dz Hy,  curl_y = dz Hx - dx Hz,  curl_z = dx Hy - dy Hx
+template <typename R, int MODE>
+__global__ void __launch_bounds__(TBX *TBY *TBZ) k_e3d_in(Geo3D g, State3D<R> s, Coef<R> c, Step3D<R> a3)
+{
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TBY, z0 = blockIdx.z * TBZ;
+    if (!tile_interior(g, x0, y0, z0)) return;
+    const int i0 = x0 + threadIdx.x * VX, j = y0 + threadIdx.y, k = z0 + threadIdx.z;
+    const long long q = k * g.PP + (long long)j * g.px + i0;
+    const long long P = g.px, PP = g.PP;
+    R hx[4], hxS[4], hxD[4], hy[4], hyD[4], hz[4], hzS[4];
+    ld4(s.H[0] + q, hx);
+    ld4(s.H[0] + q - P, hxS);
+    ld4(s.H[0] + q - PP, hxD);
+    ld4(s.H[1] + q, hy);
+    ld4(s.H[1] + q - PP, hyD);
+    ld4(s.H[2] + q, hz);
+    ld4(s.H[2] + q - P, hzS);
+    const R hyW = s.H[1][q - 1], hzW = s.H[2][q - 1];
+    R curl[3][4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const R hyx = v > 0 ? hy[v - 1] : hyW, hzx = v > 0 ? hz[v - 1] : hzW;
+        curl[0][v] = c.S * ((hz[v] - hzS[v]) - (hy[v] - hyD[v]));
+        curl[1][v] = c.S * ((hx[v] - hxD[v]) - (hz[v] - hzx));
+        curl[2][v] = c.S * ((hy[v] - hyx) - (hx[v] - hxS[v]));
+    }
+    const bool touches = (x0 < g.d0[0] + g.dn[0] && x0 + TX > g.d0[0] && y0 < g.d0[1] + g.dn[1] &&
+                          y0 + TBY > g.d0[1] && z0 < g.d0[2] + g.dn[2] && z0 + TBZ > g.d0[2]) ||
+                         (MODE == 0 && x0 < g.s1[0] && x0 + TX > g.s0[0] && y0 < g.s1[1] && y0 + TBY > g.s0[1] &&
+                          z0 < g.s1[2] && z0 + TBZ > g.s0[2]);
+    const R inv_bg = rcp(k < g.sub_hi ? c.eps_sub : c.eps_s);
+    if (!touches) {
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            R e[4];
+            ld4(s.E[cc] + q, e);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) e[v] += curl[cc][v] * inv_bg;
+            st4(s.E[cc] + q, e);
+        }
+        return;
+    }
+    // Design / gap / source tile.
+    const bool rdes = in_range(j, g.d0[1], g.dn[1]) && in_range(k, g.d0[2], g.dn[2]);
+    const bool vdes = rdes && in_range(i0, g.dxa, g.dp);
+    const long long d0 = ((long long)(k - g.d0[2]) * g.dn[1] + (j - g.d0[1])) * g.dp + (i0 - g.dxa);
+    const bool rgap = in_range(j, g.g0[1], g.gn[1]) && in_range(k, g.g0[2], g.gn[2]);
+    const bool rsrc = MODE == 0 && in_range(j, g.s0[1], g.s1[1] - g.s0[1]) && in_range(k, g.s0[2], g.s1[2] - g.s0[2]);
+    R rt4[4] = {R(0), R(0), R(0), R(0)};
+    if (vdes) ld4(a3.rho_t + d0, rt4);
+    double gadd[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+        R e[4], J4[4] = {R(0), R(0), R(0), R(0)}, em4[4] = {R(0), R(0), R(0), R(0)};
+        ld4(s.E[cc] + q, e);
+        if (vdes) {
+            ld4(s.J[cc] + d0, J4);
+            if (MODE == 1) ld4(a3.rec + cc * g.Mdi + d0, em4);
+        }
+        R en[4], jn4[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int i = i0 + v;
+            const bool gap = rgap && in_range(i, g.g0[0], g.gn[0]);
+            const int gidx = ((k - g.g0[2]) * g.gn[1] + (j - g.g0[1])) * g.gn[0] + (i - g.g0[0]);
+            R src = R(0);
+            if (MODE == 0) {
+                if (rsrc && cc == g.src_comp && in_range(i, g.s0[0], g.s1[0] - g.s0[0])) src = *a3.src;
+            } else if (gap) {
+                src = -c.eps_g * a3.gap_src[(long long)cc * g.Mg + gidx];
+            }
+            jn4[v] = J4[v];
+            if (vdes && in_range(i, g.d0[0], g.dn[0]) && !gap) {
+                const R rt = rt4[v];
+                const R eps = c.eps_s + rt * c.d_eps;
+                const R psi = c.psi_s + rt * (c.psi - c.psi_s);
+                const R sig = c.sig_max * rt * (R(1) - rt);
+                const R bJ = R(0.5) * psi * c.inv1g;
+                const R hs = R(0.5) * (sig + bJ);
+                const R cb = rcp(eps + hs);
+                const R ca = (eps - hs) * cb;
+                en[v] = ca * e[v] + cb * (curl[cc][v] - c.half1pkJ * J4[v] - src);
+                jn4[v] = c.kJ * J4[v] + bJ * (en[v] + e[v]);
+                if (MODE == 1) {
+                    // Eq. (25a-c) folded through the chain rule of Eq. (27).
+                    const R term = -c.d_eps * (en[v] - e[v]) -
+                                   c.sig_max * (R(1) - R(2) * rt) * R(0.5) * (en[v] + e[v]) -
+                                   (c.psi - c.psi_s) * rcp(psi) * R(0.5) * (jn4[v] + J4[v]);
+                    gadd[v] += (double)em4[v] * (double)term;
+                }
+            } else {
+                en[v] = e[v] + (curl[cc][v] - src) * (gap ? rcp(c.eps_g) : inv_bg);
+            }
+            if (MODE == 0 && gap && a3.gap_rec) a3.gap_rec[(long long)cc * g.Mg + gidx] = en[v];
+        }
+        st4(s.E[cc] + q, en);
+        if (vdes) {
+            st4(s.J[cc] + d0, jn4);
+            if (MODE == 0 && a3.rec) st4(a3.rec + cc * g.Mdi + d0, en);
+        }
+    }
+    if (MODE == 1 && vdes) {
+        double G4[4];
+        ld4(a3.G + d0, G4);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) G4[v] += gadd[v];
+        st4(a3.G + d0, G4);
+    }
+}
+
 }  // namespace
 
 template <typename R>
@@ -161,10 +352,19 @@ int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, const Coef<R> &
                   const Step3D<R> &a, cudaStream_t st)
 {
     dim3 block(BX, BY, BZ), grid((g.n[0] + BX - 1) / BX, (g.n[1] + BY - 1) / BY, (g.n[2] + BZ - 1) / BZ);
+    dim3 vblock(TBX, TBY, TBZ), vgrid((g.n[0] + TX - 1) / TX, (g.n[1] + TBY - 1) / TBY, (g.n[2] + TBZ - 1) / TBZ);
+    // Interior tiles and border nodes are disjoint, so each pair of kernels
+    // may run in either order; H must finish before E reads it.
+    k_h3d_in<R><<<vgrid, vblock, 0, st>>>(g, s, c);
     k_h3d<R><<<grid, block, 0, st>>>(g, s, c, pm);
-    if (mode == 0) k_e3d<R, 0><<<grid, block, 0, st>>>(g, s, c, pm, a);
-    else k_e3d<R, 1><<<grid, block, 0, st>>>(g, s, c, pm, a);
-    return 2;
+    if (mode == 0) {
+        k_e3d_in<R, 0><<<vgrid, vblock, 0, st>>>(g, s, c, a);
+        k_e3d<R, 0><<<grid, block, 0, st>>>(g, s, c, pm, a);
+    } else {
+        k_e3d_in<R, 1><<<vgrid, vblock, 0, st>>>(g, s, c, a);
+        k_e3d<R, 1><<<grid, block, 0, st>>>(g, s, c, pm, a);
+    }
+    return 4;
 }
 
 template int launch_step3d<float>(int, const Geo3D &, const State3D<float> &, const Coef<float> &,

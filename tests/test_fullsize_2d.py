@@ -4,8 +4,13 @@ in the launch configuration bench.py times (FP32, snapshots every 64).
 The oracle cannot run this size in seconds, so these use properties that
 hold at any size: the adjoint gradient against central differences of the
 objective, along a random direction in FP32 and per design cell in FP64 on
-16 seeded random cells, and the autograd wrapper (normalised objective) in
-FP32 against the library's FP64 gradient."""
+16 seeded random cells; FP32 against FP64 fields; and the autograd wrapper
+(normalised objective) in FP32 against the library's FP64 gradient.
+
+With rho ~ U[0.1, 0.9] over the 1024^2 box the 3 x 3 gap sits behind about
+1 um of lossy half-metal and its field is ~1e-7 of the incident one, at the
+rounding level of FP32 arithmetic; FP32 checks therefore use the bowtie
+nanoantenna design, which leaves vacuum paths to the gap."""
 import json
 import os
 
@@ -29,18 +34,25 @@ def _report(name, d):
         json.dump(d, f)
 
 
+def bowtie_rho(w):
+    # rho = 0.01 outside the triangles: for gold at 800 nm the interpolated
+    # material is then a dielectric (eps ~ 0.3); already at rho = 0.05 it is
+    # metallic (eps ~ -1).
+    return I.zero_gap(w, 0.01 + 0.98 * I.rho_bowtie(w))
+
+
 def test_fullsize_fp32_directional_derivative_and_autograd():
     import torch
     from paper_2203_01462_gb300.autograd import objective
     from paper_2203_01462_gb300.binding import Solver
     w = I.cfg_2d_2048()
     s = Solver(w)
-    rho = interior_rho(w, 3)
+    rho = bowtie_rho(w)
     W0, g = s.evaluate(rho, 0.0, 10.0)
     W0 = float(W0.item())
     g = g.cpu().numpy()
     v = I.zero_gap(w, np.random.default_rng(5).standard_normal(rho.shape)).reshape(-1)
-    h = 0.05 / np.abs(v).max()
+    h = 0.01 / np.abs(v).max()
 
     def Wat(x):
         s.set_design(x.reshape(rho.shape).astype(np.float32))
@@ -90,3 +102,19 @@ def test_fullsize_fp64_gradient_on_16_random_cells():
     _report("fp64_cells", dict(W=float(W.item()), gmax=float(gmax), h=h, cells=rows))
     for r in rows:
         assert abs(r["fd"] - r["adjoint"]) <= 1e-3 * abs(r["fd"]) + 1e-5 * gmax, r
+
+
+def test_fullsize_fp32_matches_fp64_fields():
+    """The benchmark's FP32 configuration against the same run in FP64
+    (W 1e-4 relative, gradient 1e-3 L2-relative) on the bowtie design."""
+    from paper_2203_01462_gb300.binding import Solver
+    w32 = I.cfg_2d_2048()
+    rho = bowtie_rho(w32)
+    W32, g32 = Solver(w32).evaluate(rho, 5e5, 10.0)
+    W64, g64 = Solver(dict(w32, real="f64")).evaluate(rho, 5e5, 10.0)
+    W32, W64 = float(W32.item()), float(W64.item())
+    g32, g64 = g32.cpu().numpy(), g64.cpu().numpy()
+    gerr = float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64))
+    _report("fp32_vs_fp64", dict(W32=W32, W64=W64, W_rel=abs(W32 - W64) / abs(W64), grad_l2_rel=gerr))
+    assert abs(W32 - W64) <= 1e-4 * abs(W64)
+    assert gerr <= 1e-3

@@ -66,3 +66,19 @@ def test_fp32_3d_dipole_run_host():
     Wh, gh = s.run_host(rho.astype(np.float32))
     assert abs(Wh - ref["W"]) <= 1e-4 * abs(ref["W"])
     assert l2rel(gh, ref["grad"]) <= 1e-3
+
+
+@pytest.mark.parametrize("real,source", [("f64", "sheet"), ("f32", "dipole")])
+def test_3d_interior_tiles_match_oracle(real, source):
+    """80 x 34 x 34 nodes, 4-cell CPML: some 32 x 8 x 4 tiles are clear of the
+    CPML (vector kernels) and hold design, gap and source nodes."""
+    w = case3d(real, source, npml=4, nx=80, ny=34, nz=34, design=(26, 12, 10), nsteps=200, snapshot_every=16,
+               substrate=(source == "sheet"))
+    rho = I.rho_uniform(w, 24)
+    ref = O.gradient(w, rho, 5e5, 3.0)
+    s = solver(w)
+    W, g = s.evaluate(rho, 5e5, 3.0)
+    s.sync()
+    tol_w, tol_g = (1e-10, 1e-9) if real == "f64" else (1e-4, 1e-3)
+    assert abs(float(W.item()) - ref["W"]) <= tol_w * abs(ref["W"])
+    assert l2rel(g.cpu().numpy(), ref["grad"]) <= tol_g
