@@ -334,7 +334,9 @@ struct Ctx2D final : fdtd_ctx {
         gstage = cv.take<double>(Md);
         gap_hist = cv.take<R>((size_t)(N + 1) * (Mg ? Mg : 1));
         const long long K = c.snapshot_every;
-        rec = cv.take<R>((size_t)(K > 0 ? std::min<long long>(K, N) : N) * Mdi);
+        // Full history: N slots.  Checkpoints: two segment buffers of K slots
+        // (the adjoint of one segment runs beside the recompute of the next).
+        rec = cv.take<R>((size_t)(K > 0 ? 2 * std::min<long long>(K, N) : N) * Mdi);
         nsnap = K > 0 ? (int)((N + K - 1) / K) : 0;
         snap_stride = snapshot_bytes<R>(c.snapshot_dtype, state_bytes);
         snaps = cv.take<char>((size_t)nsnap * snap_stride);
@@ -442,19 +444,23 @@ struct Ctx2D final : fdtd_ctx {
     }
 
     // Adjoint steps for m = m_hi down to m_lo + 1 (adjoint step N - m), the
-    // forward E^m of the design box in slot (m - 1 - slot0) of rec.
-    void advance_adjoint(const Coef<R> &k, int m_hi, int m_lo, int slot0)
+    // forward E^m of the design box in slot (m - 1 - slot0) of base.
+    void advance_adjoint_buf(const Coef<R> &k, int m_hi, int m_lo, R *base, int slot0)
     {
         Step2D<R> a{};
         a.rho_t = rho_t;
         a.G = G;
         for (int m = m_hi; m > m_lo; --m) {
             a.gap_src = Mg ? gap_hist + (size_t)m * Mg : nullptr;
-            a.rec = rec + (size_t)(m - 1 - slot0) * Mdi;
+            a.rec = base + (size_t)(m - 1 - slot0) * Mdi;
             launches += launch_step2d<R>(1, geo, A[curA], A[curA ^ 1], k, px, py, a, stream);
             curA ^= 1;
         }
         cell_updates += (long long)(m_hi - m_lo) * ncells;
+    }
+    void advance_adjoint(const Coef<R> &k, int m_hi, int m_lo, int slot0)
+    {
+        advance_adjoint_buf(k, m_hi, m_lo, rec, slot0);
     }
 
     fdtd_status forward(double *d_W) override
@@ -494,18 +500,48 @@ struct Ctx2D final : fdtd_ctx {
         launch_zero_bytes(A_base[0], state_bytes, st);
         launch_zero_bytes(A_base[1], state_bytes, st);
         launch_zero_bytes(G, Mdi * sizeof(double), st);
-        launches += 2;
+        launches += 3;
         if (K <= 0) {
             advance_adjoint(k, N, 0, 0);
-        } else {
-            for (int s = nsnap - 1; s >= 0; --s) {
-                const int n0 = s * K, n1 = std::min(n0 + K, N);
-                snapshot_load<R>(cfg.snapshot_dtype, snaps + (size_t)s * snap_stride, F_base[curF], state_bytes, st);
-                ++launches;
-                advance_forward(k, n0, n1 - n0, false, rec);
-                advance_adjoint(k, n1, n0, n0);
-            }
+            return check_launch();
         }
+        // Segments in reverse.  Segment s covers steps [s K, min(s K + K, N));
+        // its recomputed design-box fields go to buffer s % 2.  The adjoint
+        // steps of segment s run in the same launches as the recompute of
+        // segment s - 1 (independent states and buffers).
+        auto seg_lo = [&](int s) { return s * K; };
+        auto seg_hi = [&](int s) { return std::min(s * K + K, N); };
+        auto buf = [&](int s) { return rec + (size_t)(s % 2) * K * Mdi; };
+        auto restore = [&](int s) {
+            snapshot_load<R>(cfg.snapshot_dtype, snaps + (size_t)s * snap_stride, F_base[curF], state_bytes, st);
+            ++launches;
+        };
+        restore(nsnap - 1);
+        advance_forward(k, seg_lo(nsnap - 1), seg_hi(nsnap - 1) - seg_lo(nsnap - 1), false, buf(nsnap - 1));
+        for (int s = nsnap - 1; s >= 1; --s) {
+            restore(s - 1);
+            const int f0 = seg_lo(s - 1), nf = seg_hi(s - 1) - f0;  // recompute of segment s - 1
+            const int a_hi = seg_hi(s), a_lo = seg_lo(s);          // adjoint m = a_hi .. a_lo + 1
+            const int pairs = std::min(nf, a_hi - a_lo);
+            Step2D<R> fa{}, aa{};
+            fa.rho_t = aa.rho_t = rho_t;
+            aa.G = G;
+            for (int t = 0; t < pairs; ++t) {
+                const int n = f0 + t, m = a_hi - t;
+                fa.src = src_tab + n;
+                fa.rec = buf(s - 1) + (size_t)t * Mdi;
+                aa.gap_src = Mg ? gap_hist + (size_t)m * Mg : nullptr;
+                aa.rec = buf(s) + (size_t)(m - 1 - a_lo) * Mdi;
+                launches += launch_step2d_pair<R>(geo, F[curF], F[curF ^ 1], fa, A[curA], A[curA ^ 1], aa, k, px,
+                                                  py, stream);
+                curF ^= 1;
+                curA ^= 1;
+            }
+            cell_updates += 2LL * pairs * ncells;
+            if (nf > pairs) advance_forward(k, f0 + pairs, nf - pairs, false, buf(s - 1) + (size_t)pairs * Mdi);
+            if (a_hi - a_lo > pairs) advance_adjoint_buf(k, a_hi - pairs, a_lo, buf(s), a_lo);
+        }
+        advance_adjoint_buf(k, seg_hi(0), seg_lo(0), buf(0), seg_lo(0));
         return check_launch();
     }
 

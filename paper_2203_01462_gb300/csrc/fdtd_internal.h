@@ -136,6 +136,13 @@ template <typename R>
 int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, const Coef<R> &c, const Pml3D<R> &pm,
                   const Step3D<R> &a, cudaStream_t st);
 
+// A forward (recompute) step of one state and an adjoint step of another in
+// one launch (independent work; see k_step2d_pair).
+template <typename R>
+int launch_step2d_pair(const Geo2D &g, const State2D<R> &fin, const State2D<R> &fout, const Step2D<R> &fa,
+                       const State2D<R> &ain, const State2D<R> &aout, const Step2D<R> &aa, const Coef<R> &c,
+                       const Pml1D<R> &px, const Pml1D<R> &py, cudaStream_t st);
+
 // Compact (dnx x dny) <-> pitched (dny rows of dp, box at column off).
 template <typename T>
 void launch_pitch2d(const T *compact, T *pitched, int dnx, int dny, int off, int dp, cudaStream_t st);

@@ -179,13 +179,11 @@ __device__ __forceinline__ void border_step(const Geo2D &g, const State2D<R> &in
 }
 
 template <typename R, int MODE>
-__global__ void __launch_bounds__(BX *BY, 5)
-    k_step2d(const __grid_constant__ Geo2D g, const __grid_constant__ State2D<R> in,
-             const __grid_constant__ State2D<R> out, const __grid_constant__ Coef<R> c,
-             const __grid_constant__ Pml1D<R> px, const __grid_constant__ Pml1D<R> py,
-             const __grid_constant__ Step2D<R> a)
+__device__ __forceinline__ void step2d_body(const Geo2D &g, const State2D<R> &in, const State2D<R> &out,
+                                            const Coef<R> &c, const Pml1D<R> &px, const Pml1D<R> &py,
+                                            const Step2D<R> &a, int bx, int by)
 {
-    const int x0 = blockIdx.x * TILE_X, y0 = blockIdx.y * BY;
+    const int x0 = bx * TILE_X, y0 = by * BY;
     const int i0 = x0 + threadIdx.x * VX, j = y0 + threadIdx.y;
     const int nx = g.nx, ny = g.ny, np = g.npml, P = g.px;
     const R S = c.S;
@@ -286,6 +284,31 @@ __global__ void __launch_bounds__(BX *BY, 5)
     border_step<R, MODE>(g, in, out, c, px, py, a, i0, j);
 }
 
+template <typename R, int MODE>
+__global__ void __launch_bounds__(BX *BY, 5)
+    k_step2d(const __grid_constant__ Geo2D g, const __grid_constant__ State2D<R> in,
+             const __grid_constant__ State2D<R> out, const __grid_constant__ Coef<R> c,
+             const __grid_constant__ Pml1D<R> px, const __grid_constant__ Pml1D<R> py,
+             const __grid_constant__ Step2D<R> a)
+{
+    step2d_body<R, MODE>(g, in, out, c, px, py, a, blockIdx.x, blockIdx.y);
+}
+
+// One forward (recompute) step and one adjoint step of independent states in
+// one launch: blocks with blockIdx.z == 0 advance the forward state, those
+// with blockIdx.z == 1 the adjoint state.
+template <typename R>
+__global__ void __launch_bounds__(BX *BY, 5)
+    k_step2d_pair(const __grid_constant__ Geo2D g, const __grid_constant__ State2D<R> fin,
+                  const __grid_constant__ State2D<R> fout, const __grid_constant__ Step2D<R> fa,
+                  const __grid_constant__ State2D<R> ain, const __grid_constant__ State2D<R> aout,
+                  const __grid_constant__ Step2D<R> aa, const __grid_constant__ Coef<R> c,
+                  const __grid_constant__ Pml1D<R> px, const __grid_constant__ Pml1D<R> py)
+{
+    if (blockIdx.z == 0) step2d_body<R, 0>(g, fin, fout, c, px, py, fa, blockIdx.x, blockIdx.y);
+    else step2d_body<R, 1>(g, ain, aout, c, px, py, aa, blockIdx.x, blockIdx.y);
+}
+
 }  // namespace
 
 template <typename R>
@@ -298,6 +321,24 @@ int launch_step2d(int mode, const Geo2D &g, const State2D<R> &in, const State2D<
     return 1;
 }
 
+template <typename R>
+int launch_step2d_pair(const Geo2D &g, const State2D<R> &fin, const State2D<R> &fout, const Step2D<R> &fa,
+                       const State2D<R> &ain, const State2D<R> &aout, const Step2D<R> &aa, const Coef<R> &c,
+                       const Pml1D<R> &px, const Pml1D<R> &py, cudaStream_t st)
+{
+    dim3 grid((g.nx + TILE_X - 1) / TILE_X, (g.ny + BY - 1) / BY, 2), block(BX, BY);
+    k_step2d_pair<R><<<grid, block, 0, st>>>(g, fin, fout, fa, ain, aout, aa, c, px, py);
+    return 1;
+}
+
+template int launch_step2d_pair<float>(const Geo2D &, const State2D<float> &, const State2D<float> &,
+                                       const Step2D<float> &, const State2D<float> &, const State2D<float> &,
+                                       const Step2D<float> &, const Coef<float> &, const Pml1D<float> &,
+                                       const Pml1D<float> &, cudaStream_t);
+template int launch_step2d_pair<double>(const Geo2D &, const State2D<double> &, const State2D<double> &,
+                                        const Step2D<double> &, const State2D<double> &, const State2D<double> &,
+                                        const Step2D<double> &, const Coef<double> &, const Pml1D<double> &,
+                                        const Pml1D<double> &, cudaStream_t);
 template int launch_step2d<float>(int, const Geo2D &, const State2D<float> &, const State2D<float> &,
                                   const Coef<float> &, const Pml1D<float> &, const Pml1D<float> &,
                                   const Step2D<float> &, cudaStream_t);
