@@ -19,6 +19,8 @@
 // run a scalar path with CPML.  The design-box arrays (J, rho~, records, G) use the library's
 // pitched layout: column origin dxa (a multiple of 4) and row pitch dp (a
 // multiple of 4), so that they load as vectors too.  Indices are 32-bit.
+#include <utility>
+
 #include "fdtd_internal.h"
 
 namespace fdtd {
@@ -29,6 +31,12 @@ constexpr int BX = 32, BY = 8, VX = 4;
 constexpr int TILE_X = BX * VX;
 
 __device__ __forceinline__ bool in_range(int v, int lo, int n) { return (unsigned)(v - lo) < (unsigned)n; }
+
+// Programmatic dependent launch: the step kernels are launched with
+// programmatic stream serialisation, so a step's blocks may be scheduled
+// while the previous step drains; they wait here, before touching any state,
+// until the previous grid has completed and its writes are visible.
+__device__ __forceinline__ void wait_previous_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
 
@@ -291,6 +299,7 @@ __global__ void __launch_bounds__(BX *BY, 5)
              const __grid_constant__ Pml1D<R> px, const __grid_constant__ Pml1D<R> py,
              const __grid_constant__ Step2D<R> a)
 {
+    wait_previous_grid();
     step2d_body<R, MODE>(g, in, out, c, px, py, a, blockIdx.x, blockIdx.y);
 }
 
@@ -305,19 +314,37 @@ __global__ void __launch_bounds__(BX *BY, 5)
                   const __grid_constant__ Step2D<R> aa, const __grid_constant__ Coef<R> c,
                   const __grid_constant__ Pml1D<R> px, const __grid_constant__ Pml1D<R> py)
 {
+    wait_previous_grid();
     if (blockIdx.z == 0) step2d_body<R, 0>(g, fin, fout, c, px, py, fa, blockIdx.x, blockIdx.y);
     else step2d_body<R, 1>(g, ain, aout, c, px, py, aa, blockIdx.x, blockIdx.y);
 }
 
 }  // namespace
 
+// Launch with programmatic stream serialisation (see wait_previous_grid).
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 template <typename R>
 int launch_step2d(int mode, const Geo2D &g, const State2D<R> &in, const State2D<R> &out, const Coef<R> &c,
                   const Pml1D<R> &px, const Pml1D<R> &py, const Step2D<R> &a, cudaStream_t st)
 {
     dim3 grid((g.nx + TILE_X - 1) / TILE_X, (g.ny + BY - 1) / BY), block(BX, BY);
-    if (mode == 0) k_step2d<R, 0><<<grid, block, 0, st>>>(g, in, out, c, px, py, a);
-    else k_step2d<R, 1><<<grid, block, 0, st>>>(g, in, out, c, px, py, a);
+    if (mode == 0) launch_pdl(k_step2d<R, 0>, grid, block, st, g, in, out, c, px, py, a);
+    else launch_pdl(k_step2d<R, 1>, grid, block, st, g, in, out, c, px, py, a);
     return 1;
 }
 
@@ -327,7 +354,7 @@ int launch_step2d_pair(const Geo2D &g, const State2D<R> &fin, const State2D<R> &
                        const Pml1D<R> &px, const Pml1D<R> &py, cudaStream_t st)
 {
     dim3 grid((g.nx + TILE_X - 1) / TILE_X, (g.ny + BY - 1) / BY, 2), block(BX, BY);
-    k_step2d_pair<R><<<grid, block, 0, st>>>(g, fin, fout, fa, ain, aout, aa, c, px, py);
+    launch_pdl(k_step2d_pair<R>, grid, block, st, g, fin, fout, fa, ain, aout, aa, c, px, py);
     return 1;
 }
 
