@@ -8,27 +8,32 @@
 // Eq. (10a,b) per component (J and sigma E averaged over the step, scaled
 // units, see Coef).  Curl component c uses the cyclic axes a = c+1, b = c+2:
 // curl_c = d_a F_b - d_b F_a, each derivative with its own CPML term in the
-// slab of its axis.  Tiles of 32 x 8 x 4 nodes clear of walls and CPML
-// (halo included) run vector kernels with the curls written out; the other
-// nodes run generic one-node-per-thread kernels with CPML.
+// slab of its axis.  Each thread owns four x-adjacent nodes (32 x 8 x 4-node
+// blocks): where those nodes and their halo are clear of walls and CPML it
+// runs vector code with the curls written out, elsewhere generic per-node
+// code with CPML.
 //
 // Every E component of a node inside the design box takes the material of
 // rho~ at that node (Eq. 5); the adjoint sums the Eq. (25) brackets of the
 // three components into the node's FP64 accumulator.
+#include <utility>
+
 #include "fdtd_internal.h"
 
 namespace fdtd {
 
 namespace {
 
-// Generic (border) kernels: one node per thread.
-constexpr int BX = 32, BY = 4, BZ = 2;
-// Interior tiles: 8 x 8 x 4 threads, four x-adjacent nodes each, i.e.
+// Tiles: 8 x 8 x 4 threads, four x-adjacent nodes each, i.e.
 // 32 x 8 x 4 nodes (a warp reads 128 contiguous bytes per row).
 constexpr int VX = 4, TBX = 8, TBY = 8, TBZ = 4;
 constexpr int TX = TBX * VX;
 
 __device__ __forceinline__ bool in_range(int v, int lo, int n) { return (unsigned)(v - lo) < (unsigned)n; }
+
+// Programmatic dependent launch (as in the 2D kernels): wait, before touching
+// any state, until the previous grid in the stream has completed.
+__device__ __forceinline__ void wait_previous_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
 
@@ -52,13 +57,13 @@ __device__ __forceinline__ void st4(double *p, const double (&o)[4])
     reinterpret_cast<double2 *>(p)[1] = make_double2(o[2], o[3]);
 }
 
-// Is the interior tile at (x0, y0, z0) clear of walls and CPML slabs, its
-// one-node halo included?
-__device__ __forceinline__ bool tile_interior(const Geo3D &g, int x0, int y0, int z0)
+// Are the four nodes i0 .. i0+3 of row (j, k) and their one-node halo clear
+// of walls and CPML slabs?
+__device__ __forceinline__ bool thread_interior(const Geo3D &g, int i0, int j, int k)
 {
     const int np = g.npml;
-    return x0 - 1 >= np + 1 && x0 + TX <= g.n[0] - np - 2 && y0 - 1 >= np + 1 && y0 + TBY <= g.n[1] - np - 2 &&
-           z0 - 1 >= np + 1 && z0 + TBZ <= g.n[2] - np - 2;
+    return i0 - 1 >= np + 1 && i0 + VX <= g.n[0] - np - 2 && j - 1 >= np + 1 && j + 1 <= g.n[1] - np - 2 &&
+           k - 1 >= np + 1 && k + 1 <= g.n[2] - np - 2;
 }
 
 // Slab index of position p along an axis of n nodes (E: node positions,
@@ -78,20 +83,11 @@ __device__ __forceinline__ long long pidx(const Geo3D &g, int ax, int s, int i, 
     return ((long long)s * g.n[1] + j) * g.px + i;
 }
 
-// Node (i, j, k) lies in an interior tile (updated by the vector kernels)?
-__device__ __forceinline__ bool in_interior_tile(const Geo3D &g, int i, int j, int k)
-{
-    return tile_interior(g, i / TX * TX, j / TBY * TBY, k / TBZ * TBZ);
-}
-
+// Generic H update of node (i, j, k): every component, CPML where needed.
 template <typename R>
-__global__ void __launch_bounds__(BX *BY *BZ) k_h3d(Geo3D g, State3D<R> s, Coef<R> c, Pml3D<R> pm)
+__device__ __forceinline__ void h_node(const Geo3D &g, const State3D<R> &s, const Coef<R> &c, const Pml3D<R> &pm,
+                                       int i, int j, int k)
 {
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z * BZ + threadIdx.z;
-    if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
-    if (in_interior_tile(g, i, j, k)) return;
     const int p[3] = {i, j, k};
     const long long st[3] = {1, g.px, g.PP};
     const long long q = k * g.PP + (long long)j * g.px + i;
@@ -118,14 +114,12 @@ __global__ void __launch_bounds__(BX *BY *BZ) k_h3d(Geo3D g, State3D<R> s, Coef<
     }
 }
 
+// Generic E (and J) update of node (i, j, k): every component, CPML where
+// needed, design / gap / source logic, records and sensitivity.
 template <typename R, int MODE>
-__global__ void __launch_bounds__(BX *BY *BZ) k_e3d(Geo3D g, State3D<R> s, Coef<R> c, Pml3D<R> pm, Step3D<R> a3)
+__device__ __forceinline__ void e_node(const Geo3D &g, const State3D<R> &s, const Coef<R> &c, const Pml3D<R> &pm,
+                                       const Step3D<R> &a3, int i, int j, int k)
 {
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z * BZ + threadIdx.z;
-    if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
-    if (in_interior_tile(g, i, j, k)) return;
     const int p[3] = {i, j, k};
     const long long st[3] = {1, g.px, g.PP};
     const long long q = k * g.PP + (long long)j * g.px + i;
@@ -201,11 +195,17 @@ __global__ void __launch_bounds__(BX *BY *BZ) k_e3d(Geo3D g, State3D<R> s, Coef<
 // Interior H half step: curl E with forward differences, no CPML.
 //   Hx -= S (dy Ez - dz Ey),  Hy -= S (dz Ex - dx Ez),  Hz -= S (dx Ey - dy Ex)
 template <typename R>
-__global__ void __launch_bounds__(TBX *TBY *TBZ) k_h3d_in(Geo3D g, State3D<R> s, Coef<R> c)
+__global__ void __launch_bounds__(TBX *TBY *TBZ) k_h3d_in(Geo3D g, State3D<R> s, Coef<R> c, Pml3D<R> pm)
 {
+    wait_previous_grid();
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TBY, z0 = blockIdx.z * TBZ;
-    if (!tile_interior(g, x0, y0, z0)) return;  // handled by the border kernel
     const int i0 = x0 + threadIdx.x * VX, j = y0 + threadIdx.y, k = z0 + threadIdx.z;
+    if (j >= g.n[1] || k >= g.n[2]) return;
+    if (!thread_interior(g, i0, j, k)) {
+        for (int v = 0; v < VX; ++v)
+            if (i0 + v < g.n[0]) h_node<R>(g, s, c, pm, i0 + v, j, k);
+        return;
+    }
     const long long q = k * g.PP + (long long)j * g.px + i0;
     const long long P = g.px, PP = g.PP;
     R ex[4], exN[4], exU[4], ey[4], eyU[4], ez[4], ezN[4], hx[4], hy[4], hz[4];
@@ -237,11 +237,18 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ) k_h3d_in(Geo3D g, State3D<R> s,
 // component the Drude update of Eq. (10a,b) in the design box.
 //   curl_x = dy Hz - dz Hy,  curl_y = dz Hx - dx Hz,  curl_z = dx Hy - dy Hx
 template <typename R, int MODE>
-__global__ void __launch_bounds__(TBX *TBY *TBZ) k_e3d_in(Geo3D g, State3D<R> s, Coef<R> c, Step3D<R> a3)
+__global__ void __launch_bounds__(TBX *TBY *TBZ)
+    k_e3d_in(Geo3D g, State3D<R> s, Coef<R> c, Pml3D<R> pm, Step3D<R> a3)
 {
+    wait_previous_grid();
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TBY, z0 = blockIdx.z * TBZ;
-    if (!tile_interior(g, x0, y0, z0)) return;
     const int i0 = x0 + threadIdx.x * VX, j = y0 + threadIdx.y, k = z0 + threadIdx.z;
+    if (j >= g.n[1] || k >= g.n[2]) return;
+    if (!thread_interior(g, i0, j, k)) {
+        for (int v = 0; v < VX; ++v)
+            if (i0 + v < g.n[0]) e_node<R, MODE>(g, s, c, pm, a3, i0 + v, j, k);
+        return;
+    }
     const long long q = k * g.PP + (long long)j * g.px + i0;
     const long long P = g.px, PP = g.PP;
     R hx[4], hxS[4], hxD[4], hy[4], hyD[4], hz[4], hzS[4];
@@ -347,24 +354,30 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ) k_e3d_in(Geo3D g, State3D<R> s,
 
 }  // namespace
 
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 template <typename R>
 int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, const Coef<R> &c, const Pml3D<R> &pm,
                   const Step3D<R> &a, cudaStream_t st)
 {
-    dim3 block(BX, BY, BZ), grid((g.n[0] + BX - 1) / BX, (g.n[1] + BY - 1) / BY, (g.n[2] + BZ - 1) / BZ);
     dim3 vblock(TBX, TBY, TBZ), vgrid((g.n[0] + TX - 1) / TX, (g.n[1] + TBY - 1) / TBY, (g.n[2] + TBZ - 1) / TBZ);
-    // Interior tiles and border nodes are disjoint, so each pair of kernels
-    // may run in either order; H must finish before E reads it.
-    k_h3d_in<R><<<vgrid, vblock, 0, st>>>(g, s, c);
-    k_h3d<R><<<grid, block, 0, st>>>(g, s, c, pm);
-    if (mode == 0) {
-        k_e3d_in<R, 0><<<vgrid, vblock, 0, st>>>(g, s, c, a);
-        k_e3d<R, 0><<<grid, block, 0, st>>>(g, s, c, pm, a);
-    } else {
-        k_e3d_in<R, 1><<<vgrid, vblock, 0, st>>>(g, s, c, a);
-        k_e3d<R, 1><<<grid, block, 0, st>>>(g, s, c, pm, a);
-    }
-    return 4;
+    launch_pdl(k_h3d_in<R>, vgrid, vblock, st, g, s, c, pm);
+    if (mode == 0) launch_pdl(k_e3d_in<R, 0>, vgrid, vblock, st, g, s, c, pm, a);
+    else launch_pdl(k_e3d_in<R, 1>, vgrid, vblock, st, g, s, c, pm, a);
+    return 2;
 }
 
 template int launch_step3d<float>(int, const Geo3D &, const State3D<float> &, const Coef<float> &,
