@@ -55,6 +55,13 @@ def workload(name: str, nsteps: int | None):
     return w
 
 
+# DRAM bytes (read + write) of one forward time step, from the ncu captures
+# summarised in profiles/step2d_2048.md (k_step2d<float,0>, one launch) and
+# profiles/step3d_256.md (k_h3d_in + k_e3d_in<float,0>).  Cold-L2 captures of
+# the current kernels; reset to None whenever a kernel changes.
+NCU_TRAFFIC_PER_STEP = {"cfg_2d_2048": 73.77e6, "cfg_3d_256": 1278.2e6}
+
+
 def damping(k: int) -> float:
     """Artificial-damping schedule: gamma x10 decaying geometrically to x1 over 50 iterations."""
     return 10.0 ** (1.0 - min(k, 50) / 50.0)
@@ -311,7 +318,8 @@ def main() -> None:
                     parallelism="replicas" if world > 1 else "1 GPU",
                     l2="flushed (256 MB write) between timed steps"),
         roofline=dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm,
-                      traffic=None,
+                      traffic=NCU_TRAFFIC_PER_STEP.get(w["name"]), traffic_unit="bytes per forward step",
+                      algorithmic_bytes_per_step=ab["forward"],
                       kernel="k_step2d<float,0> (fused forward leapfrog step)" if w["ndim"] == 2
                       else "k_h3d + k_e3d<float,0> (forward H and E half steps)",
                       peak_source=peak_src),
