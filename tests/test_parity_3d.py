@@ -82,3 +82,26 @@ def test_3d_interior_tiles_match_oracle(real, source):
     tol_w, tol_g = (1e-10, 1e-9) if real == "f64" else (1e-4, 1e-3)
     assert abs(float(W.item()) - ref["W"]) <= tol_w * abs(ref["W"])
     assert l2rel(g.cpu().numpy(), ref["grad"]) <= tol_g
+
+
+@pytest.mark.slow
+def test_cfg512_code_path_on_a_64_cube_crop():
+    """The 512 x 512 x 384 configuration's code path (z-dipole in the gap, two
+    bands 650-750 and 850-950 nm, FP16 per-slab checkpoints with segment
+    recompute, FP32 fields) on a 64^3 crop: 64^3 nodes, 12-cell CPML, 32 x 32 x 24
+    design box, 4400 steps (the two-band pulse peaks near step 3860), against the
+    FP64 oracle."""
+    big = I.cfg_3d_512()
+    w = I.workload_3d(64, 64, 64, dx=5e-9, nsteps=4400, npml=12, design=(32, 32, 24), gap=(4, 4, 4),
+                      source="dipole", snapshot_every=100, snapshot_dtype="f16")
+    for key in ("nbands", "f0", "tau", "t0"):
+        w[key] = big[key]
+    rho = I.rho_uniform(w, 25)
+    O.set_threads(16)
+    ref = O.gradient(w, rho, 0.0, 1.0)
+    O.set_threads(1)
+    s = solver(w)
+    W, g = s.evaluate(rho)
+    s.sync()
+    assert abs(float(W.item()) - ref["W"]) <= 1e-4 * abs(ref["W"])
+    assert l2rel(g.cpu().numpy(), ref["grad"]) <= 1e-3
