@@ -181,6 +181,26 @@ fdtd_status fdtd_gradient_static(fdtd_ctx *ctx, double *d_grad, size_t n);
  * n = (N + 1) * 3 * M_g, layout [step][component x, y, z][gap node]. */
 fdtd_status fdtd_gap_history(fdtd_ctx *ctx, double *d_out, size_t n);
 
+/* ---- optimization-loop helpers (Sec. 3.2, Eq. 28) ----
+ * The paper updates the design with GCMMA; this library provides a projected,
+ * normalised gradient-ascent step instead, and the paper's grayness measure
+ * and final thresholding. */
+
+/* d_rho <- clip(d_rho + move * d_grad / max|d_grad|, 0, 1) on the device
+ * (n = M_d; d_rho in the field precision, d_grad FP64).  A zero gradient
+ * leaves rho unchanged.  Asynchronous; uses a word of the context's
+ * workspace. */
+fdtd_status fdtd_ascent_step(fdtd_ctx *ctx, void *d_rho, const double *d_grad, size_t n, double move);
+
+/* Grayness zeta = 4 rho~^T (1 - rho~) / M of the filtered design of the last
+ * fdtd_set_design, gap nodes excluded (Sec. 3.2): 0 for a black-and-white
+ * design, 1 for rho~ = 0.5 everywhere.  Written to d_zeta (device, one
+ * double), asynchronously. */
+fdtd_status fdtd_grayness(fdtd_ctx *ctx, double *d_zeta);
+
+/* d_rho <- (d_rho >= level) ? 1 : 0 (the paper's final step, level 0.5). */
+fdtd_status fdtd_threshold(fdtd_ctx *ctx, void *d_rho, size_t n, double level);
+
 /* Wait for the context's stream and report (then clear) device-side errors:
  * FDTD_ERANGE, FDTD_EUNSTABLE, or FDTD_ECUDA for a failed kernel. */
 fdtd_status fdtd_sync(fdtd_ctx *ctx);

@@ -186,3 +186,16 @@ def material(w: dict, rho: float, sigma_max: float = 0.0) -> tuple[float, float,
     e, p, s = C.c_double(), C.c_double(), C.c_double()
     lib().or_material(C.byref(cfg), float(rho), float(sigma_max), C.byref(e), C.byref(p), C.byref(s))
     return e.value, p.value, s.value
+
+
+def grayness(w: dict, rho: np.ndarray) -> float:
+    """zeta = 4 rho~^T (1 - rho~) / M over the design nodes outside the gap
+    (Sec. 3.2), rho~ = F(rho)."""
+    rt = filt(w, rho).reshape(-1)
+    lo, hi, dlo = w["gap_lo"], w["gap_hi"], w["design_lo"]
+    shape = tuple(w["design_hi"][a] - w["design_lo"][a] for a in reversed(range(w["ndim"])))
+    mask = np.ones(shape, dtype=bool)
+    sl = tuple(slice(lo[a] - dlo[a], hi[a] - dlo[a]) for a in reversed(range(w["ndim"])))
+    mask[sl] = False
+    v = rt[mask.reshape(-1)]
+    return float(4.0 * np.sum(v * (1.0 - v)) / v.size)

@@ -25,7 +25,7 @@ ACC = {"f64": 0, "comp_f32": 1}
 EXPORTS = ["fdtd_workspace_bytes", "fdtd_create", "fdtd_set_design", "fdtd_set_damping",
            "fdtd_forward", "fdtd_adjoint", "fdtd_gradient", "fdtd_gap_history", "fdtd_sync",
            "fdtd_run_host", "fdtd_get_info", "fdtd_status_string", "fdtd_destroy",
-           "fdtd_gradient_static"]
+           "fdtd_gradient_static", "fdtd_ascent_step", "fdtd_grayness", "fdtd_threshold"]
 
 
 class FdtdError(RuntimeError):
@@ -84,6 +84,9 @@ def load():
             "fdtd_adjoint": [P],
             "fdtd_gradient": [P, P, C.c_size_t],
             "fdtd_gradient_static": [P, P, C.c_size_t],
+            "fdtd_ascent_step": [P, P, P, C.c_size_t, C.c_double],
+            "fdtd_grayness": [P, P],
+            "fdtd_threshold": [P, P, C.c_size_t, C.c_double],
             "fdtd_gap_history": [P, P, C.c_size_t],
             "fdtd_sync": [P],
             "fdtd_run_host": [P, P, C.c_size_t, P, P],
@@ -223,6 +226,22 @@ class Solver:
         _check(self.lib.fdtd_gradient_static(self.ctx, C.c_void_p(out.data_ptr()), out.numel()),
                "fdtd_gradient_static")
         return out
+
+    def ascent_step(self, rho, grad, move: float) -> None:
+        """rho <- clip(rho + move * grad / max|grad|, 0, 1) in place (device tensors)."""
+        _check(self.lib.fdtd_ascent_step(self.ctx, C.c_void_p(rho.data_ptr()), C.c_void_p(grad.data_ptr()),
+                                         rho.numel(), float(move)), "fdtd_ascent_step")
+
+    def grayness(self):
+        """zeta = 4 rho~^T (1 - rho~) / M of the current filtered design (device FP64 scalar)."""
+        t = self.torch
+        out = t.zeros(1, dtype=t.float64, device=self.device)
+        _check(self.lib.fdtd_grayness(self.ctx, C.c_void_p(out.data_ptr())), "fdtd_grayness")
+        return out
+
+    def threshold(self, rho, level: float = 0.5) -> None:
+        _check(self.lib.fdtd_threshold(self.ctx, C.c_void_p(rho.data_ptr()), rho.numel(), float(level)),
+               "fdtd_threshold")
 
     def gap_history(self):
         """(N+1, M_g) in 2D; (N+1, 3, M_g) in 3D."""

@@ -154,6 +154,9 @@ struct fdtd_ctx {
     virtual fdtd_status gap_history(double *d_out) = 0;
     // fdtd_gradient with the filter-transpose intermediates in s1, s2.
     virtual fdtd_status gradient_scratch(double *d_grad, double *s1, double *s2) = 0;
+    // Optimization-loop helpers.
+    virtual fdtd_status grayness(double *d_zeta) = 0;
+    long long n_free = 0;  // design nodes outside the gap
     virtual void *rho_stage() = 0;
     virtual double *grad_stage() = 0;
     virtual double *W_dev() = 0;
@@ -565,6 +568,15 @@ struct Ctx2D final : fdtd_ctx {
         return check_launch();
     }
 
+    fdtd_status grayness(double *d_zeta) override
+    {
+        launch_grayness<R>(rho_t, geo.dny, geo.dnx, geo.dp, geo.dx0 - geo.dxa, geo.dny, geo.gx0 - geo.dx0,
+                           geo.gy0 - geo.dy0, 0, geo.gnx, geo.gny, 1, d_zeta, stream);
+        launch_scale1(d_zeta, n_free > 0 ? 4.0 / (double)n_free : 0.0, stream);
+        launches += 3;
+        return check_launch();
+    }
+
     fdtd_status gradient_scratch(double *d_grad, double *s1, double *s2) override
     {
         cudaStream_t st = stream;
@@ -817,6 +829,16 @@ struct Ctx3D final : fdtd_ctx {
         return check_launch();
     }
 
+    fdtd_status grayness(double *d_zeta) override
+    {
+        launch_grayness<R>(rho_t, (long long)geo.dn[1] * geo.dn[2], geo.dn[0], geo.dp, geo.d0[0] - geo.dxa, geo.dn[1],
+                           geo.g0[0] - geo.d0[0], geo.g0[1] - geo.d0[1], geo.g0[2] - geo.d0[2], geo.gn[0], geo.gn[1],
+                           geo.gn[2], d_zeta, stream);
+        launch_scale1(d_zeta, n_free > 0 ? 4.0 / (double)n_free : 0.0, stream);
+        launches += 3;
+        return check_launch();
+    }
+
     fdtd_status gradient_scratch(double *d_grad, double *, double *) override { return gradient(d_grad); }
 
     fdtd_status gap_history(double *d_out) override
@@ -863,6 +885,7 @@ static fdtd_ctx *make_ctx(const fdtd_config *cfg)
     c->dt = cfg->courant * cfg->dx / kC0;
     c->Md = box_count(cfg->design_lo, cfg->design_hi, cfg->ndim);
     c->Mg = box_count(cfg->gap_lo, cfg->gap_hi, cfg->ndim);
+    c->n_free = c->Md - c->Mg;
     c->ncells = (long long)cfg->nx * cfg->ny * (cfg->ndim == 3 ? cfg->nz : 1);
     return c;
 }
@@ -967,6 +990,32 @@ fdtd_status fdtd_gap_history(fdtd_ctx *ctx, double *d_out, size_t n)
         return FDTD_EINVAL;
     if (!ctx->fwd_done) return FDTD_ESTATE;
     return ctx->gap_history(d_out);
+}
+
+fdtd_status fdtd_ascent_step(fdtd_ctx *ctx, void *d_rho, const double *d_grad, size_t n, double move)
+{
+    if (!ctx || !d_rho || !d_grad || (long long)n != ctx->Md || !(move >= 0) || !isfinite(move)) return FDTD_EINVAL;
+    unsigned long long *gmax = (unsigned long long *)(ctx->W_dev() + 1);
+    if (ctx->cfg.real_bytes == 4) launch_ascent<float>((float *)d_rho, d_grad, (long long)n, move, gmax, ctx->stream);
+    else launch_ascent<double>((double *)d_rho, d_grad, (long long)n, move, gmax, ctx->stream);
+    ctx->launches += 3;
+    return cuda_ok(cudaGetLastError());
+}
+
+fdtd_status fdtd_grayness(fdtd_ctx *ctx, double *d_zeta)
+{
+    if (!ctx || !d_zeta) return FDTD_EINVAL;
+    if (!ctx->has_design) return FDTD_ESTATE;
+    return ctx->grayness(d_zeta);
+}
+
+fdtd_status fdtd_threshold(fdtd_ctx *ctx, void *d_rho, size_t n, double level)
+{
+    if (!ctx || !d_rho || (long long)n != ctx->Md || !isfinite(level)) return FDTD_EINVAL;
+    if (ctx->cfg.real_bytes == 4) launch_threshold<float>((float *)d_rho, (long long)n, level, ctx->stream);
+    else launch_threshold<double>((double *)d_rho, (long long)n, level, ctx->stream);
+    ++ctx->launches;
+    return cuda_ok(cudaGetLastError());
 }
 
 fdtd_status fdtd_sync(fdtd_ctx *ctx)

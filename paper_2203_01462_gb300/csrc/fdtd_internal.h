@@ -157,6 +157,16 @@ template <typename R>
 void launch_to_double(const R *in, double *out, long long n, cudaStream_t st);
 void launch_copy_bytes(const void *src, void *dst, size_t bytes, cudaStream_t st);
 
+// Optimization-loop kernels (kernels_opt.cu).
+template <typename R>
+void launch_ascent(R *rho, const double *g, long long n, double move, unsigned long long *gmax, cudaStream_t st);
+template <typename R>
+void launch_grayness(const R *rt, long long rows, int dnx, int dp, int off, int rows_per_plane, int gx0, int gy0,
+                     int gz0, int gnx, int gny, int gnz, double *acc, cudaStream_t st);
+void launch_scale1(double *x, double s, cudaStream_t st);
+template <typename R>
+void launch_threshold(R *rho, long long n, double level, cudaStream_t st);
+
 // 16-bit checkpoints (kind 1: BF16, 2: FP16) with one float scale per slab
 // of SNAP_SLAB consecutive words of the state block.
 constexpr long long SNAP_SLAB = 2048;

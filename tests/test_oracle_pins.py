@@ -318,3 +318,12 @@ def test_3d_objective_literal_sum():
     out = O.forward(w, I.rho_uniform(w, 9), record_gap=True)
     dt = w["courant"] * w["dx"] / C0
     assert abs(out["W"] - 0.5 * w["eps_g"] * dt * w["dx"] ** 3 * np.sum(out["gap_hist"] ** 2)) <= 1e-13 * out["W"]
+
+
+def test_grayness_definition():
+    """Sec. 3.2: zeta = 0 for a black-and-white design, 1 for rho~ = 0.5."""
+    w = fast_case()
+    shape = I.design_shape(w)
+    assert O.grayness(w, np.zeros(shape)) == 0.0
+    assert O.grayness(w, I.zero_gap(w, np.ones(shape))) == 0.0
+    assert abs(O.grayness(w, np.full(shape, 0.5)) - 1.0) < 1e-15
