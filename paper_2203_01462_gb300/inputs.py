@@ -230,3 +230,35 @@ def with_(w: dict, **kw) -> dict:
     v = copy.deepcopy(w)
     v.update(kw)
     return v
+
+
+# ---------------------------------------------------------------- surrogate
+
+def unet_layers(base: int = 24, in_ch: int = 2) -> list[tuple[str, int, int, int]]:
+    """Layers (name, c_in, c_out, kernel) of the 4-level U-Net surrogate, in
+    forward order.  Encoder levels double the width (base, 2b, 4b), the
+    bottleneck has 8b channels; each decoder level takes [upsampled deeper
+    features, skip] concatenated; a 1 x 1 head gives one channel."""
+    b = base
+    return [("enc1a", in_ch, b, 3), ("enc1b", b, b, 3),
+            ("enc2a", b, 2 * b, 3), ("enc2b", 2 * b, 2 * b, 3),
+            ("enc3a", 2 * b, 4 * b, 3), ("enc3b", 4 * b, 4 * b, 3),
+            ("bota", 4 * b, 8 * b, 3), ("botb", 8 * b, 8 * b, 3),
+            ("dec3a", 12 * b, 4 * b, 3), ("dec3b", 4 * b, 4 * b, 3),
+            ("dec2a", 6 * b, 2 * b, 3), ("dec2b", 2 * b, 2 * b, 3),
+            ("dec1a", 3 * b, b, 3), ("dec1b", b, b, 3),
+            ("head", b, 1, 1)]
+
+
+def unet_params(base: int = 24, seed: int = 0, in_ch: int = 2) -> dict:
+    """He-normal weights (W[c_out][c_in][k][k]) and zero biases, PCG64(seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = {}
+    for name, ci, co, k in unet_layers(base, in_ch):
+        p[name + ".w"] = rng.standard_normal((co, ci, k, k)) * math.sqrt(2.0 / (ci * k * k))
+        p[name + ".b"] = np.zeros(co)
+    return p
+
+
+def unet_param_count(base: int = 24, in_ch: int = 2) -> int:
+    return sum(co * ci * k * k + co for _, ci, co, k in unet_layers(base, in_ch))
