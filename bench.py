@@ -178,6 +178,56 @@ def run_reference(args, w) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_surrogate(args) -> None:
+    """Design iterations/s at a matched objective: the plain adjoint loop
+    (one forward + adjoint solve per design step) against the
+    surrogate-assisted loop (one solve + four U-Net steps per round), on the
+    256^2-design workload.  The surrogate loop stops once its judged W~ is
+    within 1 % of the plain loop's final W~."""
+    import torch
+    from paper_2203_01462_gb300.binding import Solver
+    from paper_2203_01462_gb300.optimize import optimize
+    from paper_2203_01462_gb300.surrogate_loop import Trainer, collect_pairs, surrogate_optimize
+    w = I.cfg_2d_316()
+    s = Solver(w)
+    t = time.perf_counter()
+    rho0s = [I.zero_gap(w, 0.02 * I.rho_uniform(w, 300 + k)) for k in range(args.sur_trajectories)]
+    pairs = collect_pairs(s, rho0s, iters=args.sur_pairs_per_trajectory, move=0.05, damping_start=1.0,
+                          damping_iters=0)
+    torch.cuda.synchronize()
+    collect_s = time.perf_counter() - t
+    tr = Trainer(256, 256, base=24, batch=8, seed=0, lr=1e-3)
+    t = time.perf_counter()
+    loss = tr.fit(pairs, 300)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t
+    rho_start = I.zero_gap(w, np.zeros(I.design_shape(w)))
+    U = args.sur_updates
+    t = time.perf_counter()
+    _, hp = optimize(s, rho_start, iters=U, move=0.05, zeta_stop=0.0, damping_start=1.0, damping_iters=0,
+                     move_decay=1.0)
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t
+    target = hp.W[-1]
+    t = time.perf_counter()
+    _, hs, st = surrogate_optimize(s, tr, rho_start, updates=3 * U, inner=4, move=0.05, damping_start=1.0,
+                                   damping_iters=0, pairs=pairs, fit_steps=0, target_W=0.99 * target)
+    torch.cuda.synchronize()
+    sur_s = time.perf_counter() - t
+    Ws = [x for x in hs.W if x == x]
+    line = dict(metric="design iters/s at matched objective", value=len(hs.W) / sur_s, unit="design updates/s",
+                higher_is_better=True, n_gpus=1, data="synthetic",
+                config=dict(workload=I.describe(w), network="U-Net base 24 (%d parameters), FP32"
+                            % I.unet_param_count(24), inner_steps=4, matched="within 1 % of the plain loop's final W"),
+                plain=dict(updates=U, seconds=plain_s, updates_per_s=U / plain_s, final_W=target),
+                surrogate=dict(updates=len(hs.W), seconds=sur_s, final_W=Ws[-1], reached=Ws[-1] >= 0.99 * target,
+                               **st),
+                wall_time_ratio=sur_s / plain_s,
+                pretraining=dict(pairs=len(pairs), collect_s=collect_s, train_steps=300, train_s=train_s,
+                                 final_loss=loss))
+    print(json.dumps(line), flush=True)
+
+
 def max_over_ranks(x: float, dist, device) -> float:
     """The slowest rank's time (all ranks call this after their timed region)."""
     import torch
@@ -199,7 +249,15 @@ def main() -> None:
     ap.add_argument("--ref-nsteps", type=int, default=200)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--surrogate", action="store_true",
+                    help="measure the surrogate-assisted optimization loop against the plain adjoint loop")
+    ap.add_argument("--sur-trajectories", type=int, default=8)
+    ap.add_argument("--sur-pairs-per-trajectory", type=int, default=25)
+    ap.add_argument("--sur-updates", type=int, default=40)
     args = ap.parse_args()
+    if args.surrogate:
+        run_surrogate(args)
+        return
     w = workload(args.workload, args.nsteps)
     w["name"] = args.workload
     if args.impl == "reference":

@@ -24,16 +24,21 @@ inline int blocks_for(long long n, int cap = 152 * 16)
 // tiles, 16-deep K slices in shared memory, 4 x 4 outputs per thread.
 constexpr int GT = 64, GK = 16;
 
+// Split K: blockIdx.z takes the K slice [z kc, (z + 1) kc); with more than
+// one slice the partial tiles are added to C atomically (C scaled by beta
+// beforehand).
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, float alpha, const float *__restrict__ A, int lda,
-                                              const float *__restrict__ B, int ldb, float beta, float *C, int ldc)
+                                              const float *__restrict__ B, int ldb, float beta, float *C, int ldc,
+                                              int kc)
 {
     __shared__ float As[GK][GT + 4];
     __shared__ float Bs[GK][GT + 4];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
     float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += GK) {
+    const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
+    for (int k0 = kb; k0 < ke; k0 += GK) {
         // 64 x 16 elements of each operand, 4 per thread.
         for (int e = threadIdx.x; e < GT * GK; e += 256) {
             int mm, kk;
@@ -41,14 +46,14 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, float alpha, 
             else { mm = e / GK; kk = e % GK; }      // A stored M x K: consecutive k
             const int gm = m0 + mm, gk = k0 + kk;
             float v = 0.0f;
-            if (gm < M && gk < K) v = TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
+            if (gm < M && gk < ke) v = TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
             As[kk][mm] = v;
             int nn2, kk2;
             if (TB) { nn2 = e / GK; kk2 = e % GK; }  // B stored N x K: consecutive k
             else { kk2 = e / GT; nn2 = e % GT; }     // B stored K x N: consecutive n
             const int gn = n0 + nn2, gk2 = k0 + kk2;
             float u = 0.0f;
-            if (gn < N && gk2 < K) u = TB ? B[(long long)gn * ldb + gk2] : B[(long long)gk2 * ldb + gn];
+            if (gn < N && gk2 < ke) u = TB ? B[(long long)gn * ldb + gk2] : B[(long long)gk2 * ldb + gn];
             Bs[kk2][nn2] = u;
         }
         __syncthreads();
@@ -75,7 +80,8 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, float alpha, 
             const int gn = n0 + tx + 16 * j;
             if (gn >= N) continue;
             float *c = C + (long long)gm * ldc + gn;
-            *c = alpha * acc[i][j] + (beta != 0.0f ? beta * *c : 0.0f);
+            if (gridDim.z > 1) atomicAdd(c, alpha * acc[i][j]);
+            else *c = alpha * acc[i][j] + (beta != 0.0f ? beta * *c : 0.0f);
         }
     }
 }
@@ -221,6 +227,15 @@ __global__ void k_adam(float *p, const float *g, float *m, float *v, long long n
     }
 }
 
+__global__ void k_scale_mat(float *C, int M, int N, int ldc, float beta)
+{
+    const long long n = (long long)M * N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        float *c = C + (e / N) * ldc + e % N;
+        *c = beta != 0.0f ? beta * *c : 0.0f;
+    }
+}
+
 __global__ void k_zero_f(float *x, long long n)
 {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
@@ -239,11 +254,22 @@ int nn_gemm(int transA, int transB, int M, int N, int K, float alpha, const floa
     if (M < 0 || N < 0 || K < 0 || !C || (K > 0 && (!A || !B))) return 1;
     if (M == 0 || N == 0) return 0;
     cudaStream_t st = (cudaStream_t)stream;
-    dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT);
-    if (!transA && !transB) k_gemm<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    else if (!transA && transB) k_gemm<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    else if (transA && !transB) k_gemm<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    else k_gemm<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    // Few output tiles and a long K (weight gradients): split K over enough
+    // slices to give every SM a couple of blocks.
+    const long long tiles = (long long)((N + GT - 1) / GT) * ((M + GT - 1) / GT);
+    int splits = 1;
+    if (tiles < 2 * 152 && K > 8 * GK) {
+        const long long want = (2 * 152 + tiles - 1) / tiles, most = (K + 4 * GK - 1) / (4 * GK);
+        splits = (int)(want < most ? want : most);
+    }
+    const int kc = ((K + splits - 1) / splits + GK - 1) / GK * GK;
+    splits = (K + kc - 1) / kc;
+    if (splits > 1) k_scale_mat<<<blocks_for((long long)M * N), TPB, 0, st>>>(C, M, N, ldc, beta);
+    dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT, splits);
+    if (!transA && !transB) k_gemm<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
+    else if (!transA && transB) k_gemm<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
+    else if (transA && !transB) k_gemm<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
+    else k_gemm<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
     return status(st);
 }
 

@@ -100,6 +100,13 @@ def cfg_2d_2048(nsteps: int = 20000) -> dict:
                        snapshot_every=64, snapshot_dtype="f32", accum="f64")
 
 
+def cfg_2d_316(nsteps: int = 4000) -> dict:
+    """Surrogate-loop workload: 256 x 256 design box on a 316^2 grid, dx = 5 nm,
+    10-cell CPML, 4000 steps, FP32, full design-box history (1 GB)."""
+    return workload_2d(316, 316, dx=5e-9, nsteps=nsteps, npml=10, design=(256, 256), gap=(3, 3), real="f32",
+                       snapshot_every=0)
+
+
 def small_2d(nx: int = 40, ny: int = 36, nsteps: int = 300, real: str = "f64", **kw) -> dict:
     """A small 2D case that spans several GPU tiles with ragged edges."""
     d = kw.pop("design", (16, 14))

@@ -101,6 +101,21 @@ class UNet:
         self.dcol = torch.zeros(col_elems, **f32)
         self.loss = torch.zeros(1, dtype=torch.float64, device=self.dev)
 
+    def sibling(self, batch: int) -> "UNet":
+        """A network for another batch size that shares this one's parameter
+        tensors (its gradients and Adam state are its own)."""
+        twin = UNet(self.base, batch, self.H, self.W, device=self.dev, stream=self.stream,
+                    params=self.numpy_params())
+        twin.w, twin.b = self.w, self.b
+        return twin
+
+    def numpy_params(self) -> dict:
+        out = {}
+        for n, ci, co, k in self.layers:
+            out[n + ".w"] = self.w[n].double().cpu().numpy().reshape(co, ci, k, k)
+            out[n + ".b"] = self.b[n].double().cpu().numpy()
+        return out
+
     # ------------------------------------------------------------ helpers
     def _params(self):
         for n in self.w:
