@@ -182,15 +182,51 @@ fdtd_status fdtd_gradient_static(fdtd_ctx *ctx, double *d_grad, size_t n);
 fdtd_status fdtd_gap_history(fdtd_ctx *ctx, double *d_out, size_t n);
 
 /* ---- optimization-loop helpers (Sec. 3.2, Eq. 28) ----
- * The paper updates the design with GCMMA; this library provides a projected,
- * normalised gradient-ascent step instead, and the paper's grayness measure
- * and final thresholding. */
+ * The paper updates the design with GCMMA; this library provides its
+ * per-variable steps (below), a projected, normalised gradient-ascent step
+ * as a simpler alternative, and the paper's grayness measure and final
+ * thresholding. */
 
 /* d_rho <- clip(d_rho + move * d_grad / max|d_grad|, 0, 1) on the device
  * (n = M_d; d_rho in the field precision, d_grad FP64).  A zero gradient
  * leaves rho unchanged.  Asynchronous; uses a word of the context's
  * workspace. */
 fdtd_status fdtd_ascent_step(fdtd_ctx *ctx, void *d_rho, const double *d_grad, size_t n, double move);
+
+/* Method of moving asymptotes with the conservative inner loop of GCMMA
+ * (Svanberg, Int. J. Numer. Meth. Eng. 24, 1987; SIAM J. Optim. 12, 2002),
+ * the paper's design update (Sec. 3.2), for max W~ over 0 <= rho <= 1
+ * written as min f, f = -scale * W~.  The host runs the loop; these two
+ * calls do the per-variable work.
+ *
+ * d_state: caller-owned device array of 4*n doubles (x^{k-1}, x^{k-2}, L, U,
+ * back to back), any content before iteration 0.  n = M_d; d_rho and
+ * d_rho_new in the field precision; d_grad = dW~/drho (FP64, as from
+ * fdtd_gradient); d_sums: two device doubles, overwritten.
+ *
+ * fdtd_mma_asymptotes, once per outer iteration k = 0, 1, ...: sets the
+ * asymptotes L, U from x^k = d_rho and the two previous iterates (distance
+ * 0.5 for k < 2; else 0.7x where a coordinate oscillates, 1.2x where it moves
+ * monotonically, within [0.01, 10]), shifts the iterate history, and writes
+ * d_sums[0] = sum |g|, d_sums[1] = the squared 2-norm of the first-order
+ * optimality residual (g without the entries where a bound is active and g
+ * points out of the box).
+ *
+ * fdtd_mma_solve, once per inner iteration: with df = -scale*g and the
+ * GCMMA term raa0 > 0, writes into d_rho_new the closed-form minimiser of
+ * the separable approximation p/(U-y) + q/(y-L) over
+ * max(0, L+0.1(x-L), x-move) <= y <= min(1, U-0.1(U-x), x+move)
+ * (0 < move <= 1); entries with g = 0 (gap nodes) keep x.  d_sums[0] =
+ * f~(y) - f(x) of the approximation and d_sums[1] = sum (U-L)(y-x)^2 /
+ * ((U-y)(y-L)), both for y as stored, for the caller's conservativeness test
+ * f(x) + d_sums[0] >= f(y) and its raa0 update.
+ *
+ * Both are asynchronous on the context's stream; FDTD_EINVAL for a null
+ * pointer, n != M_d, k < 0, or scale, raa0, move out of range. */
+fdtd_status fdtd_mma_asymptotes(fdtd_ctx *ctx, const void *d_rho, const double *d_grad, double *d_state, size_t n,
+                                int k, double *d_sums);
+fdtd_status fdtd_mma_solve(fdtd_ctx *ctx, const double *d_state, const double *d_grad, size_t n, double scale,
+                           double raa0, double move, void *d_rho_new, double *d_sums);
 
 /* Grayness zeta = 4 rho~^T (1 - rho~) / M of the filtered design of the last
  * fdtd_set_design, gap nodes excluded (Sec. 3.2): 0 for a black-and-white

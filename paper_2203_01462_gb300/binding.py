@@ -25,7 +25,8 @@ ACC = {"f64": 0, "comp_f32": 1}
 EXPORTS = ["fdtd_workspace_bytes", "fdtd_create", "fdtd_set_design", "fdtd_set_damping",
            "fdtd_forward", "fdtd_adjoint", "fdtd_gradient", "fdtd_gap_history", "fdtd_sync",
            "fdtd_run_host", "fdtd_get_info", "fdtd_status_string", "fdtd_destroy",
-           "fdtd_gradient_static", "fdtd_ascent_step", "fdtd_grayness", "fdtd_threshold"]
+           "fdtd_gradient_static", "fdtd_ascent_step", "fdtd_mma_asymptotes", "fdtd_mma_solve",
+           "fdtd_grayness", "fdtd_threshold"]
 
 
 class FdtdError(RuntimeError):
@@ -85,6 +86,8 @@ def load():
             "fdtd_gradient": [P, P, C.c_size_t],
             "fdtd_gradient_static": [P, P, C.c_size_t],
             "fdtd_ascent_step": [P, P, P, C.c_size_t, C.c_double],
+            "fdtd_mma_asymptotes": [P, P, P, P, C.c_size_t, C.c_int, P],
+            "fdtd_mma_solve": [P, P, P, C.c_size_t, C.c_double, C.c_double, C.c_double, P, P],
             "fdtd_grayness": [P, P],
             "fdtd_threshold": [P, P, C.c_size_t, C.c_double],
             "fdtd_gap_history": [P, P, C.c_size_t],
@@ -231,6 +234,31 @@ class Solver:
         """rho <- clip(rho + move * grad / max|grad|, 0, 1) in place (device tensors)."""
         _check(self.lib.fdtd_ascent_step(self.ctx, C.c_void_p(rho.data_ptr()), C.c_void_p(grad.data_ptr()),
                                          rho.numel(), float(move)), "fdtd_ascent_step")
+
+    def mma_state(self):
+        """Device state of the moving-asymptote update (4 M_d doubles)."""
+        t = self.torch
+        return t.zeros(4 * self.n_design, dtype=t.float64, device=self.device)
+
+    def mma_asymptotes(self, rho, grad, state, k: int):
+        """Outer MMA iteration k: asymptotes from rho = x^k and the history in
+        ``state``.  Returns a device tensor (sum |g|, squared optimality residual)."""
+        t = self.torch
+        sums = t.empty(2, dtype=t.float64, device=self.device)
+        _check(self.lib.fdtd_mma_asymptotes(self.ctx, C.c_void_p(rho.data_ptr()), C.c_void_p(grad.data_ptr()),
+                                            C.c_void_p(state.data_ptr()), rho.numel(), int(k),
+                                            C.c_void_p(sums.data_ptr())), "fdtd_mma_asymptotes")
+        return sums
+
+    def mma_solve(self, state, grad, scale: float, raa0: float, move: float, out):
+        """Subproblem minimiser into ``out`` (field precision).  Returns a device
+        tensor (approximation change f~(y) - f(x), GCMMA term d(y))."""
+        t = self.torch
+        sums = t.empty(2, dtype=t.float64, device=self.device)
+        _check(self.lib.fdtd_mma_solve(self.ctx, C.c_void_p(state.data_ptr()), C.c_void_p(grad.data_ptr()),
+                                       out.numel(), float(scale), float(raa0), float(move),
+                                       C.c_void_p(out.data_ptr()), C.c_void_p(sums.data_ptr())), "fdtd_mma_solve")
+        return sums
 
     def grayness(self):
         """zeta = 4 rho~^T (1 - rho~) / M of the current filtered design (device FP64 scalar)."""

@@ -276,7 +276,7 @@ struct Ctx2D final : fdtd_ctx {
     Pml1D<R> px{}, py{};
     R *fw_R = nullptr, *fnx_R = nullptr, *fny_R = nullptr;
     double *fw_D = nullptr, *fnx_D = nullptr, *fny_D = nullptr;
-    double *misc = nullptr;   // [0] W
+    double *misc = nullptr;   // [0] W, [1] ascent max, [4 ..] MMA partial sums
     unsigned *err = nullptr;
     void *rho_stage() override { return rstage; }
     double *grad_stage() override { return gstage; }
@@ -352,7 +352,7 @@ struct Ctx2D final : fdtd_ctx {
         fw_D = cv.take<double>(2 * FR + 1);
         fnx_D = cv.take<double>(geo.dnx);
         fny_D = cv.take<double>(geo.dny);
-        misc = cv.take<double>(4);
+        misc = cv.take<double>(4 + 2 * MMA_BLOCKS);
         err = cv.take<unsigned>(4);
         if (pml_tab) {
             R *t = pml_tab;
@@ -696,7 +696,7 @@ struct Ctx3D final : fdtd_ctx {
         snaps = cv.take<char>((size_t)nsnap * snap_stride);
         src_tab = cv.take<R>(N);
         pml_tab = cv.take<R>(6 * (size_t)(c.nx + c.ny + c.nz));
-        misc = cv.take<double>(4);
+        misc = cv.take<double>(4 + 2 * MMA_BLOCKS);
         err = cv.take<unsigned>(4);
         if (pml_tab) {
             R *t = pml_tab;
@@ -999,6 +999,36 @@ fdtd_status fdtd_ascent_step(fdtd_ctx *ctx, void *d_rho, const double *d_grad, s
     if (ctx->cfg.real_bytes == 4) launch_ascent<float>((float *)d_rho, d_grad, (long long)n, move, gmax, ctx->stream);
     else launch_ascent<double>((double *)d_rho, d_grad, (long long)n, move, gmax, ctx->stream);
     ctx->launches += 3;
+    return cuda_ok(cudaGetLastError());
+}
+
+fdtd_status fdtd_mma_asymptotes(fdtd_ctx *ctx, const void *d_rho, const double *d_grad, double *d_state, size_t n,
+                                int k, double *d_sums)
+{
+    if (!ctx || !d_rho || !d_grad || !d_state || !d_sums || (long long)n != ctx->Md || k < 0) return FDTD_EINVAL;
+    if (ctx->cfg.real_bytes == 4)
+        launch_mma_asymptotes<float>((const float *)d_rho, d_grad, d_state, (long long)n, k, ctx->W_dev() + 4, d_sums,
+                                     ctx->stream);
+    else
+        launch_mma_asymptotes<double>((const double *)d_rho, d_grad, d_state, (long long)n, k, ctx->W_dev() + 4,
+                                      d_sums, ctx->stream);
+    ctx->launches += 2;
+    return cuda_ok(cudaGetLastError());
+}
+
+fdtd_status fdtd_mma_solve(fdtd_ctx *ctx, const double *d_state, const double *d_grad, size_t n, double scale,
+                           double raa0, double move, void *d_rho_new, double *d_sums)
+{
+    if (!ctx || !d_state || !d_grad || !d_rho_new || !d_sums || (long long)n != ctx->Md) return FDTD_EINVAL;
+    if (!(scale > 0) || !isfinite(scale) || !(raa0 > 0) || !isfinite(raa0) || !(move > 0) || !(move <= 1))
+        return FDTD_EINVAL;
+    if (ctx->cfg.real_bytes == 4)
+        launch_mma_solve<float>(d_state, d_grad, (long long)n, scale, raa0, move, (float *)d_rho_new,
+                                ctx->W_dev() + 4, d_sums, ctx->stream);
+    else
+        launch_mma_solve<double>(d_state, d_grad, (long long)n, scale, raa0, move, (double *)d_rho_new,
+                                 ctx->W_dev() + 4, d_sums, ctx->stream);
+    ctx->launches += 2;
     return cuda_ok(cudaGetLastError());
 }
 

@@ -166,6 +166,15 @@ void launch_grayness(const R *rt, long long rows, int dnx, int dp, int off, int 
 void launch_scale1(double *x, double s, cudaStream_t st);
 template <typename R>
 void launch_threshold(R *rho, long long n, double level, cudaStream_t st);
+// Block count of the MMA kernels; the context keeps 2 * MMA_BLOCKS doubles of
+// per-block partial sums.
+constexpr int MMA_BLOCKS = 152 * 8;
+template <typename R>
+void launch_mma_asymptotes(const R *rho, const double *g, double *state, long long n, int k, double *part,
+                           double *sums, cudaStream_t st);
+template <typename R>
+void launch_mma_solve(const double *state, const double *g, long long n, double s, double raa0, double move, R *out,
+                      double *part, double *sums, cudaStream_t st);
 
 // 16-bit checkpoints (kind 1: BF16, 2: FP16) with one float scale per slab
 // of SNAP_SLAB consecutive words of the state block.

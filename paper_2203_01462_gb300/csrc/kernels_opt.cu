@@ -1,5 +1,6 @@
 // Design-update kernels of the optimization loop (Sec. 3.2): the ascent step
-// on rho, the grayness measure zeta = 4 rho~^T (1 - rho~) / M of the filtered
+// on rho, the method of moving asymptotes with the conservative inner loop of
+// GCMMA, the grayness measure zeta = 4 rho~^T (1 - rho~) / M of the filtered
 // design, and the final thresholding.
 #include "fdtd_internal.h"
 
@@ -74,6 +75,116 @@ __global__ void k_gray(const R *rt, long long rows, int dnx, int dp, int off, in
 
 __global__ void k_scale1(double *x, double s) { *x *= s; }
 
+// Two FP64 sums per block, reduced by shuffles and shared memory, written
+// to part[2 * block + 0/1]; k_sum_partials then adds the blocks in a fixed
+// order, so the totals do not depend on scheduling.
+__device__ __forceinline__ void block_sum2(double a, double b, double *part)
+{
+    __shared__ double sh[2][TPB / 32];
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { sh[0][w] = a; sh[1][w] = b; }
+    __syncthreads();
+    if (w == 0) {
+        a = l < TPB / 32 ? sh[0][l] : 0.0;
+        b = l < TPB / 32 ? sh[1][l] : 0.0;
+        a = warp_sum(a);
+        b = warp_sum(b);
+        if (l == 0) { part[2 * blockIdx.x] = a; part[2 * blockIdx.x + 1] = b; }
+    }
+}
+
+// One warp: sums[c] = sum over blocks of part[2 * block + c], c = 0, 1.
+__global__ void k_sum_partials(const double *part, int nblocks, double *sums)
+{
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += 32) {
+        a += part[2 * i];
+        b += part[2 * i + 1];
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (threadIdx.x == 0) { sums[0] = a; sums[1] = b; }
+}
+
+// Method of moving asymptotes (Svanberg, IJNME 1987) for max W~ over the box
+// [0, 1]^M, written as min f with f = -s W~.  State: four FP64 arrays of n
+// entries, back to back: x^{k-1} (x^k once this kernel has run), x^{k-2},
+// L, U.  Iteration k sets the asymptotes from the last three iterates:
+// distance 0.5 for k < 2, else the previous distance times 0.7 where the
+// coordinate oscillates, 1.2 where it moves monotonically, 1 where it
+// stalled, kept within [0.01, 10].  Also sums |g| (for the initial GCMMA
+// rho0) and the squared first-order optimality residual (g with the entries
+// removed where a bound is active and g points out of the box).
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_mma_asymptotes(const R *rho, const double *g, double *st, long long n, int k,
+                                                        double *part)
+{
+    double *x1 = st, *x2 = st + n, *lo = st + 2 * n, *up = st + 3 * n;
+    double sa = 0.0, sr = 0.0;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+        const double x = (double)rho[j];
+        double L, U;
+        if (k < 2) {
+            L = x - 0.5;
+            U = x + 0.5;
+        } else {
+            const double a = x1[j], t = (x - a) * (a - x2[j]);
+            const double fac = t < 0.0 ? 0.7 : (t > 0.0 ? 1.2 : 1.0);
+            L = fmin(fmax(x - fac * (a - lo[j]), x - 10.0), x - 0.01);
+            U = fmin(fmax(x + fac * (up[j] - a), x + 0.01), x + 10.0);
+        }
+        x2[j] = x1[j];
+        x1[j] = x;
+        lo[j] = L;
+        up[j] = U;
+        const double gj = g[j];
+        sa += fabs(gj);
+        if (!((x <= 0.0 && gj < 0.0) || (x >= 1.0 && gj > 0.0))) sr += gj * gj;
+    }
+    block_sum2(sa, sr, part);
+}
+
+// The MMA subproblem with the GCMMA term raa0 (Svanberg, SIAM J. Optim.
+// 2002): with df = -s g,
+//   p = (U-x)^2 (1.001 max(df,0) + 0.001 max(-df,0) + raa0),
+//   q = (x-L)^2 (0.001 max(df,0) + 1.001 max(-df,0) + raa0),
+// each coordinate's minimiser of p/(U-y) + q/(y-L) is
+// (sqrt(p) L + sqrt(q) U)/(sqrt(p) + sqrt(q)), clipped to
+// alpha = max(0, L + 0.1 (x-L), x - move), beta = min(1, U - 0.1 (U-x), x + move).
+// Entries with g = 0 (gap nodes) stay at x.  Writes y in the field
+// precision and sums, with y as stored, the approximation change
+// f~(y) - f(x) and the GCMMA term d(y) = sum (U-L)(y-x)^2/((U-y)(y-L)).
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_mma_solve(const double *st, const double *g, long long n, double s,
+                                                   double raa0, double move, R *out, double *part)
+{
+    const double *xk = st, *lo = st + 2 * n, *up = st + 3 * n;
+    double sa = 0.0, sd = 0.0;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+        const double x = xk[j], gj = g[j];
+        if (gj == 0.0) {
+            out[j] = (R)x;
+            continue;
+        }
+        const double L = lo[j], U = up[j], df = -s * gj;
+        const double pos = fmax(df, 0.0), neg = fmax(-df, 0.0);
+        const double p = (U - x) * (U - x) * (1.001 * pos + 0.001 * neg + raa0);
+        const double q = (x - L) * (x - L) * (0.001 * pos + 1.001 * neg + raa0);
+        const double alpha = fmax(fmax(0.0, L + 0.1 * (x - L)), x - move);
+        const double beta = fmin(fmin(1.0, U - 0.1 * (U - x)), x + move);
+        const double sp = sqrt(p), sq = sqrt(q);
+        const double y = fmin(fmax((sp * L + sq * U) / (sp + sq), alpha), beta);
+        const R yr = (R)y;
+        const double yd = (double)yr;
+        out[j] = yr;
+        sa += p * (yd - x) / ((U - yd) * (U - x)) + q * (x - yd) / ((yd - L) * (x - L));
+        sd += (U - L) * (yd - x) * (yd - x) / ((U - yd) * (yd - L));
+    }
+    block_sum2(sa, sd, part);
+}
+
 template <typename R>
 __global__ void k_threshold(R *rho, long long n, double level)
 {
@@ -103,6 +214,24 @@ void launch_grayness(const R *rt, long long rows, int dnx, int dp, int off, int 
 void launch_scale1(double *x, double s, cudaStream_t st) { k_scale1<<<1, 1, 0, st>>>(x, s); }
 
 template <typename R>
+void launch_mma_asymptotes(const R *rho, const double *g, double *state, long long n, int k, double *part,
+                           double *sums, cudaStream_t st)
+{
+    const int nb = blocks_for(n, MMA_BLOCKS);
+    k_mma_asymptotes<R><<<nb, TPB, 0, st>>>(rho, g, state, n, k, part);
+    k_sum_partials<<<1, 32, 0, st>>>(part, nb, sums);
+}
+
+template <typename R>
+void launch_mma_solve(const double *state, const double *g, long long n, double s, double raa0, double move, R *out,
+                      double *part, double *sums, cudaStream_t st)
+{
+    const int nb = blocks_for(n, MMA_BLOCKS);
+    k_mma_solve<R><<<nb, TPB, 0, st>>>(state, g, n, s, raa0, move, out, part);
+    k_sum_partials<<<1, 32, 0, st>>>(part, nb, sums);
+}
+
+template <typename R>
 void launch_threshold(R *rho, long long n, double level, cudaStream_t st)
 {
     k_threshold<R><<<blocks_for(n), TPB, 0, st>>>(rho, n, level);
@@ -114,6 +243,14 @@ template void launch_grayness<float>(const float *, long long, int, int, int, in
                                      double *, cudaStream_t);
 template void launch_grayness<double>(const double *, long long, int, int, int, int, int, int, int, int, int, int,
                                       double *, cudaStream_t);
+template void launch_mma_asymptotes<float>(const float *, const double *, double *, long long, int, double *,
+                                           double *, cudaStream_t);
+template void launch_mma_asymptotes<double>(const double *, const double *, double *, long long, int, double *,
+                                            double *, cudaStream_t);
+template void launch_mma_solve<float>(const double *, const double *, long long, double, double, double, float *,
+                                      double *, double *, cudaStream_t);
+template void launch_mma_solve<double>(const double *, const double *, long long, double, double, double, double *,
+                                       double *, double *, cudaStream_t);
 template void launch_threshold<float>(float *, long long, double, cudaStream_t);
 template void launch_threshold<double>(double *, long long, double, cudaStream_t);
 

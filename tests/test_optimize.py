@@ -57,3 +57,75 @@ def test_plain_optimization_raises_the_objective():
     assert np.sum(np.diff(W) > 0) >= len(W) - 3
     _, Wbin = final_design(s, rho)
     assert Wbin > 0
+
+
+@pytest.mark.parametrize("real", ["f64", "f32"])
+@pytest.mark.parametrize("k", [0, 1, 5])
+def test_mma_kernels_match_oracle(real, k):
+    import torch
+    from oracle import mma_oracle as M
+    from paper_2203_01462_gb300.binding import Solver
+    w = medium(real)
+    s = Solver(w)
+    n = s.n_design
+    npt = np.float64 if real == "f64" else np.float32
+    rng = np.random.default_rng(60 + k)
+    x = rng.random(n).astype(npt)
+    x[rng.random(n) < 0.05] = 0.0
+    x[rng.random(n) < 0.05] = 1.0
+    g = rng.standard_normal(n) * 1e-30
+    g[rng.random(n) < 0.03] = 0.0
+    x1 = rng.random(n)
+    x2 = rng.random(n)
+    L0 = x1 - rng.uniform(0.01, 1.0, n)
+    U0 = x1 + rng.uniform(0.01, 1.0, n)
+    state = torch.tensor(np.concatenate([x1, x2, L0, U0]), device="cuda")
+    xt = torch.tensor(x, device="cuda")
+    gt = torch.tensor(g, device="cuda")
+    sums = s.mma_asymptotes(xt, gt, state, k).cpu().numpy()
+    xd = x.astype(np.float64)
+    L, U = M.asymptotes(xd, x1, x2, L0, U0, k)
+    st = state.cpu().numpy()
+    np.testing.assert_array_equal(st[:n], xd)
+    np.testing.assert_array_equal(st[n:2 * n], x1)
+    np.testing.assert_allclose(st[2 * n:3 * n], L, rtol=0, atol=4e-15)
+    np.testing.assert_allclose(st[3 * n:], U, rtol=0, atol=4e-15)
+    assert sums[0] == pytest.approx(np.sum(np.abs(g)), rel=1e-12)
+    assert sums[1] == pytest.approx(M.optimality_norm(xd, g) ** 2, rel=1e-12)
+    scale, raa0, move = 3e29, 1e-3, 0.3
+    out = torch.empty(n, dtype=xt.dtype, device="cuda")
+    sd = s.mma_solve(state, gt, scale, raa0, move, out).cpu().numpy()
+    y, p, q = M.subproblem(xd, -scale * g, L, U, raa0, move)
+    y = y.astype(npt)
+    got = out.cpu().numpy()
+    if real == "f64":
+        np.testing.assert_allclose(got, y, rtol=0, atol=1e-14)
+    else:
+        # the FP64 minimiser may differ in its last bits, so the FP32 rounding may differ by one ulp
+        assert np.max(np.abs(got.astype(np.float64) - y)) <= 2 ** -24 * 1.0001
+        assert np.mean(got != y) < 1e-3
+    yd = got.astype(np.float64)
+    assert np.array_equal(got[g == 0], x[g == 0])
+    assert sd[0] == pytest.approx(M.approx_change(xd, yd, p, q, L, U), rel=1e-10)
+    assert sd[1] == pytest.approx(M.d_term(xd, yd, L, U), rel=1e-10)
+
+
+def test_gcmma_on_the_device_is_monotone_and_resumes_exactly(tmp_path):
+    from paper_2203_01462_gb300.binding import Solver
+    from paper_2203_01462_gb300.optimize import optimize_gcmma
+    w = medium("f32")
+    s = Solver(w)
+    rho0 = I.zero_gap(w, np.full(I.design_shape(w), 0.3))
+    kw = dict(levels=[3.0, 1.0], min_inner=2, norm_drop=0.5, zeta_stop=0.0, move=0.2)
+    r_full, h = optimize_gcmma(s, rho0, max_iters=8, **kw)
+    W = np.array(h.W)
+    st = np.array(h.stage)
+    assert W[-1] > 1.5 * W[0]
+    for j in set(st.tolist()):
+        wj = W[st == j]
+        assert np.all(np.diff(wj) >= -2e-10 * wj[0])
+    ck = str(tmp_path / "gcmma.npz")
+    optimize_gcmma(Solver(w), rho0, max_iters=4, checkpoint=ck, **kw)
+    r_res, h_res = optimize_gcmma(Solver(w), None, max_iters=8, resume=ck, **kw)
+    assert np.array_equal(r_full.cpu().numpy(), r_res.cpu().numpy())
+    assert h.W == h_res.W and h.inner == h_res.inner
