@@ -9,9 +9,14 @@
 // units, see Coef).  Curl component c uses the cyclic axes a = c+1, b = c+2:
 // curl_c = d_a F_b - d_b F_a, each derivative with its own CPML term in the
 // slab of its axis.  Each thread owns four x-adjacent nodes (32 x 8 x 4-node
-// blocks): where those nodes and their halo are clear of walls and CPML it
-// runs vector code with the curls written out, elsewhere generic per-node
-// code with CPML.
+// blocks) and runs one vector code path everywhere: next to the PEC walls
+// it skips the neighbour loads that fall outside the grid and masks the
+// components that are not updated there (H_c exists where p <= n-2 along
+// both of its derivative axes; E_c is updated where p <= n-2 along c and
+// 1 <= p <= n-2 across), so no warp diverges into per-node code.  The CPML
+// terms of a y- or z-slab are uniform over the four nodes and their psi
+// arrays are x-contiguous, so they move as vectors; x-slab terms are taken
+// per node.
 //
 // Every E component of a node inside the design box takes the material of
 // rho~ at that node (Eq. 5); the adjoint sums the Eq. (25) brackets of the
@@ -56,14 +61,10 @@ __device__ __forceinline__ void st4(double *p, const double (&o)[4])
     reinterpret_cast<double2 *>(p)[0] = make_double2(o[0], o[1]);
     reinterpret_cast<double2 *>(p)[1] = make_double2(o[2], o[3]);
 }
-
-// Are the four nodes i0 .. i0+3 of row (j, k) and their one-node halo clear
-// of walls and CPML slabs?
-__device__ __forceinline__ bool thread_interior(const Geo3D &g, int i0, int j, int k)
+template <typename R>
+__device__ __forceinline__ void zero4(R (&o)[4])
 {
-    const int np = g.npml;
-    return i0 - 1 >= np + 1 && i0 + VX <= g.n[0] - np - 2 && j - 1 >= np + 1 && j + 1 <= g.n[1] - np - 2 &&
-           k - 1 >= np + 1 && k + 1 <= g.n[2] - np - 2;
+    o[0] = o[1] = o[2] = o[3] = R(0);
 }
 
 // Slab index of position p along an axis of n nodes (E: node positions,
@@ -83,191 +84,244 @@ __device__ __forceinline__ long long pidx(const Geo3D &g, int ax, int s, int i, 
     return ((long long)s * g.n[1] + j) * g.px + i;
 }
 
-// Generic H update of node (i, j, k): every component, CPML where needed.
-template <typename R>
-__device__ __forceinline__ void h_node(const Geo3D &g, const State3D<R> &s, const Coef<R> &c, const Pml3D<R> &pm,
-                                       int i, int j, int k)
+// CPML-corrected curl of four x-adjacent nodes (i0 .. i0+3, row j, plane k)
+// for all three components: component c takes the derivative d[c][0] along
+// a = c+1 and d[c][1] along b = c+2 (cyclic), each divided by kappa and, in
+// the slab of its axis, plus psi <- b psi + c d; out[c] = S (t_a - t_b).
+// Along y and z the slab index and coefficients are those of row j / plane
+// k, and the psi arrays of y- and z-slabs are x-contiguous, so psi moves as
+// one vector; along x both are taken per node.  Every psi and coefficient
+// load is issued before any store.
+template <typename R, bool HALF>
+__device__ __forceinline__ void cpml_curl(const Geo3D &g, R *const (&psi)[3][2], const R *const (&tb)[3],
+                                          const R *const (&tc)[3], const R *const (&tk)[3], int i0, int j, int k,
+                                          int sy, int sz, R S, const R (&d)[3][2][4], R (&out)[3][4])
 {
-    const int p[3] = {i, j, k};
-    const long long st[3] = {1, g.px, g.PP};
-    const long long q = k * g.PP + (long long)j * g.px + i;
+    const int np = g.npml;
+    int sx[4];
 #pragma unroll
-    for (int cc = 0; cc < 3; ++cc) {
-        const int a = (cc + 1) % 3, b = (cc + 2) % 3;
-        // H component cc exists where the node is not on the last plane of a or b.
-        if (p[a] > g.n[a] - 2 || p[b] > g.n[b] - 2) continue;
-        const R da = s.E[b][q + st[a]] - s.E[b][q];  // d_a E_b (forward)
-        const R db = s.E[a][q + st[b]] - s.E[a][q];  // d_b E_a
-        R ta = da * pm.kiH[a][p[a]], tb = db * pm.kiH[b][p[b]];
-        const int sa = slabH(p[a], g.n[a], g.npml), sb = slabH(p[b], g.n[b], g.npml);
-        if (sa >= 0) {
-            R &ps = s.ph[cc][0][pidx(g, a, sa, i, j, k)];
-            ps = pm.bH[a][p[a]] * ps + pm.cH[a][p[a]] * da;
-            ta += ps;
-        }
-        if (sb >= 0) {
-            R &ps = s.ph[cc][1][pidx(g, b, sb, i, j, k)];
-            ps = pm.bH[b][p[b]] * ps + pm.cH[b][p[b]] * db;
-            tb += ps;
-        }
-        s.H[cc][q] -= c.S * (ta - tb);
-    }
-}
-
-// Generic E (and J) update of node (i, j, k): every component, CPML where
-// needed, design / gap / source logic, records and sensitivity.
-template <typename R, int MODE>
-__device__ __forceinline__ void e_node(const Geo3D &g, const State3D<R> &s, const Coef<R> &c, const Pml3D<R> &pm,
-                                       const Step3D<R> &a3, int i, int j, int k)
-{
-    const int p[3] = {i, j, k};
-    const long long st[3] = {1, g.px, g.PP};
-    const long long q = k * g.PP + (long long)j * g.px + i;
-    const bool gap = in_range(i, g.g0[0], g.gn[0]) && in_range(j, g.g0[1], g.gn[1]) && in_range(k, g.g0[2], g.gn[2]);
-    const int gidx = ((k - g.g0[2]) * g.gn[1] + (j - g.g0[1])) * g.gn[0] + (i - g.g0[0]);
-    const bool des = in_range(i, g.d0[0], g.dn[0]) && in_range(j, g.d0[1], g.dn[1]) && in_range(k, g.d0[2], g.dn[2]);
-    const long long d = ((long long)(k - g.d0[2]) * g.dn[1] + (j - g.d0[1])) * g.dp + (i - g.dxa);
-    const bool src_node = MODE == 0 && in_range(i, g.s0[0], g.s1[0] - g.s0[0]) &&
-                          in_range(j, g.s0[1], g.s1[1] - g.s0[1]) && in_range(k, g.s0[2], g.s1[2] - g.s0[2]);
-    const R eps_bg = gap ? c.eps_g : (k < g.sub_hi ? c.eps_sub : c.eps_s);
-    R rt = R(0);
-    if (des && !gap) rt = a3.rho_t[d];
-    double gsum = 0.0;
+    for (int v = 0; v < 4; ++v)  // nodes past the last one are row padding: no slab
+        sx[v] = i0 + v >= g.n[0] ? -1 : (HALF ? slabH(i0 + v, g.n[0], np) : slabE(i0 + v, g.n[0], np));
+    const long long iy = pidx(g, 1, sy, i0, j, k), iz = pidx(g, 2, sz, i0, j, k);
+    R ps[3][2][4];
 #pragma unroll
-    for (int cc = 0; cc < 3; ++cc) {
-        const int a = (cc + 1) % 3, b = (cc + 2) % 3;
-        // E component cc is updated away from the walls: 0 < p < n-1 across,
-        // p <= n-2 along its own axis.
-        if (p[cc] > g.n[cc] - 2 || p[a] < 1 || p[a] > g.n[a] - 2 || p[b] < 1 || p[b] > g.n[b] - 2) continue;
-        const R da = s.H[b][q] - s.H[b][q - st[a]];  // d_a H_b (backward)
-        const R db = s.H[a][q] - s.H[a][q - st[b]];  // d_b H_a
-        R ta = da * pm.kiE[a][p[a]], tb = db * pm.kiE[b][p[b]];
-        const int sa = slabE(p[a], g.n[a], g.npml), sb = slabE(p[b], g.n[b], g.npml);
-        if (sa >= 0) {
-            R &ps = s.pe[cc][0][pidx(g, a, sa, i, j, k)];
-            ps = pm.bE[a][p[a]] * ps + pm.cE[a][p[a]] * da;
-            ta += ps;
-        }
-        if (sb >= 0) {
-            R &ps = s.pe[cc][1][pidx(g, b, sb, i, j, k)];
-            ps = pm.bE[b][p[b]] * ps + pm.cE[b][p[b]] * db;
-            tb += ps;
-        }
-        const R curl = c.S * (ta - tb);
-        R src = R(0);
-        if (MODE == 0) {
-            if (src_node && cc == g.src_comp) src = *a3.src;
-        } else if (gap) {
-            src = -c.eps_g * a3.gap_src[(long long)cc * g.Mg + gidx];
-        }
-        const R e = s.E[cc][q];
-        R en;
-        if (des && !gap) {
-            const R eps = c.eps_s + rt * c.d_eps;
-            const R psi = c.psi_s + rt * (c.psi - c.psi_s);
-            const R sig = c.sig_max * rt * (R(1) - rt);
-            const R bJ = R(0.5) * psi * c.inv1g;
-            const R hs = R(0.5) * (sig + bJ);
-            const R cb = rcp(eps + hs);
-            const R ca = (eps - hs) * cb;
-            const R jo = s.J[cc][d];
-            en = ca * e + cb * (curl - c.half1pkJ * jo - src);
-            const R jn = c.kJ * jo + bJ * (en + e);
-            s.J[cc][d] = jn;
-            if (MODE == 0) {
-                if (a3.rec) a3.rec[(long long)cc * g.Mdi + d] = en;
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int ax = (c + 1 + h) % 3;
+            if (ax == 0) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    ps[c][h][v] = sx[v] >= 0 ? psi[c][h][pidx(g, 0, sx[v], i0 + v, j, k)] : R(0);
+            } else if (ax == 1) {
+                if (sy >= 0) ld4(psi[c][h] + iy, ps[c][h]);
             } else {
-                // Eq. (25a-c) folded through the chain rule of Eq. (27).
-                const R term = -c.d_eps * (en - e) - c.sig_max * (R(1) - R(2) * rt) * R(0.5) * (en + e) -
-                               (c.psi - c.psi_s) * rcp(psi) * R(0.5) * (jn + jo);
-                gsum += (double)a3.rec[(long long)cc * g.Mdi + d] * (double)term;
+                if (sz >= 0) ld4(psi[c][h] + iz, ps[c][h]);
             }
-        } else {
-            en = e + (curl - src) * rcp(eps_bg);
-            if (MODE == 0 && des && a3.rec) a3.rec[(long long)cc * g.Mdi + d] = en;
         }
-        s.E[cc][q] = en;
-        if (MODE == 0 && gap && a3.gap_rec) a3.gap_rec[(long long)cc * g.Mg + gidx] = en;
+    // coefficient tables are read-only: non-coherent loads, free to move past stores
+    const R by = __ldg(tb[1] + j), cy = __ldg(tc[1] + j), ky = __ldg(tk[1] + j);
+    const R bz = __ldg(tb[2] + k), cz = __ldg(tc[2] + k), kz = __ldg(tk[2] + k);
+    R t[2][4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int ax = (c + 1 + h) % 3;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const bool in = ax == 0 ? sx[v] >= 0 : (ax == 1 ? sy >= 0 : sz >= 0);
+                const R kk = ax == 0 ? (i0 + v < g.n[0] ? __ldg(tk[0] + i0 + v) : R(1)) : (ax == 1 ? ky : kz);
+                t[h][v] = d[c][h][v] * kk;
+                if (in) {
+                    const R bb = ax == 0 ? __ldg(tb[0] + i0 + v) : (ax == 1 ? by : bz);
+                    const R cc = ax == 0 ? __ldg(tc[0] + i0 + v) : (ax == 1 ? cy : cz);
+                    ps[c][h][v] = bb * ps[c][h][v] + cc * d[c][h][v];
+                    t[h][v] += ps[c][h][v];
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) out[c][v] = S * (t[0][v] - t[1][v]);
     }
-    if (MODE == 1 && des && !gap) a3.G[d] += gsum;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int ax = (c + 1 + h) % 3;
+            if (ax == 0) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    if (sx[v] >= 0) psi[c][h][pidx(g, 0, sx[v], i0 + v, j, k)] = ps[c][h][v];
+            } else if (ax == 1) {
+                if (sy >= 0) st4(psi[c][h] + iy, ps[c][h]);
+            } else {
+                if (sz >= 0) st4(psi[c][h] + iz, ps[c][h]);
+            }
+        }
 }
 
-// Interior H half step: curl E with forward differences, no CPML.
+// H half step, four x-adjacent nodes per thread:
 //   Hx -= S (dy Ez - dz Ey),  Hy -= S (dz Ex - dx Ez),  Hz -= S (dx Ey - dy Ex)
+// (forward differences).  Threads clear of every CPML slab run the plain
+// update; the others add the CPML terms (cpml_curl).
 template <typename R>
-__global__ void __launch_bounds__(TBX *TBY *TBZ) k_h3d_in(Geo3D g, State3D<R> s, Coef<R> c, Pml3D<R> pm)
+__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 3 : 1)
+    k_h3d(Geo3D g, State3D<R> s, Coef<R> c, Pml3D<R> pm)
 {
     wait_previous_grid();
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TBY, z0 = blockIdx.z * TBZ;
-    const int i0 = x0 + threadIdx.x * VX, j = y0 + threadIdx.y, k = z0 + threadIdx.z;
-    if (j >= g.n[1] || k >= g.n[2]) return;
-    if (!thread_interior(g, i0, j, k)) {
-        for (int v = 0; v < VX; ++v)
-            if (i0 + v < g.n[0]) h_node<R>(g, s, c, pm, i0 + v, j, k);
-        return;
-    }
+    const int i0 = (blockIdx.x * TBX + threadIdx.x) * VX, j = blockIdx.y * TBY + threadIdx.y,
+              k = blockIdx.z * TBZ + threadIdx.z;
+    const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+    if (i0 >= n0 || j >= n1 || k >= n2) return;
     const long long q = k * g.PP + (long long)j * g.px + i0;
     const long long P = g.px, PP = g.PP;
+    const bool yin = j <= n1 - 2, zin = k <= n2 - 2, xin = i0 + VX <= n0 - 1;  // next row / plane / node exist
     R ex[4], exN[4], exU[4], ey[4], eyU[4], ez[4], ezN[4], hx[4], hy[4], hz[4];
     ld4(s.E[0] + q, ex);
-    ld4(s.E[0] + q + P, exN);
-    ld4(s.E[0] + q + PP, exU);
     ld4(s.E[1] + q, ey);
-    ld4(s.E[1] + q + PP, eyU);
     ld4(s.E[2] + q, ez);
-    ld4(s.E[2] + q + P, ezN);
+    if (yin) {
+        ld4(s.E[0] + q + P, exN);
+        ld4(s.E[2] + q + P, ezN);
+    } else {
+        zero4(exN);
+        zero4(ezN);
+    }
+    if (zin) {
+        ld4(s.E[0] + q + PP, exU);
+        ld4(s.E[1] + q + PP, eyU);
+    } else {
+        zero4(exU);
+        zero4(eyU);
+    }
     ld4(s.H[0] + q, hx);
     ld4(s.H[1] + q, hy);
     ld4(s.H[2] + q, hz);
-    const R eyE = s.E[1][q + VX], ezE = s.E[2][q + VX];
+    const R eyE = xin ? s.E[1][q + VX] : R(0), ezE = xin ? s.E[2][q + VX] : R(0);
     const R S = c.S;
+    const int np = g.npml;
+    const int sy = slabH(j, n1, np), sz = slabH(k, n2, np);
+    const bool xslab = i0 < np || i0 + VX - 1 >= n0 - 1 - np;
+    R cu[3][4];
+    if (!xslab && sy < 0 && sz < 0) {
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const R ezx = v < 3 ? ez[v + 1] : ezE, eyx = v < 3 ? ey[v + 1] : eyE;
-        hx[v] -= S * ((ezN[v] - ez[v]) - (eyU[v] - ey[v]));
-        hy[v] -= S * ((exU[v] - ex[v]) - (ezx - ez[v]));
-        hz[v] -= S * ((eyx - ey[v]) - (exN[v] - ex[v]));
+        for (int v = 0; v < 4; ++v) {
+            const R ezx = v < 3 ? ez[v + 1] : ezE, eyx = v < 3 ? ey[v + 1] : eyE;
+            cu[0][v] = S * ((ezN[v] - ez[v]) - (eyU[v] - ey[v]));
+            cu[1][v] = S * ((exU[v] - ex[v]) - (ezx - ez[v]));
+            cu[2][v] = S * ((eyx - ey[v]) - (exN[v] - ex[v]));
+        }
+    } else {
+        R d[3][2][4];  // d[c][0]: along c+1, d[c][1]: along c+2 (forward differences of E)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            d[0][0][v] = ezN[v] - ez[v];                         // d_y Ez
+            d[0][1][v] = eyU[v] - ey[v];                         // d_z Ey
+            d[1][0][v] = exU[v] - ex[v];                         // d_z Ex
+            d[1][1][v] = (v < 3 ? ez[v + 1] : ezE) - ez[v];      // d_x Ez
+            d[2][0][v] = (v < 3 ? ey[v + 1] : eyE) - ey[v];      // d_x Ey
+            d[2][1][v] = exN[v] - ex[v];                         // d_y Ex
+        }
+        cpml_curl<R, true>(g, s.ph, pm.bH, pm.cH, pm.kiH, i0, j, k, sy, sz, S, d, cu);
+    }
+    if (xin && yin && zin) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            hx[v] -= cu[0][v];
+            hy[v] -= cu[1][v];
+            hz[v] -= cu[2][v];
+        }
+    } else {
+        // last row / plane / node: H_x exists where j, k <= n-2, H_y where
+        // k, i <= n-2, H_z where i, j <= n-2 (nodes past n0 are padding)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int i = i0 + v;
+            if (yin && zin && i < n0) hx[v] -= cu[0][v];
+            if (zin && i <= n0 - 2) hy[v] -= cu[1][v];
+            if (yin && i <= n0 - 2) hz[v] -= cu[2][v];
+        }
     }
     st4(s.H[0] + q, hx);
     st4(s.H[1] + q, hy);
     st4(s.H[2] + q, hz);
 }
 
-// Interior E half step: curl H with backward differences, no CPML; per
-// component the Drude update of Eq. (10a,b) in the design box.
+// E half step: curl H with backward differences (CPML terms as in the H
+// kernel); per component the Drude update of Eq. (10a,b) in the design box.
 //   curl_x = dy Hz - dz Hy,  curl_y = dz Hx - dx Hz,  curl_z = dx Hy - dy Hx
 template <typename R, int MODE>
-__global__ void __launch_bounds__(TBX *TBY *TBZ)
-    k_e3d_in(Geo3D g, State3D<R> s, Coef<R> c, Pml3D<R> pm, Step3D<R> a3)
+__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 3 : 1)
+    k_e3d(Geo3D g, State3D<R> s, Coef<R> c, Pml3D<R> pm, Step3D<R> a3)
 {
     wait_previous_grid();
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TBY, z0 = blockIdx.z * TBZ;
     const int i0 = x0 + threadIdx.x * VX, j = y0 + threadIdx.y, k = z0 + threadIdx.z;
-    if (j >= g.n[1] || k >= g.n[2]) return;
-    if (!thread_interior(g, i0, j, k)) {
-        for (int v = 0; v < VX; ++v)
-            if (i0 + v < g.n[0]) e_node<R, MODE>(g, s, c, pm, a3, i0 + v, j, k);
-        return;
-    }
+    const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+    if (i0 >= n0 || j >= n1 || k >= n2) return;
     const long long q = k * g.PP + (long long)j * g.px + i0;
     const long long P = g.px, PP = g.PP;
-    R hx[4], hxS[4], hxD[4], hy[4], hyD[4], hz[4], hzS[4];
+    R hx[4], hxS[4], hxD[4], hy[4], hyD[4], hz[4], hzS[4], e[3][4];
     ld4(s.H[0] + q, hx);
-    ld4(s.H[0] + q - P, hxS);
-    ld4(s.H[0] + q - PP, hxD);
     ld4(s.H[1] + q, hy);
-    ld4(s.H[1] + q - PP, hyD);
     ld4(s.H[2] + q, hz);
-    ld4(s.H[2] + q - P, hzS);
-    const R hyW = s.H[1][q - 1], hzW = s.H[2][q - 1];
-    R curl[3][4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const R hyx = v > 0 ? hy[v - 1] : hyW, hzx = v > 0 ? hz[v - 1] : hzW;
-        curl[0][v] = c.S * ((hz[v] - hzS[v]) - (hy[v] - hyD[v]));
-        curl[1][v] = c.S * ((hx[v] - hxD[v]) - (hz[v] - hzx));
-        curl[2][v] = c.S * ((hy[v] - hyx) - (hx[v] - hxS[v]));
+    if (j >= 1) {
+        ld4(s.H[0] + q - P, hxS);
+        ld4(s.H[2] + q - P, hzS);
+    } else {
+        zero4(hxS);
+        zero4(hzS);
     }
+    if (k >= 1) {
+        ld4(s.H[0] + q - PP, hxD);
+        ld4(s.H[1] + q - PP, hyD);
+    } else {
+        zero4(hxD);
+        zero4(hyD);
+    }
+    const R hyW = i0 >= 1 ? s.H[1][q - 1] : R(0), hzW = i0 >= 1 ? s.H[2][q - 1] : R(0);
+    // all E loads before any store (the compiler cannot reorder them past
+    // stores through other field pointers)
+    ld4(s.E[0] + q, e[0]);
+    ld4(s.E[1] + q, e[1]);
+    ld4(s.E[2] + q, e[2]);
+    R curl[3][4];
+    const int np = g.npml;
+    const int sy = slabE(j, n1, np), sz = slabE(k, n2, np);
+    const bool xslab = i0 < np || i0 + VX - 1 >= n0 - np;
+    if (!xslab && sy < 0 && sz < 0) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const R hyx = v > 0 ? hy[v - 1] : hyW, hzx = v > 0 ? hz[v - 1] : hzW;
+            curl[0][v] = c.S * ((hz[v] - hzS[v]) - (hy[v] - hyD[v]));
+            curl[1][v] = c.S * ((hx[v] - hxD[v]) - (hz[v] - hzx));
+            curl[2][v] = c.S * ((hy[v] - hyx) - (hx[v] - hxS[v]));
+        }
+    } else {
+        R d[3][2][4];  // backward differences of H
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            d[0][0][v] = hz[v] - hzS[v];                         // d_y Hz
+            d[0][1][v] = hy[v] - hyD[v];                         // d_z Hy
+            d[1][0][v] = hx[v] - hxD[v];                         // d_z Hx
+            d[1][1][v] = hz[v] - (v > 0 ? hz[v - 1] : hzW);      // d_x Hz
+            d[2][0][v] = hy[v] - (v > 0 ? hy[v - 1] : hyW);      // d_x Hy
+            d[2][1][v] = hx[v] - hxS[v];                         // d_y Hx
+        }
+        cpml_curl<R, false>(g, s.pe, pm.bE, pm.cE, pm.kiE, i0, j, k, sy, sz, c.S, d, curl);
+    }
+    // E_c is updated where p <= n-2 along c and 1 <= p <= n-2 across; a
+    // component that is not updated keeps its value (zero on the walls).
+    const bool full = i0 >= 1 && i0 + VX <= n0 - 1 && j >= 1 && j <= n1 - 2 && k >= 1 && k <= n2 - 2;
+    const bool jmid = j >= 1 && j <= n1 - 2, kmid = k >= 1 && k <= n2 - 2;
+    auto upd = [&](int cc, int v) -> bool {
+        const int i = i0 + v;
+        const bool imid = i >= 1 && i <= n0 - 2;
+        if (cc == 0) return i <= n0 - 2 && jmid && kmid;
+        if (cc == 1) return j <= n1 - 2 && imid && kmid;
+        return k <= n2 - 2 && imid && jmid;
+    };
     const bool touches = (x0 < g.d0[0] + g.dn[0] && x0 + TX > g.d0[0] && y0 < g.d0[1] + g.dn[1] &&
                           y0 + TBY > g.d0[1] && z0 < g.d0[2] + g.dn[2] && z0 + TBZ > g.d0[2]) ||
                          (MODE == 0 && x0 < g.s1[0] && x0 + TX > g.s0[0] && y0 < g.s1[1] && y0 + TBY > g.s0[1] &&
@@ -276,31 +330,38 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ)
     if (!touches) {
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
-            R e[4];
-            ld4(s.E[cc] + q, e);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) e[v] += curl[cc][v] * inv_bg;
-            st4(s.E[cc] + q, e);
+            for (int v = 0; v < 4; ++v)
+                if (full || upd(cc, v)) e[cc][v] += curl[cc][v] * inv_bg;
+            st4(s.E[cc] + q, e[cc]);
         }
         return;
     }
-    // Design / gap / source tile.
+    // Design / gap / source tile: every design-array load first, then the
+    // per-node updates, then the stores.
     const bool rdes = in_range(j, g.d0[1], g.dn[1]) && in_range(k, g.d0[2], g.dn[2]);
     const bool vdes = rdes && in_range(i0, g.dxa, g.dp);
     const long long d0 = ((long long)(k - g.d0[2]) * g.dn[1] + (j - g.d0[1])) * g.dp + (i0 - g.dxa);
     const bool rgap = in_range(j, g.g0[1], g.gn[1]) && in_range(k, g.g0[2], g.gn[2]);
     const bool rsrc = MODE == 0 && in_range(j, g.s0[1], g.s1[1] - g.s0[1]) && in_range(k, g.s0[2], g.s1[2] - g.s0[2]);
-    R rt4[4] = {R(0), R(0), R(0), R(0)};
-    if (vdes) ld4(a3.rho_t + d0, rt4);
-    double gadd[4] = {0.0, 0.0, 0.0, 0.0};
+    R rt4[4] = {R(0), R(0), R(0), R(0)}, J4[3][4], em4[3][4];
+    double G4[4] = {0.0, 0.0, 0.0, 0.0}, gadd[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) J4[cc][v] = em4[cc][v] = R(0);
+    if (vdes) {
+        ld4(a3.rho_t + d0, rt4);
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            ld4(s.J[cc] + d0, J4[cc]);
+            if (MODE == 1) ld4(a3.rec + cc * g.Mdi + d0, em4[cc]);
+        }
+        if (MODE == 1) ld4(a3.G + d0, G4);
+    }
+    const R src_fwd = (MODE == 0 && rsrc) ? *a3.src : R(0);
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
-        R e[4], J4[4] = {R(0), R(0), R(0), R(0)}, em4[4] = {R(0), R(0), R(0), R(0)};
-        ld4(s.E[cc] + q, e);
-        if (vdes) {
-            ld4(s.J[cc] + d0, J4);
-            if (MODE == 1) ld4(a3.rec + cc * g.Mdi + d0, em4);
-        }
         R en[4], jn4[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
@@ -309,12 +370,14 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ)
             const int gidx = ((k - g.g0[2]) * g.gn[1] + (j - g.g0[1])) * g.gn[0] + (i - g.g0[0]);
             R src = R(0);
             if (MODE == 0) {
-                if (rsrc && cc == g.src_comp && in_range(i, g.s0[0], g.s1[0] - g.s0[0])) src = *a3.src;
+                if (rsrc && cc == g.src_comp && in_range(i, g.s0[0], g.s1[0] - g.s0[0])) src = src_fwd;
             } else if (gap) {
                 src = -c.eps_g * a3.gap_src[(long long)cc * g.Mg + gidx];
             }
-            jn4[v] = J4[v];
-            if (vdes && in_range(i, g.d0[0], g.dn[0]) && !gap) {
+            jn4[v] = J4[cc][v];
+            if (!full && !upd(cc, v)) {
+                en[v] = e[cc][v];
+            } else if (vdes && in_range(i, g.d0[0], g.dn[0]) && !gap) {
                 const R rt = rt4[v];
                 const R eps = c.eps_s + rt * c.d_eps;
                 const R psi = c.psi_s + rt * (c.psi - c.psi_s);
@@ -323,19 +386,20 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ)
                 const R hs = R(0.5) * (sig + bJ);
                 const R cb = rcp(eps + hs);
                 const R ca = (eps - hs) * cb;
-                en[v] = ca * e[v] + cb * (curl[cc][v] - c.half1pkJ * J4[v] - src);
-                jn4[v] = c.kJ * J4[v] + bJ * (en[v] + e[v]);
+                en[v] = ca * e[cc][v] + cb * (curl[cc][v] - c.half1pkJ * J4[cc][v] - src);
+                jn4[v] = c.kJ * J4[cc][v] + bJ * (en[v] + e[cc][v]);
                 if (MODE == 1) {
                     // Eq. (25a-c) folded through the chain rule of Eq. (27).
-                    const R term = -c.d_eps * (en[v] - e[v]) -
-                                   c.sig_max * (R(1) - R(2) * rt) * R(0.5) * (en[v] + e[v]) -
-                                   (c.psi - c.psi_s) * rcp(psi) * R(0.5) * (jn4[v] + J4[v]);
-                    gadd[v] += (double)em4[v] * (double)term;
+                    const R term = -c.d_eps * (en[v] - e[cc][v]) -
+                                   c.sig_max * (R(1) - R(2) * rt) * R(0.5) * (en[v] + e[cc][v]) -
+                                   (c.psi - c.psi_s) * rcp(psi) * R(0.5) * (jn4[v] + J4[cc][v]);
+                    gadd[v] += (double)em4[cc][v] * (double)term;
                 }
             } else {
-                en[v] = e[v] + (curl[cc][v] - src) * (gap ? rcp(c.eps_g) : inv_bg);
+                en[v] = e[cc][v] + (curl[cc][v] - src) * (gap ? rcp(c.eps_g) : inv_bg);
             }
-            if (MODE == 0 && gap && a3.gap_rec) a3.gap_rec[(long long)cc * g.Mg + gidx] = en[v];
+            if (MODE == 0 && gap && a3.gap_rec && (full || upd(cc, v)))
+                a3.gap_rec[(long long)cc * g.Mg + gidx] = en[v];
         }
         st4(s.E[cc] + q, en);
         if (vdes) {
@@ -344,8 +408,6 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ)
         }
     }
     if (MODE == 1 && vdes) {
-        double G4[4];
-        ld4(a3.G + d0, G4);
 #pragma unroll
         for (int v = 0; v < 4; ++v) G4[v] += gadd[v];
         st4(a3.G + d0, G4);
@@ -374,9 +436,9 @@ int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, const Coef<R> &
                   const Step3D<R> &a, cudaStream_t st)
 {
     dim3 vblock(TBX, TBY, TBZ), vgrid((g.n[0] + TX - 1) / TX, (g.n[1] + TBY - 1) / TBY, (g.n[2] + TBZ - 1) / TBZ);
-    launch_pdl(k_h3d_in<R>, vgrid, vblock, st, g, s, c, pm);
-    if (mode == 0) launch_pdl(k_e3d_in<R, 0>, vgrid, vblock, st, g, s, c, pm, a);
-    else launch_pdl(k_e3d_in<R, 1>, vgrid, vblock, st, g, s, c, pm, a);
+    launch_pdl(k_h3d<R>, vgrid, vblock, st, g, s, c, pm);
+    if (mode == 0) launch_pdl(k_e3d<R, 0>, vgrid, vblock, st, g, s, c, pm, a);
+    else launch_pdl(k_e3d<R, 1>, vgrid, vblock, st, g, s, c, pm, a);
     return 2;
 }
 
