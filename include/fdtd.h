@@ -70,6 +70,14 @@ enum { FDTD_SNAP_F32 = 0, FDTD_SNAP_BF16 = 1, FDTD_SNAP_F16 = 2 };
 enum { FDTD_ACC_F64 = 0, FDTD_ACC_COMP_F32 = 1 };
 enum { FDTD_SIGMA_PAPER = 0, FDTD_SIGMA_PEAK_NORMALISED = 1 };
 
+/* Excitation g(t) = envelope(u) * sum_b sin(2 pi f0[b] u), u = t - t0.
+ * FDTD_WAVE_GAUSS: envelope exp(-(u/tau)^2).
+ * FDTD_WAVE_SINC_HANN (the paper's excitation, Sec. 2, Fig. 1c-d): a sinc
+ * with a rectangular spectrum of width B = bandwidth, sin(pi B u)/(pi B u),
+ * kept for |u| < T = lobes / B and smoothed by the Hanning window
+ * (1 + cos(pi u / T)) / 2; zero outside.  t0 >= T starts it from rest. */
+enum { FDTD_WAVE_GAUSS = 0, FDTD_WAVE_SINC_HANN = 1 };
+
 /* Problem description.  Boxes are half-open node ranges [lo, hi) per axis
  * (x, y, z); in 2D the z range must be [0, 1).  Grid: nx x ny Ez nodes in
  * 2D; nx x ny x nz Yee nodes in 3D. */
@@ -91,9 +99,9 @@ typedef struct fdtd_config {
     int gap_lo[3], gap_hi[3];
     int src_lo[3], src_hi[3]; /* soft current source box (Ez in 2D, src_comp   */
                               /* edges in 3D)                                 */
-    int nbands;               /* 1 or 2 Gaussian-modulated carriers            */
+    int nbands;               /* 1 or 2 carriers under one envelope            */
     double f0[2];             /* carrier frequencies, Hz                       */
-    double tau, t0;           /* envelope exp(-((t - t0) / tau)^2), s          */
+    double tau, t0;           /* Gaussian width (FDTD_WAVE_GAUSS) and delay, s */
     double src_amp;           /* J_src = src_amp eps0 c0 / dx g(t), A/m^2      */
     int nsteps;               /* N                                             */
     int filter_radius;        /* Gaussian filter half-width, cells; 0 = none   */
@@ -108,6 +116,9 @@ typedef struct fdtd_config {
     int accum_kind;           /* FDTD_ACC_*: sensitivity accumulator           */
     int src_comp;             /* 3D: E component the source drives (0 x, 1 y, */
                               /* 2 z); the source box holds those edges      */
+    int waveform;             /* FDTD_WAVE_*: envelope of the carrier(s)       */
+    double bandwidth;         /* FDTD_WAVE_SINC_HANN: rectangle width B, Hz    */
+    int lobes;                /* FDTD_WAVE_SINC_HANN: lobes kept per side      */
 } fdtd_config;
 
 typedef struct fdtd_ctx fdtd_ctx;

@@ -69,7 +69,7 @@ typedef struct or_config {
     int design_lo[3], design_hi[3]; /* design box, half-open node/cell ranges   */
     int gap_lo[3], gap_hi[3];       /* gap box (inside the design box)          */
     int src_lo[3], src_hi[3];       /* soft current source box (Ez nodes/edges) */
-    int nbands;            /* 1 or 2 Gaussian-modulated carriers                */
+    int nbands;            /* 1 or 2 carriers under one envelope                */
     double f0[2];          /* carrier frequencies, Hz                           */
     double tau, t0;        /* Gaussian envelope exp(-((t-t0)/tau)^2), s         */
     double src_amp;        /* J_src = src_amp * eps0 c0 / dx * g(t), A/m^2      */
@@ -80,6 +80,9 @@ typedef struct or_config {
     double sub_eps;        /* 3D: background eps for cells with k < sub_hi      */
     int sub_hi;
     int src_comp;          /* 3D: component driven by the source (0 x, 1 y, 2 z) */
+    int waveform;          /* 0: Gaussian envelope; 1: truncated sinc x Hanning */
+    double bandwidth;      /* waveform 1: width B of the rectangular spectrum, Hz */
+    int lobes;             /* waveform 1: sinc kept for |t - t0| < lobes / B     */
 } or_config;
 
 static int g_threads = 1;
@@ -97,15 +100,32 @@ int or_get_threads(void) { return g_threads; }
 static double or_eps0(void) { return 1.0 / (OR_MU0 * OR_C0 * OR_C0); }
 static double or_dt(const or_config *c) { return c->courant * c->dx / OR_C0; }
 
-/* Excitation: Gaussian-modulated carrier(s).  The paper drives with a
- * windowed sinc (Sec. 2); the workloads here use a Gaussian envelope. */
+/* Excitation: carrier(s) sin(2 pi f0 (t - t0)) under an envelope.
+ * waveform 0: Gaussian exp(-((t - t0)/tau)^2).
+ * waveform 1 (the paper's, Sec. 2 and Fig. 1c-d): a sinc whose spectrum is
+ * a rectangle of width B, sin(pi B u)/(pi B u) with u = t - t0, truncated
+ * after `lobes` lobes on each side (|u| < T = lobes/B) and smoothed by the
+ * Hanning window (1 + cos(pi u / T))/2, which rounds the spectrum's edges. */
 static double or_signal(const or_config *c, double t)
 {
-    double env = exp(-((t - c->t0) / c->tau) * ((t - c->t0) / c->tau));
+    const double u = t - c->t0;
     double s = 0.0;
     for (int b = 0; b < c->nbands; ++b)
-        s += sin(2.0 * OR_PI * c->f0[b] * (t - c->t0));
-    return env * s;
+        s += sin(2.0 * OR_PI * c->f0[b] * u);
+    if (c->waveform == 1) {
+        const double T = c->lobes / c->bandwidth;
+        if (fabs(u) >= T) return 0.0;
+        const double x = OR_PI * c->bandwidth * u;
+        const double sinc = x == 0.0 ? 1.0 : sin(x) / x;
+        return sinc * 0.5 * (1.0 + cos(OR_PI * u / T)) * s;
+    }
+    return exp(-(u / c->tau) * (u / c->tau)) * s;
+}
+
+/* The excitation sampled at times t (n samples), for tests. */
+void or_signal_samples(const or_config *c, const double *t, int n, double *out)
+{
+    for (int k = 0; k < n; ++k) out[k] = or_signal(c, t[k]);
 }
 
 /* Eq. (5a-c): material of one design node from its filtered density. */

@@ -37,7 +37,7 @@ class OrConfig(C.Structure):
         ("src_amp", C.c_double), ("nsteps", C.c_int),
         ("filter_radius", C.c_int), ("filter_sigma", C.c_double),
         ("sigma_form", C.c_int), ("sub_eps", C.c_double), ("sub_hi", C.c_int),
-        ("src_comp", C.c_int),
+        ("src_comp", C.c_int), ("waveform", C.c_int), ("bandwidth", C.c_double), ("lobes", C.c_int),
     ]
 
 
@@ -65,6 +65,7 @@ def lib():
             L.or_filter.argtypes = [C.POINTER(OrConfig), dp, dp]
             L.or_filter_T.argtypes = [C.POINTER(OrConfig), dp, dp]
             L.or_material.argtypes = [C.POINTER(OrConfig), C.c_double, C.c_double, dp, dp, dp]
+            L.or_signal_samples.argtypes = [C.POINTER(OrConfig), dp, C.c_int, dp]
             L.or_set_threads.argtypes = [C.c_int]
             L.or_get_threads.restype = C.c_int
             _lib = L
@@ -82,7 +83,7 @@ def threads() -> int:
 def config(w: dict) -> OrConfig:
     c = OrConfig()
     for name, ctype in OrConfig._fields_:
-        v = w.get(name, 2 if name == "src_comp" else None)
+        v = w.get(name, {"src_comp": 2, "waveform": 0, "bandwidth": 0.0, "lobes": 0}.get(name))
         if name == "f0":
             c.f0[0], c.f0[1] = float(v[0]), float(v[1])
         elif isinstance(getattr(c, name), C.Array):
@@ -178,6 +179,15 @@ def filt(w: dict, x: np.ndarray, transpose: bool = False) -> np.ndarray:
     out = np.zeros(M)
     cfg = config(w)
     (lib().or_filter_T if transpose else lib().or_filter)(C.byref(cfg), _dptr(x), _dptr(out))
+    return out
+
+
+def signal(w: dict, t: np.ndarray) -> np.ndarray:
+    """The excitation g(t) of the workload at times t (s)."""
+    c = config(w)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    out = np.empty_like(t)
+    lib().or_signal_samples(C.byref(c), _dptr(t), t.size, _dptr(out))
     return out
 
 

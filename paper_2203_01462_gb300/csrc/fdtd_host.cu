@@ -78,7 +78,14 @@ fdtd_status validate(const fdtd_config *c)
     if (c->nsteps < 1) return FDTD_EINVAL;
     if (!(c->omega_p > 0) || !(c->psi_s_ratio > 0) || c->gamma_p < 0) return FDTD_EINVAL;
     if (!(c->eps_s > 0) || !(c->eps_g > 0) || !(c->eps_inf > 0)) return FDTD_EINVAL;
-    if (c->nbands < 1 || c->nbands > 2 || !(c->tau > 0)) return FDTD_EINVAL;
+    if (c->nbands < 1 || c->nbands > 2) return FDTD_EINVAL;
+    if (c->waveform == FDTD_WAVE_GAUSS) {
+        if (!(c->tau > 0)) return FDTD_EINVAL;
+    } else if (c->waveform == FDTD_WAVE_SINC_HANN) {
+        if (!(c->bandwidth > 0) || !isfinite(c->bandwidth) || c->lobes < 1) return FDTD_EINVAL;
+    } else {
+        return FDTD_EINVAL;
+    }
     int n[3] = {c->nx, c->ny, c->nz};
     if (!box_ok(c->design_lo, c->design_hi, n, c->ndim, false)) return FDTD_EINVAL;
     if (!box_ok(c->gap_lo, c->gap_hi, n, c->ndim, true)) return FDTD_EINVAL;
@@ -122,12 +129,22 @@ PmlPoint pml_point(const fdtd_config *c, int n, double p)
     return r;
 }
 
+// Excitation g(t) (see FDTD_WAVE_* in the header): carriers times either a
+// Gaussian envelope or the paper's Hanning-smoothed, truncated sinc.
 double excitation(const fdtd_config *c, double t)
 {
-    const double u = (t - c->t0) / c->tau;
+    const double u = t - c->t0;
     double s = 0.0;
-    for (int b = 0; b < c->nbands; ++b) s += sin(2.0 * kPi * c->f0[b] * (t - c->t0));
-    return exp(-u * u) * s;
+    for (int b = 0; b < c->nbands; ++b) s += sin(2.0 * kPi * c->f0[b] * u);
+    if (c->waveform == FDTD_WAVE_SINC_HANN) {
+        const double half = c->lobes / c->bandwidth;  // T: the window's half-length
+        if (!(fabs(u) < half)) return 0.0;
+        const double a = kPi * c->bandwidth * u;
+        const double envelope = (a == 0.0 ? 1.0 : sin(a) / a) * 0.5 * (1.0 + cos(kPi * u / half));
+        return envelope * s;
+    }
+    const double v = u / c->tau;
+    return exp(-v * v) * s;
 }
 
 }  // namespace

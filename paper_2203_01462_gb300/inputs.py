@@ -46,6 +46,17 @@ def pulse(center_m: float = 800e-9, half_width_hz: float = 100e12, nbands: int =
     return dict(nbands=len(cs), f0=f0, tau=tau, t0=4.0 * tau)
 
 
+def sinc_hanning(center_m: float = 500e-9, rel_bandwidth: float = 0.2, lobes: int = 4) -> dict:
+    """The paper's excitation (Sec. 2, Fig. 1c-d): a sinc truncated after
+    ``lobes`` lobes per side, Hanning-smoothed, on a carrier at c/center.
+    Its spectrum is a rectangle of width B = rel_bandwidth * f0 with rounded
+    edges, i.e. ``rel_bandwidth`` of f0 at half maximum; t0 = lobes / B."""
+    f0 = C0 / center_m
+    B = rel_bandwidth * f0
+    t0 = lobes / B
+    return dict(waveform=1, bandwidth=B, lobes=int(lobes), nbands=1, f0=[f0, 0.0], tau=t0, t0=t0)
+
+
 def _centered_box(n: int, w: int) -> tuple[int, int]:
     lo = (n - w) // 2
     return lo, lo + w

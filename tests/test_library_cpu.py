@@ -52,6 +52,9 @@ def test_workspace_sizes():
     dict(nsteps=0),
     dict(omega_p=0.0),
     dict(psi_s_ratio=0.0),                 # Eq. (25a) divides by psi_i
+    dict(waveform=2),                      # no such excitation
+    dict(waveform=1, bandwidth=0.0, lobes=4),
+    dict(waveform=1, bandwidth=1e14, lobes=0),
 ])
 def test_bad_configurations_rejected(bad):
     w = I.small_2d()

@@ -327,3 +327,47 @@ def test_grayness_definition():
     assert O.grayness(w, np.zeros(shape)) == 0.0
     assert O.grayness(w, I.zero_gap(w, np.ones(shape))) == 0.0
     assert abs(O.grayness(w, np.full(shape, 0.5)) - 1.0) < 1e-15
+
+
+# ---- the paper's excitation (Sec. 2, Fig. 1c-d)
+
+def test_sinc_hanning_spectrum_has_the_stated_bandwidth():
+    """A sinc truncated after four lobes, Hanning-smoothed, on a 600 THz
+    carrier: the paper states a 20 % bandwidth at half maximum.  The
+    amplitude spectrum must be centred on the carrier with a half-maximum
+    width of 20 % of it (the rounding of the edges keeps the half-maximum
+    points at the edges of the rectangle)."""
+    w = I.workload_2d(41, 37, dx=20e-9, nsteps=10)
+    w.update(I.sinc_hanning(center_m=C0 / 600e12, rel_bandwidth=0.2, lobes=4))
+    f0, B = 600e12, 120e12
+    dt = 1e-17
+    t = np.arange(0.0, 2 * w["t0"] + 50e-15, dt)
+    g = O.signal(w, t)
+    assert g[0] == 0.0 and g[-1] == 0.0
+    nfft = 1 << 22
+    spec = np.abs(np.fft.rfft(g, nfft))
+    f = np.fft.rfftfreq(nfft, dt)
+    band = (f > 300e12) & (f < 900e12)
+    fb, sb = f[band], spec[band]
+    half = sb >= 0.5 * sb.max()
+    lo, hi = fb[half][0], fb[half][-1]
+    assert abs(0.5 * (lo + hi) - f0) <= 0.005 * f0
+    assert abs((hi - lo) - B) <= 0.03 * B
+    # outside the band the rounded rectangle has fallen well below its plateau
+    assert spec[(f > 0) & (f < f0 - B)].max() < 0.05 * sb.max()
+    assert spec[f > f0 + B].max() < 0.05 * sb.max()
+
+
+def test_sinc_hanning_envelope_zeros_and_support():
+    """The envelope vanishes at the sinc zeros t0 +- m/B (m = 1 .. 3) and
+    beyond t0 +- 4/B."""
+    w = I.workload_2d(41, 37, dx=20e-9, nsteps=10)
+    w.update(I.sinc_hanning(center_m=C0 / 600e12, rel_bandwidth=0.2, lobes=4))
+    B, t0 = w["bandwidth"], w["t0"]
+    # probe the envelope through the carrier's quarter period after each zero
+    tq = 0.25 / w["f0"][0]
+    for m in (1, 2, 3):
+        for sgn in (-1, 1):
+            tz = t0 + sgn * m / B
+            assert abs(O.signal(w, np.array([tz]))[0]) < 1e-12
+    assert O.signal(w, np.array([t0 + 4 / B + tq, t0 - 4 / B - tq])).tolist() == [0.0, 0.0]

@@ -138,3 +138,19 @@ def test_autograd_matches_oracle_gradient():
     (3.0 * W).backward()
     assert abs(W.item() - ref["W"]) <= 1e-10 * abs(ref["W"])
     assert l2rel(r.grad.cpu().numpy().reshape(-1), 3.0 * ref["grad"]) <= 1e-9
+
+
+@pytest.mark.parametrize("real", ["f64", "f32"])
+def test_sinc_hanning_excitation_matches_oracle(real):
+    """The paper's truncated, Hanning-smoothed sinc excitation (Sec. 2),
+    20 % bandwidth around 600 THz, against the oracle."""
+    w = fast_case(real, snapshot_every=9 if real == "f32" else 0, nsteps=500)
+    w.update(I.sinc_hanning(center_m=500e-9, rel_bandwidth=0.5, lobes=4))
+    rho = I.rho_uniform(w, 17)
+    ref = O.gradient(w, rho, 0.0, 1.0)
+    s = solver(w)
+    W, g = s.evaluate(rho, 0.0, 1.0)
+    s.sync()
+    tol_w, tol_g = (1e-10, 1e-9) if real == "f64" else (1e-4, 1e-3)
+    assert abs(float(W.item()) - ref["W"]) <= tol_w * abs(ref["W"])
+    assert l2rel(g.cpu().numpy(), ref["grad"]) <= tol_g
