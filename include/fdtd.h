@@ -204,6 +204,17 @@ fdtd_status fdtd_gap_history(fdtd_ctx *ctx, double *d_out, size_t n);
  * workspace. */
 fdtd_status fdtd_ascent_step(fdtd_ctx *ctx, void *d_rho, const double *d_grad, size_t n, double move);
 
+/* Spectrum of the recorded gap field (the observation domain of Sec. 3.2,
+ * whose average |E| / |E_in| is the paper's field enhancement): with the
+ * e^{j w t} convention, E(w) = dt sum_{n=0..N} E^n e^{-j w n dt}, for each
+ * of nf frequencies d_freqs (device, Hz) and each recorded gap value
+ * (2D: M_g E_z nodes; 3D: 3 components x M_g nodes, component-major).
+ * d_out (device) receives nf x ncomp x M_g complex values as (re, im)
+ * double pairs, frequency-major.  Requires a forward run since the last
+ * fdtd_set_design (FDTD_ESTATE otherwise); FDTD_EINVAL for null pointers,
+ * nf < 1 or an empty gap.  Asynchronous. */
+fdtd_status fdtd_gap_spectrum(fdtd_ctx *ctx, const double *d_freqs, int nf, double *d_out);
+
 /* Method of moving asymptotes with the conservative inner loop of GCMMA
  * (Svanberg, Int. J. Numer. Meth. Eng. 24, 1987; SIAM J. Optim. 12, 2002),
  * the paper's design update (Sec. 3.2), for max W~ over 0 <= rho <= 1

@@ -14,6 +14,7 @@ import threading
 
 import numpy as np
 
+C0 = 299792458.0  # speed of light in vacuum, m/s
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fdtd_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
@@ -189,6 +190,20 @@ def signal(w: dict, t: np.ndarray) -> np.ndarray:
     out = np.empty_like(t)
     lib().or_signal_samples(C.byref(c), _dptr(t), t.size, _dptr(out))
     return out
+
+
+def gap_spectrum(w: dict, gap_hist: np.ndarray, freqs) -> np.ndarray:
+    """E(f) = dt sum_n E^n exp(-j 2 pi f n dt) of each recorded gap value
+    (the e^{j w t} convention of Sec. 2), from the history of ``forward``:
+    (nf, M_g) in 2D, (nf, 3, M_g) in 3D."""
+    dt = w["courant"] * w["dx"] / C0
+    h = np.asarray(gap_hist, dtype=np.float64)
+    n = np.arange(h.shape[0])
+    out = []
+    for f in np.atleast_1d(np.asarray(freqs, dtype=np.float64)):
+        ph = np.exp(-2j * np.pi * f * n * dt)
+        out.append(dt * np.tensordot(ph, h, axes=(0, 0)))
+    return np.array(out)
 
 
 def material(w: dict, rho: float, sigma_max: float = 0.0) -> tuple[float, float, float]:

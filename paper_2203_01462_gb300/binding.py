@@ -25,7 +25,7 @@ ACC = {"f64": 0, "comp_f32": 1}
 EXPORTS = ["fdtd_workspace_bytes", "fdtd_create", "fdtd_set_design", "fdtd_set_damping",
            "fdtd_forward", "fdtd_adjoint", "fdtd_gradient", "fdtd_gap_history", "fdtd_sync",
            "fdtd_run_host", "fdtd_get_info", "fdtd_status_string", "fdtd_destroy",
-           "fdtd_gradient_static", "fdtd_ascent_step", "fdtd_mma_asymptotes", "fdtd_mma_solve",
+           "fdtd_gradient_static", "fdtd_gap_spectrum", "fdtd_ascent_step", "fdtd_mma_asymptotes", "fdtd_mma_solve",
            "fdtd_grayness", "fdtd_threshold"]
 
 
@@ -87,6 +87,7 @@ def load():
             "fdtd_gradient": [P, P, C.c_size_t],
             "fdtd_gradient_static": [P, P, C.c_size_t],
             "fdtd_ascent_step": [P, P, P, C.c_size_t, C.c_double],
+            "fdtd_gap_spectrum": [P, P, C.c_int, P],
             "fdtd_mma_asymptotes": [P, P, P, P, C.c_size_t, C.c_int, P],
             "fdtd_mma_solve": [P, P, P, C.c_size_t, C.c_double, C.c_double, C.c_double, P, P],
             "fdtd_grayness": [P, P],
@@ -236,6 +237,18 @@ class Solver:
         """rho <- clip(rho + move * grad / max|grad|, 0, 1) in place (device tensors)."""
         _check(self.lib.fdtd_ascent_step(self.ctx, C.c_void_p(rho.data_ptr()), C.c_void_p(grad.data_ptr()),
                                          rho.numel(), float(move)), "fdtd_ascent_step")
+
+    def gap_spectrum(self, freqs):
+        """Spectrum of the gap field of the last forward run at ``freqs`` (Hz):
+        complex128 tensor (nf, M_g) in 2D, (nf, 3, M_g) in 3D."""
+        t = self.torch
+        f = t.as_tensor(freqs, dtype=t.float64).to(self.device).contiguous().reshape(-1)
+        nc = 3 if self.cfg.ndim == 3 else 1
+        out = t.empty(f.numel() * nc * self.n_gap * 2, dtype=t.float64, device=self.device)
+        _check(self.lib.fdtd_gap_spectrum(self.ctx, C.c_void_p(f.data_ptr()), f.numel(),
+                                          C.c_void_p(out.data_ptr())), "fdtd_gap_spectrum")
+        z = t.view_as_complex(out.reshape(-1, 2))
+        return z.reshape((f.numel(), 3, self.n_gap) if nc == 3 else (f.numel(), self.n_gap))
 
     def mma_state(self):
         """Device state of the moving-asymptote update (4 M_d doubles)."""

@@ -169,6 +169,7 @@ struct fdtd_ctx {
     virtual fdtd_status adjoint() = 0;
     virtual fdtd_status gradient(double *d_grad) = 0;
     virtual fdtd_status gap_history(double *d_out) = 0;
+    virtual fdtd_status gap_spectrum(const double *d_freqs, int nf, double *d_out) = 0;
     // fdtd_gradient with the filter-transpose intermediates in s1, s2.
     virtual fdtd_status gradient_scratch(double *d_grad, double *s1, double *s2) = 0;
     // Optimization-loop helpers.
@@ -620,6 +621,12 @@ struct Ctx2D final : fdtd_ctx {
         ++launches;
         return check_launch();
     }
+    fdtd_status gap_spectrum(const double *d_freqs, int nf, double *d_out) override
+    {
+        launch_gap_dft<R>(gap_hist, (long long)cfg.nsteps + 1, (int)Mg, dt, d_freqs, nf, d_out, stream);
+        ++launches;
+        return check_launch();
+    }
 };
 
 // ------------------------------------------------------------------ 3D
@@ -864,6 +871,12 @@ struct Ctx3D final : fdtd_ctx {
         ++launches;
         return check_launch();
     }
+    fdtd_status gap_spectrum(const double *d_freqs, int nf, double *d_out) override
+    {
+        launch_gap_dft<R>(gap_hist, (long long)cfg.nsteps + 1, (int)(3 * Mg), dt, d_freqs, nf, d_out, stream);
+        ++launches;
+        return check_launch();
+    }
 };
 
 }  // namespace
@@ -1007,6 +1020,13 @@ fdtd_status fdtd_gap_history(fdtd_ctx *ctx, double *d_out, size_t n)
         return FDTD_EINVAL;
     if (!ctx->fwd_done) return FDTD_ESTATE;
     return ctx->gap_history(d_out);
+}
+
+fdtd_status fdtd_gap_spectrum(fdtd_ctx *ctx, const double *d_freqs, int nf, double *d_out)
+{
+    if (!ctx || !d_freqs || !d_out || nf < 1 || ctx->Mg < 1) return FDTD_EINVAL;
+    if (!ctx->fwd_done) return FDTD_ESTATE;
+    return ctx->gap_spectrum(d_freqs, nf, d_out);
 }
 
 fdtd_status fdtd_ascent_step(fdtd_ctx *ctx, void *d_rho, const double *d_grad, size_t n, double move)

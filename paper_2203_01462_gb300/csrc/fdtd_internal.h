@@ -155,6 +155,9 @@ void launch_assemble_3d(const double *G, double *out, int dx, int dy, int dz, in
 void launch_zero_gap_2d(double *g, int dnx, int gx0, int gy0, int gnx, int gny, cudaStream_t st);
 template <typename R>
 void launch_to_double(const R *in, double *out, long long n, cudaStream_t st);
+template <typename R>
+void launch_gap_dft(const R *x, long long nt, int m, double dt, const double *freqs, int nf, double *out,
+                    cudaStream_t st);
 void launch_copy_bytes(const void *src, void *dst, size_t bytes, cudaStream_t st);
 
 // Optimization-loop kernels (kernels_opt.cu).

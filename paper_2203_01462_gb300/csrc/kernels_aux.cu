@@ -303,6 +303,48 @@ void launch_zero_gap_2d(double *g, int dnx, int gx0, int gy0, int gnx, int gny, 
     k_zero_gap_2d<<<(n + TPB - 1) / TPB, TPB, 0, st>>>(g, dnx, gx0, gy0, gnx, gny);
 }
 
+// Discrete Fourier transform of a recorded time series (nt steps of m
+// entries, x[n * m + e]) at nf frequencies, one thread per (frequency,
+// entry):  out[2 (f m + e) + 0/1] = dt sum_n x[n m + e] (cos, -sin)(w n),
+// w = 2 pi freq[f] dt.  The phase factor advances by one complex rotation
+// per step and is re-seeded from sincos every 256 steps, so its rounding
+// error stays at a few ulp.
+template <typename R>
+__global__ void k_gap_dft(const R *x, long long nt, int m, double dt, const double *freqs, int nf, double *out)
+{
+    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= (long long)nf * m) return;
+    const int f = (int)(id / m), e = (int)(id % m);
+    const double w = 2.0 * 3.14159265358979323846 * freqs[f] * dt;
+    double sw, cw;
+    sincos(w, &sw, &cw);
+    double re = 0.0, im = 0.0;
+    for (long long n0 = 0; n0 < nt; n0 += 256) {
+        double zs, zc;
+        sincos(w * (double)n0, &zs, &zc);
+        double zr = zc, zi = -zs;  // e^{-i w n}
+        const long long n1 = n0 + 256 < nt ? n0 + 256 : nt;
+        for (long long n = n0; n < n1; ++n) {
+            const double v = (double)x[n * m + e];
+            re += v * zr;
+            im += v * zi;
+            const double t = zr * cw + zi * sw;  // times e^{-i w}
+            zi = zi * cw - zr * sw;
+            zr = t;
+        }
+    }
+    out[2 * id] = re * dt;
+    out[2 * id + 1] = im * dt;
+}
+
+template <typename R>
+void launch_gap_dft(const R *x, long long nt, int m, double dt, const double *freqs, int nf, double *out,
+                    cudaStream_t st)
+{
+    const long long n = (long long)nf * m;
+    k_gap_dft<R><<<(unsigned)((n + TPB - 1) / TPB), TPB, 0, st>>>(x, nt, m, dt, freqs, nf, out);
+}
+
 template <typename R>
 void launch_to_double(const R *in, double *out, long long n, cudaStream_t st)
 {
@@ -341,6 +383,10 @@ template void launch_objective<double>(const double *, long long, double, double
                                        cudaStream_t);
 template void launch_pitch2d<float>(const float *, float *, int, int, int, int, cudaStream_t);
 template void launch_pitch2d<double>(const double *, double *, int, int, int, int, cudaStream_t);
+template void launch_gap_dft<float>(const float *, long long, int, double, const double *, int, double *,
+                                    cudaStream_t);
+template void launch_gap_dft<double>(const double *, long long, int, double, const double *, int, double *,
+                                     cudaStream_t);
 template void launch_to_double<float>(const float *, double *, long long, cudaStream_t);
 template void launch_to_double<double>(const double *, double *, long long, cudaStream_t);
 

@@ -371,3 +371,32 @@ def test_sinc_hanning_envelope_zeros_and_support():
             tz = t0 + sgn * m / B
             assert abs(O.signal(w, np.array([tz]))[0]) < 1e-12
     assert O.signal(w, np.array([t0 + 4 / B + tq, t0 - 4 / B - tq])).tolist() == [0.0, 0.0]
+
+
+# ---- gap spectrum (the field-enhancement monitor)
+
+def test_gap_spectrum_equals_fft_at_bin_frequencies():
+    """At f_k = k / (N dt) the spectrum reduces to dt times numpy's FFT (with
+    the e^{-j w n dt} kernel of the e^{j w t} convention)."""
+    w = I.small_2d(nsteps=255)
+    w.update(I.pulse(800e-9, 300e12))
+    dt = w["courant"] * w["dx"] / C0
+    rng = np.random.default_rng(5)
+    h = rng.standard_normal((256, 7))
+    k = np.array([0, 1, 5, 17, 100, 128])
+    z = O.gap_spectrum(w, h, k / (256 * dt))
+    ref = dt * np.fft.fft(h, axis=0)[k]
+    np.testing.assert_allclose(z, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_gap_spectrum_of_a_cosine():
+    """A cosine with an integer number m of periods over N samples:
+    E(f_m) = dt N / 2 exactly, real, and zero at the other bins."""
+    w = I.small_2d(nsteps=999)
+    dt = w["courant"] * w["dx"] / C0
+    N, m = 1000, 37
+    n = np.arange(N)
+    h = np.cos(2 * np.pi * m * n / N)[:, None]
+    z = O.gap_spectrum(w, h, np.array([m, m + 3]) / (N * dt))[:, 0]
+    assert z[0] == pytest.approx(dt * N / 2, rel=1e-12)
+    assert abs(z[1]) <= 1e-12 * dt * N
