@@ -83,6 +83,9 @@ typedef struct or_config {
     int waveform;          /* 0: Gaussian envelope; 1: truncated sinc x Hanning */
     double bandwidth;      /* waveform 1: width B of the rectangular spectrum, Hz */
     int lobes;             /* waveform 1: sinc kept for |t - t0| < lobes / B     */
+    int pol;               /* 2D: 0 = E_z out of plane (Ez, Hx, Hy, Jz);        */
+                           /* 1 = E in plane (Ex, Ey, Hz, Jx, Jy), design and   */
+                           /* gap per Yee edge                                  */
 } or_config;
 
 static int g_threads = 1;
@@ -156,11 +159,57 @@ static long box_count(const int *lo, const int *hi, int ndim)
     return n;
 }
 
+/* In-plane 2D (pol 1): the design and gap boxes are cell ranges; their
+ * Yee edges are E_x edges (i+1/2, j) with lo_x <= i < hi_x, lo_y <= j <= hi_y
+ * and E_y edges (i, j+1/2) with lo_x <= i <= hi_x, lo_y <= j < hi_y. */
+static long edge_count(const int *lo, const int *hi)
+{
+    long w = hi[0] - lo[0], h = hi[1] - lo[1];
+    if (w <= 0 || h <= 0) return 0;
+    return w * (h + 1) + (w + 1) * h;
+}
+
 int or_sizes(const or_config *c, long *n_design, long *n_gap)
 {
+    if (c->ndim == 2 && c->pol == 1) {
+        *n_design = edge_count(c->design_lo, c->design_hi);
+        *n_gap = edge_count(c->gap_lo, c->gap_hi);
+        return 0;
+    }
     *n_design = box_count(c->design_lo, c->design_hi, c->ndim);
     *n_gap = box_count(c->gap_lo, c->gap_hi, c->ndim);
     return 0;
+}
+
+/* Index of an edge within the edge list of a cell box (E_x edges first, row
+ * by row, then E_y edges), or -1 if the edge is not in the box's set. */
+static long edge_index(const int *lo, const int *hi, int comp, int i, int j)
+{
+    long w = hi[0] - lo[0], h = hi[1] - lo[1];
+    if (comp == 0) {
+        if (i < lo[0] || i >= hi[0] || j < lo[1] || j > hi[1]) return -1;
+        return (long)(j - lo[1]) * w + (i - lo[0]);
+    }
+    if (i < lo[0] || i > hi[0] || j < lo[1] || j >= hi[1]) return -1;
+    return w * (h + 1) + (long)(j - lo[1]) * (w + 1) + (i - lo[0]);
+}
+
+/* Free design variables: design edges outside the gap (the counts of Sec. 3.2). */
+long or_free_design(const or_config *c)
+{
+    long M, G;
+    or_sizes(c, &M, &G);
+    if (c->ndim == 2 && c->pol == 1) {
+        long n = 0;
+        for (int comp = 0; comp < 2; ++comp)
+            for (int j = c->design_lo[1]; j <= c->design_hi[1]; ++j)
+                for (int i = c->design_lo[0]; i <= c->design_hi[0]; ++i)
+                    if (edge_index(c->design_lo, c->design_hi, comp, i, j) >= 0 &&
+                        edge_index(c->gap_lo, c->gap_hi, comp, i, j) < 0)
+                        ++n;
+        return n;
+    }
+    return M - G;
 }
 
 /* ------------------------------------------------------------- filter */
@@ -565,6 +614,272 @@ static int gradient2(const or_config *c, const double *rho, double sigma_max, do
     return 0;
 }
 
+/* ===================================================== 2D, E in plane */
+
+/* Grid of nx x ny nodes: Ex(i,j) on the edge (i+1/2, j), Ey(i,j) on
+ * (i, j+1/2), Hz(i,j) at the cell centre (i+1/2, j+1/2); Drude Jx, Jy on the
+ * edges of the design box.  This is the paper's 2D "TM" case (H out of
+ * plane, E in plane, surface plasmons possible; Sec. 3.2 names it with H_x
+ * and E_y, E_z in the y-z plane).  PEC walls: Ex vanishes on the rows j = 0
+ * and ny-1, Ey on the columns i = 0 and nx-1; with periodic x every column
+ * is updated and x indices wrap. */
+typedef struct {
+    double *Ex, *Ey, *Jx, *Jy, *Hz;
+    double *pexy, *peyx, *phzx, *phzy;   /* CPML terms: Ex d/dy, Ey d/dx, Hz d/dx, Hz d/dy */
+} st2t;
+
+typedef struct {
+    double *eps[2], *psi[2], *sig[2];    /* per edge, component 0 = x, 1 = y */
+    double gam;
+    pml_coef *ex, *ey, *hx, *hy;
+} mat2t;
+
+static void st2t_alloc(const or_config *c, st2t *s)
+{
+    size_t n = (size_t)c->nx * c->ny;
+    s->Ex = calloc(n, sizeof(double)); s->Ey = calloc(n, sizeof(double));
+    s->Jx = calloc(n, sizeof(double)); s->Jy = calloc(n, sizeof(double));
+    s->Hz = calloc(n, sizeof(double));
+    s->pexy = calloc(n, sizeof(double)); s->peyx = calloc(n, sizeof(double));
+    s->phzx = calloc(n, sizeof(double)); s->phzy = calloc(n, sizeof(double));
+}
+
+static void st2t_free(st2t *s)
+{
+    free(s->Ex); free(s->Ey); free(s->Jx); free(s->Jy); free(s->Hz);
+    free(s->pexy); free(s->peyx); free(s->phzx); free(s->phzy);
+}
+
+/* Material of every edge: background eps_s; gap edges eps_g; design edges
+ * Eq. (5a-c) of their own density (no filter in this mode). */
+static void mat2t_build(const or_config *c, const double *rho, double sigma_max, double gamma_scale, mat2t *m)
+{
+    int nx = c->nx, ny = c->ny;
+    size_t n = (size_t)nx * ny;
+    m->gam = c->gamma_p * gamma_scale;
+    for (int comp = 0; comp < 2; ++comp) {
+        m->eps[comp] = malloc(n * sizeof(double));
+        m->psi[comp] = calloc(n, sizeof(double));
+        m->sig[comp] = calloc(n, sizeof(double));
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t q = (size_t)j * nx + i;
+                m->eps[comp][q] = c->eps_s;
+                long d = edge_index(c->design_lo, c->design_hi, comp, i, j);
+                if (edge_index(c->gap_lo, c->gap_hi, comp, i, j) >= 0)
+                    m->eps[comp][q] = c->eps_g;
+                else if (d >= 0)
+                    or_material(c, rho[d], sigma_max, &m->eps[comp][q], &m->psi[comp][q], &m->sig[comp][q]);
+            }
+    }
+    m->ex = malloc(nx * sizeof(pml_coef)); m->hx = malloc(nx * sizeof(pml_coef));
+    m->ey = malloc(ny * sizeof(pml_coef)); m->hy = malloc(ny * sizeof(pml_coef));
+    or_config cx = *c;
+    if (c->periodic_x) cx.npml = 0;
+    for (int i = 0; i < nx; ++i) { m->ex[i] = pml_at(&cx, nx, i); m->hx[i] = pml_at(&cx, nx, i + 0.5); }
+    for (int j = 0; j < ny; ++j) { m->ey[j] = pml_at(c, ny, j); m->hy[j] = pml_at(c, ny, j + 0.5); }
+}
+
+static void mat2t_free(mat2t *m)
+{
+    for (int comp = 0; comp < 2; ++comp) { free(m->eps[comp]); free(m->psi[comp]); free(m->sig[comp]); }
+    free(m->ex); free(m->ey); free(m->hx); free(m->hy);
+}
+
+/* H half step: mu0 dHz/dt = -(dEy/dx - dEx/dy), forward differences. */
+static void step2t_h(const or_config *c, const mat2t *m, st2t *s)
+{
+    int nx = c->nx, ny = c->ny, per = c->periodic_x;
+    double dx = c->dx, ch = or_dt(c) / OR_MU0;
+    #pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny - 1; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int ip = i + 1;
+            if (ip == nx) {
+                if (!per) continue;
+                ip = 0;
+            }
+            size_t q = (size_t)j * nx + i;
+            double dEy = (s->Ey[(size_t)j * nx + ip] - s->Ey[q]) / dx;
+            double dEx = (s->Ex[q + nx] - s->Ex[q]) / dx;
+            s->phzx[q] = m->hx[i].b * s->phzx[q] + m->hx[i].c * dEy;
+            s->phzy[q] = m->hy[j].b * s->phzy[q] + m->hy[j].c * dEx;
+            s->Hz[q] -= ch * (dEy / m->hx[i].kappa + s->phzx[q] - dEx / m->hy[j].kappa - s->phzy[q]);
+        }
+}
+
+/* E, J half step: Eq. (10a,b) on every updated edge, with
+ * curl_x = dHz/dy, curl_y = -dHz/dx (backward differences); jx, jy are the
+ * source current densities per edge. */
+static void step2t_e(const or_config *c, const mat2t *m, st2t *s, const double *jx, const double *jy)
+{
+    int nx = c->nx, ny = c->ny, per = c->periodic_x;
+    double dt = or_dt(c), dx = c->dx;
+    #pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t q = (size_t)j * nx + i;
+            /* Ex(i, j): an edge inside the grid, not on the rows j = 0, ny-1 */
+            if (j >= 1 && j <= ny - 2 && (per || i <= nx - 2)) {
+                double d = (s->Hz[q] - s->Hz[q - nx]) / dx;
+                s->pexy[q] = m->ey[j].b * s->pexy[q] + m->ey[j].c * d;
+                double curl = d / m->ey[j].kappa + s->pexy[q];
+                node_solve(m->eps[0][q], m->psi[0][q], m->sig[0][q], m->gam, dt, curl, jx[q], &s->Ex[q], &s->Jx[q]);
+            }
+            /* Ey(i, j): not on the columns i = 0, nx-1 (unless periodic) */
+            if (j <= ny - 2 && (per || (i >= 1 && i <= nx - 2))) {
+                int im = i == 0 ? nx - 1 : i - 1;
+                double d = (s->Hz[q] - s->Hz[(size_t)j * nx + im]) / dx;
+                s->peyx[q] = m->ex[i].b * s->peyx[q] + m->ex[i].c * d;
+                double curl = -(d / m->ex[i].kappa + s->peyx[q]);
+                node_solve(m->eps[1][q], m->psi[1][q], m->sig[1][q], m->gam, dt, curl, jy[q], &s->Ey[q], &s->Jy[q]);
+            }
+        }
+}
+
+static double energy2t(const or_config *c, const mat2t *m, const st2t *s, const double *Hz_old)
+{
+    double eps0 = or_eps0(), e = 0.0;
+    size_t n = (size_t)c->nx * c->ny;
+    for (size_t q = 0; q < n; ++q) {
+        e += 0.5 * eps0 * (m->eps[0][q] * s->Ex[q] * s->Ex[q] + m->eps[1][q] * s->Ey[q] * s->Ey[q]);
+        e += 0.5 * OR_MU0 * Hz_old[q] * s->Hz[q];
+    }
+    return e * c->dx * c->dx;
+}
+
+/* Record the edges of a cell box (E_x edges, then E_y edges) of E^t. */
+static void record_edges(const or_config *c, const int *lo, const int *hi, const st2t *s, double *out)
+{
+    int nx = c->nx;
+    for (int comp = 0; comp < 2; ++comp) {
+        const double *E = comp ? s->Ey : s->Ex;
+        for (int j = lo[1]; j <= hi[1]; ++j)
+            for (int i = lo[0]; i <= hi[0]; ++i) {
+                long d = edge_index(lo, hi, comp, i, j);
+                if (d >= 0) out[d] = E[(size_t)j * nx + i];
+            }
+    }
+}
+
+/* Forward solve, E in plane.  The source drives E_x edges of the source box
+ * (i in [src_lo_x, src_hi_x), j in [src_lo_y, src_hi_y)); probes are E_x
+ * edges (i, j). */
+static int forward2t(const or_config *c, const double *rho, double sigma_max, double gamma_scale,
+                     double *W, double *gap_hist, double *design_hist,
+                     const int *probes, int nprobe, double *probe_hist, double *energy)
+{
+    int nx = c->nx, N = c->nsteps;
+    long M, G;
+    or_sizes(c, &M, &G);
+    mat2t m;
+    mat2t_build(c, rho, sigma_max, gamma_scale, &m);
+    st2t s;
+    st2t_alloc(c, &s);
+    size_t n = (size_t)nx * c->ny;
+    double *jx = calloc(n, sizeof(double)), *jy = calloc(n, sizeof(double));
+    double *hzo = energy ? calloc(n, sizeof(double)) : NULL;
+    double *gbuf = malloc(sizeof(double) * (G ? G : 1));
+    double dt = or_dt(c);
+    double J0 = c->src_amp * or_eps0() * OR_C0 / c->dx;
+    double sum = 0.0;
+    for (int t = 0; t <= N; ++t) {
+        record_edges(c, c->gap_lo, c->gap_hi, &s, gbuf);
+        for (long g = 0; g < G; ++g) sum += gbuf[g] * gbuf[g];
+        if (gap_hist) memcpy(gap_hist + (size_t)t * G, gbuf, sizeof(double) * G);
+        if (design_hist) record_edges(c, c->design_lo, c->design_hi, &s, design_hist + (size_t)t * M);
+        for (int p = 0; p < nprobe; ++p)
+            probe_hist[(size_t)t * nprobe + p] = s.Ex[(size_t)probes[2 * p + 1] * nx + probes[2 * p]];
+        if (t == N) break;
+        double js = J0 * or_signal(c, (t + 0.5) * dt);
+        for (int j = c->src_lo[1]; j < c->src_hi[1]; ++j)
+            for (int i = c->src_lo[0]; i < c->src_hi[0]; ++i)
+                jx[(size_t)j * nx + i] = js;
+        if (energy) memcpy(hzo, s.Hz, n * sizeof(double));
+        step2t_h(c, &m, &s);
+        if (energy) energy[t] = energy2t(c, &m, &s, hzo);
+        step2t_e(c, &m, &s, jx, jy);
+    }
+    *W = 0.5 * c->eps_g * dt * c->dx * c->dx * sum;
+    free(jx); free(jy); free(hzo); free(gbuf);
+    st2t_free(&s);
+    mat2t_free(&m);
+    return 0;
+}
+
+/* Forward, adjoint and gradient, E in plane: the adjoint is the same solver
+ * driven by J_src = -eps_g E^{N-n} on every gap edge (Eq. 20), and the
+ * Eq. (25a-c) sums run over every design edge with that edge's own forward
+ * field, adjoint field and current, then Eq. (27) per edge (no filter);
+ * gap edges get a zero gradient. */
+static int gradient2t(const or_config *c, const double *rho, double sigma_max, double gamma_scale,
+                      double *W, double *grad, double *g_psi, double *g_eps, double *g_sig)
+{
+    int nx = c->nx, N = c->nsteps;
+    long M, G;
+    or_sizes(c, &M, &G);
+    if (M == 0) return -1;
+    double *ghist = malloc(sizeof(double) * (size_t)(N + 1) * (G ? G : 1));
+    double *dhist = malloc(sizeof(double) * (size_t)(N + 1) * M);
+    forward2t(c, rho, sigma_max, gamma_scale, W, ghist, dhist, NULL, 0, NULL, NULL);
+    mat2t m;
+    mat2t_build(c, rho, sigma_max, gamma_scale, &m);
+    st2t a;
+    st2t_alloc(c, &a);
+    size_t n = (size_t)nx * c->ny;
+    double *jx = calloc(n, sizeof(double)), *jy = calloc(n, sizeof(double));
+    double *sp = calloc(M, sizeof(double)), *se = calloc(M, sizeof(double)), *ss = calloc(M, sizeof(double));
+    double *Eold = malloc(sizeof(double) * M), *Jold = malloc(sizeof(double) * M);
+    double *Enew = malloc(sizeof(double) * M), *Jnew = malloc(sizeof(double) * M);
+    st2t jview = a;
+    for (int t = 0; t <= N; ++t) {
+        for (int comp = 0; comp < 2; ++comp)
+            for (int j = c->gap_lo[1]; j <= c->gap_hi[1]; ++j)
+                for (int i = c->gap_lo[0]; i <= c->gap_hi[0]; ++i) {
+                    long g = edge_index(c->gap_lo, c->gap_hi, comp, i, j);
+                    if (g >= 0) (comp ? jy : jx)[(size_t)j * nx + i] = -c->eps_g * ghist[(size_t)(N - t) * G + g];
+                }
+        record_edges(c, c->design_lo, c->design_hi, &a, Eold);
+        jview.Ex = a.Jx;
+        jview.Ey = a.Jy;
+        record_edges(c, c->design_lo, c->design_hi, &jview, Jold);
+        step2t_h(c, &m, &a);
+        step2t_e(c, &m, &a, jx, jy);
+        record_edges(c, c->design_lo, c->design_hi, &a, Enew);
+        record_edges(c, c->design_lo, c->design_hi, &jview, Jnew);
+        for (long d = 0; d < M; ++d) {
+            double Ef = dhist[(size_t)(N - t) * M + d];
+            sp[d] += Ef * 0.5 * (Jnew[d] + Jold[d]);
+            se[d] += Ef * (Enew[d] - Eold[d]);
+            ss[d] += Ef * 0.5 * (Enew[d] + Eold[d]);
+        }
+    }
+    double eps0 = or_eps0(), dt = or_dt(c), dx2 = c->dx * c->dx;
+    double psi = c->omega_p * c->omega_p, psi_s = c->psi_s_ratio * psi;
+    for (int comp = 0; comp < 2; ++comp)
+        for (int j = c->design_lo[1]; j <= c->design_hi[1]; ++j)
+            for (int i = c->design_lo[0]; i <= c->design_hi[0]; ++i) {
+                long d = edge_index(c->design_lo, c->design_hi, comp, i, j);
+                if (d < 0) continue;
+                double ep, ps, sg;
+                or_material(c, rho[d], sigma_max, &ep, &ps, &sg);
+                double dpsi = -(dt * dx2 / ps) * sp[d];
+                double deps = -eps0 * dx2 * se[d];
+                double dsig = -dt * dx2 * ss[d];
+                if (edge_index(c->gap_lo, c->gap_hi, comp, i, j) >= 0) dpsi = deps = dsig = 0.0;
+                if (g_psi) g_psi[d] = dpsi;
+                if (g_eps) g_eps[d] = deps;
+                if (g_sig) g_sig[d] = dsig;
+                double dsdr = sigma_max * (1.0 - 2.0 * rho[d]) * (c->sigma_form ? 4.0 : 1.0);
+                grad[d] = (psi - psi_s) * dpsi + (c->eps_inf - c->eps_s) * deps + dsdr * dsig;
+            }
+    free(Eold); free(Jold); free(Enew); free(Jnew); free(sp); free(se); free(ss);
+    free(jx); free(jy); free(ghist); free(dhist);
+    st2t_free(&a);
+    mat2t_free(&m);
+    return 0;
+}
+
 /* ================================================================ 3D */
 
 /* Full Yee grid of nx x ny x nz nodes: Ex(i,j,k) at (i+1/2, j, k), Ey at
@@ -923,6 +1238,9 @@ int or_forward(const or_config *c, const double *rho, double sigma_max, double g
                double *W, double *gap_hist, double *design_hist,
                const int *probes, int nprobe, double *probe_hist, double *energy)
 {
+    if (c->ndim == 2 && c->pol == 1)
+        return forward2t(c, rho, sigma_max, gamma_scale, W, gap_hist, design_hist,
+                         probes, nprobe, probe_hist, energy);
     if (c->ndim == 2)
         return forward2(c, rho, sigma_max, gamma_scale, W, gap_hist, design_hist,
                         probes, nprobe, probe_hist, energy);
@@ -935,6 +1253,7 @@ int or_forward(const or_config *c, const double *rho, double sigma_max, double g
 int or_gradient(const or_config *c, const double *rho, double sigma_max, double gamma_scale,
                 double *W, double *grad, double *g_psi, double *g_eps, double *g_sig)
 {
+    if (c->ndim == 2 && c->pol == 1) return gradient2t(c, rho, sigma_max, gamma_scale, W, grad, g_psi, g_eps, g_sig);
     if (c->ndim == 2) return gradient2(c, rho, sigma_max, gamma_scale, W, grad, g_psi, g_eps, g_sig);
     if (c->ndim == 3) return gradient3(c, rho, sigma_max, gamma_scale, W, grad, g_psi, g_eps, g_sig);
     return -1;

@@ -39,6 +39,7 @@ class OrConfig(C.Structure):
         ("filter_radius", C.c_int), ("filter_sigma", C.c_double),
         ("sigma_form", C.c_int), ("sub_eps", C.c_double), ("sub_hi", C.c_int),
         ("src_comp", C.c_int), ("waveform", C.c_int), ("bandwidth", C.c_double), ("lobes", C.c_int),
+        ("pol", C.c_int),
     ]
 
 
@@ -67,6 +68,9 @@ def lib():
             L.or_filter_T.argtypes = [C.POINTER(OrConfig), dp, dp]
             L.or_material.argtypes = [C.POINTER(OrConfig), C.c_double, C.c_double, dp, dp, dp]
             L.or_signal_samples.argtypes = [C.POINTER(OrConfig), dp, C.c_int, dp]
+            L.or_sizes.argtypes = [C.POINTER(OrConfig), C.POINTER(C.c_long), C.POINTER(C.c_long)]
+            L.or_free_design.argtypes = [C.POINTER(OrConfig)]
+            L.or_free_design.restype = C.c_long
             L.or_set_threads.argtypes = [C.c_int]
             L.or_get_threads.restype = C.c_int
             _lib = L
@@ -84,7 +88,7 @@ def threads() -> int:
 def config(w: dict) -> OrConfig:
     c = OrConfig()
     for name, ctype in OrConfig._fields_:
-        v = w.get(name, {"src_comp": 2, "waveform": 0, "bandwidth": 0.0, "lobes": 0}.get(name))
+        v = w.get(name, {"src_comp": 2, "waveform": 0, "bandwidth": 0.0, "lobes": 0, "pol": 0}.get(name))
         if name == "f0":
             c.f0[0], c.f0[1] = float(v[0]), float(v[1])
         elif isinstance(getattr(c, name), C.Array):
@@ -106,12 +110,16 @@ def _dptr(a: np.ndarray | None):
 
 
 def _sizes(w: dict) -> tuple[int, int]:
-    def cnt(lo, hi):
-        n = 1
-        for a in range(w["ndim"]):
-            n *= max(0, hi[a] - lo[a])
-        return n
-    return cnt(w["design_lo"], w["design_hi"]), cnt(w["gap_lo"], w["gap_hi"])
+    M, G = C.c_long(0), C.c_long(0)
+    cfg = config(w)
+    lib().or_sizes(C.byref(cfg), C.byref(M), C.byref(G))
+    return int(M.value), int(G.value)
+
+
+def free_design(w: dict) -> int:
+    """Design variables outside the gap (per Yee edge in the in-plane 2D mode)."""
+    cfg = config(w)
+    return int(lib().or_free_design(C.byref(cfg)))
 
 
 def forward(w: dict, rho: np.ndarray, sigma_max: float = 0.0, gamma_scale: float = 1.0,
@@ -119,7 +127,8 @@ def forward(w: dict, rho: np.ndarray, sigma_max: float = 0.0, gamma_scale: float
             energy: bool = False) -> dict:
     """Forward solve; returns W and whatever histories were asked for.
 
-    2D: gap_hist (N+1, M_g), design_hist (N+1, M_d), probes (i, j) of Ez.
+    2D: gap_hist (N+1, M_g), design_hist (N+1, M_d), probes (i, j) of Ez
+    (E in plane: of the E_x edge (i+1/2, j); gap and design values per edge).
     3D: gap_hist (N+1, 3, M_g), design_hist (N+1, 3, M_d) with components
     x, y, z, probes (i, j, k, component)."""
     M, G = _sizes(w)

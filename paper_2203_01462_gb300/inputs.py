@@ -98,6 +98,45 @@ def workload_2d(nx: int, ny: int, *, dx: float, nsteps: int, npml: int = 10,
     return w
 
 
+def workload_2d_inplane(nx: int, ny: int, *, dx: float, nsteps: int, npml: int = 10,
+                        design: tuple[int, int] = (60, 60), gap: tuple[int, int] = (4, 4),
+                        courant: float = 0.5, real: str = "f64", material: dict | None = None,
+                        snapshot_every: int = 0, snapshot_dtype: str = "f32", accum: str = "f64",
+                        src_offset: int = 5, **over) -> dict:
+    """A 2D workload with E in plane (Ex, Ey, Hz; the paper's 2D "TM" case,
+    in which surface plasmons exist).  Design and gap boxes are centred cell
+    ranges whose Yee edges carry the design variables; the source is one row
+    of E_x edges ``src_offset`` rows inside the lower CPML across the non-CPML
+    x range, so it launches an E_x-polarised wave along +y and -y."""
+    w = workload_2d(nx, ny, dx=dx, nsteps=nsteps, npml=npml, design=design, gap=gap, courant=courant, real=real,
+                    material=material, snapshot_every=snapshot_every, snapshot_dtype=snapshot_dtype, accum=accum,
+                    src_offset=src_offset)
+    dlo_x, dhi_x = _centered_box(nx - 1, design[0])
+    dlo_y, dhi_y = _centered_box(ny - 1, design[1])
+    glo_x, ghi_x = _centered_box(nx - 1, gap[0])
+    glo_y, ghi_y = _centered_box(ny - 1, gap[1])
+    w.update(pol=1, design_lo=[dlo_x, dlo_y, 0], design_hi=[dhi_x, dhi_y, 1],
+             gap_lo=[glo_x, glo_y, 0], gap_hi=[ghi_x, ghi_y, 1],
+             src_lo=[npml, npml + src_offset, 0], src_hi=[nx - 1 - npml, npml + src_offset + 1, 1])
+    w.update(over)
+    return w
+
+
+def cfg_2d_inplane_paper(design_nm: float = 100.0, nsteps: int = 6000, real: str = "f32") -> dict:
+    """The geometry of the paper's 2D nanoantennas with E in plane (Sec. 3.2):
+    dx = 0.5 nm, a square design box of ``design_nm`` (100 or 200 nm), a
+    centred 10 nm gap, 15 absorbing cells placed 30 cells beyond the design
+    box, the truncated-sinc excitation of 20 % bandwidth around 413 nm."""
+    dx = 0.5e-9
+    d = int(round(design_nm * 1e-9 / dx))
+    g = int(round(10e-9 / dx))
+    n = d + 2 * 30 + 2 * 15 + 1
+    w = workload_2d_inplane(n, n, dx=dx, nsteps=nsteps, npml=15, design=(d, d), gap=(g, g), real=real,
+                            material=SILVER, src_offset=5)
+    w.update(sinc_hanning(center_m=413e-9, rel_bandwidth=0.2, lobes=4))
+    return w
+
+
 def cfg_2d_160() -> dict:
     """160^2 FP64 parity workload: full forward + adjoint + gradient."""
     return workload_2d(160, 160, dx=5e-9, nsteps=2000, npml=10, design=(60, 60), gap=(3, 3),
@@ -193,14 +232,27 @@ def describe(w: dict) -> str:
     """One-line description of a workload."""
     dims = "x".join(str(v) for v in grid_shape(w))
     des = "x".join(str(v) for v in reversed(design_shape(w)))
-    kind = "2D TM_z" if w["ndim"] == 2 else "3D Yee"
+    kind = ("2D in-plane E" if inplane(w) else "2D TM_z") if w["ndim"] == 2 else "3D Yee"
     snap = ("snapshots every %d (%s)" % (w["snapshot_every"], w.get("snapshot_dtype", "f32"))
             if w.get("snapshot_every") else "full history")
     filt = ", %d-cell Gaussian filter" % w["filter_radius"] if w.get("filter_radius") else ""
     return "%s %s %s, %d steps, %s design%s, %s" % (kind, dims, w["real"].upper(), w["nsteps"], des, filt, snap)
 
 
+def inplane(w: dict) -> bool:
+    return w["ndim"] == 2 and w.get("pol", 0) == 1
+
+
+def edge_shapes(lo, hi) -> tuple[tuple[int, int], tuple[int, int]]:
+    """Shapes (rows, columns) of the E_x and E_y edge sets of a cell box."""
+    wd, h = hi[0] - lo[0], hi[1] - lo[1]
+    return (h + 1, wd), (h, wd + 1)
+
+
 def n_design(w: dict) -> int:
+    if inplane(w):
+        (a, b), (c, d) = edge_shapes(w["design_lo"], w["design_hi"])
+        return a * b + c * d
     n = 1
     for a in range(w["ndim"]):
         n *= w["design_hi"][a] - w["design_lo"][a]
@@ -208,9 +260,29 @@ def n_design(w: dict) -> int:
 
 
 def design_shape(w: dict) -> tuple[int, ...]:
-    """Design-array shape, slowest axis first (x fastest)."""
+    """Design-array shape, slowest axis first (x fastest); the in-plane 2D
+    mode keeps its E_x edges then its E_y edges in one flat vector."""
+    if inplane(w):
+        return (n_design(w),)
     s = [w["design_hi"][a] - w["design_lo"][a] for a in range(w["ndim"])]
     return tuple(reversed(s))
+
+
+def split_edges(w: dict, v: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """(E_x-edge array, E_y-edge array) views of an in-plane design vector."""
+    (a, b), (c, d) = edge_shapes(w["design_lo"], w["design_hi"])
+    v = np.asarray(v).reshape(-1)
+    return v[:a * b].reshape(a, b), v[a * b:].reshape(c, d)
+
+
+def gap_edge_mask(w: dict) -> np.ndarray:
+    """True on the design edges that belong to the gap (in-plane 2D mode)."""
+    m = np.zeros(n_design(w), dtype=bool)
+    mx, my = split_edges(w, m)
+    dl, gl, gh = w["design_lo"], w["gap_lo"], w["gap_hi"]
+    mx[gl[1] - dl[1]:gh[1] - dl[1] + 1, gl[0] - dl[0]:gh[0] - dl[0]] = True
+    my[gl[1] - dl[1]:gh[1] - dl[1], gl[0] - dl[0]:gh[0] - dl[0] + 1] = True
+    return m
 
 
 def rho_uniform(w: dict, seed: int) -> np.ndarray:
@@ -222,23 +294,42 @@ def rho_uniform(w: dict, seed: int) -> np.ndarray:
 
 def zero_gap(w: dict, r: np.ndarray) -> np.ndarray:
     r = np.array(r, dtype=np.float64, copy=True)
+    if inplane(w):
+        r = r.reshape(-1)
+        r[gap_edge_mask(w)] = 0.0
+        return r
     sl = tuple(slice(w["gap_lo"][a] - w["design_lo"][a], w["gap_hi"][a] - w["design_lo"][a])
                for a in reversed(range(w["ndim"])))
     r[sl] = 0.0
     return r
 
 
+def _bowtie_at(x, y, cx, cy, gx):
+    ax = np.abs(y - cy)
+    return (np.abs(x - cx) >= gx) & (ax <= 0.6 * (np.abs(x - cx) - gx) + 1.0)
+
+
 def rho_bowtie(w: dict) -> np.ndarray:
     """Binary bowtie: two triangles whose tips face each other across the gap."""
+    if inplane(w):
+        # the same shape sampled at the edge midpoints (cell units from the box corner)
+        dl, gl, gh = w["design_lo"], w["gap_lo"], w["gap_hi"]
+        cx = (gl[0] + gh[0]) / 2.0 - dl[0]
+        cy = (gl[1] + gh[1]) / 2.0 - dl[1]
+        gx = (gh[0] - gl[0]) / 2.0 + 0.5
+        (a, b), (c, d) = edge_shapes(w["design_lo"], w["design_hi"])
+        yx, xx = np.mgrid[0:a, 0:b]
+        yy, xy = np.mgrid[0:c, 0:d]
+        r = np.concatenate([_bowtie_at(xx + 0.5, yx, cx, cy, gx).reshape(-1),
+                            _bowtie_at(xy, yy + 0.5, cx, cy, gx).reshape(-1)]).astype(np.float64)
+        return zero_gap(w, r)
     shape = design_shape(w)
     h, wd = shape[-2], shape[-1]
     y, x = np.mgrid[0:h, 0:wd]
     cx = (w["gap_lo"][0] + w["gap_hi"][0]) / 2.0 - w["design_lo"][0] - 0.5
     cy = (w["gap_lo"][1] + w["gap_hi"][1]) / 2.0 - w["design_lo"][1] - 0.5
     gx = (w["gap_hi"][0] - w["gap_lo"][0]) / 2.0 + 0.5
-    ax = np.abs(y - cy)
-    tri = (np.abs(x - cx) >= gx) & (ax <= 0.6 * (np.abs(x - cx) - gx) + 1.0)
-    r = tri.astype(np.float64)
+    r = _bowtie_at(x, y, cx, cy, gx).astype(np.float64)
     if len(shape) == 3:
         r = np.broadcast_to(r, shape).copy()
     return zero_gap(w, r)
