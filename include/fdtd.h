@@ -78,11 +78,26 @@ enum { FDTD_SIGMA_PAPER = 0, FDTD_SIGMA_PEAK_NORMALISED = 1 };
  * (1 + cos(pi u / T)) / 2; zero outside.  t0 >= T starts it from rest. */
 enum { FDTD_WAVE_GAUSS = 0, FDTD_WAVE_SINC_HANN = 1 };
 
+/* 2D polarisation.
+ * FDTD_POL_EZ: E out of plane (Ez, Hx, Hy, Jz on nx x ny nodes; the paper's
+ *   2D TE case); boxes are node ranges; one design variable per node.
+ * FDTD_POL_INPLANE: E in plane (the paper's 2D TM case, Sec. 3.2, in which
+ *   surface plasmons exist): Ex on the edges (i+1/2, j), Ey on (i, j+1/2),
+ *   Hz at cell centres, Drude Jx, Jy per edge.  Design, gap and source boxes
+ *   are cell ranges [lo, hi) with hi <= n - 1 (the source box: E_x edges
+ *   i < nx - 1).  The design variables are the Yee edges of the design box,
+ *   as the paper assigns them: rho holds the E_x edges (i in [lo_x, hi_x),
+ *   j in [lo_y, hi_y], row-major) followed by the E_y edges (i in
+ *   [lo_x, hi_x], j in [lo_y, hi_y)), M_d = w (h + 1) + (w + 1) h; the gap
+ *   edges are fixed (gradient 0) and W~ sums E^2 over them (Eq. 24, dx^2).
+ *   The source drives E_x edges.  No design filter (filter_radius 0). */
+enum { FDTD_POL_EZ = 0, FDTD_POL_INPLANE = 1 };
+
 /* Problem description.  Boxes are half-open node ranges [lo, hi) per axis
  * (x, y, z); in 2D the z range must be [0, 1).  Grid: nx x ny Ez nodes in
  * 2D; nx x ny x nz Yee nodes in 3D. */
 typedef struct fdtd_config {
-    int ndim;                 /* 2: TM_z (Ez, Hx, Hy, Jz); 3: full Yee        */
+    int ndim;                 /* 2: see pol; 3: full Yee                      */
     int nx, ny, nz;
     double dx;                /* grid step, m (dx = dy = dz, Sec. 3.2)         */
     double courant;           /* S = c0 dt / dx                                */
@@ -119,6 +134,7 @@ typedef struct fdtd_config {
     int waveform;             /* FDTD_WAVE_*: envelope of the carrier(s)       */
     double bandwidth;         /* FDTD_WAVE_SINC_HANN: rectangle width B, Hz    */
     int lobes;                /* FDTD_WAVE_SINC_HANN: lobes kept per side      */
+    int pol;                  /* 2D: FDTD_POL_*                                */
 } fdtd_config;
 
 typedef struct fdtd_ctx fdtd_ctx;

@@ -86,6 +86,18 @@ fdtd_status validate(const fdtd_config *c)
     } else {
         return FDTD_EINVAL;
     }
+    if (c->pol != FDTD_POL_EZ && c->pol != FDTD_POL_INPLANE) return FDTD_EINVAL;
+    if (c->pol == FDTD_POL_INPLANE) {
+        // 2D only, no filter; boxes are cell ranges (nx-1 x ny-1 cells); the
+        // source box holds E_x edges (i <= nx-2).
+        if (c->ndim != 2 || c->filter_radius != 0) return FDTD_EINVAL;
+        const int cells[3] = {c->nx - 1, c->ny - 1, 1};
+        const int xedges[3] = {c->nx - 1, c->ny, 1};
+        if (!box_ok(c->design_lo, c->design_hi, cells, 2, false)) return FDTD_EINVAL;
+        if (!box_ok(c->gap_lo, c->gap_hi, cells, 2, true)) return FDTD_EINVAL;
+        if (!box_ok(c->src_lo, c->src_hi, xedges, 2, true)) return FDTD_EINVAL;
+        if (!box_inside(c->gap_lo, c->gap_hi, c->design_lo, c->design_hi, 2)) return FDTD_EINVAL;
+    }
     int n[3] = {c->nx, c->ny, c->nz};
     if (!box_ok(c->design_lo, c->design_hi, n, c->ndim, false)) return FDTD_EINVAL;
     if (!box_ok(c->gap_lo, c->gap_hi, n, c->ndim, true)) return FDTD_EINVAL;
@@ -629,6 +641,290 @@ struct Ctx2D final : fdtd_ctx {
     }
 };
 
+// ------------------------------------------------------ 2D, E in plane
+
+// Edges of a cell box [lo, hi) per component, as array-index rectangles:
+// E_x edges i in [lo_x, hi_x), j in [lo_y, hi_y]; E_y edges i in
+// [lo_x, hi_x], j in [lo_y, hi_y).
+void edge_rect(const int *lo, const int *hi, int cc, int *o, int *n)
+{
+    const int w = hi[0] - lo[0], h = hi[1] - lo[1];
+    o[0] = lo[0];
+    o[1] = lo[1];
+    if (w <= 0 || h <= 0) {
+        n[0] = n[1] = 0;
+        return;
+    }
+    n[0] = cc == 0 ? w : w + 1;
+    n[1] = cc == 0 ? h + 1 : h;
+}
+
+long long edge_total(const int *lo, const int *hi)
+{
+    long long t = 0;
+    for (int cc = 0; cc < 2; ++cc) {
+        int o[2], n[2];
+        edge_rect(lo, hi, cc, o, n);
+        t += (long long)n[0] * n[1];
+    }
+    return t;
+}
+
+template <typename R>
+struct CtxP final : fdtd_ctx {
+    GeoP geo{};
+    StateP<R> F{}, A{};  // updated in place (split H and E launches)
+    char *F_base = nullptr, *A_base = nullptr;
+    size_t state_bytes = 0;
+    long long Mdx = 0;  // design entries of the E_x edges (first part of rho)
+    R *rho = nullptr, *rho_t[2] = {nullptr, nullptr}, *rstage = nullptr;
+    double *G[2] = {nullptr, nullptr}, *gstage = nullptr;
+    R *gap_hist = nullptr, *rec = nullptr, *src_tab = nullptr;
+    char *snaps = nullptr;
+    size_t snap_stride = 0;
+    int nsnap = 0;
+    R *pml_tab = nullptr;
+    PmlP<R> pm{};
+    double *misc = nullptr;
+    unsigned *err = nullptr;
+
+    void *rho_stage() override { return rstage; }
+    double *grad_stage() override { return gstage; }
+    double *W_dev() override { return misc; }
+    unsigned *err_dev() override { return err; }
+
+    long long Mdi_all() const { return geo.Mdi[0] + geo.Mdi[1]; }
+
+    void carve_state(Carver &cv, StateP<R> &s, char *&base)
+    {
+        const size_t grid = (size_t)geo.px * geo.ny, np2 = 2 * (size_t)cfg.npml;
+        size_t start = (cv.off + 255) & ~(size_t)255;
+        s.Ex = cv.take<R>(grid);
+        s.Ey = cv.take<R>(grid);
+        s.Hz = cv.take<R>(grid);
+        s.J[0] = cv.take<R>((size_t)geo.Mdi[0]);
+        s.J[1] = cv.take<R>((size_t)geo.Mdi[1]);
+        s.pexy = cv.take<R>(np2 * geo.px);
+        s.phzy = cv.take<R>(np2 * geo.px);
+        s.peyx = cv.take<R>((size_t)geo.ny * np2);
+        s.phzx = cv.take<R>((size_t)geo.ny * np2);
+        cv.off = (cv.off + 255) & ~(size_t)255;
+        base = cv.base ? cv.base + start : nullptr;
+        state_bytes = cv.off - start;
+    }
+
+    fdtd_status carve(Carver &cv) override
+    {
+        const fdtd_config &c = cfg;
+        geo.nx = c.nx;
+        geo.ny = c.ny;
+        geo.px = (c.nx + 31) / 32 * 32;
+        geo.npml = c.npml;
+        for (int cc = 0; cc < 2; ++cc) {
+            edge_rect(c.design_lo, c.design_hi, cc, geo.d0[cc], geo.dn[cc]);
+            edge_rect(c.gap_lo, c.gap_hi, cc, geo.g0[cc], geo.gn[cc]);
+            geo.Mgc[cc] = geo.gn[cc][0] * geo.gn[cc][1];
+            geo.dxa[cc] = geo.d0[cc][0] & ~3;
+            geo.dp[cc] = (geo.d0[cc][0] + geo.dn[cc][0] - geo.dxa[cc] + 3) & ~3;
+            geo.Mdi[cc] = (long long)geo.dn[cc][1] * geo.dp[cc];
+        }
+        Mdx = (long long)geo.dn[0][0] * geo.dn[0][1];
+        for (int a = 0; a < 2; ++a) {
+            geo.s0[a] = c.src_lo[a];
+            geo.s1[a] = c.src_hi[a];
+        }
+        const long long N = c.nsteps;
+        carve_state(cv, F, F_base);
+        carve_state(cv, A, A_base);
+        rho = cv.take<R>(Md);
+        rho_t[0] = cv.take<R>((size_t)geo.Mdi[0]);
+        rho_t[1] = cv.take<R>((size_t)geo.Mdi[1]);
+        rstage = cv.take<R>(Md);
+        G[0] = cv.take<double>((size_t)geo.Mdi[0]);
+        G[1] = cv.take<double>((size_t)geo.Mdi[1]);
+        gstage = cv.take<double>(Md);
+        gap_hist = cv.take<R>((size_t)(N + 1) * (Mg ? Mg : 1));
+        const long long K = c.snapshot_every;
+        rec = cv.take<R>((size_t)(K > 0 ? std::min<long long>(K, N) : N) * Mdi_all());
+        nsnap = K > 0 ? (int)((N + K - 1) / K) : 0;
+        snap_stride = snapshot_bytes<R>(c.snapshot_dtype, state_bytes);
+        snaps = cv.take<char>((size_t)nsnap * snap_stride);
+        src_tab = cv.take<R>(N);
+        pml_tab = cv.take<R>(6 * (size_t)(c.nx + c.ny));
+        misc = cv.take<double>(4 + 2 * MMA_BLOCKS);
+        err = cv.take<unsigned>(4);
+        if (pml_tab) {
+            R *t = pml_tab;
+            const int nn[2] = {c.nx, c.ny};
+            for (int a = 0; a < 2; ++a) {
+                const int n = nn[a];
+                pm.bE[a] = t; pm.cE[a] = t + n; pm.kiE[a] = t + 2 * n;
+                pm.bH[a] = t + 3 * n; pm.cH[a] = t + 4 * n; pm.kiH[a] = t + 5 * n;
+                t += 6 * n;
+            }
+        }
+        return FDTD_OK;
+    }
+
+    fdtd_status upload_tables() override
+    {
+        const fdtd_config &c = cfg;
+        std::vector<R> tab(6 * (size_t)(c.nx + c.ny));
+        fill_pml<R>(c, c.nx, tab.data());
+        fill_pml<R>(c, c.ny, tab.data() + 6 * c.nx);
+        std::vector<R> src = source_table<R>(c, dt);
+        cudaStream_t st = stream;
+        FDTD_TRY(cuda_ok(cudaMemcpyAsync(pml_tab, tab.data(), tab.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
+        FDTD_TRY(cuda_ok(cudaMemcpyAsync(src_tab, src.data(), src.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
+        launch_zero_bytes(err, 4 * sizeof(unsigned), st);
+        ++launches;
+        return cuda_ok(cudaStreamSynchronize(st));
+    }
+
+    Coef<R> coef() const { return make_coef<R>(cfg, dt, sigma_max, gamma_scale); }
+    fdtd_status check_launch() { return cuda_ok(cudaGetLastError()); }
+
+    fdtd_status set_design(const void *d_rho) override
+    {
+        cudaStream_t st = stream;
+        launch_copy_check_rho<R>((const R *)d_rho, rho, Md, err, st);
+        launch_pitch2d<R>(rho, rho_t[0], geo.dn[0][0], geo.dn[0][1], geo.d0[0][0] - geo.dxa[0], geo.dp[0], st);
+        launch_pitch2d<R>(rho + Mdx, rho_t[1], geo.dn[1][0], geo.dn[1][1], geo.d0[1][0] - geo.dxa[1], geo.dp[1], st);
+        launches += 3;
+        FDTD_TRY(check_launch());
+        unsigned h_err = 0;
+        FDTD_TRY(cuda_ok(cudaMemcpyAsync(&h_err, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st)));
+        FDTD_TRY(cuda_ok(cudaStreamSynchronize(st)));
+        if (h_err & ERR_RANGE) {
+            launch_zero_bytes(err, sizeof(unsigned), st);
+            cudaStreamSynchronize(st);
+            return FDTD_ERANGE;
+        }
+        return FDTD_OK;
+    }
+
+    StepP<R> step_args() const
+    {
+        StepP<R> a{};
+        a.rho_t[0] = rho_t[0];
+        a.rho_t[1] = rho_t[1];
+        return a;
+    }
+
+    void advance_forward(const Coef<R> &k, int n0, int count, bool gap, R *rec_base)
+    {
+        StepP<R> a = step_args();
+        for (int n = n0; n < n0 + count; ++n) {
+            a.src = src_tab + n;
+            a.gap_rec = (gap && Mg) ? gap_hist + (size_t)(n + 1) * Mg : nullptr;
+            R *slot = rec_base ? rec_base + (size_t)(n - n0) * Mdi_all() : nullptr;
+            a.rec[0] = slot;
+            a.rec[1] = slot ? slot + geo.Mdi[0] : nullptr;
+            launches += launch_stepp<R>(0, geo, F, k, pm, a, stream);
+        }
+        cell_updates += (long long)count * ncells;
+    }
+
+    void advance_adjoint(const Coef<R> &k, int m_hi, int m_lo, int slot0)
+    {
+        StepP<R> a = step_args();
+        a.G[0] = G[0];
+        a.G[1] = G[1];
+        for (int m = m_hi; m > m_lo; --m) {
+            a.gap_src = Mg ? gap_hist + (size_t)m * Mg : nullptr;
+            R *slot = rec + (size_t)(m - 1 - slot0) * Mdi_all();
+            a.rec[0] = slot;
+            a.rec[1] = slot + geo.Mdi[0];
+            launches += launch_stepp<R>(1, geo, A, k, pm, a, stream);
+        }
+        cell_updates += (long long)(m_hi - m_lo) * ncells;
+    }
+
+    fdtd_status forward(double *d_W) override
+    {
+        cudaStream_t st = stream;
+        const Coef<R> k = coef();
+        const int N = cfg.nsteps, K = cfg.snapshot_every;
+        launch_zero_bytes(F_base, state_bytes, st);
+        if (Mg) launch_zero_bytes(gap_hist, Mg * sizeof(R), st);
+        launches += 2;
+        if (K <= 0) {
+            advance_forward(k, 0, N, true, rec);
+        } else {
+            for (int s = 0; s < nsnap; ++s) {
+                const int n0 = s * K, cnt = std::min(K, N - n0);
+                snapshot_save<R>(cfg.snapshot_dtype, F_base, state_bytes, snaps + (size_t)s * snap_stride, st);
+                ++launches;
+                advance_forward(k, n0, cnt, true, nullptr);
+            }
+        }
+        const double coefW = 0.5 * cfg.eps_g * dt * cfg.dx * cfg.dx;
+        launch_objective<R>(gap_hist, (long long)(N + 1) * Mg, coefW, misc, d_W, err, st);
+        ++launches;
+        return check_launch();
+    }
+
+    fdtd_status adjoint() override
+    {
+        cudaStream_t st = stream;
+        const Coef<R> k = coef();
+        const int N = cfg.nsteps, K = cfg.snapshot_every;
+        launch_zero_bytes(A_base, state_bytes, st);
+        launch_zero_bytes(G[0], geo.Mdi[0] * sizeof(double), st);
+        launch_zero_bytes(G[1], geo.Mdi[1] * sizeof(double), st);
+        launches += 3;
+        if (K <= 0) {
+            advance_adjoint(k, N, 0, 0);
+        } else {
+            for (int s = nsnap - 1; s >= 0; --s) {
+                const int n0 = s * K, n1 = std::min(n0 + K, N);
+                snapshot_load<R>(cfg.snapshot_dtype, snaps + (size_t)s * snap_stride, F_base, state_bytes, st);
+                ++launches;
+                advance_forward(k, n0, n1 - n0, false, rec);
+                advance_adjoint(k, n1, n0, n0);
+            }
+        }
+        return check_launch();
+    }
+
+    fdtd_status gradient(double *d_grad) override
+    {
+        const double scale = dt * cfg.dx * cfg.dx;
+        for (int cc = 0; cc < 2; ++cc)
+            launch_assemble_2d(G[cc], d_grad + (cc ? Mdx : 0), geo.dn[cc][0], geo.dn[cc][1],
+                               geo.d0[cc][0] - geo.dxa[cc], geo.dp[cc], geo.g0[cc][0] - geo.d0[cc][0],
+                               geo.g0[cc][1] - geo.d0[cc][1], geo.gn[cc][0], geo.gn[cc][1], scale, stream);
+        launches += 2;
+        return check_launch();
+    }
+
+    fdtd_status grayness(double *d_zeta) override
+    {
+        for (int cc = 0; cc < 2; ++cc)
+            launch_grayness<R>(rho_t[cc], geo.dn[cc][1], geo.dn[cc][0], geo.dp[cc], geo.d0[cc][0] - geo.dxa[cc],
+                               geo.dn[cc][1], geo.g0[cc][0] - geo.d0[cc][0], geo.g0[cc][1] - geo.d0[cc][1], 0,
+                               geo.gn[cc][0], geo.gn[cc][1], 1, d_zeta, stream, cc == 1);
+        launch_scale1(d_zeta, n_free > 0 ? 4.0 / (double)n_free : 0.0, stream);
+        launches += 4;
+        return check_launch();
+    }
+
+    fdtd_status gradient_scratch(double *d_grad, double *, double *) override { return gradient(d_grad); }
+
+    fdtd_status gap_history(double *d_out) override
+    {
+        launch_to_double<R>(gap_hist, d_out, (long long)(cfg.nsteps + 1) * Mg, stream);
+        ++launches;
+        return check_launch();
+    }
+    fdtd_status gap_spectrum(const double *d_freqs, int nf, double *d_out) override
+    {
+        launch_gap_dft<R>(gap_hist, (long long)cfg.nsteps + 1, (int)Mg, dt, d_freqs, nf, d_out, stream);
+        ++launches;
+        return check_launch();
+    }
+};
+
 // ------------------------------------------------------------------ 3D
 
 template <typename R>
@@ -906,6 +1202,9 @@ static fdtd_ctx *make_ctx(const fdtd_config *cfg)
     if (cfg->ndim == 3) {
         if (cfg->real_bytes == 4) c = new (std::nothrow) Ctx3D<float>();
         else c = new (std::nothrow) Ctx3D<double>();
+    } else if (cfg->pol == FDTD_POL_INPLANE) {
+        if (cfg->real_bytes == 4) c = new (std::nothrow) CtxP<float>();
+        else c = new (std::nothrow) CtxP<double>();
     } else {
         if (cfg->real_bytes == 4) c = new (std::nothrow) Ctx2D<float>();
         else c = new (std::nothrow) Ctx2D<double>();
@@ -913,8 +1212,13 @@ static fdtd_ctx *make_ctx(const fdtd_config *cfg)
     if (!c) return nullptr;
     c->cfg = *cfg;
     c->dt = cfg->courant * cfg->dx / kC0;
-    c->Md = box_count(cfg->design_lo, cfg->design_hi, cfg->ndim);
-    c->Mg = box_count(cfg->gap_lo, cfg->gap_hi, cfg->ndim);
+    if (cfg->ndim == 2 && cfg->pol == FDTD_POL_INPLANE) {
+        c->Md = edge_total(cfg->design_lo, cfg->design_hi);
+        c->Mg = edge_total(cfg->gap_lo, cfg->gap_hi);
+    } else {
+        c->Md = box_count(cfg->design_lo, cfg->design_hi, cfg->ndim);
+        c->Mg = box_count(cfg->gap_lo, cfg->gap_hi, cfg->ndim);
+    }
     c->n_free = c->Md - c->Mg;
     c->ncells = (long long)cfg->nx * cfg->ny * (cfg->ndim == 3 ? cfg->nz : 1);
     return c;

@@ -131,6 +131,51 @@ struct Step3D {
     double *G;           // adjoint: sensitivity accumulator [Mdi]
 };
 
+// 2D with E in plane (the paper's 2D "TM" case): Ex(i, j) on the edge
+// (i+1/2, j), Ey(i, j) on (i, j+1/2), Hz(i, j) at (i+1/2, j+1/2); [ny][px]
+// arrays.  Design variables, Drude currents and the gap live on edges: for
+// component c (0 = x, 1 = y) the edges of the design box form a rectangle
+// of array indices with origin d0[c] and extent dn[c] (E_x: dnx x (dny+1),
+// E_y: (dnx+1) x dny); their arrays use the pitched layout of the 2D design
+// box (column origin dxa[c], pitch dp[c]).
+struct GeoP {
+    int nx, ny, px, npml;
+    int d0[2][2], dn[2][2], dxa[2], dp[2];
+    long long Mdi[2];
+    int g0[2][2], gn[2][2], Mgc[2];  // gap edges per component; a gap record is Mgc[0] E_x then Mgc[1] E_y values
+    int s0[2], s1[2];                // source E_x edges: i in [s0x, s1x), j in [s0y, s1y)
+};
+
+// State: fields, per-component Drude currents (pitched design layout) and
+// the CPML terms: pexy (Ex, d/dy) and phzy (Hz, d/dy) in the y-slabs,
+// [2 npml][px]; peyx (Ey, d/dx) and phzx (Hz, d/dx) in the x-slabs,
+// [ny][2 npml].
+template <typename R>
+struct StateP {
+    R *Ex, *Ey, *Hz, *J[2];
+    R *pexy, *peyx, *phzx, *phzy;
+};
+
+template <typename R>
+struct PmlP {
+    const R *bE[2], *cE[2], *kiE[2], *bH[2], *cH[2], *kiH[2];  // per axis (0 = x, 1 = y)
+};
+
+template <typename R>
+struct StepP {
+    const R *rho_t[2];   // pitched densities of the E_x and E_y design edges
+    const R *src;        // forward: source table entry of this step
+    const R *gap_src;    // adjoint: forward gap record E^m
+    R *gap_rec;          // forward: gap record receiving E^{n+1} (or null)
+    R *rec[2];           // forward: design-edge record slots (or null); adjoint: forward E^m
+    double *G[2];        // adjoint: sensitivity accumulators
+};
+
+// H then E half steps of the in-plane 2D grid, in place (two launches).
+template <typename R>
+int launch_stepp(int mode, const GeoP &g, const StateP<R> &s, const Coef<R> &c, const PmlP<R> &pm,
+                 const StepP<R> &a, cudaStream_t st);
+
 // H then E half steps of the whole grid, in place (two launches).
 template <typename R>
 int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, const Coef<R> &c, const Pml3D<R> &pm,
@@ -165,7 +210,7 @@ template <typename R>
 void launch_ascent(R *rho, const double *g, long long n, double move, unsigned long long *gmax, cudaStream_t st);
 template <typename R>
 void launch_grayness(const R *rt, long long rows, int dnx, int dp, int off, int rows_per_plane, int gx0, int gy0,
-                     int gz0, int gnx, int gny, int gnz, double *acc, cudaStream_t st);
+                     int gz0, int gnx, int gny, int gnz, double *acc, cudaStream_t st, bool accumulate = false);
 void launch_scale1(double *x, double s, cudaStream_t st);
 template <typename R>
 void launch_threshold(R *rho, long long n, double level, cudaStream_t st);

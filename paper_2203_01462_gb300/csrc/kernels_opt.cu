@@ -204,9 +204,9 @@ void launch_ascent(R *rho, const double *g, long long n, double move, unsigned l
 
 template <typename R>
 void launch_grayness(const R *rt, long long rows, int dnx, int dp, int off, int rows_per_plane, int gx0, int gy0,
-                     int gz0, int gnx, int gny, int gnz, double *acc, cudaStream_t st)
+                     int gz0, int gnx, int gny, int gnz, double *acc, cudaStream_t st, bool accumulate)
 {
-    launch_zero_bytes(acc, sizeof(double), st);
+    if (!accumulate) launch_zero_bytes(acc, sizeof(double), st);
     k_gray<R><<<blocks_for(rows * dnx), TPB, 0, st>>>(rt, rows, dnx, dp, off, rows_per_plane, gx0, gy0, gz0, gnx, gny,
                                                        gnz, acc);
 }
@@ -240,9 +240,9 @@ void launch_threshold(R *rho, long long n, double level, cudaStream_t st)
 template void launch_ascent<float>(float *, const double *, long long, double, unsigned long long *, cudaStream_t);
 template void launch_ascent<double>(double *, const double *, long long, double, unsigned long long *, cudaStream_t);
 template void launch_grayness<float>(const float *, long long, int, int, int, int, int, int, int, int, int, int,
-                                     double *, cudaStream_t);
+                                     double *, cudaStream_t, bool);
 template void launch_grayness<double>(const double *, long long, int, int, int, int, int, int, int, int, int, int,
-                                      double *, cudaStream_t);
+                                      double *, cudaStream_t, bool);
 template void launch_mma_asymptotes<float>(const float *, const double *, double *, long long, int, double *,
                                            double *, cudaStream_t);
 template void launch_mma_asymptotes<double>(const double *, const double *, double *, long long, int, double *,
