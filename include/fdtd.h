@@ -266,6 +266,25 @@ fdtd_status fdtd_mma_asymptotes(fdtd_ctx *ctx, const void *d_rho, const double *
 fdtd_status fdtd_mma_solve(fdtd_ctx *ctx, const double *d_state, const double *d_grad, size_t n, double scale,
                            double raa0, double move, void *d_rho_new, double *d_sums);
 
+/* Design constraints of the paper's studies (Sec. 3.2, 3.4).
+ *
+ * fdtd_mirror_average: d_vec (device, n = M_d entries, elem_bytes 4 = float
+ * or 8 = double, in the design layout of the context) becomes symmetric
+ * under the mirror across the mid-plane of the design box normal to `axis`
+ * (0 x, 1 y, 2 z; < ndim): each entry and its image both take their mean.
+ * Applied to rho it makes a symmetric design; applied to a gradient it gives
+ * the ascent direction of the symmetric design.  In the in-plane 2D mode
+ * E_x edges map to E_x edges and E_y edges to E_y edges.
+ *
+ * fdtd_fix_design: where d_mask[k] != 0 (device bytes, n = M_d), sets
+ * d_rho[k] = value (field precision; may be null) and d_grad[k] = 0 (FP64;
+ * may be null): fixed material such as the silver blocks beside the gap.
+ *
+ * Both asynchronous; FDTD_EINVAL for bad sizes, pointers, axis or value. */
+fdtd_status fdtd_mirror_average(fdtd_ctx *ctx, void *d_vec, size_t n, int elem_bytes, int axis);
+fdtd_status fdtd_fix_design(fdtd_ctx *ctx, void *d_rho, double *d_grad, const unsigned char *d_mask, size_t n,
+                            double value);
+
 /* Grayness zeta = 4 rho~^T (1 - rho~) / M of the filtered design of the last
  * fdtd_set_design, gap nodes excluded (Sec. 3.2): 0 for a black-and-white
  * design, 1 for rho~ = 0.5 everywhere.  Written to d_zeta (device, one

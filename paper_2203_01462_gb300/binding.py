@@ -26,7 +26,7 @@ EXPORTS = ["fdtd_workspace_bytes", "fdtd_create", "fdtd_set_design", "fdtd_set_d
            "fdtd_forward", "fdtd_adjoint", "fdtd_gradient", "fdtd_gap_history", "fdtd_sync",
            "fdtd_run_host", "fdtd_get_info", "fdtd_status_string", "fdtd_destroy",
            "fdtd_gradient_static", "fdtd_gap_spectrum", "fdtd_ascent_step", "fdtd_mma_asymptotes", "fdtd_mma_solve",
-           "fdtd_grayness", "fdtd_threshold"]
+           "fdtd_mirror_average", "fdtd_fix_design", "fdtd_grayness", "fdtd_threshold"]
 
 
 class FdtdError(RuntimeError):
@@ -90,6 +90,8 @@ def load():
             "fdtd_gap_spectrum": [P, P, C.c_int, P],
             "fdtd_mma_asymptotes": [P, P, P, P, C.c_size_t, C.c_int, P],
             "fdtd_mma_solve": [P, P, P, C.c_size_t, C.c_double, C.c_double, C.c_double, P, P],
+            "fdtd_mirror_average": [P, P, C.c_size_t, C.c_int, C.c_int],
+            "fdtd_fix_design": [P, P, P, P, C.c_size_t, C.c_double],
             "fdtd_grayness": [P, P],
             "fdtd_threshold": [P, P, C.c_size_t, C.c_double],
             "fdtd_gap_history": [P, P, C.c_size_t],
@@ -249,6 +251,19 @@ class Solver:
                                           C.c_void_p(out.data_ptr())), "fdtd_gap_spectrum")
         z = t.view_as_complex(out.reshape(-1, 2))
         return z.reshape((f.numel(), 3, self.n_gap) if nc == 3 else (f.numel(), self.n_gap))
+
+    def mirror_average(self, vec, axis: int) -> None:
+        """Make ``vec`` (rho in the field precision, or an FP64 gradient)
+        mirror-symmetric across the design box's mid-plane normal to ``axis``."""
+        _check(self.lib.fdtd_mirror_average(self.ctx, C.c_void_p(vec.data_ptr()), vec.numel(),
+                                            vec.element_size(), int(axis)), "fdtd_mirror_average")
+
+    def fix_design(self, mask, rho=None, grad=None, value: float = 1.0) -> None:
+        """rho = value and grad = 0 where the uint8 device ``mask`` is set."""
+        _check(self.lib.fdtd_fix_design(self.ctx, C.c_void_p(rho.data_ptr() if rho is not None else None),
+                                        C.c_void_p(grad.data_ptr() if grad is not None else None),
+                                        C.c_void_p(mask.data_ptr()), mask.numel(), float(value)),
+               "fdtd_fix_design")
 
     def mma_state(self):
         """Device state of the moving-asymptote update (4 M_d doubles)."""

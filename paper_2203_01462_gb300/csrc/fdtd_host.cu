@@ -1373,6 +1373,54 @@ fdtd_status fdtd_mma_solve(fdtd_ctx *ctx, const double *d_state, const double *d
     return cuda_ok(cudaGetLastError());
 }
 
+static DesignRects design_rects(const fdtd_config &c)
+{
+    DesignRects r{};
+    if (c.ndim == 2 && c.pol == FDTD_POL_INPLANE) {
+        r.n = 2;
+        long long off = 0;
+        for (int cc = 0; cc < 2; ++cc) {
+            int o[2], n[2];
+            edge_rect(c.design_lo, c.design_hi, cc, o, n);
+            r.off[cc] = off;
+            r.w[cc] = n[0];
+            r.h[cc] = n[1];
+            r.d[cc] = 1;
+            off += (long long)n[0] * n[1];
+        }
+        return r;
+    }
+    r.n = 1;
+    r.off[0] = 0;
+    r.w[0] = c.design_hi[0] - c.design_lo[0];
+    r.h[0] = c.design_hi[1] - c.design_lo[1];
+    r.d[0] = c.ndim == 3 ? c.design_hi[2] - c.design_lo[2] : 1;
+    return r;
+}
+
+fdtd_status fdtd_mirror_average(fdtd_ctx *ctx, void *d_vec, size_t n, int elem_bytes, int axis)
+{
+    if (!ctx || !d_vec || (long long)n != ctx->Md || (elem_bytes != 4 && elem_bytes != 8) || axis < 0 ||
+        axis >= ctx->cfg.ndim)
+        return FDTD_EINVAL;
+    const DesignRects r = design_rects(ctx->cfg);
+    if (elem_bytes == 4) launch_mirror_avg<float>((float *)d_vec, r, axis, ctx->stream);
+    else launch_mirror_avg<double>((double *)d_vec, r, axis, ctx->stream);
+    ++ctx->launches;
+    return cuda_ok(cudaGetLastError());
+}
+
+fdtd_status fdtd_fix_design(fdtd_ctx *ctx, void *d_rho, double *d_grad, const unsigned char *d_mask, size_t n,
+                            double value)
+{
+    if (!ctx || !d_mask || (!d_rho && !d_grad) || (long long)n != ctx->Md || !(value >= 0.0 && value <= 1.0))
+        return FDTD_EINVAL;
+    if (ctx->cfg.real_bytes == 4) launch_fix<float>((float *)d_rho, d_grad, d_mask, (long long)n, value, ctx->stream);
+    else launch_fix<double>((double *)d_rho, d_grad, d_mask, (long long)n, value, ctx->stream);
+    ++ctx->launches;
+    return cuda_ok(cudaGetLastError());
+}
+
 fdtd_status fdtd_grayness(fdtd_ctx *ctx, double *d_zeta)
 {
     if (!ctx || !d_zeta) return FDTD_EINVAL;

@@ -214,6 +214,19 @@ void launch_grayness(const R *rt, long long rows, int dnx, int dp, int off, int 
 void launch_scale1(double *x, double s, cudaStream_t st);
 template <typename R>
 void launch_threshold(R *rho, long long n, double level, cudaStream_t st);
+// The design layout as one or two x-fastest rectangles (w x h x d entries
+// from offset off): the node box in TM_z 2D and 3D, the E_x and E_y edge
+// rectangles in the in-plane 2D mode.
+struct DesignRects {
+    int n;
+    long long off[2];
+    int w[2], h[2], d[2];
+};
+template <typename T>
+void launch_mirror_avg(T *v, const DesignRects &r, int axis, cudaStream_t st);
+template <typename T>
+void launch_fix(T *rho, double *g, const unsigned char *mask, long long n, double value, cudaStream_t st);
+
 // Block count of the MMA kernels; the context keeps 2 * MMA_BLOCKS doubles of
 // per-block partial sums.
 constexpr int MMA_BLOCKS = 152 * 8;

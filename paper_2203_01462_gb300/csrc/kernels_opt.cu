@@ -231,6 +231,67 @@ void launch_mma_solve(const double *state, const double *g, long long n, double 
     k_sum_partials<<<1, 32, 0, st>>>(part, nb, sums);
 }
 
+// Mirror average over the design layout: each entry and its image across the
+// mid-plane of its rectangle normal to `axis` both become their mean.  The
+// layout is one or two rectangles (x fastest); only the lower index of each
+// pair writes, so pairs never race.
+template <typename T>
+__global__ void k_mirror_avg(T *v, DesignRects r, int axis)
+{
+    long long total = 0;
+    for (int q = 0; q < r.n; ++q) total += (long long)r.w[q] * r.h[q] * r.d[q];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int q = 0;
+        long long k = t;
+        while (q + 1 < r.n && k >= (long long)r.w[q] * r.h[q] * r.d[q]) {
+            k -= (long long)r.w[q] * r.h[q] * r.d[q];
+            ++q;
+        }
+        const int w = r.w[q], h = r.h[q], d = r.d[q];
+        int x = (int)(k % w), y = (int)((k / w) % h), z = (int)(k / ((long long)w * h));
+        if (axis == 0) x = w - 1 - x;
+        else if (axis == 1) y = h - 1 - y;
+        else z = d - 1 - z;
+        const long long km = ((long long)z * h + y) * w + x;
+        if (km <= k) continue;
+        T *base = v + r.off[q];
+        const double m = 0.5 * ((double)base[k] + (double)base[km]);
+        base[k] = (T)m;
+        base[km] = (T)m;
+    }
+}
+
+// Fixed design variables: rho = value and gradient 0 where mask is set.
+template <typename T>
+__global__ void k_fix(T *rho, double *g, const unsigned char *mask, long long n, double value)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        if (mask[k]) {
+            if (rho) rho[k] = (T)value;
+            if (g) g[k] = 0.0;
+        }
+}
+
+template <typename T>
+void launch_mirror_avg(T *v, const DesignRects &r, int axis, cudaStream_t st)
+{
+    long long total = 0;
+    for (int q = 0; q < r.n; ++q) total += (long long)r.w[q] * r.h[q] * r.d[q];
+    k_mirror_avg<T><<<blocks_for(total), TPB, 0, st>>>(v, r, axis);
+}
+
+template <typename T>
+void launch_fix(T *rho, double *g, const unsigned char *mask, long long n, double value, cudaStream_t st)
+{
+    k_fix<T><<<blocks_for(n), TPB, 0, st>>>(rho, g, mask, n, value);
+}
+
+template void launch_mirror_avg<float>(float *, const DesignRects &, int, cudaStream_t);
+template void launch_mirror_avg<double>(double *, const DesignRects &, int, cudaStream_t);
+template void launch_fix<float>(float *, double *, const unsigned char *, long long, double, cudaStream_t);
+template void launch_fix<double>(double *, double *, const unsigned char *, long long, double, cudaStream_t);
+
 template <typename R>
 void launch_threshold(R *rho, long long n, double level, cudaStream_t st)
 {

@@ -304,6 +304,37 @@ def zero_gap(w: dict, r: np.ndarray) -> np.ndarray:
     return r
 
 
+def fixed_blocks_mask(w: dict, axis: int = 0) -> np.ndarray:
+    """Design variables of two blocks beside the gap along ``axis``, each the
+    gap's size: the paper fixes such regions to metal (Sec. 3.2, AntTM3/4).
+    Along x (the E_x polarisation of the in-plane workloads) they make the
+    two arms of a dipole gap.  Gap entries are not included."""
+    lo, hi = list(w["gap_lo"]), list(w["gap_hi"])
+    size = hi[axis] - lo[axis]
+    boxes = []
+    for sgn in (-1, 1):
+        blo, bhi = list(lo), list(hi)
+        if sgn < 0:
+            blo[axis], bhi[axis] = lo[axis] - size, lo[axis]
+        else:
+            blo[axis], bhi[axis] = hi[axis], hi[axis] + size
+        boxes.append((blo, bhi))
+    dl = w["design_lo"]
+    if inplane(w):
+        m = np.zeros(n_design(w), dtype=bool)
+        mx, my = split_edges(w, m)
+        for blo, bhi in boxes:
+            mx[blo[1] - dl[1]:bhi[1] - dl[1] + 1, blo[0] - dl[0]:bhi[0] - dl[0]] = True
+            my[blo[1] - dl[1]:bhi[1] - dl[1], blo[0] - dl[0]:bhi[0] - dl[0] + 1] = True
+        m[gap_edge_mask(w)] = False
+        return m
+    m = np.zeros(design_shape(w), dtype=bool)
+    for blo, bhi in boxes:
+        sl = tuple(slice(blo[a] - dl[a], bhi[a] - dl[a]) for a in reversed(range(w["ndim"])))
+        m[sl] = True
+    return m.reshape(-1)
+
+
 def _bowtie_at(x, y, cx, cy, gx):
     ax = np.abs(y - cy)
     return (np.abs(x - cx) >= gx) & (ax <= 0.6 * (np.abs(x - cx) - gx) + 1.0)

@@ -120,7 +120,8 @@ def _save(path, **kw):
 def optimize_gcmma(s: Solver, rho0=None, max_iters: int = 600, levels=None, sigma_max: float = 0.0,
                    move: float = 0.5, min_inner: int = 12, norm_drop: float = 0.7, zeta_stop: float = 0.005,
                    max_inner: int = 10, tol: float = 1e-10, checkpoint: str | None = None,
-                   checkpoint_every: int = 1, resume: str | None = None):
+                   checkpoint_every: int = 1, resume: str | None = None, fixed=None, fixed_value: float = 1.0,
+                   symmetry: int | None = None):
     """GCMMA loop of Sec. 3.2 with the damping continuation.
 
     Stage j solves max W~ at damping factor ``levels[j]`` with GCMMA from the
@@ -135,11 +136,32 @@ def optimize_gcmma(s: Solver, rho0=None, max_iters: int = 600, levels=None, sigm
 
     ``checkpoint``: file written every ``checkpoint_every`` outer iterations
     (design, MMA state, gradient, counters, history); ``resume``: such a file
-    to continue from (the same workload and settings).  Returns (rho, history)."""
+    to continue from (the same workload and settings).
+
+    ``fixed``: boolean mask of design variables held at ``fixed_value`` (the
+    paper's fixed metal blocks); ``symmetry``: an axis across whose design
+    mid-plane the design stays mirror-symmetric (gradients are
+    mirror-averaged).  Variables with a zero gradient do not move under MMA,
+    so both constraints hold exactly.  Returns (rho, history)."""
     t = torch
     levels = list(damping_levels() if levels is None else levels)
     n = s.n_design
     h = GcmmaHistory()
+    mask = None
+    if fixed is not None:
+        mask = t.as_tensor(np.asarray(fixed, dtype=np.uint8).reshape(-1), device=s.device).contiguous()
+
+    def constrain(g):
+        if mask is not None:
+            s.fix_design(mask, grad=g)
+        if symmetry is not None:
+            s.mirror_average(g, symmetry)
+        return g
+
+    def evaluate(r, gs):
+        Wt, g = s.evaluate(r, sigma_max, gs)
+        return float(Wt.item()), constrain(g)
+
     if resume is not None:
         z = np.load(resume)
         rho = t.as_tensor(z["rho"], device=s.device).to(s.real).contiguous()
@@ -154,11 +176,14 @@ def optimize_gcmma(s: Solver, rho0=None, max_iters: int = 600, levels=None, sigm
         s.set_damping(sigma_max, levels[stage])
     else:
         rho = t.as_tensor(rho0, device=s.device).to(s.real).contiguous().reshape(-1).clone()
+        if mask is not None:
+            s.fix_design(mask, rho=rho, value=fixed_value)
+        if symmetry is not None:
+            s.mirror_average(rho, symmetry)
         state = s.mma_state()
         k = kk = stage = it_stage = 0
         norm0 = 0.0
-        Wt, g = s.evaluate(rho, sigma_max, levels[0])
-        W = float(Wt.item())
+        W, g = evaluate(rho, levels[0])
     y = t.empty_like(rho)
     while True:
         gs = levels[stage]
@@ -171,8 +196,7 @@ def optimize_gcmma(s: Solver, rho0=None, max_iters: int = 600, levels=None, sigm
             # subproblem solved: next damping level, a fresh GCMMA run from this design
             stage += 1
             it_stage = kk = 0
-            Wt, g = s.evaluate(rho, sigma_max, levels[stage])
-            W = float(Wt.item())
+            W, g = evaluate(rho, levels[stage])
             continue
         h.W.append(W)
         h.zeta.append(zeta)
@@ -200,7 +224,7 @@ def optimize_gcmma(s: Solver, rho0=None, max_iters: int = 600, levels=None, sigm
         rho.copy_(y)
         W = Wy
         s.adjoint()
-        g = s.gradient()
+        g = constrain(s.gradient())
         k += 1
         kk += 1
         it_stage += 1
