@@ -43,6 +43,7 @@ WORKLOADS = {
     "cfg_2d_160": I.cfg_2d_160,
     "cfg_3d_256": I.cfg_3d_256,
     "cfg_3d_512": I.cfg_3d_512,
+    "cfg_2d_inplane_200": lambda: I.cfg_2d_inplane_paper(200.0, nsteps=78000, snapshot_every=64),
 }
 
 
@@ -378,7 +379,8 @@ def main() -> None:
         roofline=dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm,
                       traffic=NCU_TRAFFIC_PER_STEP.get(w["name"]), traffic_unit="bytes per forward step",
                       algorithmic_bytes_per_step=ab["forward"],
-                      kernel="k_step2d<float,0> (fused forward leapfrog step)" if w["ndim"] == 2
+                      kernel=("k_hp + k_ep<float,0> (forward H and E half steps, E in plane)" if I.inplane(w)
+                              else "k_step2d<float,0> (fused forward leapfrog step)") if w["ndim"] == 2
                       else "k_h3d + k_e3d<float,0> (forward H and E half steps)",
                       peak_source=peak_src),
         phases_ms=dict(forward=statistics.median(fwd_ms), adjoint_with_recompute=statistics.median(adj_ms)),
