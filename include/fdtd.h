@@ -294,6 +294,16 @@ fdtd_status fdtd_grayness(fdtd_ctx *ctx, double *d_zeta);
 /* d_rho <- (d_rho >= level) ? 1 : 0 (the paper's final step, level 0.5). */
 fdtd_status fdtd_threshold(fdtd_ctx *ctx, void *d_rho, size_t n, double level);
 
+/* CUDA graphs for the time-step loops.  mode 0: every kernel is launched
+ * from the host; 1: each whole forward / adjoint pass is captured into a
+ * CUDA graph on its first call and replayed afterwards (the graph stays valid
+ * across fdtd_set_design and fdtd_set_damping: every pointer is fixed and the
+ * material coefficients live in a per-context constant-memory slot);
+ * 2 (default): graphs for grids of at most 2^20 nodes, where launch latency
+ * rather than bandwidth bounds a step.  Results are identical in every
+ * mode.  A context holds at most one graph per pass kind. */
+fdtd_status fdtd_set_graphs(fdtd_ctx *ctx, int mode);
+
 /* Wait for the context's stream and report (then clear) device-side errors:
  * FDTD_ERANGE, FDTD_EUNSTABLE, or FDTD_ECUDA for a failed kernel. */
 fdtd_status fdtd_sync(fdtd_ctx *ctx);

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <memory>
 #include <new>
+#include <mutex>
 #include <vector>
 
 #include "../../include/fdtd.h"
@@ -173,7 +174,22 @@ struct fdtd_ctx {
     bool has_design = false, fwd_done = false, adj_done = false;
     double sigma_max = 0.0, gamma_scale = 1.0;
     long long launches = 0, cell_updates = 0;
-    virtual ~fdtd_ctx() {}
+    int coef_slot = -1;  // constant-memory coefficient slot (coef_slots.cuh)
+    // CUDA graphs of whole forward / adjoint passes (replayed when enabled):
+    // 0 off, 1 on, 2 automatic (grids of at most GRAPH_AUTO_CELLS nodes).
+    int graphs = 2;
+    struct Captured {
+        cudaGraphExec_t exec = nullptr;
+        long long launches = 0, cells = 0;
+        int curF = 0, curA = 0;
+    } cap[2];
+    cudaStream_t capture_stream = nullptr;  // private stream the passes are captured on
+    virtual ~fdtd_ctx()
+    {
+        for (auto &c : cap)
+            if (c.exec) cudaGraphExecDestroy(c.exec);
+        if (capture_stream) cudaStreamDestroy(capture_stream);
+    }
     virtual fdtd_status carve(Carver &cv) = 0;
     virtual fdtd_status upload_tables() = 0;
     virtual fdtd_status set_design(const void *d_rho) = 0;
@@ -201,6 +217,65 @@ fdtd_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? FDTD_OK : FDTD_EC
         fdtd_status s__ = (x);               \
         if (s__ != FDTD_OK) return s__;      \
     } while (0)
+
+constexpr long long GRAPH_AUTO_CELLS = 1LL << 20;
+
+bool use_graphs(const fdtd_ctx *c) { return c->graphs == 1 || (c->graphs == 2 && c->ncells <= GRAPH_AUTO_CELLS); }
+
+// Run `enqueue` (which only enqueues work on c->stream) directly, or through
+// a CUDA graph captured on its first call and replayed afterwards.  The
+// graph is valid for the context's lifetime: every pointer is fixed and the
+// coefficients come from the context's constant-memory slot.  Capture runs
+// on a private non-blocking stream (the caller's stream may be the legacy
+// default stream, which cannot be captured); nothing executes during
+// capture, and the graph is launched on the caller's stream.  curF / curA
+// receive the ping-pong parities the pass leaves behind.
+template <typename F>
+fdtd_status run_pass(fdtd_ctx *c, int which, int &curF, int &curA, F &&enqueue)
+{
+    if (!use_graphs(c)) return enqueue();
+    fdtd_ctx::Captured &g = c->cap[which];
+    if (!g.exec) {
+        if (!c->capture_stream)
+            FDTD_TRY(cuda_ok(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking)));
+        const long long l0 = c->launches, c0 = c->cell_updates;
+        cudaStream_t user = c->stream;
+        c->stream = c->capture_stream;
+        fdtd_status s = cuda_ok(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        if (s != FDTD_OK) {
+            c->stream = user;
+            return s;
+        }
+        s = enqueue();
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        c->stream = user;
+        if (s != FDTD_OK || e != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return s != FDTD_OK ? s : FDTD_ECUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            g.exec = nullptr;
+            return FDTD_ECUDA;
+        }
+        g.launches = c->launches - l0;
+        g.cells = c->cell_updates - c0;
+        g.curF = curF;
+        g.curA = curA;
+        c->launches = l0;
+        c->cell_updates = c0;
+    }
+    FDTD_TRY(cuda_ok(cudaGraphLaunch(g.exec, c->stream)));
+    c->launches += g.launches;
+    c->cell_updates += g.cells;
+    curF = g.curF;
+    curA = g.curA;
+    return FDTD_OK;
+}
+
 
 // Bytes of one checkpoint of a state block of `state_bytes` bytes of R
 // words: a plain copy, or 16-bit words plus one float scale per slab (each
@@ -430,6 +505,24 @@ struct Ctx2D final : fdtd_ctx {
 
     Coef<R> coef() const { return make_coef<R>(cfg, dt, sigma_max, gamma_scale); }
 
+    // A pass enqueues its launches (enqueue_*), directly or as a replayed
+    // CUDA graph; the coefficients go to the context's constant slot first.
+    fdtd_status forward(double *d_W) override
+    {
+        FDTD_TRY(cuda_ok(upload_coef_2d<R>(coef_slot, coef(), stream)));
+        int keepA = curA;
+        FDTD_TRY(run_pass(this, 0, curF, keepA, [&] { return enqueue_forward(); }));
+        if (d_W && d_W != misc)
+            FDTD_TRY(cuda_ok(cudaMemcpyAsync(d_W, misc, sizeof(double), cudaMemcpyDeviceToDevice, stream)));
+        return check_launch();
+    }
+
+    fdtd_status adjoint() override
+    {
+        FDTD_TRY(cuda_ok(upload_coef_2d<R>(coef_slot, coef(), stream)));
+        return run_pass(this, 1, curF, curA, [&] { return enqueue_adjoint(); });
+    }
+
     fdtd_status check_launch() { return cuda_ok(cudaGetLastError()); }
 
     fdtd_status set_design(const void *d_rho) override
@@ -462,7 +555,7 @@ struct Ctx2D final : fdtd_ctx {
     // Advance the forward state from step n0 by count steps.  gap: record
     // E^{n+1} of the gap; rec_base: record design-box E^{n+1} in slot
     // (n - n0) of rec_base (null: no record).
-    void advance_forward(const Coef<R> &k, int n0, int count, bool gap, R *rec_base)
+    void advance_forward(int n0, int count, bool gap, R *rec_base)
     {
         Step2D<R> a{};
         a.rho_t = rho_t;
@@ -470,7 +563,7 @@ struct Ctx2D final : fdtd_ctx {
             a.src = src_tab + n;
             a.gap_rec = (gap && Mg) ? gap_hist + (size_t)(n + 1) * Mg : nullptr;
             a.rec = rec_base ? rec_base + (size_t)(n - n0) * Mdi : nullptr;
-            launches += launch_step2d<R>(0, geo, F[curF], F[curF ^ 1], k, px, py, a, stream);
+            launches += launch_step2d<R>(0, geo, F[curF], F[curF ^ 1], coef_slot, px, py, a, stream);
             curF ^= 1;
         }
         cell_updates += (long long)count * ncells;
@@ -478,7 +571,7 @@ struct Ctx2D final : fdtd_ctx {
 
     // Adjoint steps for m = m_hi down to m_lo + 1 (adjoint step N - m), the
     // forward E^m of the design box in slot (m - 1 - slot0) of base.
-    void advance_adjoint_buf(const Coef<R> &k, int m_hi, int m_lo, R *base, int slot0)
+    void advance_adjoint_buf(int m_hi, int m_lo, R *base, int slot0)
     {
         Step2D<R> a{};
         a.rho_t = rho_t;
@@ -486,20 +579,19 @@ struct Ctx2D final : fdtd_ctx {
         for (int m = m_hi; m > m_lo; --m) {
             a.gap_src = Mg ? gap_hist + (size_t)m * Mg : nullptr;
             a.rec = base + (size_t)(m - 1 - slot0) * Mdi;
-            launches += launch_step2d<R>(1, geo, A[curA], A[curA ^ 1], k, px, py, a, stream);
+            launches += launch_step2d<R>(1, geo, A[curA], A[curA ^ 1], coef_slot, px, py, a, stream);
             curA ^= 1;
         }
         cell_updates += (long long)(m_hi - m_lo) * ncells;
     }
-    void advance_adjoint(const Coef<R> &k, int m_hi, int m_lo, int slot0)
+    void advance_adjoint(int m_hi, int m_lo, int slot0)
     {
-        advance_adjoint_buf(k, m_hi, m_lo, rec, slot0);
+        advance_adjoint_buf(m_hi, m_lo, rec, slot0);
     }
 
-    fdtd_status forward(double *d_W) override
+    fdtd_status enqueue_forward()
     {
         cudaStream_t st = stream;
-        const Coef<R> k = coef();
         const int N = cfg.nsteps, K = cfg.snapshot_every;
         curF = 0;
         // Both buffers of the pair: padding words are never written by the
@@ -509,25 +601,24 @@ struct Ctx2D final : fdtd_ctx {
         if (Mg) launch_zero_bytes(gap_hist, Mg * sizeof(R), st);
         launches += 3;
         if (K <= 0) {
-            advance_forward(k, 0, N, true, rec);
+            advance_forward(0, N, true, rec);
         } else {
             for (int s = 0; s < nsnap; ++s) {
                 const int n0 = s * K, cnt = std::min(K, N - n0);
                 snapshot_save<R>(cfg.snapshot_dtype, F_base[curF], state_bytes, snaps + (size_t)s * snap_stride, st);
                 ++launches;
-                advance_forward(k, n0, cnt, true, nullptr);
+                advance_forward(n0, cnt, true, nullptr);
             }
         }
         const double coefW = 0.5 * cfg.eps_g * dt * pow(cfg.dx, cfg.ndim);
-        launch_objective<R>(gap_hist, (long long)(N + 1) * Mg, coefW, misc, d_W, err, st);
+        launch_objective<R>(gap_hist, (long long)(N + 1) * Mg, coefW, misc, nullptr, err, st);
         ++launches;
         return check_launch();
     }
 
-    fdtd_status adjoint() override
+    fdtd_status enqueue_adjoint()
     {
         cudaStream_t st = stream;
-        const Coef<R> k = coef();
         const int N = cfg.nsteps, K = cfg.snapshot_every;
         curA = 0;
         launch_zero_bytes(A_base[0], state_bytes, st);
@@ -535,7 +626,7 @@ struct Ctx2D final : fdtd_ctx {
         launch_zero_bytes(G, Mdi * sizeof(double), st);
         launches += 3;
         if (K <= 0) {
-            advance_adjoint(k, N, 0, 0);
+            advance_adjoint(N, 0, 0);
             return check_launch();
         }
         // Segments in reverse.  Segment s covers steps [s K, min(s K + K, N));
@@ -550,7 +641,7 @@ struct Ctx2D final : fdtd_ctx {
             ++launches;
         };
         restore(nsnap - 1);
-        advance_forward(k, seg_lo(nsnap - 1), seg_hi(nsnap - 1) - seg_lo(nsnap - 1), false, buf(nsnap - 1));
+        advance_forward(seg_lo(nsnap - 1), seg_hi(nsnap - 1) - seg_lo(nsnap - 1), false, buf(nsnap - 1));
         for (int s = nsnap - 1; s >= 1; --s) {
             restore(s - 1);
             const int f0 = seg_lo(s - 1), nf = seg_hi(s - 1) - f0;  // recompute of segment s - 1
@@ -565,16 +656,16 @@ struct Ctx2D final : fdtd_ctx {
                 fa.rec = buf(s - 1) + (size_t)t * Mdi;
                 aa.gap_src = Mg ? gap_hist + (size_t)m * Mg : nullptr;
                 aa.rec = buf(s) + (size_t)(m - 1 - a_lo) * Mdi;
-                launches += launch_step2d_pair<R>(geo, F[curF], F[curF ^ 1], fa, A[curA], A[curA ^ 1], aa, k, px,
+                launches += launch_step2d_pair<R>(geo, F[curF], F[curF ^ 1], fa, A[curA], A[curA ^ 1], aa, coef_slot, px,
                                                   py, stream);
                 curF ^= 1;
                 curA ^= 1;
             }
             cell_updates += 2LL * pairs * ncells;
-            if (nf > pairs) advance_forward(k, f0 + pairs, nf - pairs, false, buf(s - 1) + (size_t)pairs * Mdi);
-            if (a_hi - a_lo > pairs) advance_adjoint_buf(k, a_hi - pairs, a_lo, buf(s), a_lo);
+            if (nf > pairs) advance_forward(f0 + pairs, nf - pairs, false, buf(s - 1) + (size_t)pairs * Mdi);
+            if (a_hi - a_lo > pairs) advance_adjoint_buf(a_hi - pairs, a_lo, buf(s), a_lo);
         }
-        advance_adjoint_buf(k, seg_hi(0), seg_lo(0), buf(0), seg_lo(0));
+        advance_adjoint_buf(seg_hi(0), seg_lo(0), buf(0), seg_lo(0));
         return check_launch();
     }
 
@@ -782,6 +873,23 @@ struct CtxP final : fdtd_ctx {
     }
 
     Coef<R> coef() const { return make_coef<R>(cfg, dt, sigma_max, gamma_scale); }
+
+    fdtd_status forward(double *d_W) override
+    {
+        FDTD_TRY(cuda_ok(upload_coef_p<R>(coef_slot, coef(), stream)));
+        int f = 0, a = 0;
+        FDTD_TRY(run_pass(this, 0, f, a, [&] { return enqueue_forward(); }));
+        if (d_W && d_W != misc)
+            FDTD_TRY(cuda_ok(cudaMemcpyAsync(d_W, misc, sizeof(double), cudaMemcpyDeviceToDevice, stream)));
+        return check_launch();
+    }
+
+    fdtd_status adjoint() override
+    {
+        FDTD_TRY(cuda_ok(upload_coef_p<R>(coef_slot, coef(), stream)));
+        int f = 0, a = 0;
+        return run_pass(this, 1, f, a, [&] { return enqueue_adjoint(); });
+    }
     fdtd_status check_launch() { return cuda_ok(cudaGetLastError()); }
 
     fdtd_status set_design(const void *d_rho) override
@@ -811,7 +919,7 @@ struct CtxP final : fdtd_ctx {
         return a;
     }
 
-    void advance_forward(const Coef<R> &k, int n0, int count, bool gap, R *rec_base)
+    void advance_forward(int n0, int count, bool gap, R *rec_base)
     {
         StepP<R> a = step_args();
         for (int n = n0; n < n0 + count; ++n) {
@@ -820,12 +928,12 @@ struct CtxP final : fdtd_ctx {
             R *slot = rec_base ? rec_base + (size_t)(n - n0) * Mdi_all() : nullptr;
             a.rec[0] = slot;
             a.rec[1] = slot ? slot + geo.Mdi[0] : nullptr;
-            launches += launch_stepp<R>(0, geo, F, k, pm, a, stream);
+            launches += launch_stepp<R>(0, geo, F, coef_slot, pm, a, stream);
         }
         cell_updates += (long long)count * ncells;
     }
 
-    void advance_adjoint(const Coef<R> &k, int m_hi, int m_lo, int slot0)
+    void advance_adjoint(int m_hi, int m_lo, int slot0)
     {
         StepP<R> a = step_args();
         a.G[0] = G[0];
@@ -835,53 +943,51 @@ struct CtxP final : fdtd_ctx {
             R *slot = rec + (size_t)(m - 1 - slot0) * Mdi_all();
             a.rec[0] = slot;
             a.rec[1] = slot + geo.Mdi[0];
-            launches += launch_stepp<R>(1, geo, A, k, pm, a, stream);
+            launches += launch_stepp<R>(1, geo, A, coef_slot, pm, a, stream);
         }
         cell_updates += (long long)(m_hi - m_lo) * ncells;
     }
 
-    fdtd_status forward(double *d_W) override
+    fdtd_status enqueue_forward()
     {
         cudaStream_t st = stream;
-        const Coef<R> k = coef();
         const int N = cfg.nsteps, K = cfg.snapshot_every;
         launch_zero_bytes(F_base, state_bytes, st);
         if (Mg) launch_zero_bytes(gap_hist, Mg * sizeof(R), st);
         launches += 2;
         if (K <= 0) {
-            advance_forward(k, 0, N, true, rec);
+            advance_forward(0, N, true, rec);
         } else {
             for (int s = 0; s < nsnap; ++s) {
                 const int n0 = s * K, cnt = std::min(K, N - n0);
                 snapshot_save<R>(cfg.snapshot_dtype, F_base, state_bytes, snaps + (size_t)s * snap_stride, st);
                 ++launches;
-                advance_forward(k, n0, cnt, true, nullptr);
+                advance_forward(n0, cnt, true, nullptr);
             }
         }
         const double coefW = 0.5 * cfg.eps_g * dt * cfg.dx * cfg.dx;
-        launch_objective<R>(gap_hist, (long long)(N + 1) * Mg, coefW, misc, d_W, err, st);
+        launch_objective<R>(gap_hist, (long long)(N + 1) * Mg, coefW, misc, nullptr, err, st);
         ++launches;
         return check_launch();
     }
 
-    fdtd_status adjoint() override
+    fdtd_status enqueue_adjoint()
     {
         cudaStream_t st = stream;
-        const Coef<R> k = coef();
         const int N = cfg.nsteps, K = cfg.snapshot_every;
         launch_zero_bytes(A_base, state_bytes, st);
         launch_zero_bytes(G[0], geo.Mdi[0] * sizeof(double), st);
         launch_zero_bytes(G[1], geo.Mdi[1] * sizeof(double), st);
         launches += 3;
         if (K <= 0) {
-            advance_adjoint(k, N, 0, 0);
+            advance_adjoint(N, 0, 0);
         } else {
             for (int s = nsnap - 1; s >= 0; --s) {
                 const int n0 = s * K, n1 = std::min(n0 + K, N);
                 snapshot_load<R>(cfg.snapshot_dtype, snaps + (size_t)s * snap_stride, F_base, state_bytes, st);
                 ++launches;
-                advance_forward(k, n0, n1 - n0, false, rec);
-                advance_adjoint(k, n1, n0, n0);
+                advance_forward(n0, n1 - n0, false, rec);
+                advance_adjoint(n1, n0, n0);
             }
         }
         return check_launch();
@@ -1047,6 +1153,23 @@ struct Ctx3D final : fdtd_ctx {
     }
 
     Coef<R> coef() const { return make_coef<R>(cfg, dt, sigma_max, gamma_scale); }
+
+    fdtd_status forward(double *d_W) override
+    {
+        FDTD_TRY(cuda_ok(upload_coef_3d<R>(coef_slot, coef(), stream)));
+        int f = 0, a = 0;
+        FDTD_TRY(run_pass(this, 0, f, a, [&] { return enqueue_forward(); }));
+        if (d_W && d_W != misc)
+            FDTD_TRY(cuda_ok(cudaMemcpyAsync(d_W, misc, sizeof(double), cudaMemcpyDeviceToDevice, stream)));
+        return check_launch();
+    }
+
+    fdtd_status adjoint() override
+    {
+        FDTD_TRY(cuda_ok(upload_coef_3d<R>(coef_slot, coef(), stream)));
+        int f = 0, a = 0;
+        return run_pass(this, 1, f, a, [&] { return enqueue_adjoint(); });
+    }
     fdtd_status check_launch() { return cuda_ok(cudaGetLastError()); }
 
     fdtd_status set_design(const void *d_rho) override
@@ -1067,7 +1190,7 @@ struct Ctx3D final : fdtd_ctx {
         return FDTD_OK;
     }
 
-    void advance_forward(const Coef<R> &k, int n0, int count, bool gap, R *rec_base)
+    void advance_forward(int n0, int count, bool gap, R *rec_base)
     {
         Step3D<R> a{};
         a.rho_t = rho_t;
@@ -1075,12 +1198,12 @@ struct Ctx3D final : fdtd_ctx {
             a.src = src_tab + n;
             a.gap_rec = (gap && Mg) ? gap_hist + (size_t)(n + 1) * 3 * Mg : nullptr;
             a.rec = rec_base ? rec_base + (size_t)(n - n0) * 3 * Mdi : nullptr;
-            launches += launch_step3d<R>(0, geo, F, k, pm, a, stream);
+            launches += launch_step3d<R>(0, geo, F, coef_slot, pm, a, stream);
         }
         cell_updates += (long long)count * ncells;
     }
 
-    void advance_adjoint(const Coef<R> &k, int m_hi, int m_lo, int slot0)
+    void advance_adjoint(int m_hi, int m_lo, int slot0)
     {
         Step3D<R> a{};
         a.rho_t = rho_t;
@@ -1088,52 +1211,50 @@ struct Ctx3D final : fdtd_ctx {
         for (int m = m_hi; m > m_lo; --m) {
             a.gap_src = Mg ? gap_hist + (size_t)m * 3 * Mg : nullptr;
             a.rec = rec + (size_t)(m - 1 - slot0) * 3 * Mdi;
-            launches += launch_step3d<R>(1, geo, A, k, pm, a, stream);
+            launches += launch_step3d<R>(1, geo, A, coef_slot, pm, a, stream);
         }
         cell_updates += (long long)(m_hi - m_lo) * ncells;
     }
 
-    fdtd_status forward(double *d_W) override
+    fdtd_status enqueue_forward()
     {
         cudaStream_t st = stream;
-        const Coef<R> k = coef();
         const int N = cfg.nsteps, K = cfg.snapshot_every;
         launch_zero_bytes(F_base, state_bytes, st);
         if (Mg) launch_zero_bytes(gap_hist, 3 * Mg * sizeof(R), st);
         launches += 2;
         if (K <= 0) {
-            advance_forward(k, 0, N, true, rec);
+            advance_forward(0, N, true, rec);
         } else {
             for (int s = 0; s < nsnap; ++s) {
                 const int n0 = s * K, cnt = std::min(K, N - n0);
                 snapshot_save<R>(cfg.snapshot_dtype, F_base, state_bytes, snaps + (size_t)s * snap_stride, st);
                 ++launches;
-                advance_forward(k, n0, cnt, true, nullptr);
+                advance_forward(n0, cnt, true, nullptr);
             }
         }
         const double coefW = 0.5 * cfg.eps_g * dt * pow(cfg.dx, 3);
-        launch_objective<R>(gap_hist, (long long)(N + 1) * 3 * Mg, coefW, misc, d_W, err, st);
+        launch_objective<R>(gap_hist, (long long)(N + 1) * 3 * Mg, coefW, misc, nullptr, err, st);
         ++launches;
         return check_launch();
     }
 
-    fdtd_status adjoint() override
+    fdtd_status enqueue_adjoint()
     {
         cudaStream_t st = stream;
-        const Coef<R> k = coef();
         const int N = cfg.nsteps, K = cfg.snapshot_every;
         launch_zero_bytes(A_base, state_bytes, st);
         launch_zero_bytes(G, Mdi * sizeof(double), st);
         launches += 2;
         if (K <= 0) {
-            advance_adjoint(k, N, 0, 0);
+            advance_adjoint(N, 0, 0);
         } else {
             for (int s = nsnap - 1; s >= 0; --s) {
                 const int n0 = s * K, n1 = std::min(n0 + K, N);
                 snapshot_load<R>(cfg.snapshot_dtype, snaps + (size_t)s * snap_stride, F_base, state_bytes, st);
                 ++launches;
-                advance_forward(k, n0, n1 - n0, false, rec);
-                advance_adjoint(k, n1, n0, n0);
+                advance_forward(n0, n1 - n0, false, rec);
+                advance_adjoint(n1, n0, n0);
             }
         }
         return check_launch();
@@ -1196,6 +1317,28 @@ const char *fdtd_status_string(fdtd_status s)
     return "unknown status";
 }
 
+// Constant-memory coefficient slots of the live contexts.
+static std::mutex g_slot_mu;
+static bool g_slot_used[COEF_SLOTS];
+
+static int take_slot()
+{
+    std::lock_guard<std::mutex> lk(g_slot_mu);
+    for (int i = 0; i < COEF_SLOTS; ++i)
+        if (!g_slot_used[i]) {
+            g_slot_used[i] = true;
+            return i;
+        }
+    return -1;
+}
+
+static void give_slot(int i)
+{
+    if (i < 0) return;
+    std::lock_guard<std::mutex> lk(g_slot_mu);
+    g_slot_used[i] = false;
+}
+
 static fdtd_ctx *make_ctx(const fdtd_config *cfg)
 {
     fdtd_ctx *c = nullptr;
@@ -1247,6 +1390,11 @@ fdtd_status fdtd_create(const fdtd_config *cfg, void *d_workspace, size_t bytes,
     if (bytes < need) return FDTD_ENOMEM;
     fdtd_ctx *c = make_ctx(cfg);
     if (!c) return FDTD_ENOMEM;
+    c->coef_slot = take_slot();
+    if (c->coef_slot < 0) {
+        delete c;
+        return FDTD_ENOMEM;
+    }
     c->stream = (cudaStream_t)stream;
     c->ws = d_workspace;
 
@@ -1255,6 +1403,7 @@ fdtd_status fdtd_create(const fdtd_config *cfg, void *d_workspace, size_t bytes,
     fdtd_status s = c->carve(cv);
     if (s == FDTD_OK) s = c->upload_tables();
     if (s != FDTD_OK) {
+        give_slot(c->coef_slot);
         delete c;
         return s;
     }
@@ -1481,6 +1630,18 @@ fdtd_status fdtd_get_info(const fdtd_ctx *ctx, fdtd_info *info)
     return FDTD_OK;
 }
 
-void fdtd_destroy(fdtd_ctx *ctx) { delete ctx; }
+void fdtd_destroy(fdtd_ctx *ctx)
+{
+    if (!ctx) return;
+    give_slot(ctx->coef_slot);
+    delete ctx;
+}
+
+fdtd_status fdtd_set_graphs(fdtd_ctx *ctx, int mode)
+{
+    if (!ctx || mode < 0 || mode > 2) return FDTD_EINVAL;
+    ctx->graphs = mode;
+    return FDTD_OK;
+}
 
 }  // extern "C"

@@ -56,6 +56,17 @@ struct Coef {
     R half1pkJ;     // (1 + kJ) / 2
 };
 
+// Constant-memory coefficient slots (one per live context; coef_slots.cuh).
+constexpr int COEF_SLOTS = 128;
+// Write the coefficients of a slot for the step kernels of one translation
+// unit (stream ordered; the host struct may go out of scope on return).
+template <typename R>
+cudaError_t upload_coef_2d(int slot, const Coef<R> &c, cudaStream_t st);
+template <typename R>
+cudaError_t upload_coef_3d(int slot, const Coef<R> &c, cudaStream_t st);
+template <typename R>
+cudaError_t upload_coef_p(int slot, const Coef<R> &c, cudaStream_t st);
+
 // Per-step arguments of the fused step kernel (kernels_2d.cu); the host
 // resolves every per-step offset into a base pointer.
 template <typename R>
@@ -72,7 +83,7 @@ struct Step2D {
 // One fused time step of the whole grid, reading state `in`, writing `out`.
 // mode 0: forward / recompute; 1: adjoint.
 template <typename R>
-int launch_step2d(int mode, const Geo2D &g, const State2D<R> &in, const State2D<R> &out, const Coef<R> &c,
+int launch_step2d(int mode, const Geo2D &g, const State2D<R> &in, const State2D<R> &out, int coef_slot,
                   const Pml1D<R> &px, const Pml1D<R> &py, const Step2D<R> &a, cudaStream_t st);
 
 // Auxiliary kernels (kernels_aux.cu).
@@ -173,19 +184,19 @@ struct StepP {
 
 // H then E half steps of the in-plane 2D grid, in place (two launches).
 template <typename R>
-int launch_stepp(int mode, const GeoP &g, const StateP<R> &s, const Coef<R> &c, const PmlP<R> &pm,
+int launch_stepp(int mode, const GeoP &g, const StateP<R> &s, int coef_slot, const PmlP<R> &pm,
                  const StepP<R> &a, cudaStream_t st);
 
 // H then E half steps of the whole grid, in place (two launches).
 template <typename R>
-int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, const Coef<R> &c, const Pml3D<R> &pm,
+int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, int coef_slot, const Pml3D<R> &pm,
                   const Step3D<R> &a, cudaStream_t st);
 
 // A forward (recompute) step of one state and an adjoint step of another in
 // one launch (independent work; see k_step2d_pair).
 template <typename R>
 int launch_step2d_pair(const Geo2D &g, const State2D<R> &fin, const State2D<R> &fout, const Step2D<R> &fa,
-                       const State2D<R> &ain, const State2D<R> &aout, const Step2D<R> &aa, const Coef<R> &c,
+                       const State2D<R> &ain, const State2D<R> &aout, const Step2D<R> &aa, int coef_slot,
                        const Pml1D<R> &px, const Pml1D<R> &py, cudaStream_t st);
 
 // Compact (dnx x dny) <-> pitched (dny rows of dp, box at column off).

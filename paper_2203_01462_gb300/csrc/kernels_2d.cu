@@ -21,6 +21,7 @@
 // multiple of 4), so that they load as vectors too.  Indices are 32-bit.
 #include <utility>
 
+#include "coef_slots.cuh"
 #include "fdtd_internal.h"
 
 namespace fdtd {
@@ -295,12 +296,12 @@ __device__ __forceinline__ void step2d_body(const Geo2D &g, const State2D<R> &in
 template <typename R, int MODE>
 __global__ void __launch_bounds__(BX *BY, 5)
     k_step2d(const __grid_constant__ Geo2D g, const __grid_constant__ State2D<R> in,
-             const __grid_constant__ State2D<R> out, const __grid_constant__ Coef<R> c,
+             const __grid_constant__ State2D<R> out, int slot,
              const __grid_constant__ Pml1D<R> px, const __grid_constant__ Pml1D<R> py,
              const __grid_constant__ Step2D<R> a)
 {
     wait_previous_grid();
-    step2d_body<R, MODE>(g, in, out, c, px, py, a, blockIdx.x, blockIdx.y);
+    step2d_body<R, MODE>(g, in, out, coef_at<R>(slot), px, py, a, blockIdx.x, blockIdx.y);
 }
 
 // One forward (recompute) step and one adjoint step of independent states in
@@ -311,12 +312,12 @@ __global__ void __launch_bounds__(BX *BY, 5)
     k_step2d_pair(const __grid_constant__ Geo2D g, const __grid_constant__ State2D<R> fin,
                   const __grid_constant__ State2D<R> fout, const __grid_constant__ Step2D<R> fa,
                   const __grid_constant__ State2D<R> ain, const __grid_constant__ State2D<R> aout,
-                  const __grid_constant__ Step2D<R> aa, const __grid_constant__ Coef<R> c,
+                  const __grid_constant__ Step2D<R> aa, int slot,
                   const __grid_constant__ Pml1D<R> px, const __grid_constant__ Pml1D<R> py)
 {
     wait_previous_grid();
-    if (blockIdx.z == 0) step2d_body<R, 0>(g, fin, fout, c, px, py, fa, blockIdx.x, blockIdx.y);
-    else step2d_body<R, 1>(g, ain, aout, c, px, py, aa, blockIdx.x, blockIdx.y);
+    if (blockIdx.z == 0) step2d_body<R, 0>(g, fin, fout, coef_at<R>(slot), px, py, fa, blockIdx.x, blockIdx.y);
+    else step2d_body<R, 1>(g, ain, aout, coef_at<R>(slot), px, py, aa, blockIdx.x, blockIdx.y);
 }
 
 }  // namespace
@@ -339,7 +340,7 @@ void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, 
 }
 
 template <typename R>
-int launch_step2d(int mode, const Geo2D &g, const State2D<R> &in, const State2D<R> &out, const Coef<R> &c,
+int launch_step2d(int mode, const Geo2D &g, const State2D<R> &in, const State2D<R> &out, int c,
                   const Pml1D<R> &px, const Pml1D<R> &py, const Step2D<R> &a, cudaStream_t st)
 {
     dim3 grid((g.nx + TILE_X - 1) / TILE_X, (g.ny + BY - 1) / BY), block(BX, BY);
@@ -350,7 +351,7 @@ int launch_step2d(int mode, const Geo2D &g, const State2D<R> &in, const State2D<
 
 template <typename R>
 int launch_step2d_pair(const Geo2D &g, const State2D<R> &fin, const State2D<R> &fout, const Step2D<R> &fa,
-                       const State2D<R> &ain, const State2D<R> &aout, const Step2D<R> &aa, const Coef<R> &c,
+                       const State2D<R> &ain, const State2D<R> &aout, const Step2D<R> &aa, int c,
                        const Pml1D<R> &px, const Pml1D<R> &py, cudaStream_t st)
 {
     dim3 grid((g.nx + TILE_X - 1) / TILE_X, (g.ny + BY - 1) / BY, 2), block(BX, BY);
@@ -360,17 +361,27 @@ int launch_step2d_pair(const Geo2D &g, const State2D<R> &fin, const State2D<R> &
 
 template int launch_step2d_pair<float>(const Geo2D &, const State2D<float> &, const State2D<float> &,
                                        const Step2D<float> &, const State2D<float> &, const State2D<float> &,
-                                       const Step2D<float> &, const Coef<float> &, const Pml1D<float> &,
+                                       const Step2D<float> &, int, const Pml1D<float> &,
                                        const Pml1D<float> &, cudaStream_t);
 template int launch_step2d_pair<double>(const Geo2D &, const State2D<double> &, const State2D<double> &,
                                         const Step2D<double> &, const State2D<double> &, const State2D<double> &,
-                                        const Step2D<double> &, const Coef<double> &, const Pml1D<double> &,
+                                        const Step2D<double> &, int, const Pml1D<double> &,
                                         const Pml1D<double> &, cudaStream_t);
 template int launch_step2d<float>(int, const Geo2D &, const State2D<float> &, const State2D<float> &,
-                                  const Coef<float> &, const Pml1D<float> &, const Pml1D<float> &,
+                                  int, const Pml1D<float> &, const Pml1D<float> &,
                                   const Step2D<float> &, cudaStream_t);
 template int launch_step2d<double>(int, const Geo2D &, const State2D<double> &, const State2D<double> &,
-                                   const Coef<double> &, const Pml1D<double> &, const Pml1D<double> &,
+                                   int, const Pml1D<double> &, const Pml1D<double> &,
                                    const Step2D<double> &, cudaStream_t);
 
+}  // namespace fdtd
+
+namespace fdtd {
+template <typename R>
+cudaError_t upload_coef_2d(int slot, const Coef<R> &c, cudaStream_t st)
+{
+    return write_coef_slot(slot, c, st);
+}
+template cudaError_t upload_coef_2d<float>(int, const Coef<float> &, cudaStream_t);
+template cudaError_t upload_coef_2d<double>(int, const Coef<double> &, cudaStream_t);
 }  // namespace fdtd

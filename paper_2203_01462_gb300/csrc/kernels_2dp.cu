@@ -15,6 +15,7 @@
 // consecutive entries of a row of each array.
 #include <utility>
 
+#include "coef_slots.cuh"
 #include "fdtd_internal.h"
 
 namespace fdtd {
@@ -37,9 +38,10 @@ __device__ __forceinline__ int slabH(int p, int n, int np)
 }
 
 template <typename R>
-__global__ void __launch_bounds__(BX *BY) k_hp(GeoP g, StateP<R> s, Coef<R> c, PmlP<R> pm)
+__global__ void __launch_bounds__(BX *BY) k_hp(GeoP g, StateP<R> s, int slot, PmlP<R> pm)
 {
     wait_previous_grid();
+    const Coef<R> &c = coef_at<R>(slot);
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     if (i > g.nx - 2 || j > g.ny - 2) return;  // Hz exists on the (nx-1) x (ny-1) cells
     const long long q = (long long)j * g.px + i;
@@ -110,9 +112,10 @@ __device__ __forceinline__ void e_edge(const GeoP &g, const Coef<R> &c, const St
 }
 
 template <typename R, int MODE>
-__global__ void __launch_bounds__(BX *BY) k_ep(GeoP g, StateP<R> s, Coef<R> c, PmlP<R> pm, StepP<R> a)
+__global__ void __launch_bounds__(BX *BY) k_ep(GeoP g, StateP<R> s, int slot, PmlP<R> pm, StepP<R> a)
 {
     wait_previous_grid();
+    const Coef<R> &c = coef_at<R>(slot);
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     if (i >= g.nx || j >= g.ny) return;
     const long long q = (long long)j * g.px + i;
@@ -171,7 +174,7 @@ static void launch_pdl_p(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStre
 }
 
 template <typename R>
-int launch_stepp(int mode, const GeoP &g, const StateP<R> &s, const Coef<R> &c, const PmlP<R> &pm,
+int launch_stepp(int mode, const GeoP &g, const StateP<R> &s, int c, const PmlP<R> &pm,
                  const StepP<R> &a, cudaStream_t st)
 {
     const dim3 block(BX, BY), grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY);
@@ -181,9 +184,19 @@ int launch_stepp(int mode, const GeoP &g, const StateP<R> &s, const Coef<R> &c, 
     return 2;
 }
 
-template int launch_stepp<float>(int, const GeoP &, const StateP<float> &, const Coef<float> &, const PmlP<float> &,
+template int launch_stepp<float>(int, const GeoP &, const StateP<float> &, int, const PmlP<float> &,
                                  const StepP<float> &, cudaStream_t);
-template int launch_stepp<double>(int, const GeoP &, const StateP<double> &, const Coef<double> &,
+template int launch_stepp<double>(int, const GeoP &, const StateP<double> &, int,
                                   const PmlP<double> &, const StepP<double> &, cudaStream_t);
 
+}  // namespace fdtd
+
+namespace fdtd {
+template <typename R>
+cudaError_t upload_coef_p(int slot, const Coef<R> &c, cudaStream_t st)
+{
+    return write_coef_slot(slot, c, st);
+}
+template cudaError_t upload_coef_p<float>(int, const Coef<float> &, cudaStream_t);
+template cudaError_t upload_coef_p<double>(int, const Coef<double> &, cudaStream_t);
 }  // namespace fdtd

@@ -23,6 +23,7 @@
 // three components into the node's FP64 accumulator.
 #include <utility>
 
+#include "coef_slots.cuh"
 #include "fdtd_internal.h"
 
 namespace fdtd {
@@ -167,9 +168,10 @@ __device__ __forceinline__ void cpml_curl(const Geo3D &g, R *const (&psi)[3][2],
 // update; the others add the CPML terms (cpml_curl).
 template <typename R>
 __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 3 : 1)
-    k_h3d(Geo3D g, State3D<R> s, Coef<R> c, Pml3D<R> pm)
+    k_h3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm)
 {
     wait_previous_grid();
+    const Coef<R> &c = coef_at<R>(slot);
     const int i0 = (blockIdx.x * TBX + threadIdx.x) * VX, j = blockIdx.y * TBY + threadIdx.y,
               k = blockIdx.z * TBZ + threadIdx.z;
     const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
@@ -253,9 +255,10 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 3 : 1)
 //   curl_x = dy Hz - dz Hy,  curl_y = dz Hx - dx Hz,  curl_z = dx Hy - dy Hx
 template <typename R, int MODE>
 __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 3 : 1)
-    k_e3d(Geo3D g, State3D<R> s, Coef<R> c, Pml3D<R> pm, Step3D<R> a3)
+    k_e3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm, Step3D<R> a3)
 {
     wait_previous_grid();
+    const Coef<R> &c = coef_at<R>(slot);
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TBY, z0 = blockIdx.z * TBZ;
     const int i0 = x0 + threadIdx.x * VX, j = y0 + threadIdx.y, k = z0 + threadIdx.z;
     const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
@@ -432,7 +435,7 @@ void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, 
 }
 
 template <typename R>
-int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, const Coef<R> &c, const Pml3D<R> &pm,
+int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, int c, const Pml3D<R> &pm,
                   const Step3D<R> &a, cudaStream_t st)
 {
     dim3 vblock(TBX, TBY, TBZ), vgrid((g.n[0] + TX - 1) / TX, (g.n[1] + TBY - 1) / TBY, (g.n[2] + TBZ - 1) / TBZ);
@@ -442,9 +445,19 @@ int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, const Coef<R> &
     return 2;
 }
 
-template int launch_step3d<float>(int, const Geo3D &, const State3D<float> &, const Coef<float> &,
+template int launch_step3d<float>(int, const Geo3D &, const State3D<float> &, int,
                                   const Pml3D<float> &, const Step3D<float> &, cudaStream_t);
-template int launch_step3d<double>(int, const Geo3D &, const State3D<double> &, const Coef<double> &,
+template int launch_step3d<double>(int, const Geo3D &, const State3D<double> &, int,
                                    const Pml3D<double> &, const Step3D<double> &, cudaStream_t);
 
+}  // namespace fdtd
+
+namespace fdtd {
+template <typename R>
+cudaError_t upload_coef_3d(int slot, const Coef<R> &c, cudaStream_t st)
+{
+    return write_coef_slot(slot, c, st);
+}
+template cudaError_t upload_coef_3d<float>(int, const Coef<float> &, cudaStream_t);
+template cudaError_t upload_coef_3d<double>(int, const Coef<double> &, cudaStream_t);
 }  // namespace fdtd
