@@ -218,8 +218,8 @@ def run_surrogate(args) -> None:
     Ws = [x for x in hs.W if x == x]
     line = dict(metric="design iters/s at matched objective", value=len(hs.W) / sur_s, unit="design updates/s",
                 higher_is_better=True, n_gpus=1, data="synthetic",
-                config=dict(workload=I.describe(w), network="U-Net base 24 (%d parameters), FP32"
-                            % I.unet_param_count(24), inner_steps=4, matched="within 1 % of the plain loop's final W"),
+                config=dict(workload=I.describe(w), network="U-Net base 24 (%d parameters), BF16 GEMM operands on the "
+                            "tensor cores, FP32 accumulation and master weights" % I.unet_param_count(24), inner_steps=4, matched="within 1 % of the plain loop's final W"),
                 plain=dict(updates=U, seconds=plain_s, updates_per_s=U / plain_s, final_W=target),
                 surrogate=dict(updates=len(hs.W), seconds=sur_s, final_W=Ws[-1], reached=Ws[-1] >= 0.99 * target,
                                **st),

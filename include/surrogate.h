@@ -28,6 +28,14 @@ extern "C" {
 int nn_gemm(int transA, int transB, int M, int N, int K, float alpha, const float *A, int lda, const float *B, int ldb,
             float beta, float *C, int ldc, void *stream);
 
+/* The same product with BF16 operands on the tensor cores (cuBLAS, a plain
+ * GEMM) and FP32 accumulation and output: A and B (FP32) are rounded to
+ * BF16 (nearest even) into `scratch` (device, at least align256(2 M K) +
+ * 2 K N bytes), then C = alpha op(A16) op(B16) + beta C.  Returns 1 for a
+ * short scratch. */
+int nn_gemm_bf16(int transA, int transB, int M, int N, int K, float alpha, const float *A, int lda, const float *B,
+                 int ldb, float beta, float *C, int ldc, void *scratch, long long scratch_bytes, void *stream);
+
 /* col[(c 9 + t)][(b H + y) W + x] = x[c][b][y + t/3 - 1][x + t%3 - 1], zero
  * outside the image (3 x 3 convolution, stride 1, padding 1). */
 int nn_im2col3(const float *x, int C, int B, int H, int W, float *col, void *stream);

@@ -11,12 +11,28 @@ from __future__ import annotations
 import numpy as np
 
 
-def conv(x, w, b, relu):
+def exact(a):
+    return a
+
+
+def bf16(a):
+    """Round to BF16 (8 significant bits, nearest even) by way of FP32, the
+    storage type of the values a BF16 product is formed from; returned as
+    FP64.  Passed as `rnd` below, it makes every product's operands BF16
+    while sums stay FP64."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64).reshape(np.shape(a))
+
+
+def conv(x, w, b, relu, rnd=exact):
     """Cross-correlation with zero padding (k - 1) / 2, stride 1:
-    y[n, o, i, j] = b[o] + sum_{c, u, v} w[o, c, u, v] x[n, c, i + u - p, j + v - p]."""
+    y[n, o, i, j] = b[o] + sum_{c, u, v} w[o, c, u, v] x[n, c, i + u - p, j + v - p].
+    rnd: applied to both factors of the products (w and x)."""
     k = w.shape[2]
     p = (k - 1) // 2
-    xp = np.pad(x, ((0, 0), (0, 0), (p, p), (p, p)))
+    w = rnd(w)
+    xp = np.pad(rnd(x), ((0, 0), (0, 0), (p, p), (p, p)))
     H, W = x.shape[2], x.shape[3]
     y = np.zeros((x.shape[0], w.shape[0], H, W))
     for u in range(k):
@@ -26,20 +42,22 @@ def conv(x, w, b, relu):
     return np.maximum(y, 0.0) if relu else y
 
 
-def conv_backward(x, w, y, dy, relu):
-    """Gradients of conv() with respect to x, w and b, given dL/dy."""
+def conv_backward(x, w, y, dy, relu, rnd=exact):
+    """Gradients of conv() with respect to x, w and b, given dL/dy; rnd is
+    applied to the factors of every product (dy and x for dw, w and dy for dx)."""
     if relu:
         dy = dy * (y > 0)
     k = w.shape[2]
     p = (k - 1) // 2
     H, W = x.shape[2], x.shape[3]
-    xp = np.pad(x, ((0, 0), (0, 0), (p, p), (p, p)))
+    xp = np.pad(rnd(x), ((0, 0), (0, 0), (p, p), (p, p)))
+    dyr, wr = rnd(dy), rnd(w)
     dxp = np.zeros_like(xp)
     dw = np.zeros_like(w)
     for u in range(k):
         for v in range(k):
-            dw[:, :, u, v] = np.einsum("nohw,nchw->oc", dy, xp[:, :, u:u + H, v:v + W])
-            dxp[:, :, u:u + H, v:v + W] += np.einsum("oc,nohw->nchw", w[:, :, u, v], dy)
+            dw[:, :, u, v] = np.einsum("nohw,nchw->oc", dyr, xp[:, :, u:u + H, v:v + W])
+            dxp[:, :, u:u + H, v:v + W] += np.einsum("oc,nohw->nchw", wr[:, :, u, v], dyr)
     dx = dxp[:, :, p:p + H, p:p + W]
     return dx, dw, dy.sum(axis=(0, 2, 3))
 
@@ -60,13 +78,13 @@ def up_backward(dy):
     return dy[:, :, 0::2, 0::2] + dy[:, :, 1::2, 0::2] + dy[:, :, 0::2, 1::2] + dy[:, :, 1::2, 1::2]
 
 
-def forward(params, x):
+def forward(params, x, rnd=exact):
     """Returns the output and the cache of every layer's input and output."""
     P = params
     cache = {}
 
     def layer(name, inp, relu=True):
-        out = conv(inp, P[name + ".w"], P[name + ".b"], relu)
+        out = conv(inp, P[name + ".w"], P[name + ".b"], relu, rnd)
         cache[name] = (inp, out, relu)
         return out
 
@@ -81,13 +99,13 @@ def forward(params, x):
     return out, cache
 
 
-def backward(params, cache, dout):
+def backward(params, cache, dout, rnd=exact):
     """Gradients of every parameter given dL/dout (same keys as params)."""
     g = {}
 
     def back(name, dy):
         inp, out, relu = cache[name]
-        dx, dw, db = conv_backward(inp, params[name + ".w"], out, dy, relu)
+        dx, dw, db = conv_backward(inp, params[name + ".w"], out, dy, relu, rnd)
         g[name + ".w"], g[name + ".b"] = dw, db
         return dx
 

@@ -6,7 +6,11 @@
 // Activations use the layout [C][B][H][W]: a convolution is the product
 // W[Cout][Cin K K] . col[Cin K K][B H W], and concatenating along channels is
 // placing tensors next to each other in memory.
+#include <cublas_v2.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include "../../include/surrogate.h"
 
@@ -270,6 +274,64 @@ int nn_gemm(int transA, int transB, int M, int N, int K, float alpha, const floa
     else if (!transA && transB) k_gemm<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
     else if (transA && !transB) k_gemm<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
     else k_gemm<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
+    return status(st);
+}
+
+namespace {
+
+// One cuBLAS handle per device, created on first use.
+std::mutex g_blas_mu;
+cublasHandle_t g_blas[64];
+
+cublasHandle_t blas_handle()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_blas_mu);
+    if (!g_blas[dev] && cublasCreate(&g_blas[dev]) != CUBLAS_STATUS_SUCCESS) g_blas[dev] = nullptr;
+    return g_blas[dev];
+}
+
+// dst[r][c] = bf16(src[r][c]) for a rows x cols block with leading dimension
+// ld (round to nearest even); dst is packed (leading dimension cols).
+__global__ void k_to_bf16(const float *src, long long rows, int cols, int ld, __nv_bfloat16 *dst)
+{
+    const long long n = rows * cols;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const long long r = k / cols;
+        const int c = (int)(k % cols);
+        dst[k] = __float2bfloat16_rn(src[r * ld + c]);
+    }
+}
+
+}  // namespace
+
+int nn_gemm_bf16(int transA, int transB, int M, int N, int K, float alpha, const float *A, int lda, const float *B,
+                 int ldb, float beta, float *C, int ldc, void *scratch, long long scratch_bytes, void *stream)
+{
+    if (M < 0 || N < 0 || K < 0 || !C || (K > 0 && (!A || !B))) return 1;
+    if (M == 0 || N == 0) return 0;
+    if (K == 0) return nn_gemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream);
+    const long long na = (long long)M * K, nb = (long long)K * N;
+    const long long offb = (na * 2 + 255) / 256 * 256;
+    if (!scratch || scratch_bytes < offb + nb * 2) return 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    __nv_bfloat16 *a16 = (__nv_bfloat16 *)scratch, *b16 = (__nv_bfloat16 *)((char *)scratch + offb);
+    // packed BF16 copies of A and B as stored (M x K or K x M; K x N or N x K)
+    const long long ar = transA ? K : M, br = transB ? N : K;
+    const int ac = transA ? M : K, bc = transB ? K : N;
+    k_to_bf16<<<blocks_for(na), TPB, 0, st>>>(A, ar, ac, lda, a16);
+    k_to_bf16<<<blocks_for(nb), TPB, 0, st>>>(B, br, bc, ldb, b16);
+    if (cudaGetLastError() != cudaSuccess) return 3;
+    cublasHandle_t h = blas_handle();
+    if (!h || cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return 3;
+    // Row-major C = op(A) op(B) is column-major C^T = op(B)^T op(A)^T, and a
+    // packed row-major operand read column-major is its transpose.
+    const cublasStatus_t r =
+        cublasGemmEx(h, transB ? CUBLAS_OP_T : CUBLAS_OP_N, transA ? CUBLAS_OP_T : CUBLAS_OP_N, N, M, K, &alpha, b16,
+                     CUDA_R_16BF, bc, a16, CUDA_R_16BF, ac, &beta, C, CUDA_R_32F, ldc, CUBLAS_COMPUTE_32F,
+                     CUBLAS_GEMM_DEFAULT);
+    if (r != CUBLAS_STATUS_SUCCESS) return 3;
     return status(st);
 }
 

@@ -3,8 +3,10 @@
 produce, used to take cheap design steps between adjoint runs.
 
 The network runs on the library's own kernels (``include/surrogate.h``):
-im2col + tiled FP32 GEMM convolutions, bias + ReLU, average pooling, nearest
-upsampling, MSE and Adam.  This module only allocates buffers (PyTorch) and
+im2col + GEMM convolutions, bias + ReLU, average pooling, nearest
+upsampling, MSE and Adam.  The GEMMs run either in FP32 on the library's
+tiled kernel (precision "f32") or with BF16 operands on the tensor cores and
+FP32 accumulation (precision "bf16"; FP32 master weights and Adam state).  This module only allocates buffers (PyTorch) and
 sequences kernel calls.  Activations are [C][B][H][W]; a decoder level's
 input is one buffer [upsampled deeper features | skip], and the encoder
 writes its skip straight into the second half.
@@ -34,6 +36,8 @@ _FNS = {
     "nn_adam": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_float, C.c_float, C.c_float,
                 C.c_float, C.c_int, C.c_void_p],
     "nn_zero": [C.c_void_p, C.c_longlong, C.c_void_p],
+    "nn_gemm_bf16": [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_void_p, C.c_int, C.c_void_p,
+                     C.c_int, C.c_float, C.c_void_p, C.c_int, C.c_void_p, C.c_longlong, C.c_void_p],
 }
 EXPORTS = sorted(_FNS)
 _lib = None
@@ -64,9 +68,12 @@ class UNet:
     """The surrogate network for batches of B inputs of H x W (H, W multiples of 8)."""
 
     def __init__(self, base: int = 24, batch: int = 4, H: int = 256, W: int = 256, seed: int = 0,
-                 device="cuda", stream=None, params: dict | None = None):
+                 device="cuda", stream=None, params: dict | None = None, precision: str = "f32"):
         assert H % 8 == 0 and W % 8 == 0
+        if precision not in ("f32", "bf16"):
+            raise ValueError("precision must be 'f32' or 'bf16'")
         self.base, self.B, self.H, self.W = base, batch, H, W
+        self.precision = precision
         self.dev = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.dev)
         self.layers = I.unet_layers(base)
@@ -99,13 +106,17 @@ class UNet:
                         for n, ci, co, k in self.layers)
         self.col = torch.zeros(col_elems, **f32)
         self.dcol = torch.zeros(col_elems, **f32)
+        # BF16 operand copies of the largest GEMM (both operands bounded by
+        # the im2col buffer or the largest activation)
+        big = max(col_elems, max(t.numel() for t in self.a.values()))
+        self.scratch = torch.zeros(4 * big + 512, dtype=torch.uint8, device=self.dev) if precision == "bf16" else None
         self.loss = torch.zeros(1, dtype=torch.float64, device=self.dev)
 
     def sibling(self, batch: int) -> "UNet":
         """A network for another batch size that shares this one's parameter
         tensors (its gradients and Adam state are its own)."""
         twin = UNet(self.base, batch, self.H, self.W, device=self.dev, stream=self.stream,
-                    params=self.numpy_params())
+                    params=self.numpy_params(), precision=self.precision)
         twin.w, twin.b = self.w, self.b
         return twin
 
@@ -137,6 +148,15 @@ class UNet:
     def _st(self):
         return C.c_void_p(self.stream.cuda_stream)
 
+    def _gemm(self, ta, tb, M, N, K, A, lda, B, ldb, beta, Cm, ldc, what):
+        L, st = _nn(), self._st()
+        if self.precision == "bf16":
+            rc = L.nn_gemm_bf16(ta, tb, M, N, K, 1.0, _p(A), lda, _p(B), ldb, beta, _p(Cm), ldc, _p(self.scratch),
+                                self.scratch.numel(), st)
+        else:
+            rc = L.nn_gemm(ta, tb, M, N, K, 1.0, _p(A), lda, _p(B), ldb, beta, _p(Cm), ldc, st)
+        _ck(rc, what)
+
     def _conv_fwd(self, name, ci, co, k, x, y, relu):
         L, st = _nn(), self._st()
         Bhw = x[0].numel()
@@ -145,8 +165,7 @@ class UNet:
             src = self.col
         else:
             src = x
-        _ck(L.nn_gemm(0, 0, co, Bhw, ci * k * k, 1.0, _p(self.w[name]), ci * k * k, _p(src), Bhw, 0.0, _p(y), Bhw, st),
-            "gemm fwd")
+        self._gemm(0, 0, co, Bhw, ci * k * k, self.w[name], ci * k * k, src, Bhw, 0.0, y, Bhw, "gemm fwd")
         _ck(L.nn_bias_act(_p(y), _p(self.b[name]), co, Bhw, int(relu), st), "bias_act")
 
     def _conv_bwd(self, name, ci, co, k, x, y, dy, dx, relu):
@@ -160,15 +179,14 @@ class UNet:
         else:
             src = x
         K = ci * k * k
-        _ck(L.nn_gemm(0, 1, co, K, Bhw, 1.0, _p(dy), Bhw, _p(src), Bhw, 0.0, _p(self.gw[name]), K, st), "gemm wgrad")
+        self._gemm(0, 1, co, K, Bhw, dy, Bhw, src, Bhw, 0.0, self.gw[name], K, "gemm wgrad")
         if dx is None:
             return
         if k == 3:
-            _ck(L.nn_gemm(1, 0, K, Bhw, co, 1.0, _p(self.w[name]), K, _p(dy), Bhw, 0.0, _p(self.dcol), Bhw, st),
-                "gemm dgrad")
+            self._gemm(1, 0, K, Bhw, co, self.w[name], K, dy, Bhw, 0.0, self.dcol, Bhw, "gemm dgrad")
             _ck(L.nn_col2im3_add(_p(self.dcol), ci, self.B, x.shape[2], x.shape[3], _p(dx), st), "col2im")
         else:
-            _ck(L.nn_gemm(1, 0, K, Bhw, co, 1.0, _p(self.w[name]), K, _p(dy), Bhw, 1.0, _p(dx), Bhw, st), "gemm dgrad")
+            self._gemm(1, 0, K, Bhw, co, self.w[name], K, dy, Bhw, 1.0, dx, Bhw, "gemm dgrad")
 
     # ------------------------------------------------------------ network
     def _in_of(self, name: str, store: dict) -> torch.Tensor:

@@ -80,8 +80,9 @@ def collect_pairs(s: Solver, rho0_list, iters: int, move: float = 0.05, sigma_ma
 
 
 class Trainer:
-    def __init__(self, H: int, W: int, base: int = 24, batch: int = 8, seed: int = 0, lr: float = 1e-3):
-        self.net = UNet(base=base, batch=batch, H=H, W=W, seed=seed)
+    def __init__(self, H: int, W: int, base: int = 24, batch: int = 8, seed: int = 0, lr: float = 1e-3,
+                 precision: str = "bf16"):
+        self.net = UNet(base=base, batch=batch, H=H, W=W, seed=seed, precision=precision)
         self.pred = self.net.sibling(1)
         self.batch, self.lr = batch, lr
         self.rng = np.random.default_rng(seed)

@@ -58,3 +58,29 @@ def test_network_gradients_match_central_differences():
 
 def test_param_count_is_about_a_million():
     assert 0.9e6 < I.unet_param_count(24) < 1.3e6
+
+
+def test_bf16_rounding():
+    """Round to nearest even at 8 significant bits: 1 + 2^-8 lies halfway
+    between 1 and 1 + 2^-7 and goes to the even 1; 1 + 3 2^-8 goes to 1 + 2^-6;
+    a value off the halfway point goes to the nearer neighbour; every result
+    has at most 8 significant bits and lies within the unit roundoff 2^-8
+    relative (plus the FP32 step)."""
+    vals = np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8, 1 + 2 ** -8 + 2 ** -12, -(1 + 2 ** -8 + 2 ** -12), 3.0, 0.0])
+    r = U.bf16(vals)
+    assert r.tolist() == [1.0, 1 + 2 ** -6, 1 + 2 ** -7, -(1 + 2 ** -7), 3.0, 0.0]
+    x = np.random.default_rng(3).standard_normal(10000) * 10.0 ** np.random.default_rng(4).uniform(-5, 5, 10000)
+    r = U.bf16(x)
+    assert np.all(np.abs(r - x) <= (2 ** -8 + 2 ** -23) * np.abs(x))  # via FP32: one FP32 rounding more
+    m, _ = np.frexp(r)
+    assert np.all((m * 2 ** 8) == np.round(m * 2 ** 8))
+
+
+def test_bf16_conv_rounds_only_the_factors():
+    """With rnd = bf16 the convolution equals the exact one of the rounded
+    operands (sums stay FP64)."""
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((2, 3, 6, 5))
+    w = rng.standard_normal((4, 3, 3, 3))
+    b = rng.standard_normal(4)
+    np.testing.assert_allclose(U.conv(x, w, b, False, U.bf16), U.conv(U.bf16(x), U.bf16(w), b, False), rtol=1e-14)
