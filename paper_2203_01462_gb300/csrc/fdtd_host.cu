@@ -611,7 +611,7 @@ struct Ctx2D final : fdtd_ctx {
             }
         }
         const double coefW = 0.5 * cfg.eps_g * dt * pow(cfg.dx, cfg.ndim);
-        launch_objective<R>(gap_hist, (long long)(N + 1) * Mg, coefW, misc, nullptr, err, st);
+        launch_objective<R>(gap_hist, (long long)(N + 1) * Mg, coefW, misc, nullptr, misc + 4, err, st);
         ++launches;
         return check_launch();
     }
@@ -966,7 +966,7 @@ struct CtxP final : fdtd_ctx {
             }
         }
         const double coefW = 0.5 * cfg.eps_g * dt * cfg.dx * cfg.dx;
-        launch_objective<R>(gap_hist, (long long)(N + 1) * Mg, coefW, misc, nullptr, err, st);
+        launch_objective<R>(gap_hist, (long long)(N + 1) * Mg, coefW, misc, nullptr, misc + 4, err, st);
         ++launches;
         return check_launch();
     }
@@ -1234,7 +1234,7 @@ struct Ctx3D final : fdtd_ctx {
             }
         }
         const double coefW = 0.5 * cfg.eps_g * dt * pow(cfg.dx, 3);
-        launch_objective<R>(gap_hist, (long long)(N + 1) * 3 * Mg, coefW, misc, nullptr, err, st);
+        launch_objective<R>(gap_hist, (long long)(N + 1) * 3 * Mg, coefW, misc, nullptr, misc + 4, err, st);
         ++launches;
         return check_launch();
     }

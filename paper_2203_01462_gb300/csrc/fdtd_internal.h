@@ -96,8 +96,10 @@ template <typename T>
 void launch_filter_cols(const T *in, T *out, int w, int h, int R_, const T *wts, const T *inv_norm,
                         int transpose, cudaStream_t st);
 template <typename R>
-void launch_objective(const R *gap_hist, long long count, double coef, double *W, double *W_user,
+void launch_objective(const R *gap_hist, long long count, double coef, double *W, double *W_user, double *part,
                       unsigned *err, cudaStream_t st);
+// Blocks of the objective reduction; `part` holds OBJ_BLOCKS doubles.
+constexpr int OBJ_BLOCKS = 152 * 8;
 // ------------------------------------------------------------------ 3D
 
 // Geometry of a 3D Yee grid of n[0] x n[1] x n[2] nodes; rows padded to px

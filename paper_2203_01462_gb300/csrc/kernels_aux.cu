@@ -84,20 +84,36 @@ __device__ __forceinline__ double warp_sum(double v)
 // W~ = coef * sum of squares of the recorded gap field (Eq. 24), FP64
 // accumulation, one block (the history is a few hundred kB at most).
 template <typename R>
-__global__ void __launch_bounds__(1024) k_objective(const R *h, long long count, double coef, double *W,
-                                                    double *W_user, unsigned *err)
+__global__ void __launch_bounds__(256) k_objective_part(const R *h, long long count, double *part)
 {
-    __shared__ double part[32];
+    __shared__ double sh[8];
     double acc = 0.0;
-    for (long long k = threadIdx.x; k < count; k += blockDim.x) {
+    for (long long k = blockIdx.x * 256LL + threadIdx.x; k < count; k += (long long)gridDim.x * 256) {
         const double v = (double)h[k];
         acc += v * v;
     }
     acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x < 32) {
-        double v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+        double v = threadIdx.x < 8 ? sh[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) part[blockIdx.x] = v;
+    }
+}
+
+// W = coef * (sum of the block partials, in a fixed order).
+__global__ void __launch_bounds__(256) k_objective_final(const double *part, int nb, double coef, double *W,
+                                                         double *W_user, unsigned *err)
+{
+    __shared__ double sh[8];
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < nb; k += 256) acc += part[k];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < 8 ? sh[threadIdx.x] : 0.0;
         v = warp_sum(v);
         if (threadIdx.x == 0) {
             const double w = coef * v;
@@ -269,11 +285,17 @@ void launch_filter_cols(const T *in, T *out, int w, int h, int R_, const T *wts,
     k_filter_cols<T><<<blocks_for((long long)w * h), TPB, 0, st>>>(in, out, w, h, R_, wts, inv_norm, transpose);
 }
 
+// W~ of Eq. (24) from the recorded gap history: block partial sums of E^2
+// in FP64 (the grid size depends only on count, so the sum is
+// deterministic), then one block adds them in order and scales by coef.
 template <typename R>
-void launch_objective(const R *gap_hist, long long count, double coef, double *W, double *W_user,
+void launch_objective(const R *gap_hist, long long count, double coef, double *W, double *W_user, double *part,
                       unsigned *err, cudaStream_t st)
 {
-    k_objective<R><<<1, 1024, 0, st>>>(gap_hist, count, coef, W, W_user, err);
+    long long nb = (count + 4 * 256 - 1) / (4 * 256);
+    nb = nb < 1 ? 1 : (nb > OBJ_BLOCKS ? OBJ_BLOCKS : nb);
+    k_objective_part<R><<<(int)nb, 256, 0, st>>>(gap_hist, count, part);
+    k_objective_final<<<1, 256, 0, st>>>(part, (int)nb, coef, W, W_user, err);
 }
 
 void launch_assemble_2d(const double *G, double *out, int dnx, int dny, int off, int dp, int gx0, int gy0,
@@ -377,10 +399,10 @@ template void launch_filter_cols<float>(const float *, float *, int, int, int, c
                                         cudaStream_t);
 template void launch_filter_cols<double>(const double *, double *, int, int, int, const double *, const double *,
                                          int, cudaStream_t);
-template void launch_objective<float>(const float *, long long, double, double *, double *, unsigned *,
-                                      cudaStream_t);
-template void launch_objective<double>(const double *, long long, double, double *, double *, unsigned *,
-                                       cudaStream_t);
+template void launch_objective<float>(const float *, long long, double, double *, double *, double *,
+                                      unsigned *, cudaStream_t);
+template void launch_objective<double>(const double *, long long, double, double *, double *, double *,
+                                       unsigned *, cudaStream_t);
 template void launch_pitch2d<float>(const float *, float *, int, int, int, int, cudaStream_t);
 template void launch_pitch2d<double>(const double *, double *, int, int, int, int, cudaStream_t);
 template void launch_gap_dft<float>(const float *, long long, int, double, const double *, int, double *,
