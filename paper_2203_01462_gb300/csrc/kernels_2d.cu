@@ -19,10 +19,10 @@
 // run a scalar path with CPML.  The design-box arrays (J, rho~, records, G) use the library's
 // pitched layout: column origin dxa (a multiple of 4) and row pitch dp (a
 // multiple of 4), so that they load as vectors too.  Indices are 32-bit.
-#include <utility>
 
 #include "coef_slots.cuh"
 #include "fdtd_internal.h"
+#include "launch.cuh"
 
 namespace fdtd {
 
@@ -321,23 +321,6 @@ __global__ void __launch_bounds__(BX *BY, 5)
 }
 
 }  // namespace
-
-// Launch with programmatic stream serialisation (see wait_previous_grid).
-template <typename... KArgs, typename... Args>
-void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args &&...args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
-}
 
 template <typename R>
 int launch_step2d(int mode, const Geo2D &g, const State2D<R> &in, const State2D<R> &out, int c,

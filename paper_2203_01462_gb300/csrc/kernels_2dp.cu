@@ -13,10 +13,10 @@
 //
 // One thread per (i, j), 32 x 8 threads per block: a warp reads 32
 // consecutive entries of a row of each array.
-#include <utility>
 
 #include "coef_slots.cuh"
 #include "fdtd_internal.h"
+#include "launch.cuh"
 
 namespace fdtd {
 
@@ -158,29 +158,14 @@ __global__ void __launch_bounds__(BX *BY) k_ep(GeoP g, StateP<R> s, int slot, Pm
 
 }  // namespace
 
-template <typename... KArgs, typename... Args>
-static void launch_pdl_p(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args &&...args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
-}
-
 template <typename R>
 int launch_stepp(int mode, const GeoP &g, const StateP<R> &s, int c, const PmlP<R> &pm,
                  const StepP<R> &a, cudaStream_t st)
 {
     const dim3 block(BX, BY), grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY);
-    launch_pdl_p(k_hp<R>, grid, block, st, g, s, c, pm);
-    if (mode == 0) launch_pdl_p(k_ep<R, 0>, grid, block, st, g, s, c, pm, a);
-    else launch_pdl_p(k_ep<R, 1>, grid, block, st, g, s, c, pm, a);
+    launch_pdl(k_hp<R>, grid, block, st, g, s, c, pm);
+    if (mode == 0) launch_pdl(k_ep<R, 0>, grid, block, st, g, s, c, pm, a);
+    else launch_pdl(k_ep<R, 1>, grid, block, st, g, s, c, pm, a);
     return 2;
 }
 

@@ -21,10 +21,10 @@
 // Every E component of a node inside the design box takes the material of
 // rho~ at that node (Eq. 5); the adjoint sums the Eq. (25) brackets of the
 // three components into the node's FP64 accumulator.
-#include <utility>
 
 #include "coef_slots.cuh"
 #include "fdtd_internal.h"
+#include "launch.cuh"
 
 namespace fdtd {
 
@@ -418,21 +418,6 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 3 : 1)
 }
 
 }  // namespace
-
-template <typename... KArgs, typename... Args>
-void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args &&...args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
-}
 
 template <typename R>
 int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, int c, const Pml3D<R> &pm,
