@@ -304,6 +304,17 @@ fdtd_status fdtd_threshold(fdtd_ctx *ctx, void *d_rho, size_t n, double level);
  * mode.  A context holds at most one graph per pass kind. */
 fdtd_status fdtd_set_graphs(fdtd_ctx *ctx, int mode);
 
+/* L2 residency of the time-stepping state (2D E_z-out-of-plane contexts; a
+ * no-op for the others).  fraction in (0, 1]: sets aside fraction x (the
+ * bytes of one ping-pong pair of states) of L2 for persisting accesses
+ * (cudaLimitPersistingL2CacheSize, bounded by the device maximum; a limit of
+ * this process that applies to every context on the device) and marks the
+ * forward and the adjoint pair, through an access-policy window on each step
+ * launch, persisting in that share and streaming elsewhere, so that part of
+ * the state stays in L2 from one step to the next.  0 turns the windows off
+ * (the set-aside stays).  Results are unchanged.  Default: off. */
+fdtd_status fdtd_set_l2_residency(fdtd_ctx *ctx, double fraction);
+
 /* Wait for the context's stream and report (then clear) device-side errors:
  * FDTD_ERANGE, FDTD_EUNSTABLE, or FDTD_ECUDA for a failed kernel. */
 fdtd_status fdtd_sync(fdtd_ctx *ctx);

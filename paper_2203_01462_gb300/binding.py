@@ -26,7 +26,8 @@ EXPORTS = ["fdtd_workspace_bytes", "fdtd_create", "fdtd_set_design", "fdtd_set_d
            "fdtd_forward", "fdtd_adjoint", "fdtd_gradient", "fdtd_gap_history", "fdtd_sync",
            "fdtd_run_host", "fdtd_get_info", "fdtd_status_string", "fdtd_destroy",
            "fdtd_gradient_static", "fdtd_gap_spectrum", "fdtd_ascent_step", "fdtd_mma_asymptotes", "fdtd_mma_solve",
-           "fdtd_mirror_average", "fdtd_fix_design", "fdtd_grayness", "fdtd_threshold", "fdtd_set_graphs"]
+           "fdtd_mirror_average", "fdtd_fix_design", "fdtd_grayness", "fdtd_threshold", "fdtd_set_graphs",
+           "fdtd_set_l2_residency"]
 
 
 class FdtdError(RuntimeError):
@@ -94,6 +95,7 @@ def load():
             "fdtd_fix_design": [P, P, P, P, C.c_size_t, C.c_double],
             "fdtd_grayness": [P, P],
             "fdtd_set_graphs": [P, C.c_int],
+            "fdtd_set_l2_residency": [P, C.c_double],
             "fdtd_threshold": [P, P, C.c_size_t, C.c_double],
             "fdtd_gap_history": [P, P, C.c_size_t],
             "fdtd_sync": [P],
@@ -252,6 +254,10 @@ class Solver:
                                           C.c_void_p(out.data_ptr())), "fdtd_gap_spectrum")
         z = t.view_as_complex(out.reshape(-1, 2))
         return z.reshape((f.numel(), 3, self.n_gap) if nc == 3 else (f.numel(), self.n_gap))
+
+    def set_l2_residency(self, fraction: float) -> None:
+        """Keep ``fraction`` of the ping-pong state persisting in L2 (2D E_z mode; 0: off)."""
+        _check(self.lib.fdtd_set_l2_residency(self.ctx, float(fraction)), "fdtd_set_l2_residency")
 
     def set_graphs(self, mode: int) -> None:
         """0: plain launches, 1: replay CUDA graphs of whole passes, 2: automatic by grid size."""

@@ -202,6 +202,8 @@ struct fdtd_ctx {
     virtual fdtd_status gradient_scratch(double *d_grad, double *s1, double *s2) = 0;
     // Optimization-loop helpers.
     virtual fdtd_status grayness(double *d_zeta) = 0;
+    // L2 residency of the ping-pong state (2D E_z contexts; others ignore it).
+    virtual fdtd_status set_l2(double) { return FDTD_OK; }
     long long n_free = 0;  // design nodes outside the gap
     virtual void *rho_stage() = 0;
     virtual double *grad_stage() = 0;
@@ -369,6 +371,45 @@ struct Ctx2D final : fdtd_ctx {
     State2D<R> F[2]{}, A[2]{};  // ping-pong pairs: forward and adjoint
     char *F_base[2] = {nullptr, nullptr}, *A_base[2] = {nullptr, nullptr};
     int curF = 0, curA = 0;
+    // Optional L2 residency of the ping-pong pairs (fdtd_set_l2_residency).
+    cudaAccessPolicyWindow win[2] = {};
+    bool l2 = false;
+    const cudaAccessPolicyWindow *winF() const { return l2 ? &win[0] : nullptr; }
+    const cudaAccessPolicyWindow *winA() const { return l2 && l2_adjoint ? &win[1] : nullptr; }
+    bool l2_adjoint = false;
+    fdtd_status set_l2(double fraction) override
+    {
+        for (auto &g : cap)
+            if (g.exec) {
+                cudaGraphExecDestroy(g.exec);
+                g.exec = nullptr;
+            }
+        if (!(fraction > 0)) {
+            // release the set-aside: reserved but unused L2 slows every other access
+            if (l2) FDTD_TRY(cuda_ok(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, 0)));
+            l2 = false;
+            return FDTD_OK;
+        }
+        int dev = 0, max_persist = 0, max_window = 0;
+        FDTD_TRY(cuda_ok(cudaGetDevice(&dev)));
+        FDTD_TRY(cuda_ok(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev)));
+        FDTD_TRY(cuda_ok(cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev)));
+        if (max_persist <= 0 || max_window <= 0) return FDTD_EINVAL;
+        const double pair = 2.0 * (double)state_bytes;
+        const size_t aside = (size_t)std::min((double)max_persist, fraction * pair);
+        FDTD_TRY(cuda_ok(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, aside)));
+        const size_t bytes = (size_t)std::min(pair, (double)max_window);
+        char *base[2] = {F_base[0], A_base[0]};
+        for (int k = 0; k < 2; ++k) {
+            win[k].base_ptr = base[k];
+            win[k].num_bytes = bytes;
+            win[k].hitRatio = (float)std::min(1.0, (double)aside / (double)bytes);
+            win[k].hitProp = cudaAccessPropertyPersisting;
+            win[k].missProp = cudaAccessPropertyStreaming;
+        }
+        l2 = true;
+        return FDTD_OK;
+    }
     size_t state_bytes = 0;
     long long Mdi = 0;  // pitched design-box elements (dny x dp)
     R *rho = nullptr, *rhof = nullptr, *rho_t = nullptr, *ftmp = nullptr, *rstage = nullptr;
@@ -563,7 +604,7 @@ struct Ctx2D final : fdtd_ctx {
             a.src = src_tab + n;
             a.gap_rec = (gap && Mg) ? gap_hist + (size_t)(n + 1) * Mg : nullptr;
             a.rec = rec_base ? rec_base + (size_t)(n - n0) * Mdi : nullptr;
-            launches += launch_step2d<R>(0, geo, F[curF], F[curF ^ 1], coef_slot, px, py, a, stream);
+            launches += launch_step2d<R>(0, geo, F[curF], F[curF ^ 1], coef_slot, px, py, a, stream, winF());
             curF ^= 1;
         }
         cell_updates += (long long)count * ncells;
@@ -579,7 +620,7 @@ struct Ctx2D final : fdtd_ctx {
         for (int m = m_hi; m > m_lo; --m) {
             a.gap_src = Mg ? gap_hist + (size_t)m * Mg : nullptr;
             a.rec = base + (size_t)(m - 1 - slot0) * Mdi;
-            launches += launch_step2d<R>(1, geo, A[curA], A[curA ^ 1], coef_slot, px, py, a, stream);
+            launches += launch_step2d<R>(1, geo, A[curA], A[curA ^ 1], coef_slot, px, py, a, stream, winA());
             curA ^= 1;
         }
         cell_updates += (long long)(m_hi - m_lo) * ncells;
@@ -657,7 +698,7 @@ struct Ctx2D final : fdtd_ctx {
                 aa.gap_src = Mg ? gap_hist + (size_t)m * Mg : nullptr;
                 aa.rec = buf(s) + (size_t)(m - 1 - a_lo) * Mdi;
                 launches += launch_step2d_pair<R>(geo, F[curF], F[curF ^ 1], fa, A[curA], A[curA ^ 1], aa, coef_slot, px,
-                                                  py, stream);
+                                                  py, stream, winA());
                 curF ^= 1;
                 curA ^= 1;
             }
@@ -1635,6 +1676,12 @@ void fdtd_destroy(fdtd_ctx *ctx)
     if (!ctx) return;
     give_slot(ctx->coef_slot);
     delete ctx;
+}
+
+fdtd_status fdtd_set_l2_residency(fdtd_ctx *ctx, double fraction)
+{
+    if (!ctx || !(fraction >= 0.0 && fraction <= 1.0)) return FDTD_EINVAL;
+    return ctx->set_l2(fraction);
 }
 
 fdtd_status fdtd_set_graphs(fdtd_ctx *ctx, int mode)

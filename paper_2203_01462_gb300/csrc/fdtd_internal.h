@@ -84,7 +84,7 @@ struct Step2D {
 // mode 0: forward / recompute; 1: adjoint.
 template <typename R>
 int launch_step2d(int mode, const Geo2D &g, const State2D<R> &in, const State2D<R> &out, int coef_slot,
-                  const Pml1D<R> &px, const Pml1D<R> &py, const Step2D<R> &a, cudaStream_t st);
+                  const Pml1D<R> &px, const Pml1D<R> &py, const Step2D<R> &a, cudaStream_t st, const cudaAccessPolicyWindow *win);
 
 // Auxiliary kernels (kernels_aux.cu).
 template <typename R>
@@ -199,7 +199,7 @@ int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, int coef_slot, 
 template <typename R>
 int launch_step2d_pair(const Geo2D &g, const State2D<R> &fin, const State2D<R> &fout, const Step2D<R> &fa,
                        const State2D<R> &ain, const State2D<R> &aout, const Step2D<R> &aa, int coef_slot,
-                       const Pml1D<R> &px, const Pml1D<R> &py, cudaStream_t st);
+                       const Pml1D<R> &px, const Pml1D<R> &py, cudaStream_t st, const cudaAccessPolicyWindow *win);
 
 // Compact (dnx x dny) <-> pitched (dny rows of dp, box at column off).
 template <typename T>

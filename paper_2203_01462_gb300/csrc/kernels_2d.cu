@@ -324,38 +324,39 @@ __global__ void __launch_bounds__(BX *BY, 5)
 
 template <typename R>
 int launch_step2d(int mode, const Geo2D &g, const State2D<R> &in, const State2D<R> &out, int c,
-                  const Pml1D<R> &px, const Pml1D<R> &py, const Step2D<R> &a, cudaStream_t st)
+                  const Pml1D<R> &px, const Pml1D<R> &py, const Step2D<R> &a, cudaStream_t st,
+                  const cudaAccessPolicyWindow *win)
 {
     dim3 grid((g.nx + TILE_X - 1) / TILE_X, (g.ny + BY - 1) / BY), block(BX, BY);
-    if (mode == 0) launch_pdl(k_step2d<R, 0>, grid, block, st, g, in, out, c, px, py, a);
-    else launch_pdl(k_step2d<R, 1>, grid, block, st, g, in, out, c, px, py, a);
+    if (mode == 0) launch_pdl_win(k_step2d<R, 0>, grid, block, st, win, g, in, out, c, px, py, a);
+    else launch_pdl_win(k_step2d<R, 1>, grid, block, st, win, g, in, out, c, px, py, a);
     return 1;
 }
 
 template <typename R>
 int launch_step2d_pair(const Geo2D &g, const State2D<R> &fin, const State2D<R> &fout, const Step2D<R> &fa,
                        const State2D<R> &ain, const State2D<R> &aout, const Step2D<R> &aa, int c,
-                       const Pml1D<R> &px, const Pml1D<R> &py, cudaStream_t st)
+                       const Pml1D<R> &px, const Pml1D<R> &py, cudaStream_t st, const cudaAccessPolicyWindow *win)
 {
     dim3 grid((g.nx + TILE_X - 1) / TILE_X, (g.ny + BY - 1) / BY, 2), block(BX, BY);
-    launch_pdl(k_step2d_pair<R>, grid, block, st, g, fin, fout, fa, ain, aout, aa, c, px, py);
+    launch_pdl_win(k_step2d_pair<R>, grid, block, st, win, g, fin, fout, fa, ain, aout, aa, c, px, py);
     return 1;
 }
 
 template int launch_step2d_pair<float>(const Geo2D &, const State2D<float> &, const State2D<float> &,
                                        const Step2D<float> &, const State2D<float> &, const State2D<float> &,
                                        const Step2D<float> &, int, const Pml1D<float> &,
-                                       const Pml1D<float> &, cudaStream_t);
+                                       const Pml1D<float> &, cudaStream_t, const cudaAccessPolicyWindow *);
 template int launch_step2d_pair<double>(const Geo2D &, const State2D<double> &, const State2D<double> &,
                                         const Step2D<double> &, const State2D<double> &, const State2D<double> &,
                                         const Step2D<double> &, int, const Pml1D<double> &,
-                                        const Pml1D<double> &, cudaStream_t);
+                                        const Pml1D<double> &, cudaStream_t, const cudaAccessPolicyWindow *);
 template int launch_step2d<float>(int, const Geo2D &, const State2D<float> &, const State2D<float> &,
                                   int, const Pml1D<float> &, const Pml1D<float> &,
-                                  const Step2D<float> &, cudaStream_t);
+                                  const Step2D<float> &, cudaStream_t, const cudaAccessPolicyWindow *);
 template int launch_step2d<double>(int, const Geo2D &, const State2D<double> &, const State2D<double> &,
                                    int, const Pml1D<double> &, const Pml1D<double> &,
-                                   const Step2D<double> &, cudaStream_t);
+                                   const Step2D<double> &, cudaStream_t, const cudaAccessPolicyWindow *);
 
 }  // namespace fdtd
 

@@ -38,3 +38,23 @@ def test_graph_replay_is_bit_identical(mode):
         assert np.array_equal(gp.cpu().numpy(), gg.cpu().numpy())
     ip, ig = plain.info(), graph.info()
     assert ip.launches == ig.launches and ip.cell_updates == ig.cell_updates
+
+
+def test_l2_residency_changes_nothing():
+    """The L2 access-policy windows change where the state is cached, not what
+    is computed: W and the gradient are bit-identical with and without."""
+    from paper_2203_01462_gb300.binding import Solver
+    w = _modes()["tmz"]
+    plain, held = Solver(w), Solver(w)
+    held.set_l2_residency(0.3)
+    try:
+        for seed in (4, 5):
+            rho = I.rho_uniform(w, seed)
+            Wp, gp = plain.evaluate(rho, 2e5, 2.0)
+            Wh, gh = held.evaluate(rho, 2e5, 2.0)
+            plain.sync()
+            held.sync()
+            assert float(Wp.item()) == float(Wh.item())
+            assert np.array_equal(gp.cpu().numpy(), gh.cpu().numpy())
+    finally:
+        held.set_l2_residency(0.0)  # release the set-aside for the tests that follow
