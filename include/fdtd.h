@@ -309,9 +309,9 @@ fdtd_status fdtd_set_graphs(fdtd_ctx *ctx, int mode);
  * bytes of one ping-pong pair of states) of L2 for persisting accesses
  * (cudaLimitPersistingL2CacheSize, bounded by the device maximum; a limit of
  * this process that applies to every context on the device) and marks the
- * forward and the adjoint pair, through an access-policy window on each step
- * launch, persisting in that share and streaming elsewhere, so that part of
- * the state stays in L2 from one step to the next.  0 turns the windows off
+ * forward pair, through an access-policy window on each forward and
+ * recompute launch, persisting in that share and streaming elsewhere, so
+ * that part of the state stays in L2 from one step to the next.  0 turns the windows off
  * (the set-aside stays).  Results are unchanged.  Default: off. */
 fdtd_status fdtd_set_l2_residency(fdtd_ctx *ctx, double fraction);
 

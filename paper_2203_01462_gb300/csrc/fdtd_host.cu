@@ -371,12 +371,12 @@ struct Ctx2D final : fdtd_ctx {
     State2D<R> F[2]{}, A[2]{};  // ping-pong pairs: forward and adjoint
     char *F_base[2] = {nullptr, nullptr}, *A_base[2] = {nullptr, nullptr};
     int curF = 0, curA = 0;
-    // Optional L2 residency of the ping-pong pairs (fdtd_set_l2_residency).
-    cudaAccessPolicyWindow win[2] = {};
+    // Optional L2 residency of the forward ping-pong pair (fdtd_set_l2_residency).
+    // The window goes on the forward and recompute launches only: on the
+    // adjoint or the paired launches it measured slower.
+    cudaAccessPolicyWindow win = {};
     bool l2 = false;
-    const cudaAccessPolicyWindow *winF() const { return l2 ? &win[0] : nullptr; }
-    const cudaAccessPolicyWindow *winA() const { return l2 && l2_adjoint ? &win[1] : nullptr; }
-    bool l2_adjoint = false;
+    const cudaAccessPolicyWindow *winF() const { return l2 ? &win : nullptr; }
     fdtd_status set_l2(double fraction) override
     {
         for (auto &g : cap)
@@ -399,14 +399,11 @@ struct Ctx2D final : fdtd_ctx {
         const size_t aside = (size_t)std::min((double)max_persist, fraction * pair);
         FDTD_TRY(cuda_ok(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, aside)));
         const size_t bytes = (size_t)std::min(pair, (double)max_window);
-        char *base[2] = {F_base[0], A_base[0]};
-        for (int k = 0; k < 2; ++k) {
-            win[k].base_ptr = base[k];
-            win[k].num_bytes = bytes;
-            win[k].hitRatio = (float)std::min(1.0, (double)aside / (double)bytes);
-            win[k].hitProp = cudaAccessPropertyPersisting;
-            win[k].missProp = cudaAccessPropertyStreaming;
-        }
+        win.base_ptr = F_base[0];  // F[0] and F[1] are carved back to back
+        win.num_bytes = bytes;
+        win.hitRatio = (float)std::min(1.0, (double)aside / (double)bytes);
+        win.hitProp = cudaAccessPropertyPersisting;
+        win.missProp = cudaAccessPropertyStreaming;
         l2 = true;
         return FDTD_OK;
     }
@@ -620,7 +617,7 @@ struct Ctx2D final : fdtd_ctx {
         for (int m = m_hi; m > m_lo; --m) {
             a.gap_src = Mg ? gap_hist + (size_t)m * Mg : nullptr;
             a.rec = base + (size_t)(m - 1 - slot0) * Mdi;
-            launches += launch_step2d<R>(1, geo, A[curA], A[curA ^ 1], coef_slot, px, py, a, stream, winA());
+            launches += launch_step2d<R>(1, geo, A[curA], A[curA ^ 1], coef_slot, px, py, a, stream, nullptr);
             curA ^= 1;
         }
         cell_updates += (long long)(m_hi - m_lo) * ncells;
@@ -698,7 +695,7 @@ struct Ctx2D final : fdtd_ctx {
                 aa.gap_src = Mg ? gap_hist + (size_t)m * Mg : nullptr;
                 aa.rec = buf(s) + (size_t)(m - 1 - a_lo) * Mdi;
                 launches += launch_step2d_pair<R>(geo, F[curF], F[curF ^ 1], fa, A[curA], A[curA ^ 1], aa, coef_slot, px,
-                                                  py, stream, winA());
+                                                  py, stream, nullptr);
                 curF ^= 1;
                 curA ^= 1;
             }
