@@ -67,6 +67,9 @@ typedef enum fdtd_status {
  * (lossy: the recomputed forward fields, hence the gradient, carry the
  * rounding of the restart). */
 enum { FDTD_SNAP_F32 = 0, FDTD_SNAP_BF16 = 1, FDTD_SNAP_F16 = 2 };
+/* Sensitivity accumulator: FDTD_ACC_F64 (one FP64 sum per design node).
+ * FDTD_ACC_COMP_F32 (a compensated FP32 pair) is reserved and rejected with
+ * FDTD_EINVAL: it would move the same 16 bytes per node and step. */
 enum { FDTD_ACC_F64 = 0, FDTD_ACC_COMP_F32 = 1 };
 enum { FDTD_SIGMA_PAPER = 0, FDTD_SIGMA_PEAK_NORMALISED = 1 };
 
