@@ -70,3 +70,16 @@ def test_bad_configurations_rejected(bad):
     with pytest.raises(B.FdtdError) as e:
         B.workspace_bytes(w)
     assert e.value.status == 1
+
+
+def test_grid_beyond_32_bit_indexing_rejected():
+    """The 2D step kernel indexes one array with 32-bit integers: a grid of
+    2^31 or more padded nodes is refused before anything is allocated."""
+    w = I.small_2d()
+    w.update(nx=65536, ny=40000, npml=10, design_lo=[100, 100, 0], design_hi=[200, 200, 1],
+             gap_lo=[140, 140, 0], gap_hi=[143, 143, 1], src_lo=[10, 15, 0], src_hi=[65526, 16, 1])
+    with pytest.raises(B.FdtdError) as e:
+        B.workspace_bytes(w)
+    assert e.value.status == 1
+    w.update(ny=30000)  # 1.97e9 nodes: accepted
+    assert B.workspace_bytes(w) > 0
