@@ -168,7 +168,9 @@ def run_reference(args, w) -> None:
         times.append(time.perf_counter() - t)
     cu = 2.0 * I.n_cells(w) * ns
     value = cu * len(times) / sum(times) / 1e9
-    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=0, steps=args.steps,
+    # the oracle runs on the host cores; n_gpus repeats the launch's N so the
+    # line matches the accelerated arm it is compared with
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1e3 * sum(times) / len(times), higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                 config=dict(workload=I.describe(w), grid=I.grid_shape(w), nsteps=w["nsteps"],
