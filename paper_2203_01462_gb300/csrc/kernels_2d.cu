@@ -7,8 +7,9 @@
 // state word crosses HBM once per step (24 B per vacuum node).
 //
 // Each thread owns four adjacent nodes of one row (16-byte vector loads and
-// stores; rows are padded to 32 nodes), 32 x 8 threads per block, i.e. a
-// 128 x 8 node tile.  A thread computes the new Hx and Hy of its nodes and,
+// stores; rows are padded to 32 nodes), 32 x 4 threads per block, i.e. a
+// 128 x 4 node tile, up to 10 blocks per SM (a block-shape sweep on the
+// 2048^2 workload: 128 x 4 beat 128 x 8, 128 x 16 and 128 x 2).  A thread computes the new Hx and Hy of its nodes and,
 // in registers, the new Hy left of its first node and the new Hx below its
 // nodes, which its E updates need: 6 vector and 3 scalar loads per 4 nodes,
 // neighbour rows served by L1, no exchange between threads and no barrier.
@@ -28,7 +29,7 @@ namespace fdtd {
 
 namespace {
 
-constexpr int BX = 32, BY = 8, VX = 4;
+constexpr int BX = 32, BY = 4, VX = 4;
 constexpr int TILE_X = BX * VX;
 
 __device__ __forceinline__ bool in_range(int v, int lo, int n) { return (unsigned)(v - lo) < (unsigned)n; }
@@ -294,7 +295,7 @@ __device__ __forceinline__ void step2d_body(const Geo2D &g, const State2D<R> &in
 }
 
 template <typename R, int MODE>
-__global__ void __launch_bounds__(BX *BY, 5)
+__global__ void __launch_bounds__(BX *BY, 10)
     k_step2d(const __grid_constant__ Geo2D g, const __grid_constant__ State2D<R> in,
              const __grid_constant__ State2D<R> out, int slot,
              const __grid_constant__ Pml1D<R> px, const __grid_constant__ Pml1D<R> py,
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(BX *BY, 5)
 // one launch: blocks with blockIdx.z == 0 advance the forward state, those
 // with blockIdx.z == 1 the adjoint state.
 template <typename R>
-__global__ void __launch_bounds__(BX *BY, 5)
+__global__ void __launch_bounds__(BX *BY, 10)
     k_step2d_pair(const __grid_constant__ Geo2D g, const __grid_constant__ State2D<R> fin,
                   const __grid_constant__ State2D<R> fout, const __grid_constant__ Step2D<R> fa,
                   const __grid_constant__ State2D<R> ain, const __grid_constant__ State2D<R> aout,
