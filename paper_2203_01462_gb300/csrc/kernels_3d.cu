@@ -8,7 +8,7 @@
 // Eq. (10a,b) per component (J and sigma E averaged over the step, scaled
 // units, see Coef).  Curl component c uses the cyclic axes a = c+1, b = c+2:
 // curl_c = d_a F_b - d_b F_a, each derivative with its own CPML term in the
-// slab of its axis.  Each thread owns four x-adjacent nodes (32 x 8 x 4-node
+// slab of its axis.  Each thread owns four x-adjacent nodes (32 x 8 x 2-node
 // blocks) and runs one vector code path everywhere: next to the PEC walls
 // it skips the neighbour loads that fall outside the grid and masks the
 // components that are not updated there (H_c exists where p <= n-2 along
@@ -30,9 +30,11 @@ namespace fdtd {
 
 namespace {
 
-// Tiles: 8 x 8 x 4 threads, four x-adjacent nodes each, i.e.
-// 32 x 8 x 4 nodes (a warp reads 128 contiguous bytes per row).
-constexpr int VX = 4, TBX = 8, TBY = 8, TBZ = 4;
+// Tiles: 8 x 8 x 2 threads, four x-adjacent nodes each, i.e.
+// 32 x 8 x 2 nodes (a warp reads 128 contiguous bytes per row), up to 6
+// blocks per SM in FP32 (a sweep of 8x8x4 at 3 / 8x8x2 at 6 / 4x8x4 at 6 /
+// 8x4x2 at 12 per SM: 8x8x2 and 4x8x4 were fastest, by 3-5 %).
+constexpr int VX = 4, TBX = 8, TBY = 8, TBZ = 2;
 constexpr int TX = TBX * VX;
 
 __device__ __forceinline__ bool in_range(int v, int lo, int n) { return (unsigned)(v - lo) < (unsigned)n; }
@@ -167,7 +169,7 @@ __device__ __forceinline__ void cpml_curl(const Geo3D &g, R *const (&psi)[3][2],
 // (forward differences).  Threads clear of every CPML slab run the plain
 // update; the others add the CPML terms (cpml_curl).
 template <typename R>
-__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 6 : 1)
     k_h3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm)
 {
     wait_previous_grid();
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 3 : 1)
 // kernel); per component the Drude update of Eq. (10a,b) in the design box.
 //   curl_x = dy Hz - dz Hy,  curl_y = dz Hx - dx Hz,  curl_z = dx Hy - dy Hx
 template <typename R, int MODE>
-__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 6 : 1)
     k_e3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm, Step3D<R> a3)
 {
     wait_previous_grid();
