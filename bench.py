@@ -201,7 +201,7 @@ def run_surrogate(args) -> None:
     collect_s = time.perf_counter() - t
     tr = Trainer(256, 256, base=24, batch=8, seed=0, lr=1e-3)
     t = time.perf_counter()
-    loss = tr.fit(pairs, 300)
+    loss = tr.fit(pairs, args.sur_train_steps)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t
     rho_start = I.zero_gap(w, np.zeros(I.design_shape(w)))
@@ -226,7 +226,7 @@ def run_surrogate(args) -> None:
                 surrogate=dict(updates=len(hs.W), seconds=sur_s, final_W=Ws[-1], reached=Ws[-1] >= 0.99 * target,
                                **st),
                 wall_time_ratio=sur_s / plain_s,
-                pretraining=dict(pairs=len(pairs), collect_s=collect_s, train_steps=300, train_s=train_s,
+                pretraining=dict(pairs=len(pairs), collect_s=collect_s, train_steps=args.sur_train_steps, train_s=train_s,
                                  final_loss=loss))
     print(json.dumps(line), flush=True)
 
@@ -254,9 +254,10 @@ def main() -> None:
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--surrogate", action="store_true",
                     help="measure the surrogate-assisted optimization loop against the plain adjoint loop")
-    ap.add_argument("--sur-trajectories", type=int, default=8)
+    ap.add_argument("--sur-trajectories", type=int, default=20)
     ap.add_argument("--sur-pairs-per-trajectory", type=int, default=25)
     ap.add_argument("--sur-updates", type=int, default=40)
+    ap.add_argument("--sur-train-steps", type=int, default=300)
     args = ap.parse_args()
     if args.surrogate:
         run_surrogate(args)
