@@ -9,16 +9,17 @@
 // Each thread owns four adjacent nodes of one row (16-byte vector loads and
 // stores; rows are padded to 32 nodes), 32 x 4 threads per block, i.e. a
 // 128 x 4 node tile, up to 10 blocks per SM (a block-shape sweep on the
-// 2048^2 workload: 128 x 4 beat 128 x 8, 128 x 16 and 128 x 2).  A thread computes the new Hx and Hy of its nodes and,
-// in registers, the new Hy left of its first node and the new Hx below its
+// 2048^2 workload: 128 x 4 beat 128 x 8, 128 x 16 and 128 x 2).  A thread
+// computes the new Hx and Hy of its nodes and, in registers, the new Hy left
+// of its first node and the new Hx below its
 // nodes, which its E updates need: 6 vector and 3 scalar loads per 4 nodes,
 // neighbour rows served by L1, no exchange between threads and no barrier.
 //
 // Paths are chosen per block (uniform): blocks whose nodes and neighbours
 // are clear of walls and CPML slabs run vector code, with per-node design /
 // gap / source logic only when the tile touches those boxes; border blocks
-// run a scalar path with CPML.  The design-box arrays (J, rho~, records, G) use the library's
-// pitched layout: column origin dxa (a multiple of 4) and row pitch dp (a
+// run a scalar path with CPML.  The design-box arrays (J, rho~, records, G)
+// use the library's pitched layout: column origin dxa (a multiple of 4) and row pitch dp (a
 // multiple of 4), so that they load as vectors too.  Indices are 32-bit.
 
 #include "coef_slots.cuh"
