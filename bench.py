@@ -36,6 +36,12 @@ from paper_2203_01462_gb300 import inputs as I  # noqa: E402
 
 METRIC = "Gcell-updates/s fwd+adjoint"
 UNIT = "Gcell-updates/s"
+# Bounded oracle samples, in grid-node time steps of the forward run: the
+# 2048^2 workload cut to 300 steps (about 7 s on 16 host cores, forward +
+# adjoint) for the cpu_baseline key, and to 200 steps per reference-arm
+# evaluation.  Larger grids get proportionally fewer steps.
+CPU_CELL_STEPS = 2048 * 2048 * 300
+REF_CELL_STEPS = 2048 * 2048 * 200
 
 
 WORKLOADS = {
@@ -132,6 +138,15 @@ def parse_clocks(path: str, gpu_index: int):
     return out
 
 
+def sample_nsteps(w: dict, requested: int, cell_steps: float) -> int:
+    """Time steps of the oracle's bounded sample: ``requested`` if given, else
+    as many as fit ``cell_steps`` grid-node steps (forward), between 10 and
+    1000 and at most the workload's own count."""
+    if requested > 0:
+        return min(requested, w["nsteps"])
+    return max(1, min(w["nsteps"], 1000, max(10, int(cell_steps / I.n_cells(w)))))
+
+
 def cpu_baseline(w: dict, nsteps: int) -> dict:
     """The oracle, as it stands, on the host cores: one forward + adjoint +
     gradient of the same workload cut to ``nsteps`` time steps."""
@@ -156,7 +171,7 @@ def run_reference(args, w) -> None:
     from oracle import oracle as O
     cores = os.cpu_count() or 1
     O.set_threads(cores)
-    ns = args.ref_nsteps
+    ns = sample_nsteps(w, args.ref_nsteps, REF_CELL_STEPS)
     ws = dict(w, nsteps=ns)
     rho = I.rho_uniform(ws, 0)
     for k in range(args.warmup):
@@ -248,8 +263,10 @@ def main() -> None:
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="cfg_2d_2048")
     ap.add_argument("--nsteps", type=int, default=0, help="override the time-step count (quick runs)")
-    ap.add_argument("--cpu-nsteps", type=int, default=300)
-    ap.add_argument("--ref-nsteps", type=int, default=200)
+    ap.add_argument("--cpu-nsteps", type=int, default=0,
+                    help="time steps of the oracle sample (0: sized to 2048^2 x 300 node steps)")
+    ap.add_argument("--ref-nsteps", type=int, default=0,
+                    help="time steps per reference-arm evaluation (0: sized to 2048^2 x 200 node steps)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--surrogate", action="store_true",
@@ -281,7 +298,7 @@ def main() -> None:
     # The oracle's host-core sample runs before any GPU work.
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(w, args.cpu_nsteps)
+        cpu = cpu_baseline(w, sample_nsteps(w, args.cpu_nsteps, CPU_CELL_STEPS))
 
     from paper_2203_01462_gb300.binding import Solver
     dev = torch.device("cuda", local)
