@@ -200,8 +200,8 @@ def run_surrogate(args) -> None:
     """Design iterations/s at a matched objective: the plain adjoint loop
     (one forward + adjoint solve per design step) against the
     surrogate-assisted loop (one solve + four U-Net steps per round), on the
-    256^2-design workload.  The surrogate loop stops once its judged W~ is
-    within 1 % of the plain loop's final W~."""
+    256^2-design workload.  The surrogate loop stops once the W~ of one of
+    its full solves is within 1 % of the plain loop's final W~."""
     import torch
     from paper_2203_01462_gb300.binding import Solver
     from paper_2203_01462_gb300.optimize import optimize
@@ -332,7 +332,8 @@ def main() -> None:
         one_step(k)
     s.sync()
 
-    clk_path = os.path.join(ROOT, "gpurun_out", "clocks_bench_rank%d.csv" % rank)
+    clk_path = os.path.join(os.environ.get("FDTD_RESULTS_DIR") or os.path.join(ROOT, "results"),
+                            "clocks_bench_rank%d.csv" % rank)
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
     proc, fh = sample_clocks(clk_path)
     launches0 = s.info().launches

@@ -3,8 +3,8 @@
 A plain adjoint loop spends one forward + adjoint FDTD solve per design step.
 Here the U-Net surrogate (``surrogate.UNet``) predicts the sensitivity map
 from (rho, damping level) and takes ``inner`` cheap steps after every full
-solve.  The full solve stays the reference: it judges the previous surrogate
-steps (if W~ fell, the design returns to the last judged one and that round's
+solve.  The full solve stays the reference: it checks the previous surrogate
+steps (if W~ fell, the design returns to the last checked one and that round's
 surrogate steps are skipped), it supplies a new training pair, and the
 network is fine-tuned on the pairs collected so far.
 
@@ -12,7 +12,7 @@ Training targets are gradients normalised by their largest magnitude; the
 ascent step (``fdtd_ascent_step``) normalises its direction the same way.
 
 With ``correct=True`` (default) the network is used as a correction model
-around the last judged design rho_j: the step direction is
+around the last checked design rho_j: the step direction is
 g(rho_j) + N(rho) - N(rho_j), the exact normalised gradient of the last full
 solve plus the change the network predicts, so that the network's absolute
 errors largely cancel.
@@ -105,9 +105,9 @@ def surrogate_optimize(s: Solver, tr: Trainer, rho0, updates: int, inner: int = 
                        sigma_max: float = 0.0, damping_start: float = 10.0, damping_iters: int = 50,
                        pairs: Pairs | None = None, fit_steps: int = 2,
                        target_W: float | None = None, correct: bool = True) -> tuple[torch.Tensor, History, dict]:
-    """Up to ``updates`` design steps: each judge round is one full solve +
-    ascent step, then ``inner`` surrogate steps.  Stops early once a judged
-    W~ reaches ``target_W``.  Returns the design, the history and counters
+    """Up to ``updates`` design steps: each round is one full solve +
+    ascent step, then ``inner`` surrogate steps.  Stops early once the W~ of a full
+    solve reaches ``target_W``.  Returns the design, the history and counters
     (full solves, surrogate steps, rejected rounds)."""
     rho = torch.as_tensor(rho0, device=s.device).to(s.real).contiguous().clone()
     pairs = pairs if pairs is not None else Pairs()
@@ -123,7 +123,7 @@ def surrogate_optimize(s: Solver, tr: Trainer, rho0, updates: int, inner: int = 
         stats["solves"] += 1
         Wv = float(W.item())
         if last_W is not None and Wv < last_W and not skip:
-            # the surrogate steps made things worse: back to the judged design
+            # the surrogate steps made things worse: back to the checked design
             rho.copy_(last_rho)
             W, g, Wv = None, last_g, last_W
             stats["rejected"] += 1

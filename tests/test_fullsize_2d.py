@@ -11,8 +11,6 @@ With rho ~ U[0.1, 0.9] over the 1024^2 box the 3 x 3 gap sits behind about
 1 um of lossy half-metal and its field is ~1e-7 of the incident one, at the
 rounding level of FP32 arithmetic; FP32 checks therefore use the bowtie
 nanoantenna design, which leaves vacuum paths to the gap."""
-import json
-import os
 
 import numpy as np
 import pytest
@@ -20,18 +18,11 @@ import pytest
 from paper_2203_01462_gb300 import inputs as I
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def interior_rho(w, seed):
     # keep rho +- h inside [0, 1]
     return I.zero_gap(w, 0.1 + 0.8 * I.rho_uniform(w, seed))
-
-
-def _report(name, d):
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    with open(os.path.join(ROOT, "gpurun_out", "fullsize_%s.json" % name), "w") as f:
-        json.dump(d, f)
 
 
 def bowtie_rho(w):
@@ -41,7 +32,7 @@ def bowtie_rho(w):
     return I.zero_gap(w, 0.01 + 0.98 * I.rho_bowtie(w))
 
 
-def test_fullsize_fp32_directional_derivative_and_autograd():
+def test_fullsize_fp32_directional_derivative_and_autograd(save_report):
     import torch
     from paper_2203_01462_gb300.autograd import objective
     from paper_2203_01462_gb300.binding import Solver
@@ -69,14 +60,14 @@ def test_fullsize_fp32_directional_derivative_and_autograd():
     Wn.backward()
     ga = r.grad.double().cpu().numpy().reshape(-1)
     ag_err = float(np.linalg.norm(ga - g / W0) / np.linalg.norm(g / W0))
-    _report("fp32_directional", dict(W=W0, fd=fd, g_dot_v=gv, rel_err=abs(fd - gv) / abs(fd),
+    save_report("fullsize_fp32_directional.json", dict(W=W0, fd=fd, g_dot_v=gv, rel_err=abs(fd - gv) / abs(fd),
                                      autograd_vs_fp64=ag_err))
     assert abs(Wn.item() - 1.0) < 1e-12
     assert abs(fd - gv) <= 1e-3 * abs(fd), (fd, gv)
     assert ag_err <= 1e-6
 
 
-def test_fullsize_fp64_gradient_on_16_random_cells():
+def test_fullsize_fp64_gradient_on_16_random_cells(save_report):
     from paper_2203_01462_gb300.binding import Solver
     w = dict(I.cfg_2d_2048(), real="f64")
     s = Solver(w)
@@ -99,12 +90,12 @@ def test_fullsize_fp64_gradient_on_16_random_cells():
             vals.append(s.forward().item())
         fd = (vals[0] - vals[1]) / (2 * h)
         rows.append(dict(cell=int(c), fd=fd, adjoint=float(g[c]), rel=abs(fd - g[c]) / abs(fd)))
-    _report("fp64_cells", dict(W=float(W.item()), gmax=float(gmax), h=h, cells=rows))
+    save_report("fullsize_fp64_cells.json", dict(W=float(W.item()), gmax=float(gmax), h=h, cells=rows))
     for r in rows:
         assert abs(r["fd"] - r["adjoint"]) <= 1e-3 * abs(r["fd"]) + 1e-5 * gmax, r
 
 
-def test_fullsize_fp32_matches_fp64_fields():
+def test_fullsize_fp32_matches_fp64_fields(save_report):
     """The benchmark's FP32 configuration against the same run in FP64
     (W 1e-4 relative, gradient 1e-3 L2-relative) on the bowtie design."""
     from paper_2203_01462_gb300.binding import Solver
@@ -115,6 +106,6 @@ def test_fullsize_fp32_matches_fp64_fields():
     W32, W64 = float(W32.item()), float(W64.item())
     g32, g64 = g32.cpu().numpy(), g64.cpu().numpy()
     gerr = float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64))
-    _report("fp32_vs_fp64", dict(W32=W32, W64=W64, W_rel=abs(W32 - W64) / abs(W64), grad_l2_rel=gerr))
+    save_report("fullsize_fp32_vs_fp64.json", dict(W32=W32, W64=W64, W_rel=abs(W32 - W64) / abs(W64), grad_l2_rel=gerr))
     assert abs(W32 - W64) <= 1e-4 * abs(W64)
     assert gerr <= 1e-3

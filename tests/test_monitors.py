@@ -1,7 +1,5 @@
 """Gap-spectrum monitor (the paper's field-enhancement measure) against the
 oracle's DFT of its own gap history, through the C ABI."""
-import json
-import os
 
 import numpy as np
 import pytest
@@ -10,7 +8,6 @@ from oracle import oracle as O
 from paper_2203_01462_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 C0 = 299792458.0
 
 
@@ -55,7 +52,7 @@ def test_gap_spectrum_3d_matches_oracle():
     assert np.max(np.abs(z - ref)) <= 1e-10 * np.max(np.abs(ref))
 
 
-def test_field_enhancement_of_a_bowtie():
+def test_field_enhancement_of_a_bowtie(save_report):
     """A gold bowtie on the 160^2 grid against the structure-free run: the
     ratio is 1 for the structure-free design itself.  With E out of plane no
     surface plasmon exists (Sec. 3, TE case), so the metal shields the gap:
@@ -69,8 +66,6 @@ def test_field_enhancement_of_a_bowtie():
     same = enhancement_spectrum(s_in, np.zeros(s_in.n_design), f, s_in=Solver(incident_workload(w)))
     np.testing.assert_allclose(same, 1.0, rtol=1e-12)
     fe = enhancement_spectrum(s, I.rho_bowtie(w), f, s_in=s_in)
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    json.dump(dict(wavelength_nm=(C0 / f * 1e9).tolist(), enhancement=fe.tolist()),
-              open(os.path.join(ROOT, "gpurun_out", "bowtie_enhancement.json"), "w"))
+    save_report("bowtie_enhancement.json", dict(wavelength_nm=(C0 / f * 1e9).tolist(), enhancement=fe.tolist()))
     assert np.all(np.isfinite(fe)) and np.all(fe > 0)
     assert fe.max() < 1.0

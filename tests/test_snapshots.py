@@ -2,8 +2,6 @@
 gradient bit for bit; BF16 / FP16 per-slab-scaled snapshots perturb only the
 recomputed fields, so W~ is unchanged and the gradient error against the
 FP64 oracle stays within the stated bounds."""
-import json
-import os
 
 import numpy as np
 import pytest
@@ -12,8 +10,6 @@ from oracle import oracle as O
 from paper_2203_01462_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
-
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 # Gradient L2-relative error bounds against the FP64 oracle (FP32 fields).
 BOUND = {"f32": 1e-3, "f16": 1e-3, "bf16": 3e-3}
@@ -42,7 +38,7 @@ def grad(w, rho, smax=5e5, gs=2.0):
 
 
 @pytest.mark.parametrize("make", [medium_2d, small_3d])
-def test_snapshot_precisions(make):
+def test_snapshot_precisions(make, save_report):
     base = make(snapshot_every=0)
     rho = I.rho_uniform(base, 31)
     ref = O.gradient(base, rho, 5e5, 2.0)["grad"]
@@ -57,6 +53,4 @@ def test_snapshot_precisions(make):
             np.testing.assert_array_equal(g, g_full)
         assert err <= BOUND[dt], (dt, err)
     report["full_history_fp32"] = float(np.linalg.norm(g_full - ref) / np.linalg.norm(ref))
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    with open(os.path.join(ROOT, "gpurun_out", "snapshot_errors_%s.json" % make.__name__), "w") as f:
-        json.dump(report, f)
+    save_report("snapshot_errors_%s.json" % make.__name__, report)

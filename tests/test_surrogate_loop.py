@@ -5,8 +5,6 @@ On the 256^2-design workload (316^2 grid, 4000 steps), a U-Net pretrained on
 surrogate-assisted loop (one full forward + adjoint solve, then four
 surrogate steps, per round).  It must reach the plain loop's final objective
 (within 1 %) in less wall time than the plain loop took."""
-import json
-import os
 
 import numpy as np
 import pytest
@@ -14,10 +12,8 @@ import pytest
 from paper_2203_01462_gb300 import inputs as I
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-
-def test_surrogate_loop_matches_plain_objective_in_less_time():
+def test_surrogate_loop_matches_plain_objective_in_less_time(save_report):
     import time
     import torch
     from paper_2203_01462_gb300.binding import Solver
@@ -45,8 +41,7 @@ def test_surrogate_loop_matches_plain_objective_in_less_time():
     Ws = [x for x in hs.W if x == x]
     rep = dict(plain_s=plain_s, plain_updates=30, plain_W=target, sur_s=sur_s, sur_updates=len(hs.W),
                sur_W=Ws[-1], **st)
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    json.dump(rep, open(os.path.join(ROOT, "gpurun_out", "surrogate_loop.json"), "w"))
+    save_report("surrogate_loop.json", rep)
     assert Ws[-1] >= 0.99 * target, rep
     assert sur_s < 0.9 * plain_s, rep
     assert st["solves"] < 30
