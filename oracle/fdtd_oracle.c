@@ -34,6 +34,10 @@
  *                         F is a normalised Gaussian; the chain rule applies
  *                         F^T (the paper writes the diagonal d rho~_i/d rho_i).
  *
+ * 3D plane wave (Sec. 3.3 injects one at normal incidence): total-field /
+ * scattered-field, with the incident field taken from a 1D column of the
+ * same scheme (see the 3D part below).
+ *
  * The oracle keeps whole arrays (no slabs), loops node by node and solves
  * each node's 2x2 system by Cramer's rule.  Loops over nodes may run under
  * OpenMP; every per-node result and every sum is formed in a fixed order, so
@@ -86,6 +90,10 @@ typedef struct or_config {
     int pol;               /* 2D: 0 = E_z out of plane (Ez, Hx, Hy, Jz);        */
                            /* 1 = E in plane (Ex, Ey, Hz, Jx, Jy), design and   */
                            /* gap per Yee edge                                  */
+    int tfsf;              /* 3D: 1 = plane wave by total-field / scattered-    */
+                           /* field injection instead of the source box         */
+    int tf_lo[3], tf_hi[3]; /* total-field region: the closed box of positions  */
+                           /* tf_lo <= x <= tf_hi (node units)                  */
 } or_config;
 
 static int g_threads = 1;
@@ -1011,8 +1019,107 @@ static int h_active(const or_config *c, int comp, int i, int j, int k)
  * with (c, a, b) cyclic. */
 static void curl_axes(int comp, int *a, int *b) { *a = (comp + 1) % 3; *b = (comp + 2) % 3; }
 
-/* H half step: mu0 dH/dt = -curl E with CPML on each derivative. */
-static void step3_h(const or_config *c, const mat3 *m, st3 *s)
+/* ------------------------------------------- plane wave by TFSF (3D) */
+
+/* The incident wave is x-polarised and travels along +z.  It is the field
+ * of the laterally uniform problem: a 1D Yee column along z with the 3D
+ * grid's background layering (sub_eps below sub_hi, eps_s above), its
+ * z-CPML and PEC ends, driven by the soft E_x current of the source plane
+ * k = src_lo[2].  In the column E_x(k) sits at z = k and H_y(k) at
+ * z = k + 1/2, exactly where the 3D components of the same index sit, and
+ * each update is the 3D one with the x and y derivatives zero.
+ *
+ * The 3D arrays hold the total field at every component whose Yee position
+ * lies in the closed box tf_lo <= x <= tf_hi, and the scattered field
+ * elsewhere.  A difference taken at a field F that reaches a sample of a
+ * field G across the box boundary converts the sample into F's view first:
+ * G + (tf(F) - tf(G)) G_inc. */
+typedef struct {
+    int nz;
+    double *E, *H, *pe, *ph;     /* E_x, H_y and their z-CPML terms */
+    pml_coef *ce, *ch;           /* z-CPML at nodes / half positions */
+    double *eps;                 /* background permittivity per k */
+    double gam;
+} col1d;
+
+static void col_init(const or_config *c, double gamma_scale, col1d *L)
+{
+    int nz = c->nz;
+    L->nz = nz;
+    L->E = calloc(nz, sizeof(double)); L->H = calloc(nz, sizeof(double));
+    L->pe = calloc(nz, sizeof(double)); L->ph = calloc(nz, sizeof(double));
+    L->ce = malloc(nz * sizeof(pml_coef)); L->ch = malloc(nz * sizeof(pml_coef));
+    L->eps = malloc(nz * sizeof(double));
+    for (int k = 0; k < nz; ++k) {
+        L->ce[k] = pml_at(c, nz, k);
+        L->ch[k] = pml_at(c, nz, k + 0.5);
+        L->eps[k] = k < c->sub_hi ? c->sub_eps : c->eps_s;
+    }
+    L->gam = c->gamma_p * gamma_scale;
+}
+
+static void col_free(col1d *L)
+{
+    free(L->E); free(L->H); free(L->pe); free(L->ph); free(L->ce); free(L->ch); free(L->eps);
+}
+
+/* mu0 dH_y/dt = -(dE_x/dz), the y row of the 3D H update. */
+static void col_h(const or_config *c, col1d *L)
+{
+    double ch = or_dt(c) / OR_MU0;
+    for (int k = 0; k + 1 < L->nz; ++k) {
+        double d = (L->E[k + 1] - L->E[k]) / c->dx;
+        pml_coef p = L->ch[k];
+        L->ph[k] = p.b * L->ph[k] + p.c * d;
+        L->H[k] -= ch * (d / p.kappa + L->ph[k]);
+    }
+}
+
+/* E_x from curl_x H = -dH_y/dz and the source current jsrc on its plane. */
+static void col_e(const or_config *c, col1d *L, double jsrc)
+{
+    for (int k = 1; k + 1 < L->nz; ++k) {
+        double d = (L->H[k] - L->H[k - 1]) / c->dx;
+        pml_coef p = L->ce[k];
+        L->pe[k] = p.b * L->pe[k] + p.c * d;
+        double curl = -(d / p.kappa + L->pe[k]);
+        double J = 0.0;
+        node_solve(L->eps[k], 0.0, 0.0, L->gam, or_dt(c), curl,
+                   (k >= c->src_lo[2] && k < c->src_hi[2]) ? jsrc : 0.0, &L->E[k], &J);
+    }
+}
+
+/* Is component comp of E (isH = 0) or H (isH = 1) of index (i, j, k) in the
+ * total-field box?  E_c sits half a cell along c, H_c half a cell along the
+ * other two axes. */
+static int tf_in(const or_config *c, int isH, int comp, int i, int j, int k)
+{
+    int p[3] = {i, j, k};
+    for (int a = 0; a < 3; ++a) {
+        double x = p[a] + (((a == comp) != isH) ? 0.5 : 0.0);
+        if (x < c->tf_lo[a] || x > c->tf_hi[a]) return 0;
+    }
+    return 1;
+}
+
+/* Incident value of a component: only E_x and H_y are non-zero. */
+static double inc_at(const col1d *L, int isH, int comp, int k)
+{
+    if (!isH) return comp == X ? L->E[k] : 0.0;
+    return comp == Y ? L->H[k] : 0.0;
+}
+
+/* (tf(F) - tf(G)) G_inc for the sample of G (kind isH, component comp) at
+ * (i, j, k), seen from a field F whose flag is tfF. */
+static double tf_shift(const or_config *c, const col1d *L, int tfF, int isH, int comp, int i, int j, int k)
+{
+    int d = tfF - tf_in(c, isH, comp, i, j, k);
+    return d ? d * inc_at(L, isH, comp, k) : 0.0;
+}
+
+/* H half step: mu0 dH/dt = -curl E with CPML on each derivative; with a
+ * column L, the E samples are converted as described above. */
+static void step3_h(const or_config *c, const mat3 *m, st3 *s, const col1d *L)
 {
     double ch = or_dt(c) / OR_MU0;
     #pragma omp parallel for schedule(static)
@@ -1028,6 +1135,16 @@ static void step3_h(const or_config *c, const mat3 *m, st3 *s)
                     /* curl_comp E = d_a E_b - d_b E_a */
                     double da = dfwd(c, s->E[b], a, i, j, k);
                     double db = dfwd(c, s->E[a], b, i, j, k);
+                    if (L) {
+                        int tfF = tf_in(c, 1, comp, i, j, k);
+                        int ea[3] = {a == X, a == Y, a == Z}, eb[3] = {b == X, b == Y, b == Z};
+                        if (p[a] + 1 < (a == X ? c->nx : a == Y ? c->ny : c->nz))
+                            da += (tf_shift(c, L, tfF, 0, b, i + ea[0], j + ea[1], k + ea[2]) -
+                                   tf_shift(c, L, tfF, 0, b, i, j, k)) / c->dx;
+                        if (p[b] + 1 < (b == X ? c->nx : b == Y ? c->ny : c->nz))
+                            db += (tf_shift(c, L, tfF, 0, a, i + eb[0], j + eb[1], k + eb[2]) -
+                                   tf_shift(c, L, tfF, 0, a, i, j, k)) / c->dx;
+                    }
                     pml_coef pa = m->h[a][p[a]], pb = m->h[b][p[b]];
                     s->ph[comp][a][q] = pa.b * s->ph[comp][a][q] + pa.c * da;
                     s->ph[comp][b][q] = pb.b * s->ph[comp][b][q] + pb.c * db;
@@ -1038,8 +1155,9 @@ static void step3_h(const or_config *c, const mat3 *m, st3 *s)
 }
 
 /* E, J half step: Eq. (10a,b) for every active E component; jsrc[comp] is a
- * per-node current density (or NULL). */
-static void step3_e(const or_config *c, const mat3 *m, st3 *s, double *const *jsrc)
+ * per-node current density (or NULL); with a column L, the H samples are
+ * converted as described above. */
+static void step3_e(const or_config *c, const mat3 *m, st3 *s, double *const *jsrc, const col1d *L)
 {
     double dt = or_dt(c);
     #pragma omp parallel for schedule(static)
@@ -1054,6 +1172,16 @@ static void step3_e(const or_config *c, const mat3 *m, st3 *s, double *const *js
                     curl_axes(comp, &a, &b);
                     double da = dbwd(c, s->H[b], a, i, j, k);
                     double db = dbwd(c, s->H[a], b, i, j, k);
+                    if (L) {
+                        int tfF = tf_in(c, 0, comp, i, j, k);
+                        int ea[3] = {a == X, a == Y, a == Z}, eb[3] = {b == X, b == Y, b == Z};
+                        if (p[a] >= 1)
+                            da += (tf_shift(c, L, tfF, 1, b, i, j, k) -
+                                   tf_shift(c, L, tfF, 1, b, i - ea[0], j - ea[1], k - ea[2])) / c->dx;
+                        if (p[b] >= 1)
+                            db += (tf_shift(c, L, tfF, 1, a, i, j, k) -
+                                   tf_shift(c, L, tfF, 1, a, i - eb[0], j - eb[1], k - eb[2])) / c->dx;
+                    }
                     pml_coef pa = m->e[a][p[a]], pb = m->e[b][p[b]];
                     s->pe[comp][a][q] = pa.b * s->pe[comp][a][q] + pa.c * da;
                     s->pe[comp][b][q] = pb.b * s->pe[comp][b][q] + pb.c * db;
@@ -1094,6 +1222,9 @@ static int forward3(const or_config *c, const double *rho, double sigma_max, dou
     size_t n = n3(c);
     double *js[3] = {NULL, NULL, NULL};
     js[c->src_comp] = calloc(n, sizeof(double));
+    const int tf = c->tfsf != 0;
+    col1d col;
+    if (tf) col_init(c, gamma_scale, &col);
     double *Hold[3] = {NULL, NULL, NULL};
     if (energy)
         for (int a = 0; a < 3; ++a) Hold[a] = calloc(n, sizeof(double));
@@ -1126,15 +1257,21 @@ static int forward3(const or_config *c, const double *rho, double sigma_max, dou
                 s.E[probes[4 * pi + 3]][id3(c, probes[4 * pi], probes[4 * pi + 1], probes[4 * pi + 2])];
         if (t == N) break;
         double v = J0 * or_signal(c, (t + 0.5) * dt);
-        for (int k = c->src_lo[2]; k < c->src_hi[2]; ++k)
-            for (int j = c->src_lo[1]; j < c->src_hi[1]; ++j)
-                for (int i = c->src_lo[0]; i < c->src_hi[0]; ++i) js[c->src_comp][id3(c, i, j, k)] = v;
+        if (!tf)
+            for (int k = c->src_lo[2]; k < c->src_hi[2]; ++k)
+                for (int j = c->src_lo[1]; j < c->src_hi[1]; ++j)
+                    for (int i = c->src_lo[0]; i < c->src_hi[0]; ++i) js[c->src_comp][id3(c, i, j, k)] = v;
         if (energy)
             for (int a = 0; a < 3; ++a) memcpy(Hold[a], s.H[a], n * sizeof(double));
-        step3_h(c, &m, &s);
+        /* 3D H from E^t (incident E^t), then the column's H^{t+1/2}; 3D E
+         * from H^{t+1/2}, then the column's E^{t+1} */
+        step3_h(c, &m, &s, tf ? &col : NULL);
+        if (tf) col_h(c, &col);
         if (energy) energy[t] = energy3(c, &m, &s, Hold);
-        step3_e(c, &m, &s, js);
+        step3_e(c, &m, &s, js, tf ? &col : NULL);
+        if (tf) col_e(c, &col, v);
     }
+    if (tf) col_free(&col);
     *W = 0.5 * c->eps_g * dt * c->dx * c->dx * c->dx * sum;
     free(js[c->src_comp]);
     for (int a = 0; a < 3; ++a) free(Hold[a]);
@@ -1186,8 +1323,8 @@ static int gradient3(const or_config *c, const double *rho, double sigma_max, do
                         Eo[a * M + d] = s.E[a][id3(c, i, j, k)];
                         Jo[a * M + d] = s.J[a][id3(c, i, j, k)];
                     }
-        step3_h(c, &m, &s);
-        step3_e(c, &m, &s, js);
+        step3_h(c, &m, &s, NULL);
+        step3_e(c, &m, &s, js, NULL);
         for (int a = 0; a < 3; ++a)
             for (int k = c->design_lo[2]; k < c->design_hi[2]; ++k)
                 for (int j = c->design_lo[1]; j < c->design_hi[1]; ++j)
@@ -1233,6 +1370,27 @@ static int gradient3(const or_config *c, const double *rho, double sigma_max, do
 }
 
 /* ============================================================ public */
+
+/* The incident plane wave of a 3D workload with tfsf = 1: E_x at nodes ks[]
+ * for t = 0..N ((N+1) x nk, E_out) and H_y at the same indices for
+ * t + 1/2, t = 0..N-1 (N x nk, H_out). */
+int or_tfsf_incident(const or_config *c, double gamma_scale, const int *ks, int nk, double *E_out,
+                     double *H_out)
+{
+    if (c->ndim != 3) return -1;
+    col1d col;
+    col_init(c, gamma_scale, &col);
+    double dt = or_dt(c), J0 = c->src_amp * or_eps0() * OR_C0 / c->dx;
+    for (int t = 0; t <= c->nsteps; ++t) {
+        for (int q = 0; q < nk; ++q) E_out[(size_t)t * nk + q] = col.E[ks[q]];
+        if (t == c->nsteps) break;
+        col_h(c, &col);
+        for (int q = 0; q < nk; ++q) H_out[(size_t)t * nk + q] = col.H[ks[q]];
+        col_e(c, &col, J0 * or_signal(c, (t + 0.5) * dt));
+    }
+    col_free(&col);
+    return 0;
+}
 
 int or_forward(const or_config *c, const double *rho, double sigma_max, double gamma_scale,
                double *W, double *gap_hist, double *design_hist,

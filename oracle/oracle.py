@@ -39,8 +39,11 @@ class OrConfig(C.Structure):
         ("filter_radius", C.c_int), ("filter_sigma", C.c_double),
         ("sigma_form", C.c_int), ("sub_eps", C.c_double), ("sub_hi", C.c_int),
         ("src_comp", C.c_int), ("waveform", C.c_int), ("bandwidth", C.c_double), ("lobes", C.c_int),
-        ("pol", C.c_int),
+        ("pol", C.c_int), ("tfsf", C.c_int), ("tf_lo", C.c_int * 3), ("tf_hi", C.c_int * 3),
     ]
+
+_DEFAULTS = {"src_comp": 2, "waveform": 0, "bandwidth": 0.0, "lobes": 0, "pol": 0, "tfsf": 0,
+             "tf_lo": (0, 0, 0), "tf_hi": (0, 0, 0)}
 
 
 def build(force: bool = False) -> str:
@@ -71,6 +74,7 @@ def lib():
             L.or_sizes.argtypes = [C.POINTER(OrConfig), C.POINTER(C.c_long), C.POINTER(C.c_long)]
             L.or_free_design.argtypes = [C.POINTER(OrConfig)]
             L.or_free_design.restype = C.c_long
+            L.or_tfsf_incident.argtypes = [C.POINTER(OrConfig), C.c_double, C.POINTER(C.c_int), C.c_int, dp, dp]
             L.or_set_threads.argtypes = [C.c_int]
             L.or_get_threads.restype = C.c_int
             _lib = L
@@ -88,7 +92,7 @@ def threads() -> int:
 def config(w: dict) -> OrConfig:
     c = OrConfig()
     for name, ctype in OrConfig._fields_:
-        v = w.get(name, {"src_comp": 2, "waveform": 0, "bandwidth": 0.0, "lobes": 0, "pol": 0}.get(name))
+        v = w.get(name, _DEFAULTS.get(name))
         if name == "f0":
             c.f0[0], c.f0[1] = float(v[0]), float(v[1])
         elif isinstance(getattr(c, name), C.Array):
@@ -233,3 +237,19 @@ def grayness(w: dict, rho: np.ndarray) -> float:
     mask[sl] = False
     v = rt[mask.reshape(-1)]
     return float(4.0 * np.sum(v * (1.0 - v)) / v.size)
+
+
+def tfsf_incident(w: dict, ks, gamma_scale: float = 1.0) -> tuple[np.ndarray, np.ndarray]:
+    """The incident plane wave of a 3D workload with ``tfsf``: E_x at the
+    node indices ks along z for t = 0..N, shape (N+1, len(ks)), and H_y at
+    the same indices for t + 1/2, t = 0..N-1, shape (N, len(ks))."""
+    ks = np.ascontiguousarray(np.asarray(ks, dtype=np.int32).reshape(-1))
+    N = int(w["nsteps"])
+    E = np.zeros((N + 1, ks.size))
+    H = np.zeros((max(N, 1), ks.size))
+    cfg = config(w)
+    rc = lib().or_tfsf_incident(C.byref(cfg), float(gamma_scale), ks.ctypes.data_as(C.POINTER(C.c_int)),
+                                int(ks.size), _dptr(E), _dptr(H))
+    if rc != 0:
+        raise RuntimeError("oracle tfsf_incident failed (%d)" % rc)
+    return E, H[:N]

@@ -173,11 +173,16 @@ def workload_3d(nx: int, ny: int, nz: int, *, dx: float, nsteps: int, npml: int 
                 courant: float = 0.5, real: str = "f32", material: dict | None = None,
                 source: str = "sheet", src_offset: int = 5, substrate: bool = False,
                 snapshot_every: int = 0, snapshot_dtype: str = "f32", accum: str = "f64",
-                pulse_kw: dict | None = None, **over) -> dict:
+                pulse_kw: dict | None = None, tf_margin: int = 2, **over) -> dict:
     """A 3D nanoantenna-shaped workload: centred design slab and gap.
 
     source="sheet": a soft E_x current sheet on the plane z = npml + src_offset
     over the non-CPML x-y range (a plane wave along +z, x-polarised).
+    source="tfsf": the same x-polarised plane wave along +z, injected by
+    total-field / scattered-field: the current of the plane z = npml +
+    src_offset drives a 1D column, and the total-field box spans x and y from
+    npml + tf_margin to n - 1 - npml - tf_margin and z from two nodes above
+    the source plane to nz - 1 - npml - tf_margin.
     source="dipole": a soft E_z current at the centre node of the gap.
     substrate=True: background eps 2.25 below the design slab.
     """
@@ -194,12 +199,18 @@ def workload_3d(nx: int, ny: int, nz: int, *, dx: float, nsteps: int, npml: int 
         sub_eps=2.25 if substrate else 1.0, sub_hi=d_lo[2] if substrate else 0,
         real=real, snapshot_every=snapshot_every, snapshot_dtype=snapshot_dtype, accum=accum,
     )
-    if source == "sheet":
+    if source in ("sheet", "tfsf"):
         zs = npml + src_offset
         w.update(src_lo=[npml, npml, zs], src_hi=[nx - npml, ny - npml, zs + 1], src_comp=0)
-    else:
+        if source == "tfsf":
+            m = tf_margin
+            w.update(tfsf=1, tf_lo=[npml + m, npml + m, zs + 2],
+                     tf_hi=[nx - 1 - npml - m, ny - 1 - npml - m, nz - 1 - npml - m])
+    elif source == "dipole":
         c = [(l + h) // 2 for l, h in zip(w["gap_lo"], w["gap_hi"])]
         w.update(src_lo=c, src_hi=[x + 1 for x in c], src_comp=2)
+    else:
+        raise ValueError("unknown source " + source)
     w.update(mat)
     w.update(pulse(**(pulse_kw or {})))
     w.update(over)
@@ -238,6 +249,8 @@ def describe(w: dict) -> str:
     snap = ("snapshots every %d (%s)" % (w["snapshot_every"], w.get("snapshot_dtype", "f32"))
             if w.get("snapshot_every") else "full history")
     filt = ", %d-cell Gaussian filter" % w["filter_radius"] if w.get("filter_radius") else ""
+    if w.get("tfsf"):
+        filt += ", TFSF plane wave"
     return "%s %s %s, %d steps, %s design%s, %s" % (kind, dims, w["real"].upper(), w["nsteps"], des, filt, snap)
 
 
