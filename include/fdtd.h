@@ -96,6 +96,28 @@ enum { FDTD_WAVE_GAUSS = 0, FDTD_WAVE_SINC_HANN = 1 };
  *   The source drives E_x edges.  No design filter (filter_radius 0). */
 enum { FDTD_POL_EZ = 0, FDTD_POL_INPLANE = 1 };
 
+/* 3D plane wave by total-field / scattered-field injection (tfsf = 1; the
+ * paper's 3D study illuminates at normal incidence, Sec. 3.3).  An
+ * x-polarised plane wave travelling along +z enters through the faces of a
+ * total-field box instead of through the source box's current: a field
+ * component whose Yee position (E_x at (i+1/2, j, k), E_z at (i, j, k+1/2),
+ * H_y at (i+1/2, j, k+1/2), ...) lies in the closed box
+ * tf_lo <= x <= tf_hi (node units) holds the total field, every other one
+ * the scattered field.  The incident field is that of a 1D column along z
+ * with the grid's background layering (sub_eps below sub_hi, eps_s above),
+ * the same z-CPML and PEC ends, driven by the soft E_x current of the plane
+ * k = src_lo[2] with the configured waveform (the source box's x and y
+ * extent is unused).  fdtd_create runs the column once on the device and
+ * keeps one row of incident values per step in the workspace
+ * (nsteps x (2 (tf_hi[2] - tf_lo[2] + 1) + 1) words).  Requirements
+ * (FDTD_EINVAL otherwise): ndim = 3, src_comp = 0, src_lo[2] >= 1,
+ * src_hi[2] = src_lo[2] + 1 <= tf_lo[2]; per axis
+ * npml + 1 <= tf_lo < tf_hi <= n - npml - 2; and the box strictly around the
+ * design box, tf_lo < design_lo and tf_hi >= design_hi, so that every
+ * corrected component is background material.  The injection does not
+ * depend on rho: the adjoint run (Eq. 20) and the sensitivities (Eq. 25)
+ * are those of any other source. */
+
 /* Problem description.  Boxes are half-open node ranges [lo, hi) per axis
  * (x, y, z); in 2D the z range must be [0, 1).  Grid: nx x ny Ez nodes in
  * 2D; nx x ny x nz Yee nodes in 3D. */
@@ -138,6 +160,8 @@ typedef struct fdtd_config {
     double bandwidth;         /* FDTD_WAVE_SINC_HANN: rectangle width B, Hz    */
     int lobes;                /* FDTD_WAVE_SINC_HANN: lobes kept per side      */
     int pol;                  /* 2D: FDTD_POL_*                                */
+    int tfsf;                 /* 3D: 1 = plane wave by TFSF injection (above)  */
+    int tf_lo[3], tf_hi[3];   /* total-field box, closed, node units           */
 } fdtd_config;
 
 typedef struct fdtd_ctx fdtd_ctx;

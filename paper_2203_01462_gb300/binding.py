@@ -54,6 +54,7 @@ class FdtdConfig(C.Structure):
         ("real_bytes", C.c_int), ("snapshot_every", C.c_int), ("snapshot_dtype", C.c_int),
         ("accum_kind", C.c_int), ("src_comp", C.c_int),
         ("waveform", C.c_int), ("bandwidth", C.c_double), ("lobes", C.c_int), ("pol", C.c_int),
+        ("tfsf", C.c_int), ("tf_lo", C.c_int * 3), ("tf_hi", C.c_int * 3),
     ]
 
 
@@ -140,7 +141,8 @@ def config(w: dict) -> FdtdConfig:
             c.accum_kind = ACC[w.get("accum", "f64")]
             continue
         v = w[name] if name in w else {"snapshot_every": 0, "src_comp": 2, "waveform": 0, "bandwidth": 0.0,
-                                       "lobes": 0, "pol": 0}.get(name)
+                                       "lobes": 0, "pol": 0, "tfsf": 0, "tf_lo": (0, 0, 0),
+                                       "tf_hi": (0, 0, 0)}.get(name)
         if name == "f0":
             c.f0[0], c.f0[1] = float(v[0]), float(v[1])
         elif isinstance(getattr(c, name), C.Array):

@@ -109,6 +109,19 @@ fdtd_status validate(const fdtd_config *c)
     if (c->snapshot_dtype < FDTD_SNAP_F32 || c->snapshot_dtype > FDTD_SNAP_F16) return FDTD_EINVAL;
     if (c->accum_kind != FDTD_ACC_F64) return FDTD_EINVAL;
     if (c->sigma_form != FDTD_SIGMA_PAPER && c->sigma_form != FDTD_SIGMA_PEAK_NORMALISED) return FDTD_EINVAL;
+    if (c->tfsf != 0 && c->tfsf != 1) return FDTD_EINVAL;
+    if (c->tfsf) {
+        // x-polarised plane wave along +z: a one-plane source below the
+        // total-field box, the box clear of the CPML and strictly around the
+        // design box (its corrected faces are background material)
+        if (c->ndim != 3 || c->src_comp != 0) return FDTD_EINVAL;
+        if (c->src_lo[2] < 1 || c->src_hi[2] != c->src_lo[2] + 1 || c->src_hi[2] > c->tf_lo[2]) return FDTD_EINVAL;
+        for (int a = 0; a < 3; ++a) {
+            if (c->tf_lo[a] < c->npml + 1 || c->tf_hi[a] > n[a] - c->npml - 2 || c->tf_lo[a] >= c->tf_hi[a])
+                return FDTD_EINVAL;
+            if (c->tf_lo[a] >= c->design_lo[a] || c->tf_hi[a] < c->design_hi[a]) return FDTD_EINVAL;
+        }
+    }
     // The step kernels index one array with 32-bit integers.
     const long long px = (c->nx + 31) / 32 * 32;
     if (c->ndim == 2 && px * (long long)c->ny >= (1LL << 31)) return FDTD_EINVAL;
@@ -1088,6 +1101,7 @@ struct Ctx3D final : fdtd_ctx {
     Pml3D<R> pm{};
     double *misc = nullptr;
     unsigned *err = nullptr;
+    R *tf_tab = nullptr, *tf_col = nullptr;  // plane wave: incident table, column state
 
     void *rho_stage() override { return rstage; }
     double *grad_stage() override { return gstage; }
@@ -1144,6 +1158,12 @@ struct Ctx3D final : fdtd_ctx {
         geo.Mg = (int)Mg;
         geo.src_comp = c.src_comp;
         geo.sub_hi = c.sub_hi;
+        geo.tfsf = c.tfsf;
+        for (int a = 0; a < 3; ++a) {
+            geo.tf_lo[a] = c.tf_lo[a];
+            geo.tf_hi[a] = c.tf_hi[a];
+            if (c.tfsf) geo.s0[a] = geo.s1[a] = 0;  // the grid itself carries no source current
+        }
         const long long N = c.nsteps;
         carve_state(cv, F, F_base);
         carve_state(cv, A, A_base);
@@ -1162,6 +1182,10 @@ struct Ctx3D final : fdtd_ctx {
         pml_tab = cv.take<R>(6 * (size_t)(c.nx + c.ny + c.nz));
         misc = cv.take<double>(4 + 2 * MMA_BLOCKS);
         err = cv.take<unsigned>(4);
+        if (c.tfsf) {
+            tf_tab = cv.take<R>((size_t)N * tfsf_row(geo));
+            tf_col = cv.take<R>(4 * (size_t)c.nz);
+        }
         if (pml_tab) {
             R *t = pml_tab;
             for (int a = 0; a < 3; ++a) {
@@ -1187,6 +1211,19 @@ struct Ctx3D final : fdtd_ctx {
         FDTD_TRY(cuda_ok(cudaMemcpyAsync(src_tab, src.data(), src.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
         launch_zero_bytes(err, 4 * sizeof(unsigned), st);
         ++launches;
+        if (c.tfsf) {
+            // the incident wave does not depend on rho or the damping: one
+            // column run per context, driven by the source plane
+            Geo3D gc = geo;
+            for (int a = 0; a < 3; ++a) {
+                gc.s0[a] = c.src_lo[a];
+                gc.s1[a] = c.src_hi[a];
+            }
+            const Coef<R> k = coef();
+            launch_tfsf_column<R>(gc, pm, k.S, k.eps_s, k.eps_sub, src_tab, c.nsteps, tf_col, tf_tab, st);
+            ++launches;
+            FDTD_TRY(check_launch());
+        }
         return cuda_ok(cudaStreamSynchronize(st));
     }
 
@@ -1236,6 +1273,7 @@ struct Ctx3D final : fdtd_ctx {
             a.src = src_tab + n;
             a.gap_rec = (gap && Mg) ? gap_hist + (size_t)(n + 1) * 3 * Mg : nullptr;
             a.rec = rec_base ? rec_base + (size_t)(n - n0) * 3 * Mdi : nullptr;
+            a.tf_inc = tf_tab ? tf_tab + (size_t)n * tfsf_row(geo) : nullptr;
             launches += launch_step3d<R>(0, geo, F, coef_slot, pm, a, stream);
         }
         cell_updates += (long long)count * ncells;

@@ -117,7 +117,14 @@ struct Geo3D {
     int Mg;
     int s0[3], s1[3], src_comp;
     int sub_hi;
+    // plane wave by total-field / scattered-field injection (tfsf = 1): the
+    // closed total-field box of positions [tf_lo, tf_hi] (node units)
+    int tfsf, tf_lo[3], tf_hi[3];
 };
+
+// Incident-table row of one step of the plane wave: E_x^n at k = tf_lo[2] ..
+// tf_hi[2], then H_y^{n+1/2} at k = tf_lo[2]-1 .. tf_hi[2].
+inline int tfsf_row(const Geo3D &g) { return 2 * (g.tf_hi[2] - g.tf_lo[2] + 1) + 1; }
 
 // One 3D solver state: three E, H and J components (J over the pitched
 // design box), and the CPML terms of component c for its two derivative
@@ -142,6 +149,7 @@ struct Step3D {
     R *rec;              // forward: design record slot [component][Mdi] (or null);
                          // adjoint: forward E^m, same layout
     double *G;           // adjoint: sensitivity accumulator [Mdi]
+    const R *tf_inc;     // forward with tfsf: incident-table row of this step
 };
 
 // 2D with E in plane (the paper's 2D "TM" case): Ex(i, j) on the edge
@@ -189,10 +197,21 @@ template <typename R>
 int launch_stepp(int mode, const GeoP &g, const StateP<R> &s, int coef_slot, const PmlP<R> &pm,
                  const StepP<R> &a, cudaStream_t st);
 
-// H then E half steps of the whole grid, in place (two launches).
+// H then E half steps of the whole grid, in place (two launches); a forward
+// step with a.tf_inc adds the plane wave's face corrections after each half
+// step (four launches).  Returns the launch count.
 template <typename R>
 int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, int coef_slot, const Pml3D<R> &pm,
                   const Step3D<R> &a, cudaStream_t st);
+
+// The incident plane wave of a tfsf grid: one block steps the 1D column
+// (E_x, H_y, their z-CPML terms in col, 4 nz words, cleared here) for
+// nsteps steps and writes one tfsf_row(g) row per step into tab.  eps_s,
+// eps_sub: background permittivities above / below g.sub_hi; S: Courant
+// number; src: the source table (scaled current per step).
+template <typename R>
+void launch_tfsf_column(const Geo3D &g, const Pml3D<R> &pm, R S, R eps_s, R eps_sub, const R *src, int nsteps,
+                        R *col, R *tab, cudaStream_t st);
 
 // A forward (recompute) step of one state and an adjoint step of another in
 // one launch (independent work; see k_step2d_pair).

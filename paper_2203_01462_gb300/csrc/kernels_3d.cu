@@ -419,16 +419,158 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 6 : 1)
     }
 }
 
+// ------------------------------------------------ plane wave (TFSF)
+//
+// An x-polarised plane wave along +z enters through the faces of the
+// total-field box: components whose Yee position lies in the closed box
+// [tf_lo, tf_hi] hold the total field, the others the scattered field.  A
+// curl that reaches across the box boundary needs the incident value of the
+// component on the other side; only E_x and H_y carry one.  The faces lie in
+// background material (the box encloses the design box, away from the
+// CPML), where each half step is E += S curl / eps or H -= S curl, so the
+// correction is added after the main launch:
+//   H_y(i, j, lo_z - 1) += S Ei(lo_z)     H_y(i, j, hi_z) -= S Ei(hi_z)
+//   H_z(i, lo_y - 1, k) -= S Ei(k)        H_z(i, hi_y, k) += S Ei(k)
+//   E_x(i, j, lo_z) += S Hi(lo_z - 1) / eps(lo_z)
+//   E_x(i, j, hi_z) -= S Hi(hi_z) / eps(hi_z)
+//   E_z(lo_x, j, k) -= S Hi(k) / eps(k)   E_z(hi_x, j, k) += S Hi(k) / eps(k)
+// with i in [lo_x, hi_x), j in [lo_y, hi_y], k in [lo_z, hi_z] (H_z) or
+// [lo_z, hi_z) (E_z).  Ei = E_x^n and Hi = H_y^{n+1/2} of the incident column.
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_tfsf_h(Geo3D g, State3D<R> s, int slot, const R *__restrict__ inc)
+{
+    wait_previous_grid();
+    const R S = coef_at<R>(slot).S;
+    const int lx = g.tf_lo[0], ly = g.tf_lo[1], lz = g.tf_lo[2];
+    const int Lx = g.tf_hi[0] - lx, Ly = g.tf_hi[1] - ly + 1, Lz = g.tf_hi[2] - lz + 1;
+    const long long zf = (long long)Lx * Ly, yf = (long long)Lx * Lz;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < 2 * zf) {
+        const int top = t >= zf;
+        const long long r = t - top * zf;
+        const int i = lx + (int)(r % Lx), j = ly + (int)(r / Lx), k = top ? g.tf_hi[2] : lz - 1;
+        R *h = s.H[1] + k * g.PP + (long long)j * g.px + i;
+        *h += top ? -S * inc[Lz - 1] : S * inc[0];
+    } else if (t < 2 * zf + 2 * yf) {
+        const long long u = t - 2 * zf;
+        const int far = u >= yf;
+        const long long r = u - far * yf;
+        const int i = lx + (int)(r % Lx), k = lz + (int)(r / Lx), j = far ? g.tf_hi[1] : ly - 1;
+        R *h = s.H[2] + k * g.PP + (long long)j * g.px + i;
+        *h += far ? S * inc[k - lz] : -S * inc[k - lz];
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_tfsf_e(Geo3D g, State3D<R> s, int slot, const R *__restrict__ inc)
+{
+    wait_previous_grid();
+    const Coef<R> &c = coef_at<R>(slot);
+    const R S = c.S;
+    const int lx = g.tf_lo[0], ly = g.tf_lo[1], lz = g.tf_lo[2];
+    const int Lx = g.tf_hi[0] - lx, Ly = g.tf_hi[1] - ly + 1, Lz = g.tf_hi[2] - lz + 1;
+    const R *hi = inc + Lz;  // H_y^{n+1/2} at k = lz - 1 + q
+    const long long zf = (long long)Lx * Ly, xf = (long long)Ly * (Lz - 1);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < 2 * zf) {
+        const int top = t >= zf;
+        const long long r = t - top * zf;
+        const int i = lx + (int)(r % Lx), j = ly + (int)(r / Lx), k = top ? g.tf_hi[2] : lz;
+        const R inv = rcp(k < g.sub_hi ? c.eps_sub : c.eps_s);
+        R *e = s.E[0] + k * g.PP + (long long)j * g.px + i;
+        *e += top ? -S * hi[Lz] * inv : S * hi[0] * inv;
+    } else if (t < 2 * zf + 2 * xf) {
+        const long long u = t - 2 * zf;
+        const int far = u >= xf;
+        const long long r = u - far * xf;
+        const int j = ly + (int)(r % Ly), k = lz + (int)(r / Ly), i = far ? g.tf_hi[0] : lx;
+        const R inv = rcp(k < g.sub_hi ? c.eps_sub : c.eps_s);
+        R *e = s.E[2] + k * g.PP + (long long)j * g.px + i;
+        *e += far ? S * hi[k - lz + 1] * inv : -S * hi[k - lz + 1] * inv;
+    }
+}
+
+// The incident column: E_x(k) at z = k and H_y(k) at z = k + 1/2 of a
+// laterally uniform field, updated exactly as the 3D kernels update those
+// components (x and y derivatives zero): H_y -= S t_z, E_x += (S (0 - t_z) -
+// J) / eps, t_z the kappa-scaled z difference plus its CPML term.  One block;
+// two barriers per step.
+template <typename R>
+__global__ void __launch_bounds__(256) k_tfsf_column(Geo3D g, Pml3D<R> pm, R S, R eps_s, R eps_sub,
+                                                     const R *__restrict__ src, int nsteps, R *col, R *tab)
+{
+    const int nz = g.n[2], np = g.npml, lz = g.tf_lo[2], Lz = g.tf_hi[2] - lz + 1, row = 2 * Lz + 1;
+    R *E = col, *H = col + nz, *pE = col + 2 * nz, *pH = col + 3 * nz;
+    for (int k = threadIdx.x; k < 4 * nz; k += blockDim.x) col[k] = R(0);
+    const R inv_s = rcp(eps_s), inv_sub = rcp(eps_sub);
+    __syncthreads();
+    for (int n = 0; n < nsteps; ++n) {
+        R *out = tab + (long long)n * row;
+        for (int q = threadIdx.x; q < Lz; q += blockDim.x) out[q] = E[lz + q];
+        for (int k = threadIdx.x; k <= nz - 2; k += blockDim.x) {
+            const R d = E[k + 1] - E[k];
+            R tz = d * pm.kiH[2][k];
+            if (slabH(k, nz, np) >= 0) {
+                pH[k] = pm.bH[2][k] * pH[k] + pm.cH[2][k] * d;
+                tz += pH[k];
+            }
+            H[k] -= S * tz;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q <= Lz; q += blockDim.x) out[Lz + q] = H[lz - 1 + q];
+        const R J = src[n];
+        for (int k = 1 + threadIdx.x; k <= nz - 2; k += blockDim.x) {
+            const R d = H[k] - H[k - 1];
+            R tz = d * pm.kiE[2][k];
+            if (slabE(k, nz, np) >= 0) {
+                pE[k] = pm.bE[2][k] * pE[k] + pm.cE[2][k] * d;
+                tz += pE[k];
+            }
+            const R curl = S * (R(0) - tz);
+            const R js = (k >= g.s0[2] && k < g.s1[2]) ? J : R(0);
+            E[k] += (curl - js) * (k < g.sub_hi ? inv_sub : inv_s);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+template <typename R>
+void launch_tfsf_column(const Geo3D &g, const Pml3D<R> &pm, R S, R eps_s, R eps_sub, const R *src, int nsteps,
+                        R *col, R *tab, cudaStream_t st)
+{
+    k_tfsf_column<R><<<1, 256, 0, st>>>(g, pm, S, eps_s, eps_sub, src, nsteps, col, tab);
+}
+
+template void launch_tfsf_column<float>(const Geo3D &, const Pml3D<float> &, float, float, float, const float *,
+                                        int, float *, float *, cudaStream_t);
+template void launch_tfsf_column<double>(const Geo3D &, const Pml3D<double> &, double, double, double,
+                                         const double *, int, double *, double *, cudaStream_t);
 
 template <typename R>
 int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, int c, const Pml3D<R> &pm,
                   const Step3D<R> &a, cudaStream_t st)
 {
     dim3 vblock(TBX, TBY, TBZ), vgrid((g.n[0] + TX - 1) / TX, (g.n[1] + TBY - 1) / TBY, (g.n[2] + TBZ - 1) / TBZ);
+    const bool tf = mode == 0 && a.tf_inc;
     launch_pdl(k_h3d<R>, vgrid, vblock, st, g, s, c, pm);
+    if (tf) {
+        const long long Lx = g.tf_hi[0] - g.tf_lo[0], Ly = g.tf_hi[1] - g.tf_lo[1] + 1,
+                        Lz = g.tf_hi[2] - g.tf_lo[2] + 1;
+        const long long nh = 2 * Lx * Ly + 2 * Lx * Lz;
+        launch_pdl(k_tfsf_h<R>, dim3((unsigned)((nh + 255) / 256)), dim3(256), st, g, s, c, a.tf_inc);
+    }
     if (mode == 0) launch_pdl(k_e3d<R, 0>, vgrid, vblock, st, g, s, c, pm, a);
     else launch_pdl(k_e3d<R, 1>, vgrid, vblock, st, g, s, c, pm, a);
+    if (tf) {
+        const long long Lx = g.tf_hi[0] - g.tf_lo[0], Ly = g.tf_hi[1] - g.tf_lo[1] + 1,
+                        Lz = g.tf_hi[2] - g.tf_lo[2] + 1;
+        const long long ne = 2 * Lx * Ly + 2 * Ly * (Lz - 1);
+        launch_pdl(k_tfsf_e<R>, dim3((unsigned)((ne + 255) / 256)), dim3(256), st, g, s, c, a.tf_inc);
+        return 4;
+    }
     return 2;
 }
 

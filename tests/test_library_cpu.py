@@ -83,3 +83,39 @@ def test_grid_beyond_32_bit_indexing_rejected():
     assert e.value.status == 1
     w.update(ny=30000)  # 1.97e9 nodes: accepted
     assert B.workspace_bytes(w) > 0
+
+
+def _tfsf_case(**kw):
+    w = I.workload_3d(21, 19, 31, dx=20e-9, nsteps=50, npml=4, design=(9, 7, 6), gap=(2, 2, 2),
+                      source="tfsf", substrate=True, real="f32", tf_margin=1)
+    w.update(kw)
+    return w
+
+
+def test_plane_wave_configuration_sized_and_checked():
+    """A valid total-field box adds one incident row per step to the
+    workspace; boxes that cut the design box, reach the CPML or sit below
+    the source plane, and non-x sources, are refused."""
+    w = _tfsf_case()
+    plain = dict(w, tfsf=0)
+    row = 2 * (w["tf_hi"][2] - w["tf_lo"][2] + 1) + 1
+    extra = B.workspace_bytes(w) - B.workspace_bytes(plain)
+    assert row * w["nsteps"] * 4 <= extra <= row * w["nsteps"] * 4 + 4 * w["nz"] * 4 + 1024
+    lo, hi, d_lo, d_hi = w["tf_lo"], w["tf_hi"], w["design_lo"], w["design_hi"]
+    bad = [
+        dict(tf_lo=[d_lo[0], lo[1], lo[2]]),                     # face on the design box
+        dict(tf_hi=[d_hi[0] - 1, hi[1], hi[2]]),                 # box inside the design box
+        dict(tf_lo=[w["npml"], lo[1], lo[2]]),                   # face in the CPML
+        dict(tf_hi=[hi[0], w["ny"] - w["npml"] - 1, hi[2]]),     # far face in the CPML
+        dict(tf_lo=[lo[0], lo[1], w["src_lo"][2]]),              # source plane inside the box
+        dict(src_comp=1),                                         # only the x-polarised wave
+        dict(src_hi=[w["src_hi"][0], w["src_hi"][1], w["src_lo"][2] + 2]),  # two source planes
+        dict(tfsf=2),
+    ]
+    for kw in bad:
+        with pytest.raises(B.FdtdError) as e:
+            B.workspace_bytes(dict(w, **kw))
+        assert e.value.status == 1, kw
+    two_d = I.small_2d()
+    with pytest.raises(B.FdtdError):
+        B.workspace_bytes(dict(two_d, tfsf=1, tf_lo=[2, 2, 0], tf_hi=[10, 10, 0]))
