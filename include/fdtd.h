@@ -203,6 +203,19 @@ fdtd_status fdtd_set_design(fdtd_ctx *ctx, const void *d_rho, size_t n);
  * Invalidates earlier forward and adjoint results. */
 fdtd_status fdtd_set_damping(fdtd_ctx *ctx, double sigma_max, double gamma_scale);
 
+/* Terms of the sensitivity (Eq. 25a-c) that the adjoint run accumulates:
+ * any non-empty OR of FDTD_TERM_PSI (Eq. 25a, through d psi_i / d rho~ =
+ * psi - psi_s), FDTD_TERM_EPS (Eq. 25b, through eps_inf - eps_s) and
+ * FDTD_TERM_SIGMA (Eq. 25c, through d sigma_i / d rho~).  Default
+ * FDTD_TERM_ALL: the gradient of W~.  With one term selected, fdtd_gradient
+ * returns F^T (Eq. 27) of that term alone, gap entries zero; the three
+ * single-term gradients add up to the full one (up to rounding).  A check
+ * of the adjoint term by term against a reference; the fields are not
+ * affected.  FDTD_EINVAL for a mask outside 1..7.  Invalidates an earlier
+ * adjoint result. */
+enum { FDTD_TERM_PSI = 1, FDTD_TERM_EPS = 2, FDTD_TERM_SIGMA = 4, FDTD_TERM_ALL = 7 };
+fdtd_status fdtd_set_sensitivity_terms(fdtd_ctx *ctx, int terms);
+
 /* Forward solve of N steps.  Writes W~ (Eq. 24) to d_W (device, one double;
  * may be NULL) asynchronously.  Requires fdtd_set_design. */
 fdtd_status fdtd_forward(fdtd_ctx *ctx, double *d_W);

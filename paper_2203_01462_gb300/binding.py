@@ -27,7 +27,10 @@ EXPORTS = ["fdtd_workspace_bytes", "fdtd_create", "fdtd_set_design", "fdtd_set_d
            "fdtd_run_host", "fdtd_get_info", "fdtd_status_string", "fdtd_destroy",
            "fdtd_gradient_static", "fdtd_gap_spectrum", "fdtd_ascent_step", "fdtd_mma_asymptotes", "fdtd_mma_solve",
            "fdtd_mirror_average", "fdtd_fix_design", "fdtd_grayness", "fdtd_threshold", "fdtd_set_graphs",
-           "fdtd_set_l2_residency"]
+           "fdtd_set_l2_residency", "fdtd_set_sensitivity_terms"]
+
+
+TERM_PSI, TERM_EPS, TERM_SIGMA, TERM_ALL = 1, 2, 4, 7
 
 
 class FdtdError(RuntimeError):
@@ -97,6 +100,7 @@ def load():
             "fdtd_grayness": [P, P],
             "fdtd_set_graphs": [P, C.c_int],
             "fdtd_set_l2_residency": [P, C.c_double],
+            "fdtd_set_sensitivity_terms": [P, C.c_int],
             "fdtd_threshold": [P, P, C.c_size_t, C.c_double],
             "fdtd_gap_history": [P, P, C.c_size_t],
             "fdtd_sync": [P],
@@ -260,6 +264,11 @@ class Solver:
     def set_l2_residency(self, fraction: float) -> None:
         """Keep ``fraction`` of the ping-pong state persisting in L2 (2D E_z mode; 0: off)."""
         _check(self.lib.fdtd_set_l2_residency(self.ctx, float(fraction)), "fdtd_set_l2_residency")
+
+    def set_sensitivity_terms(self, terms: int) -> None:
+        """Eq. (25) terms the adjoint accumulates: an OR of TERM_PSI, TERM_EPS,
+        TERM_SIGMA (default TERM_ALL, the gradient of W~)."""
+        _check(self.lib.fdtd_set_sensitivity_terms(self.ctx, int(terms)), "fdtd_set_sensitivity_terms")
 
     def set_graphs(self, mode: int) -> None:
         """0: plain launches, 1: replay CUDA graphs of whole passes, 2: automatic by grid size."""

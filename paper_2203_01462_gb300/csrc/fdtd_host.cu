@@ -186,6 +186,7 @@ struct fdtd_ctx {
     long long Md = 0, Mg = 0, ncells = 0;
     bool has_design = false, fwd_done = false, adj_done = false;
     double sigma_max = 0.0, gamma_scale = 1.0;
+    int terms = FDTD_TERM_ALL;  // Eq. (25) terms the adjoint accumulates
     long long launches = 0, cell_updates = 0;
     int coef_slot = -1;  // constant-memory coefficient slot (coef_slots.cuh)
     // CUDA graphs of whole forward / adjoint passes (replayed when enabled):
@@ -331,7 +332,7 @@ void snapshot_load(int dtype, const char *snap, char *state, size_t state_bytes,
 
 // Step-invariant coefficients in the scaled units of Coef.
 template <typename R>
-Coef<R> make_coef(const fdtd_config &c, double dt, double sigma_max, double gamma_scale)
+Coef<R> make_coef(const fdtd_config &c, double dt, double sigma_max, double gamma_scale, int terms)
 {
     Coef<R> k;
     const double g = c.gamma_p * gamma_scale * dt;
@@ -350,6 +351,11 @@ Coef<R> make_coef(const fdtd_config &c, double dt, double sigma_max, double gamm
     k.kJ = (R)kJ;
     k.inv1g = (R)(1.0 / (1.0 + 0.5 * g));
     k.half1pkJ = (R)(0.5 * (1.0 + kJ));
+    // formed in R exactly as the kernels formed them before the terms could
+    // be selected, so that the default (all terms) is bit-identical
+    k.t_eps = (terms & FDTD_TERM_EPS) ? k.d_eps : R(0);
+    k.t_sig = (terms & FDTD_TERM_SIGMA) ? k.sig_max : R(0);
+    k.t_dpsi = (terms & FDTD_TERM_PSI) ? (R)(k.psi - k.psi_s) : R(0);
     return k;
 }
 
@@ -554,7 +560,7 @@ struct Ctx2D final : fdtd_ctx {
         return cuda_ok(cudaStreamSynchronize(st));
     }
 
-    Coef<R> coef() const { return make_coef<R>(cfg, dt, sigma_max, gamma_scale); }
+    Coef<R> coef() const { return make_coef<R>(cfg, dt, sigma_max, gamma_scale, terms); }
 
     // A pass enqueues its launches (enqueue_*), directly or as a replayed
     // CUDA graph; the coefficients go to the context's constant slot first.
@@ -923,7 +929,7 @@ struct CtxP final : fdtd_ctx {
         return cuda_ok(cudaStreamSynchronize(st));
     }
 
-    Coef<R> coef() const { return make_coef<R>(cfg, dt, sigma_max, gamma_scale); }
+    Coef<R> coef() const { return make_coef<R>(cfg, dt, sigma_max, gamma_scale, terms); }
 
     fdtd_status forward(double *d_W) override
     {
@@ -1227,7 +1233,7 @@ struct Ctx3D final : fdtd_ctx {
         return cuda_ok(cudaStreamSynchronize(st));
     }
 
-    Coef<R> coef() const { return make_coef<R>(cfg, dt, sigma_max, gamma_scale); }
+    Coef<R> coef() const { return make_coef<R>(cfg, dt, sigma_max, gamma_scale, terms); }
 
     fdtd_status forward(double *d_W) override
     {
@@ -1503,6 +1509,14 @@ fdtd_status fdtd_set_damping(fdtd_ctx *ctx, double sigma_max, double gamma_scale
     ctx->sigma_max = sigma_max;
     ctx->gamma_scale = gamma_scale;
     ctx->fwd_done = ctx->adj_done = false;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_set_sensitivity_terms(fdtd_ctx *ctx, int terms)
+{
+    if (!ctx || terms < 1 || terms > FDTD_TERM_ALL) return FDTD_EINVAL;
+    ctx->terms = terms;
+    ctx->adj_done = false;
     return FDTD_OK;
 }
 

@@ -54,6 +54,10 @@ struct Coef {
     R kJ;           // (1 - gamma~/2) / (1 + gamma~/2)
     R inv1g;        // 1 / (1 + gamma~/2)
     R half1pkJ;     // (1 + kJ) / 2
+    // Factors of the three Eq. (25) terms in the adjoint's accumulator, each
+    // with its chain-rule factor: d_eps, sig_max and psi - psi_s for a term
+    // that is selected (fdtd_set_sensitivity_terms), 0 for one that is not.
+    R t_eps, t_sig, t_dpsi;
 };
 
 // Constant-memory coefficient slots (one per live context; coef_slots.cuh).

@@ -78,8 +78,8 @@ __device__ __forceinline__ void drude(const Coef<R> &c, R rt, R ez, R jo, R curl
     en = ca * ez + cb * (curl - c.half1pkJ * jo - src);
     jn = c.kJ * jo + bJ * (en + ez);
     if (MODE == 1)
-        term = -c.d_eps * (en - ez) - c.sig_max * (R(1) - R(2) * rt) * R(0.5) * (en + ez) -
-               (c.psi - c.psi_s) * rcp(psi) * R(0.5) * (jn + jo);
+        term = -c.t_eps * (en - ez) - c.t_sig * (R(1) - R(2) * rt) * R(0.5) * (en + ez) -
+               c.t_dpsi * rcp(psi) * R(0.5) * (jn + jo);
 }
 
 // Scalar E update of one node (border blocks): design, gap and source

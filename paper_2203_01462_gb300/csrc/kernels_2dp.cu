@@ -100,8 +100,8 @@ __device__ __forceinline__ void e_edge(const GeoP &g, const Coef<R> &c, const St
             if (a.rec[cc]) a.rec[cc][d] = en;
         } else {
             // Eq. (25a-c) folded through the chain rule of Eq. (27).
-            const R term = -c.d_eps * (en - e) - c.sig_max * (R(1) - R(2) * rt) * R(0.5) * (en + e) -
-                           (c.psi - c.psi_s) * rcp(psi) * R(0.5) * (jn + jo);
+            const R term = -c.t_eps * (en - e) - c.t_sig * (R(1) - R(2) * rt) * R(0.5) * (en + e) -
+                           c.t_dpsi * rcp(psi) * R(0.5) * (jn + jo);
             a.G[cc][d] += (double)a.rec[cc][d] * (double)term;
         }
     } else {

@@ -395,9 +395,9 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 6 : 1)
                 jn4[v] = c.kJ * J4[cc][v] + bJ * (en[v] + e[cc][v]);
                 if (MODE == 1) {
                     // Eq. (25a-c) folded through the chain rule of Eq. (27).
-                    const R term = -c.d_eps * (en[v] - e[cc][v]) -
-                                   c.sig_max * (R(1) - R(2) * rt) * R(0.5) * (en[v] + e[cc][v]) -
-                                   (c.psi - c.psi_s) * rcp(psi) * R(0.5) * (jn4[v] + J4[cc][v]);
+                    const R term = -c.t_eps * (en[v] - e[cc][v]) -
+                                   c.t_sig * (R(1) - R(2) * rt) * R(0.5) * (en[v] + e[cc][v]) -
+                                   c.t_dpsi * rcp(psi) * R(0.5) * (jn4[v] + J4[cc][v]);
                     gadd[v] += (double)em4[cc][v] * (double)term;
                 }
             } else {
