@@ -43,4 +43,4 @@ def test_fullsize_3d_directional_derivative(save_report):
     save_report("fullsize_3d_directional.json", dict(W=W0, W_plus=Wp, W_minus=Wm, fd=fd, g_dot_v=gv, rel_err=rel))
     # the step changes W by a measurable amount, far above FP32 noise
     assert abs(Wp - Wm) > 1e-4 * W0
-    assert rel <= 1e-2, (fd, gv)
+    assert rel <= 3e-3, (fd, gv)  # the bound stated for BF16 checkpoints
