@@ -31,6 +31,9 @@ C0 = 299792458.0
 
 GOLD = dict(eps_inf=1.0, omega_p=1.37e16, gamma_p=1.0e14)
 SILVER = dict(eps_inf=4.469, omega_p=1.426e16, gamma_p=4.571e13)  # Sec. 2 fit
+# Artificial-damping conductivity sigma_max of Eq. (5c) that the paper's sweep
+# settles on (Sec. 2.1), S/m.
+SIGMA_MAX_PAPER = 5e5
 
 
 def pulse(center_m: float = 800e-9, half_width_hz: float = 100e12, nbands: int = 1,
