@@ -166,9 +166,8 @@ def cpu_baseline(w: dict, nsteps: int) -> dict:
     v_all, dt = run(cores, nsteps)
     ns1 = max(5, nsteps // cores)
     v_one, dt1 = run(1, ns1)
-    used = cores
     O.set_threads(cores)
-    return dict(value=v_all, unit=UNIT, cores=used, kind="oracle",
+    return dict(value=v_all, unit=UNIT, cores=O.threads(), kind="oracle",
                 sample="%s with %d of %d time steps, one forward+adjoint+gradient, %.1f s"
                        % (w.get("name", "workload"), nsteps, w["nsteps"], dt),
                 value_1_thread=v_one,
@@ -306,9 +305,10 @@ def main() -> None:
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    # The oracle's host-core sample runs before any GPU work.
+    # The oracle's host-core sample runs before any GPU work, on rank 0 of a
+    # one-GPU run only.
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, sample_nsteps(w, args.cpu_nsteps, CPU_CELL_STEPS))
 
     from paper_2203_01462_gb300.binding import Solver
