@@ -31,9 +31,13 @@ namespace fdtd {
 namespace {
 
 // Tiles: 8 x 8 x 2 threads, four x-adjacent nodes each, i.e.
-// 32 x 8 x 2 nodes (a warp reads 128 contiguous bytes per row), up to 6
-// blocks per SM in FP32 (a sweep of 8x8x4 at 3 / 8x8x2 at 6 / 4x8x4 at 6 /
-// 8x4x2 at 12 per SM: 8x8x2 and 4x8x4 were fastest, by 3-5 %).
+// 32 x 8 x 2 nodes (a warp reads 128 contiguous bytes per row), up to 5
+// blocks per SM in FP32.  Shapes (at 768 threads per SM): 8x8x4 at 3 /
+// 8x8x2 at 6 / 4x8x4 at 6 / 8x4x2 at 12 per SM; 8x8x2 and 4x8x4 were
+// fastest, by 3-5 %.  Occupancy against register spills (8x8x2; 256^3 and
+// 512x512x384 Gcell/s): 6 blocks (80 registers, 100-260 B of spill stores)
+// 39.2 / 45.9, 5 blocks (102 registers, 28-80 B) 39.5 / 46.6, 4 blocks (128
+// registers, no spills) 38.8 / 44.6.
 constexpr int VX = 4, TBX = 8, TBY = 8, TBZ = 2;
 constexpr int TX = TBX * VX;
 
@@ -169,7 +173,7 @@ __device__ __forceinline__ void cpml_curl(const Geo3D &g, R *const (&psi)[3][2],
 // (forward differences).  Threads clear of every CPML slab run the plain
 // update; the others add the CPML terms (cpml_curl).
 template <typename R>
-__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 6 : 1)
+__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
     k_h3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm)
 {
     wait_previous_grid();
@@ -256,7 +260,7 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 6 : 1)
 // kernel); per component the Drude update of Eq. (10a,b) in the design box.
 //   curl_x = dy Hz - dz Hy,  curl_y = dz Hx - dx Hz,  curl_z = dx Hy - dy Hx
 template <typename R, int MODE>
-__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 6 : 1)
+__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
     k_e3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm, Step3D<R> a3)
 {
     wait_previous_grid();
