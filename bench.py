@@ -66,7 +66,7 @@ def workload(name: str, nsteps: int | None):
 # summarised in profiles/step2d_2048.md (k_step2d<float,0>, one launch) and
 # profiles/step3d_256.md (k_h3d + k_e3d<float,0>).  Cold-L2 captures of
 # the current kernels; reset to None whenever a kernel changes.
-NCU_TRAFFIC_PER_STEP = {"cfg_2d_2048": 74.2e6, "cfg_3d_256": 1348.3e6}
+NCU_TRAFFIC_PER_STEP = {"cfg_2d_2048": 74.2e6, "cfg_3d_256": 1300.0e6}
 
 
 def damping(k: int) -> float:
