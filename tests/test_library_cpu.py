@@ -119,3 +119,47 @@ def test_plane_wave_configuration_sized_and_checked():
     two_d = I.small_2d()
     with pytest.raises(B.FdtdError):
         B.workspace_bytes(dict(two_d, tfsf=1, tf_lo=[2, 2, 0], tf_hi=[10, 10, 0]))
+
+
+def _c_layout(tmp_path, include: str, struct: str, fields, extra_flags=()):
+    """sizeof and offsetof of each field of a C struct, from gcc."""
+    import subprocess
+    src = tmp_path / ("layout_%s.c" % struct.replace(" ", "_"))
+    lines = ["#include <stddef.h>", "#include <stdio.h>", include, "int main(void) {",
+             '  printf("%%zu\\n", sizeof(%s));' % struct]
+    lines += ['  printf("%%zu\\n", offsetof(%s, %s));' % (struct, f) for f in fields]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / ("layout_%s" % struct.replace(" ", "_"))
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", *extra_flags, "-o", str(exe), str(src), "-lm"],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(v) for v in out[1:]]
+
+
+@pytest.mark.parametrize("struct,cls", [("fdtd_config", "FdtdConfig"), ("fdtd_info", "FdtdInfo")])
+def test_binding_structs_match_the_c_header(tmp_path, struct, cls):
+    """The ctypes mirrors of the ABI structs have the header's size and
+    field offsets (compiled as C11, so the header is valid C)."""
+    ct = getattr(B, cls)
+    names = [f[0] for f in ct._fields_]
+    size, offs = _c_layout(tmp_path, '#include "%s"' % os.path.join(ROOT, "include", "fdtd.h"), struct, names)
+    assert size == C.sizeof(ct)
+    assert offs == [getattr(ct, n).offset for n in names]
+
+
+def test_surrogate_header_is_valid_c(tmp_path):
+    import subprocess
+    src = tmp_path / "sur.c"
+    src.write_text('#include "%s"\nint main(void) { return 0; }\n' % os.path.join(ROOT, "include", "surrogate.h"))
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-c", "-o", str(tmp_path / "sur.o"), str(src)],
+                   check=True, capture_output=True)
+
+
+def test_oracle_config_mirror_matches_its_c_struct(tmp_path):
+    from oracle import oracle as O
+    names = [f[0] for f in O.OrConfig._fields_]
+    size, offs = _c_layout(tmp_path, '#include "%s"' % os.path.join(ROOT, "oracle", "fdtd_oracle.c"), "or_config",
+                           names, extra_flags=("-Wno-unused-function", "-fopenmp"))
+    assert size == C.sizeof(O.OrConfig)
+    assert offs == [getattr(O.OrConfig, n).offset for n in names]
