@@ -223,7 +223,7 @@ def workload_3d(nx: int, ny: int, nz: int, *, dx: float, nsteps: int, npml: int 
 def cfg_3d_256(nsteps: int = 10000) -> dict:
     """256^3 FP32: 128 x 128 x 64 design slab on an eps 2.25 substrate, 4^3 gap,
     x-polarised plane wave along +z injected by total-field / scattered-field
-    (box 4 nodes inside the CPML), BF16 snapshots every 32."""
+    (box 4 nodes in from the CPML), BF16 snapshots every 32."""
     return workload_3d(256, 256, 256, dx=5e-9, nsteps=nsteps, npml=12, design=(128, 128, 64), gap=(4, 4, 4),
                        source="tfsf", tf_margin=4, substrate=True, snapshot_every=32, snapshot_dtype="bf16")
 
