@@ -351,8 +351,8 @@ Coef<R> make_coef(const fdtd_config &c, double dt, double sigma_max, double gamm
     k.kJ = (R)kJ;
     k.inv1g = (R)(1.0 / (1.0 + 0.5 * g));
     k.half1pkJ = (R)(0.5 * (1.0 + kJ));
-    // formed in R exactly as the kernels formed them before the terms could
-    // be selected, so that the default (all terms) is bit-identical
+    // formed in R as the kernels formed these factors before the terms could
+    // be selected: with all terms the accumulator uses the same constants
     k.t_eps = (terms & FDTD_TERM_EPS) ? k.d_eps : R(0);
     k.t_sig = (terms & FDTD_TERM_SIGMA) ? k.sig_max : R(0);
     k.t_dpsi = (terms & FDTD_TERM_PSI) ? (R)(k.psi - k.psi_s) : R(0);
