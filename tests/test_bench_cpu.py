@@ -103,3 +103,14 @@ def test_benchmark_step_bytes_agree_with_the_worked_total():
     roofline's numerator)."""
     ab = bench.algorithmic_bytes(I.cfg_2d_2048())
     assert 115e6 < ab["forward"] < 118e6
+
+
+@pytest.mark.parametrize("name", sorted(bench.WORKLOADS))
+def test_every_bench_workload_is_a_valid_configuration(name):
+    """Each workload bench.py can time passes the library's configuration
+    checks and fits in the 280 GB of one GB300 (sized through the C ABI,
+    no GPU needed)."""
+    from paper_2203_01462_gb300 import binding as B
+    w = bench.workload(name, None)
+    nbytes = B.workspace_bytes(w)
+    assert 0 < nbytes < 280e9, (name, nbytes)
