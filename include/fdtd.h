@@ -348,11 +348,14 @@ fdtd_status fdtd_set_graphs(fdtd_ctx *ctx, int mode);
  * no-op for the others).  fraction in (0, 1]: sets aside fraction x (the
  * bytes of one ping-pong pair of states) of L2 for persisting accesses
  * (cudaLimitPersistingL2CacheSize, bounded by the device maximum; a limit of
- * this process that applies to every context on the device) and marks the
- * forward pair, through an access-policy window on each forward and
- * recompute launch, persisting in that share and streaming elsewhere, so
- * that part of the state stays in L2 from one step to the next.  0 turns the windows off
- * (the set-aside stays).  Results are unchanged.  Default: off. */
+ * this process that applies to every context on the device, so the last
+ * call wins) and marks the forward pair, through an access-policy window on
+ * each launch of the forward run (the paired recompute + adjoint launches
+ * run without one), persisting in that share and streaming elsewhere, so
+ * that part of the state stays in L2 from one step to the next.  0 turns
+ * the windows off, gives the set-aside back and demotes the lines marked
+ * persisting; fdtd_destroy does the same for a context that has it on.
+ * Results are unchanged.  FDTD_EINVAL outside [0, 1].  Default: off. */
 fdtd_status fdtd_set_l2_residency(fdtd_ctx *ctx, double fraction);
 
 /* Wait for the context's stream and report (then clear) device-side errors:

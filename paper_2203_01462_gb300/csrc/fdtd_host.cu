@@ -396,6 +396,20 @@ struct Ctx2D final : fdtd_ctx {
     cudaAccessPolicyWindow win = {};
     bool l2 = false;
     const cudaAccessPolicyWindow *winF() const { return l2 ? &win : nullptr; }
+    // Give back the persisting set-aside and demote the lines already marked
+    // persisting (best effort for the latter).
+    fdtd_status release_l2()
+    {
+        l2 = false;
+        const fdtd_status s = cuda_ok(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, 0));
+        if (cudaCtxResetPersistingL2Cache() != cudaSuccess) cudaGetLastError();
+        return s;
+    }
+    ~Ctx2D() override
+    {
+        if (l2) release_l2();
+    }
+
     fdtd_status set_l2(double fraction) override
     {
         for (auto &g : cap)
@@ -405,8 +419,7 @@ struct Ctx2D final : fdtd_ctx {
             }
         if (!(fraction > 0)) {
             // release the set-aside: reserved but unused L2 slows every other access
-            if (l2) FDTD_TRY(cuda_ok(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, 0)));
-            l2 = false;
+            if (l2) FDTD_TRY(release_l2());
             return FDTD_OK;
         }
         int dev = 0, max_persist = 0, max_window = 0;
