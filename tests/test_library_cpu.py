@@ -163,3 +163,14 @@ def test_oracle_config_mirror_matches_its_c_struct(tmp_path):
                            names, extra_flags=("-Wno-unused-function", "-fopenmp"))
     assert size == C.sizeof(O.OrConfig)
     assert offs == [getattr(O.OrConfig, n).offset for n in names]
+
+
+def test_library_exports_every_surrogate_header_symbol():
+    src = open(os.path.join(ROOT, "include", "surrogate.h")).read()
+    syms = sorted(set(re.findall(r"\b(nn_[a-z0-9_]+)\s*\(", src)))
+    assert syms, "no declarations found"
+    L = B.load()
+    for name in syms:
+        assert hasattr(L, name), name
+    from paper_2203_01462_gb300 import surrogate as S
+    assert sorted(S._FNS) == syms
