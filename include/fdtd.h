@@ -22,15 +22,16 @@
  *                dW~/drho (ascent direction; the paper maximises W~).
  *
  * Ownership: the caller owns every device buffer.  The library allocates no
- * device memory; it carves all of its state out of the caller's workspace
+ * device memory (one mapped word of pinned host memory per context carries
+ * the stability guard's flag); it carves all of its state out of the caller's workspace
  * (size from fdtd_workspace_bytes) and enqueues all work on the caller's
  * CUDA stream.  A context is used by one host thread and one stream at a
  * time.  Pointers named d_* are device pointers, h_* host pointers.
  *
  * Errors: every entry point returns an fdtd_status; nothing throws or aborts
  * across the ABI.  Calls out of order return FDTD_ESTATE.  Device-side
- * checks (density outside [0,1], a non-finite objective) set an error word
- * that fdtd_sync reports.
+ * checks (density outside [0,1], a non-finite objective, the stability
+ * guard) set an error word that fdtd_sync reports.
  *
  * Units: SI.  W~ follows Eq. (24) literally (eps_g dt dx^d / 2 times the sum
  * of |E|^2 over the gap nodes and steps n = 0..N; d = 2 in 2D, per unit
@@ -57,7 +58,9 @@ typedef enum fdtd_status {
     FDTD_ENOMEM = 2,     /* workspace smaller than fdtd_workspace_bytes       */
     FDTD_ECUDA = 3,      /* a CUDA runtime call failed                         */
     FDTD_ESTATE = 4,     /* call out of order (e.g. adjoint before forward)    */
-    FDTD_EUNSTABLE = 5,  /* non-finite objective (unstable run)                */
+    FDTD_EUNSTABLE = 5,  /* unstable run: a non-finite objective, or a state
+                            word non-finite or above the stability-guard
+                            bound (fdtd_set_stability_guard)                 */
     FDTD_ETIMEOUT = 6,   /* reserved: a bounded device wait gave up           */
     FDTD_ERANGE = 7      /* a design density outside [0, 1]                    */
 } fdtd_status;
@@ -175,6 +178,11 @@ typedef struct fdtd_info {
     long long launches;           /* kernels launched since create             */
     long long cell_updates;       /* cells x steps advanced since create       */
     size_t workspace_bytes;
+    long long step_blocks;        /* 2D E_z: thread blocks of one step launch  */
+    long long vector_blocks;      /* 2D E_z: of those, blocks whose tile and
+                                     its one-node halo are clear of walls and
+                                     CPML, which run the 16-byte vector path;
+                                     0 and 0 in the other modes                */
 } fdtd_info;
 
 /* Bytes of device workspace a context for cfg needs (256-byte aligned
@@ -216,8 +224,25 @@ fdtd_status fdtd_set_damping(fdtd_ctx *ctx, double sigma_max, double gamma_scale
 enum { FDTD_TERM_PSI = 1, FDTD_TERM_EPS = 2, FDTD_TERM_SIGMA = 4, FDTD_TERM_ALL = 7 };
 fdtd_status fdtd_set_sensitivity_terms(fdtd_ctx *ctx, int terms);
 
+/* Stability guard of the forward solve.  Every `every` forward steps (0:
+ * off; default 256) a read-only kernel checks every word of the solver
+ * state (E, H, J and the CPML terms) and flags a word that is not finite or
+ * whose magnitude exceeds `max_abs` (field units; 0: automatic, 1e3 x N x
+ * src_amp x S x the number of bands, i.e. a thousand times the field that
+ * every step's source increment could build up, which no passive
+ * configuration approaches).  A flagged run is reported as FDTD_EUNSTABLE:
+ * fdtd_forward returns it as soon as the host loop that enqueues the steps
+ * sees the flag (through one mapped word of pinned host memory per context)
+ * and stops enqueuing, after waiting for the steps already enqueued; when
+ * the pass replays as a CUDA graph, fdtd_sync reports it at the end.  The
+ * error word is then cleared, and the context can take a new design or new
+ * settings.  The checks read the state once per `every` steps (0.2 % of the
+ * forward traffic at the default) and change no result. */
+fdtd_status fdtd_set_stability_guard(fdtd_ctx *ctx, int every, double max_abs);
+
 /* Forward solve of N steps.  Writes W~ (Eq. 24) to d_W (device, one double;
- * may be NULL) asynchronously.  Requires fdtd_set_design. */
+ * may be NULL) asynchronously.  Requires fdtd_set_design.  Returns
+ * FDTD_EUNSTABLE when the stability guard stopped the pass (no W~). */
 fdtd_status fdtd_forward(fdtd_ctx *ctx, double *d_W);
 
 /* Adjoint solve (Eq. 20) with the sensitivity accumulation of Eq. (25).
@@ -237,10 +262,13 @@ fdtd_status fdtd_gradient(fdtd_ctx *ctx, double *d_grad, size_t n);
  * that loads the library, kept until the process exits) instead of the
  * context's workspace; nothing is allocated.  For callers that cannot hand
  * out or grow device memory at call time.  The paper has no counterpart.
- * Returns FDTD_EINVAL if n exceeds FDTD_STATIC_DESIGN_MAX.  The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current, so make that first call before any stream capture.
- * All calls share the array: calls that overlap on the GPU race on it. */
+ * Only a 2D E_z context with a design filter uses the array: for it, n above
+ * FDTD_STATIC_DESIGN_MAX returns FDTD_EINVAL; the other contexts need no
+ * intermediates and take any n.  Call it with the device that created the
+ * context current (otherwise FDTD_EINVAL).  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current, so make that first call before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU race on it. */
 fdtd_status fdtd_gradient_static(fdtd_ctx *ctx, double *d_grad, size_t n);
 
 /* Gap-field history E^n, n = 0..N, of the last forward run into d_out
@@ -359,7 +387,8 @@ fdtd_status fdtd_set_graphs(fdtd_ctx *ctx, int mode);
 fdtd_status fdtd_set_l2_residency(fdtd_ctx *ctx, double fraction);
 
 /* Wait for the context's stream and report (then clear) device-side errors:
- * FDTD_ERANGE, FDTD_EUNSTABLE, or FDTD_ECUDA for a failed kernel. */
+ * FDTD_ERANGE, FDTD_EUNSTABLE (a non-finite objective, or the stability
+ * guard's flag), or FDTD_ECUDA for a failed kernel. */
 fdtd_status fdtd_sync(fdtd_ctx *ctx);
 
 /* One whole design evaluation from host memory: copies h_rho (M_d values in

@@ -27,7 +27,7 @@ EXPORTS = ["fdtd_workspace_bytes", "fdtd_create", "fdtd_set_design", "fdtd_set_d
            "fdtd_run_host", "fdtd_get_info", "fdtd_status_string", "fdtd_destroy",
            "fdtd_gradient_static", "fdtd_gap_spectrum", "fdtd_ascent_step", "fdtd_mma_asymptotes", "fdtd_mma_solve",
            "fdtd_mirror_average", "fdtd_fix_design", "fdtd_grayness", "fdtd_threshold", "fdtd_set_graphs",
-           "fdtd_set_l2_residency", "fdtd_set_sensitivity_terms"]
+           "fdtd_set_l2_residency", "fdtd_set_sensitivity_terms", "fdtd_set_stability_guard"]
 
 
 TERM_PSI, TERM_EPS, TERM_SIGMA, TERM_ALL = 1, 2, 4, 7
@@ -64,7 +64,8 @@ class FdtdConfig(C.Structure):
 class FdtdInfo(C.Structure):
     _fields_ = [("dt", C.c_double), ("n_cells", C.c_longlong), ("n_design", C.c_longlong),
                 ("n_gap", C.c_longlong), ("launches", C.c_longlong), ("cell_updates", C.c_longlong),
-                ("workspace_bytes", C.c_size_t)]
+                ("workspace_bytes", C.c_size_t), ("step_blocks", C.c_longlong),
+                ("vector_blocks", C.c_longlong)]
 
 
 _lock = threading.Lock()
@@ -101,6 +102,7 @@ def load():
             "fdtd_set_graphs": [P, C.c_int],
             "fdtd_set_l2_residency": [P, C.c_double],
             "fdtd_set_sensitivity_terms": [P, C.c_int],
+            "fdtd_set_stability_guard": [P, C.c_int, C.c_double],
             "fdtd_threshold": [P, P, C.c_size_t, C.c_double],
             "fdtd_gap_history": [P, P, C.c_size_t],
             "fdtd_sync": [P],
@@ -190,6 +192,10 @@ class Solver:
         self.n_gap = int(inf.n_gap)
         self.dt = float(inf.dt)
         self._W = torch.zeros(1, dtype=torch.float64, device=self.device)
+        # Counts calls that change the solver's state (set_design,
+        # set_damping, forward); the autograd wrapper compares it to find out
+        # whether the solver still holds the forward run it needs.
+        self.generation = 0
 
     def close(self) -> None:
         if getattr(self, "ctx", None):
@@ -214,13 +220,16 @@ class Solver:
         if r.numel() != self.n_design:
             raise ValueError("rho has %d entries, design box has %d" % (r.numel(), self.n_design))
         self._rho = r
+        self.generation += 1
         _check(self.lib.fdtd_set_design(self.ctx, C.c_void_p(r.data_ptr()), r.numel()), "fdtd_set_design")
 
     def set_damping(self, sigma_max: float = 0.0, gamma_scale: float = 1.0) -> None:
+        self.generation += 1
         _check(self.lib.fdtd_set_damping(self.ctx, float(sigma_max), float(gamma_scale)), "fdtd_set_damping")
 
     def forward(self, out=None):
         out = self._W if out is None else out
+        self.generation += 1
         _check(self.lib.fdtd_forward(self.ctx, C.c_void_p(out.data_ptr())), "fdtd_forward")
         return out
 
@@ -269,6 +278,11 @@ class Solver:
         """Eq. (25) terms the adjoint accumulates: an OR of TERM_PSI, TERM_EPS,
         TERM_SIGMA (default TERM_ALL, the gradient of W~)."""
         _check(self.lib.fdtd_set_sensitivity_terms(self.ctx, int(terms)), "fdtd_set_sensitivity_terms")
+
+    def set_stability_guard(self, every: int = 256, max_abs: float = 0.0) -> None:
+        """Check the forward state every ``every`` steps (0: off) for words that
+        are not finite or exceed ``max_abs`` (0: the automatic bound)."""
+        _check(self.lib.fdtd_set_stability_guard(self.ctx, int(every), float(max_abs)), "fdtd_set_stability_guard")
 
     def set_graphs(self, mode: int) -> None:
         """0: plain launches, 1: replay CUDA graphs of whole passes, 2: automatic by grid size."""

@@ -76,6 +76,16 @@ fdtd_status validate(const fdtd_config *c)
         return FDTD_EINVAL;
     if (c->ndim == 3 && (c->filter_radius != 0 || c->src_comp < 0 || c->src_comp > 2)) return FDTD_EINVAL;
     if (!(c->dx > 0) || !(c->courant > 0) || c->courant >= 1.0 / sqrt((double)c->ndim)) return FDTD_EINVAL;
+    {
+        // The Courant limit holds in every medium of the grid: light is
+        // 1/sqrt(eps) slower, so S sqrt(d) < sqrt(eps) for the background,
+        // the gap, the metal's high-frequency limit eps_inf (design nodes
+        // lie between eps_s and eps_inf; the Drude and sigma terms only add
+        // to the effective permittivity) and a 3D substrate.
+        double emin = std::min(std::min(c->eps_s, c->eps_g), c->eps_inf);
+        if (c->ndim == 3 && c->sub_hi > 0) emin = std::min(emin, c->sub_eps);
+        if (!(emin > 0) || c->courant * sqrt((double)c->ndim) >= sqrt(emin)) return FDTD_EINVAL;
+    }
     if (c->nsteps < 1) return FDTD_EINVAL;
     if (!(c->omega_p > 0) || !(c->psi_s_ratio > 0) || c->gamma_p < 0) return FDTD_EINVAL;
     if (!(c->eps_s > 0) || !(c->eps_g > 0) || !(c->eps_inf > 0)) return FDTD_EINVAL;
@@ -198,11 +208,54 @@ struct fdtd_ctx {
         int curF = 0, curA = 0;
     } cap[2];
     cudaStream_t capture_stream = nullptr;  // private stream the passes are captured on
+    bool capturing = false;                 // a pass is being recorded into a graph
+    // Stability guard (fdtd_set_stability_guard): every guard_every forward
+    // steps a read-only kernel checks the whole state for non-finite words
+    // or magnitudes above the bound.  The host loop that enqueues the steps
+    // polls a mapped host word the kernel writes and stops enqueuing once it
+    // sees this pass's tag (not possible while capturing a graph; the error
+    // word still reports the instability).
+    int guard_every = 256;
+    double guard_bound = 0.0;  // 0: automatic, see guard_limit()
+    unsigned guard_tag = 0;
+    unsigned *guard_host = nullptr, *guard_host_dev = nullptr;
+    bool guarding = false, guard_stop = false;
     virtual ~fdtd_ctx()
     {
         for (auto &c : cap)
             if (c.exec) cudaGraphExecDestroy(c.exec);
         if (capture_stream) cudaStreamDestroy(capture_stream);
+        if (guard_host) cudaFreeHost(guard_host);
+    }
+    void drop_graphs()
+    {
+        for (auto &c : cap)
+            if (c.exec) {
+                cudaGraphExecDestroy(c.exec);
+                c = Captured{};
+            }
+    }
+    // Bound on |state word|: the set one, else 1e3 x N x the largest field
+    // increment the source gives in one step (src_amp S per band).  A
+    // passive medium cannot come near it; growth past it is an instability.
+    double guard_limit() const
+    {
+        double b = guard_bound > 0.0 ? guard_bound
+                                     : 1e3 * cfg.nsteps * fabs(cfg.src_amp) * cfg.courant * (double)cfg.nbands;
+        if (cfg.real_bytes == 4 && !(b < 1e37)) b = 1e37;
+        return b;
+    }
+    // Called by the forward loops after `done` steps of the current pass.
+    // Returns true once the pass should stop (instability seen by the host).
+    template <typename R>
+    bool guard_after(int done, const void *state, size_t state_bytes)
+    {
+        if (!guarding || guard_every <= 0 || done % guard_every != 0) return guard_stop;
+        launch_guard<R>((const R *)state, (long long)(state_bytes / sizeof(R)), guard_limit(), err_dev(),
+                        capturing ? nullptr : guard_host_dev, guard_tag, stream);
+        ++launches;
+        if (!capturing && guard_host && *(volatile unsigned *)guard_host == guard_tag) guard_stop = true;
+        return guard_stop;
     }
     virtual fdtd_status carve(Carver &cv) = 0;
     virtual fdtd_status upload_tables() = 0;
@@ -214,10 +267,15 @@ struct fdtd_ctx {
     virtual fdtd_status gap_spectrum(const double *d_freqs, int nf, double *d_out) = 0;
     // fdtd_gradient with the filter-transpose intermediates in s1, s2.
     virtual fdtd_status gradient_scratch(double *d_grad, double *s1, double *s2) = 0;
+    // True when gradient_scratch uses s1, s2 (the filter-transpose passes).
+    virtual bool gradient_uses_scratch() const { return false; }
+    int device = -1;  // the device current at fdtd_create
     // Optimization-loop helpers.
     virtual fdtd_status grayness(double *d_zeta) = 0;
     // L2 residency of the ping-pong state (2D E_z contexts; others ignore it).
     virtual fdtd_status set_l2(double) { return FDTD_OK; }
+    // Blocks of one step launch and how many take the vector path (2D E_z).
+    virtual void block_counts(long long *total, long long *vec) const { *total = *vec = 0; }
     long long n_free = 0;  // design nodes outside the gap
     virtual void *rho_stage() = 0;
     virtual double *grad_stage() = 0;
@@ -262,7 +320,9 @@ fdtd_status run_pass(fdtd_ctx *c, int which, int &curF, int &curA, F &&enqueue)
             c->stream = user;
             return s;
         }
+        c->capturing = true;
         s = enqueue();
+        c->capturing = false;
         cudaGraph_t graph = nullptr;
         const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
         c->stream = user;
@@ -396,6 +456,7 @@ struct Ctx2D final : fdtd_ctx {
     cudaAccessPolicyWindow win = {};
     bool l2 = false;
     const cudaAccessPolicyWindow *winF() const { return l2 ? &win : nullptr; }
+    void block_counts(long long *total, long long *vec) const override { step2d_block_counts(geo, total, vec); }
     // Give back the persisting set-aside and demote the lines already marked
     // persisting (best effort for the latter).
     fdtd_status release_l2()
@@ -635,8 +696,9 @@ struct Ctx2D final : fdtd_ctx {
             a.rec = rec_base ? rec_base + (size_t)(n - n0) * Mdi : nullptr;
             launches += launch_step2d<R>(0, geo, F[curF], F[curF ^ 1], coef_slot, px, py, a, stream, winF());
             curF ^= 1;
+            cell_updates += ncells;
+            if (guard_after<R>(n + 1, F_base[curF], state_bytes)) break;
         }
-        cell_updates += (long long)count * ncells;
     }
 
     // Adjoint steps for m = m_hi down to m_lo + 1 (adjoint step N - m), the
@@ -670,16 +732,20 @@ struct Ctx2D final : fdtd_ctx {
         launch_zero_bytes(F_base[1], state_bytes, st);
         if (Mg) launch_zero_bytes(gap_hist, Mg * sizeof(R), st);
         launches += 3;
+        guarding = true;
         if (K <= 0) {
             advance_forward(0, N, true, rec);
         } else {
             for (int s = 0; s < nsnap; ++s) {
+                if (guard_stop) break;
                 const int n0 = s * K, cnt = std::min(K, N - n0);
                 snapshot_save<R>(cfg.snapshot_dtype, F_base[curF], state_bytes, snaps + (size_t)s * snap_stride, st);
                 ++launches;
                 advance_forward(n0, cnt, true, nullptr);
             }
         }
+        guarding = false;
+        if (guard_stop) return FDTD_EUNSTABLE;
         const double coefW = 0.5 * cfg.eps_g * dt * pow(cfg.dx, cfg.ndim);
         launch_objective<R>(gap_hist, (long long)(N + 1) * Mg, coefW, misc, nullptr, misc + 4, err, st);
         ++launches;
@@ -768,6 +834,7 @@ struct Ctx2D final : fdtd_ctx {
         return check_launch();
     }
 
+    bool gradient_uses_scratch() const override { return cfg.filter_radius > 0; }
     fdtd_status gradient_scratch(double *d_grad, double *s1, double *s2) override
     {
         cudaStream_t st = stream;
@@ -999,8 +1066,9 @@ struct CtxP final : fdtd_ctx {
             a.rec[0] = slot;
             a.rec[1] = slot ? slot + geo.Mdi[0] : nullptr;
             launches += launch_stepp<R>(0, geo, F, coef_slot, pm, a, stream);
+            cell_updates += ncells;
+            if (guard_after<R>(n + 1, F_base, state_bytes)) break;
         }
-        cell_updates += (long long)count * ncells;
     }
 
     void advance_adjoint(int m_hi, int m_lo, int slot0)
@@ -1025,16 +1093,20 @@ struct CtxP final : fdtd_ctx {
         launch_zero_bytes(F_base, state_bytes, st);
         if (Mg) launch_zero_bytes(gap_hist, Mg * sizeof(R), st);
         launches += 2;
+        guarding = true;
         if (K <= 0) {
             advance_forward(0, N, true, rec);
         } else {
             for (int s = 0; s < nsnap; ++s) {
+                if (guard_stop) break;
                 const int n0 = s * K, cnt = std::min(K, N - n0);
                 snapshot_save<R>(cfg.snapshot_dtype, F_base, state_bytes, snaps + (size_t)s * snap_stride, st);
                 ++launches;
                 advance_forward(n0, cnt, true, nullptr);
             }
         }
+        guarding = false;
+        if (guard_stop) return FDTD_EUNSTABLE;
         const double coefW = 0.5 * cfg.eps_g * dt * cfg.dx * cfg.dx;
         launch_objective<R>(gap_hist, (long long)(N + 1) * Mg, coefW, misc, nullptr, misc + 4, err, st);
         ++launches;
@@ -1294,8 +1366,9 @@ struct Ctx3D final : fdtd_ctx {
             a.rec = rec_base ? rec_base + (size_t)(n - n0) * 3 * Mdi : nullptr;
             a.tf_inc = tf_tab ? tf_tab + (size_t)n * tfsf_row(geo) : nullptr;
             launches += launch_step3d<R>(0, geo, F, coef_slot, pm, a, stream);
+            cell_updates += ncells;
+            if (guard_after<R>(n + 1, F_base, state_bytes)) break;
         }
-        cell_updates += (long long)count * ncells;
     }
 
     void advance_adjoint(int m_hi, int m_lo, int slot0)
@@ -1318,16 +1391,20 @@ struct Ctx3D final : fdtd_ctx {
         launch_zero_bytes(F_base, state_bytes, st);
         if (Mg) launch_zero_bytes(gap_hist, 3 * Mg * sizeof(R), st);
         launches += 2;
+        guarding = true;
         if (K <= 0) {
             advance_forward(0, N, true, rec);
         } else {
             for (int s = 0; s < nsnap; ++s) {
+                if (guard_stop) break;
                 const int n0 = s * K, cnt = std::min(K, N - n0);
                 snapshot_save<R>(cfg.snapshot_dtype, F_base, state_bytes, snaps + (size_t)s * snap_stride, st);
                 ++launches;
                 advance_forward(n0, cnt, true, nullptr);
             }
         }
+        guarding = false;
+        if (guard_stop) return FDTD_EUNSTABLE;
         const double coefW = 0.5 * cfg.eps_g * dt * pow(cfg.dx, 3);
         launch_objective<R>(gap_hist, (long long)(N + 1) * 3 * Mg, coefW, misc, nullptr, misc + 4, err, st);
         ++launches;
@@ -1405,7 +1482,8 @@ const char *fdtd_status_string(fdtd_status s)
     case FDTD_ENOMEM: return "workspace too small";
     case FDTD_ECUDA: return "CUDA error";
     case FDTD_ESTATE: return "call out of order";
-    case FDTD_EUNSTABLE: return "non-finite objective (unstable run)";
+    case FDTD_EUNSTABLE: return "unstable run: non-finite objective, or a state word non-finite or above the "
+                                "stability-guard bound";
     case FDTD_ETIMEOUT: return "device wait timed out";
     case FDTD_ERANGE: return "design density outside [0, 1]";
     }
@@ -1492,6 +1570,19 @@ fdtd_status fdtd_create(const fdtd_config *cfg, void *d_workspace, size_t bytes,
     }
     c->stream = (cudaStream_t)stream;
     c->ws = d_workspace;
+    cudaGetDevice(&c->device);
+    // One mapped host word for the stability guard's early stop (host
+    // memory; without it the guard still reports through the error word).
+    if (cudaHostAlloc((void **)&c->guard_host, sizeof(unsigned), cudaHostAllocMapped) == cudaSuccess) {
+        *c->guard_host = 0;
+        if (cudaHostGetDevicePointer((void **)&c->guard_host_dev, c->guard_host, 0) != cudaSuccess) {
+            cudaFreeHost(c->guard_host);
+            c->guard_host = c->guard_host_dev = nullptr;
+        }
+    } else {
+        c->guard_host = nullptr;
+    }
+    cudaGetLastError();
 
     c->ws_bytes = bytes;
     Carver cv(d_workspace);
@@ -1525,6 +1616,15 @@ fdtd_status fdtd_set_damping(fdtd_ctx *ctx, double sigma_max, double gamma_scale
     return FDTD_OK;
 }
 
+fdtd_status fdtd_set_stability_guard(fdtd_ctx *ctx, int every, double max_abs)
+{
+    if (!ctx || every < 0 || !(max_abs >= 0) || !isfinite(max_abs)) return FDTD_EINVAL;
+    ctx->guard_every = every;
+    ctx->guard_bound = max_abs;
+    ctx->drop_graphs();  // a captured forward pass holds the old checks
+    return FDTD_OK;
+}
+
 fdtd_status fdtd_set_sensitivity_terms(fdtd_ctx *ctx, int terms)
 {
     if (!ctx || terms < 1 || terms > FDTD_TERM_ALL) return FDTD_EINVAL;
@@ -1538,7 +1638,20 @@ fdtd_status fdtd_forward(fdtd_ctx *ctx, double *d_W)
     if (!ctx) return FDTD_EINVAL;
     if (!ctx->has_design) return FDTD_ESTATE;
     ctx->fwd_done = ctx->adj_done = false;
-    FDTD_TRY(ctx->forward(d_W));
+    ctx->guard_tag = ctx->guard_tag + 1 ? ctx->guard_tag + 1 : 1;
+    ctx->guard_stop = false;
+    const fdtd_status s = ctx->forward(d_W);
+    if (s == FDTD_EUNSTABLE) {
+        // The stability guard stopped the pass: let the steps already
+        // enqueued finish, then clear the error word so that the context
+        // stays usable.
+        cudaStreamSynchronize(ctx->stream);
+        launch_zero_bytes(ctx->err_dev(), sizeof(unsigned), ctx->stream);
+        ++ctx->launches;
+        FDTD_TRY(cuda_ok(cudaStreamSynchronize(ctx->stream)));
+        return s;
+    }
+    FDTD_TRY(s);
     ctx->fwd_done = true;
     return FDTD_OK;
 }
@@ -1561,9 +1674,12 @@ fdtd_status fdtd_gradient(fdtd_ctx *ctx, double *d_grad, size_t n)
 
 }  // extern "C"
 
+int fdtd::context_device(const fdtd_ctx *ctx) { return ctx ? ctx->device : -1; }
+
 int fdtd::gradient_into(fdtd_ctx *ctx, double *d_grad, size_t n, double *scratch, size_t scratch_per_array)
 {
-    if (!ctx || !d_grad || !scratch || (long long)n != ctx->Md || n > scratch_per_array) return FDTD_EINVAL;
+    if (!ctx || !d_grad || !scratch || (long long)n != ctx->Md) return FDTD_EINVAL;
+    if (ctx->gradient_uses_scratch() && n > scratch_per_array) return FDTD_EINVAL;
     if (!ctx->adj_done) return FDTD_ESTATE;
     return ctx->gradient_scratch(d_grad, scratch, scratch + scratch_per_array);
 }
@@ -1730,6 +1846,7 @@ fdtd_status fdtd_get_info(const fdtd_ctx *ctx, fdtd_info *info)
     info->launches = ctx->launches;
     info->cell_updates = ctx->cell_updates;
     info->workspace_bytes = ctx->ws_bytes;
+    ctx->block_counts(&info->step_blocks, &info->vector_blocks);
     return FDTD_OK;
 }
 

@@ -9,7 +9,7 @@
 namespace fdtd {
 
 // Device error word bits (reported by fdtd_sync).
-enum : unsigned { ERR_RANGE = 1u, ERR_NONFINITE = 2u };
+enum : unsigned { ERR_RANGE = 1u, ERR_NONFINITE = 2u, ERR_UNSTABLE = 4u };
 
 // Geometry of a 2D TM_z grid: Ez, Hx, Hy on nx x ny nodes with row pitch px
 // (elements).  Hx[j][i] sits at (i, j + 1/2), Hy[j][i] at (i + 1/2, j).
@@ -90,7 +90,13 @@ template <typename R>
 int launch_step2d(int mode, const Geo2D &g, const State2D<R> &in, const State2D<R> &out, int coef_slot,
                   const Pml1D<R> &px, const Pml1D<R> &py, const Step2D<R> &a, cudaStream_t st, const cudaAccessPolicyWindow *win);
 
+// Blocks of one 2D step launch, and how many of them take the vector path.
+void step2d_block_counts(const Geo2D &g, long long *total, long long *vector);
+
 // Auxiliary kernels (kernels_aux.cu).
+template <typename R>
+void launch_guard(const R *state, long long n, double bound, unsigned *err, unsigned *host_flag, unsigned tag,
+                  cudaStream_t st);
 template <typename R>
 void launch_copy_check_rho(const R *src, R *dst, long long n, unsigned *err, cudaStream_t st);
 template <typename T>
@@ -287,8 +293,11 @@ void launch_zero_bytes(void *dst, size_t bytes, cudaStream_t st);
 struct fdtd_ctx;
 namespace fdtd {
 // The gradient of fdtd_gradient with the two filter-transpose intermediates
-// taken from `scratch` (at least 2 * n doubles of device memory) instead of
-// the workspace (fdtd_host.cu).
+// taken from `scratch` (two arrays of scratch_per_array doubles of device
+// memory) instead of the workspace (fdtd_host.cu).  Only a 2D E_z context
+// with a design filter uses them, and only it needs n <= scratch_per_array.
 // Returns an fdtd_status value.
 int gradient_into(fdtd_ctx *ctx, double *d_grad, size_t n, double *scratch, size_t scratch_per_array);
+// The device that was current when the context was created.
+int context_device(const fdtd_ctx *ctx);
 }  // namespace fdtd

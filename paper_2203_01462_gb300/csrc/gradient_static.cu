@@ -14,7 +14,10 @@
 // the library (FDTD_STATIC_DESIGN_MAX doubles twice, 16 MiB).  Calls share
 // it: two calls that overlap on the GPU (different streams or contexts at
 // the same time) race on it.  Each call overwrites the part it uses before
-// reading it, so nothing has to start at zero.
+// reading it, so nothing has to start at zero.  Only a 2D E_z context with a
+// design filter goes through the array, so only its design box is limited
+// to FDTD_STATIC_DESIGN_MAX; the other contexts assemble their gradient
+// directly and take any size.
 #include <mutex>
 
 #include "../../include/fdtd.h"
@@ -49,7 +52,11 @@ fdtd_status scratch_on_current_device(double **out)
 extern "C" fdtd_status fdtd_gradient_static(fdtd_ctx *ctx, double *d_grad, size_t n)
 {
     if (!ctx || !d_grad) return FDTD_EINVAL;
-    if (n > (size_t)FDTD_STATIC_DESIGN_MAX) return FDTD_EINVAL;  // design box larger than the fixed scratch
+    // The array's address is looked up per device: the context's device must
+    // be the current one, or the kernels would get another GPU's copy.
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FDTD_ECUDA;
+    if (dev != fdtd::context_device(ctx)) return FDTD_EINVAL;
     double *scratch = nullptr;
     const fdtd_status s = scratch_on_current_device(&scratch);
     if (s != FDTD_OK) return s;

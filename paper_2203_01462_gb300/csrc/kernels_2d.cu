@@ -35,6 +35,14 @@ constexpr int TILE_X = BX * VX;
 
 __device__ __forceinline__ bool in_range(int v, int lo, int n) { return (unsigned)(v - lo) < (unsigned)n; }
 
+// Vector path for blocks none of whose read nodes (x0-1 .. x0+TILE_X,
+// y0-1 .. y0+BY) is a wall or CPML node (uniform across the block).  The
+// host counts blocks with the same predicate (step2d_block_counts).
+__host__ __device__ __forceinline__ bool vector_tile(int nx, int ny, int np, int x0, int y0)
+{
+    return x0 - 1 >= np + 1 && x0 + TILE_X <= nx - np - 2 && y0 - 1 >= np + 1 && y0 + BY <= ny - np - 2;
+}
+
 // Programmatic dependent launch: the step kernels are launched with
 // programmatic stream serialisation, so a step's blocks may be scheduled
 // while the previous step drains; they wait here, before touching any state,
@@ -199,12 +207,7 @@ __device__ __forceinline__ void step2d_body(const Geo2D &g, const State2D<R> &in
     const int nx = g.nx, ny = g.ny, np = g.npml, P = g.px;
     const R S = c.S;
 
-    // Vector path for blocks none of whose read nodes (x0-1 .. x0+TILE_X,
-    // y0-1 .. y0+BY) is a wall or CPML node (uniform across the block).
-    const bool interior =
-        x0 - 1 >= np + 1 && x0 + TILE_X <= nx - np - 2 && y0 - 1 >= np + 1 && y0 + BY <= ny - np - 2;
-
-    if (interior) {
+    if (vector_tile(nx, ny, np, x0, y0)) {
         const int q = j * P + i0;
         R e[4], eN[4], eS[4], hx[4], hxS[4], hy[4];
         ld4(in.Ez + q, e);
@@ -323,6 +326,16 @@ __global__ void __launch_bounds__(BX *BY, 10)
 }
 
 }  // namespace
+
+void step2d_block_counts(const Geo2D &g, long long *total, long long *vector)
+{
+    const int gx = (g.nx + TILE_X - 1) / TILE_X, gy = (g.ny + BY - 1) / BY;
+    long long v = 0;
+    for (int by = 0; by < gy; ++by)
+        for (int bx = 0; bx < gx; ++bx) v += vector_tile(g.nx, g.ny, g.npml, bx * TILE_X, by * BY) ? 1 : 0;
+    *total = (long long)gx * gy;
+    *vector = v;
+}
 
 template <typename R>
 int launch_step2d(int mode, const Geo2D &g, const State2D<R> &in, const State2D<R> &out, int c,

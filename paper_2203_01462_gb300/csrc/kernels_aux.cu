@@ -32,6 +32,26 @@ __global__ void k_copy_check_rho(const R *src, R *dst, long long n, unsigned *er
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_RANGE);
 }
 
+// Stability guard: flag a state word that is not finite or exceeds `bound`
+// in magnitude.  Sets ERR_UNSTABLE in the device error word and, when
+// `host_flag` (a mapped host word) is given, writes `tag` there so that the
+// host loop that enqueues the steps can stop early.  Reads only.
+template <typename R>
+__global__ void k_guard(const R *state, long long n, R bound, unsigned *err, unsigned *host_flag, unsigned tag)
+{
+    bool bad = false;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        bad |= !(fabs(state[k]) <= bound);  // also catches NaN
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) {
+        atomicOr(err, ERR_UNSTABLE);
+        if (host_flag) {
+            *(volatile unsigned *)host_flag = tag;
+            __threadfence_system();
+        }
+    }
+}
+
 // One separable pass of the normalised Gaussian filter along x (rows) or y
 // (columns) of a w x h design array.  Forward:  out[i] = inv_norm[i] *
 // sum_k wts[k] in[i + k].  Transpose: out[i] = sum_k wts[k] inv_norm[i + k]
@@ -270,6 +290,16 @@ void launch_copy_check_rho(const R *src, R *dst, long long n, unsigned *err, cud
 {
     k_copy_check_rho<R><<<blocks_for(n), TPB, 0, st>>>(src, dst, n, err);
 }
+
+template <typename R>
+void launch_guard(const R *state, long long n, double bound, unsigned *err, unsigned *host_flag, unsigned tag,
+                  cudaStream_t st)
+{
+    k_guard<R><<<blocks_for(n, TPB, 152 * 8), TPB, 0, st>>>(state, n, (R)bound, err, host_flag, tag);
+}
+template void launch_guard<float>(const float *, long long, double, unsigned *, unsigned *, unsigned, cudaStream_t);
+template void launch_guard<double>(const double *, long long, double, unsigned *, unsigned *, unsigned,
+                                   cudaStream_t);
 
 template <typename T>
 void launch_filter_rows(const T *in, T *out, int w, int h, int R_, const T *wts, const T *inv_norm,

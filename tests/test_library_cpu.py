@@ -72,6 +72,31 @@ def test_bad_configurations_rejected(bad):
     assert e.value.status == 1
 
 
+@pytest.mark.parametrize("medium,ok", [
+    (dict(eps_s=0.4), False),    # background: S sqrt(2) = 0.71 > sqrt(0.4) = 0.63
+    (dict(eps_g=0.45), False),   # gap medium
+    (dict(eps_inf=0.3), False),  # the metal's high-frequency limit
+    (dict(eps_s=0.55), True),    # sqrt(0.55) = 0.74: still inside the limit
+    (dict(eps_inf=4.469), True),
+])
+def test_courant_limit_checked_in_every_medium(medium, ok):
+    """Light is 1/sqrt(eps) slower in a medium of permittivity eps, so the
+    Courant limit S sqrt(d) < 1 of vacuum becomes S sqrt(d) < sqrt(eps): a
+    configuration that breaks it in any of its media is refused."""
+    w = dict(I.small_2d(), **medium)
+    if ok:
+        assert B.workspace_bytes(w) > 0
+    else:
+        with pytest.raises(B.FdtdError) as e:
+            B.workspace_bytes(w)
+        assert e.value.status == 1
+    w3 = I.workload_3d(21, 19, 31, dx=20e-9, nsteps=10, npml=4, design=(9, 7, 6), gap=(2, 2, 2), substrate=True,
+                       courant=0.5)
+    assert B.workspace_bytes(w3) > 0
+    with pytest.raises(B.FdtdError):
+        B.workspace_bytes(dict(w3, sub_eps=0.7))  # 0.5 sqrt(3) = 0.87 > sqrt(0.7) = 0.84
+
+
 def test_grid_beyond_32_bit_indexing_rejected():
     """The 2D step kernel indexes one array with 32-bit integers: a grid of
     2^31 or more padded nodes is refused before anything is allocated."""
