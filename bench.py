@@ -1,12 +1,16 @@
 #!/usr/bin/env python3
 """Throughput of the FDTD + Drude adjoint hot path on one GB300 (or N replicas).
 
-One bench step = one design evaluation on the 2048 x 2048 FP32 workload:
-set_design (5-cell Gaussian filter) -> forward (20000 steps, FP32 snapshots
-every 64 steps) -> adjoint (segment recompute + adjoint + fused
-sensitivities) -> gradient.  The metric counts forward + adjoint
-cell-updates (2 x cells x steps per evaluation); recompute sweeps are
-work the method pays but are not counted there (the "raw" key counts them).
+One bench step = one design evaluation of the 3D 256^3 FP32 workload:
+set_design -> forward (10000 steps of the Yee + Drude + CPML leapfrog, an
+x-polarised plane wave injected through a total-field / scattered-field
+box, BF16 checkpoints every 32 steps) -> adjoint (segment recompute +
+adjoint + fused sensitivities) -> gradient.  It is the largest workload
+whose 20 + 5 evaluations fit a few minutes; the 512 x 512 x 384 one (about
+a minute per evaluation) and the 2D ones run with --workload.  The metric
+counts forward + adjoint cell-updates (2 x cells x steps per evaluation);
+recompute sweeps are work the method pays but are not counted there (the
+"raw" key counts them).
 
 Timing: CUDA events on the solver's stream around each step, L2 flushed
 (a 256 MB write) between steps outside the events, max over ranks.  Under
@@ -36,12 +40,12 @@ from paper_2203_01462_gb300 import inputs as I  # noqa: E402
 
 METRIC = "Gcell-updates/s fwd+adjoint"
 UNIT = "Gcell-updates/s"
-# Bounded oracle samples, in grid-node time steps of the forward run: the
-# 2048^2 workload cut to 300 steps (about 7 s on 16 host cores, forward +
-# adjoint) for the cpu_baseline key, and to 200 steps per reference-arm
-# evaluation.  Larger grids get proportionally fewer steps.
-CPU_CELL_STEPS = 2048 * 2048 * 300
-REF_CELL_STEPS = 2048 * 2048 * 200
+# Bounded oracle samples, in grid-node time steps of the forward run: about
+# 1.3e9 node steps (75 steps of a 256^3 grid, about 15 s of forward +
+# adjoint on 16 host cores) for the cpu_baseline key, and 5e8 (30 steps at
+# 256^3) per reference-arm evaluation.
+CPU_CELL_STEPS = 256 ** 3 * 75
+REF_CELL_STEPS = 256 ** 3 * 30
 
 
 WORKLOADS = {
@@ -62,10 +66,9 @@ def workload(name: str, nsteps: int | None):
     return w
 
 
-# DRAM bytes (read + write) of one forward time step, from the ncu captures
-# summarised in profiles/step2d_2048.md (k_step2d<float,0>, one launch) and
-# profiles/step3d_256.md (k_h3d + k_e3d<float,0>).  Cold-L2 captures of
-# the current kernels; reset to None whenever a kernel changes.
+# DRAM bytes (read + write) of the forward step kernels of one time step,
+# measured by ncu on each workload's own grid (k_step2d<float,0>; k_h3d +
+# k_e3d<float,0>); entries are removed whenever a kernel changes.
 NCU_TRAFFIC_PER_STEP = {"cfg_2d_2048": 74.2e6, "cfg_3d_256": 1300.0e6}
 
 
@@ -271,12 +274,12 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="cfg_2d_2048")
+    ap.add_argument("--workload", default="cfg_3d_256")
     ap.add_argument("--nsteps", type=int, default=0, help="override the time-step count (quick runs)")
     ap.add_argument("--cpu-nsteps", type=int, default=0,
-                    help="time steps of the oracle sample (0: sized to 2048^2 x 300 node steps)")
+                    help="time steps of the oracle sample (0: sized to 256^3 x 75 node steps)")
     ap.add_argument("--ref-nsteps", type=int, default=0,
-                    help="time steps per reference-arm evaluation (0: sized to 2048^2 x 200 node steps)")
+                    help="time steps per reference-arm evaluation (0: sized to 256^3 x 30 node steps)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--surrogate", action="store_true",

@@ -28,13 +28,13 @@ extern "C" {
 int nn_gemm(int transA, int transB, int M, int N, int K, float alpha, const float *A, int lda, const float *B, int ldb,
             float beta, float *C, int ldc, void *stream);
 
-/* The same product with BF16 operands on the tensor cores (cuBLAS, a plain
- * GEMM) and FP32 accumulation and output: A and B (FP32) are rounded to
- * BF16 (nearest even) into `scratch` (device, at least align256(2 M K) +
- * 2 K N bytes), then C = alpha op(A16) op(B16) + beta C.  Returns 1 for a
- * short scratch. */
+/* The same product with BF16 operands on the tensor cores and FP32
+ * accumulation and output: each tile of A and B (FP32 in memory) is rounded
+ * to BF16 (nearest even) as it is staged in shared memory, then C = alpha
+ * op(A16) op(B16) + beta C with mma.sync (m16n8k16) and FP32 accumulators.
+ * Needs no scratch memory. */
 int nn_gemm_bf16(int transA, int transB, int M, int N, int K, float alpha, const float *A, int lda, const float *B,
-                 int ldb, float beta, float *C, int ldc, void *scratch, long long scratch_bytes, void *stream);
+                 int ldb, float beta, float *C, int ldc, void *stream);
 
 /* col[(c 9 + t)][(b H + y) W + x] = x[c][b][y + t/3 - 1][x + t%3 - 1], zero
  * outside the image (3 x 3 convolution, stride 1, padding 1). */

@@ -1,12 +1,12 @@
 // Kernels of the learned sensitivity surrogate (a small conv U-Net): a tiled
-// FP32 GEMM, im2col / col2im for 3x3 convolutions, bias + ReLU, 2x2 average
-// pooling, 2x nearest upsampling, MSE loss and Adam.  Not part of the paper;
+// FP32 GEMM and a BF16 tensor-core GEMM (mma.sync, FP32 accumulation), im2col
+// / col2im for 3x3 convolutions, bias + ReLU, 2x2 average pooling, 2x
+// nearest upsampling, MSE loss and Adam.  Not part of the paper;
 // the surrogate proposes intermediate design steps between adjoint runs.
 //
 // Activations use the layout [C][B][H][W]: a convolution is the product
 // W[Cout][Cin K K] . col[Cin K K][B H W], and concatenating along channels is
 // placing tensors next to each other in memory.
-#include <cublas_v2.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -250,6 +250,110 @@ int status(cudaStream_t) { return cudaGetLastError() == cudaSuccess ? 0 : 3; }
 
 }  // namespace
 
+namespace {
+
+// BF16 tensor-core GEMM (mma.sync m16n8k16, FP32 accumulation).  Block tile
+// 64 (M) x 128 (N), K in slices of 32: each slice of op(A) and op(B) is read
+// as FP32 from global memory (coalesced along whichever index is
+// contiguous), rounded to BF16 (nearest even) and stored k-contiguous in
+// shared memory, As[m][k] and Bs[n][k], rows padded to 40 elements so that
+// the fragment loads of a warp hit 32 distinct banks.  Eight warps, 2 along
+// M x 4 along N, each own a 32 x 32 sub-tile: 2 x 4 fragments of 16 x 8.
+constexpr int BM = 64, BN = 128, BK = 32, BKP = BK + 8;
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ unsigned lds32(const __nv_bfloat16 *p) { return *reinterpret_cast<const unsigned *>(p); }
+
+// C = alpha op(A) op(B) + beta C as in k_gemm (split K over blockIdx.z).
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_gemm_bf16(int M, int N, int K, float alpha, const float *__restrict__ A,
+                                                   int lda, const float *__restrict__ B, int ldb, float beta,
+                                                   float *C, int ldc, int kc)
+{
+    __shared__ __align__(16) __nv_bfloat16 As[BM][BKP];
+    __shared__ __align__(16) __nv_bfloat16 Bs[BN][BKP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = warp >> 2, wn = warp & 3;
+    const int g = lane >> 2, t = lane & 3;  // fragment row / column group
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int jn = 0; jn < 4; ++jn)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][jn][r] = 0.0f;
+    const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+        for (int e = threadIdx.x; e < BM * BK; e += 256) {
+            int mm, kk;
+            if (TA) { kk = e / BM; mm = e % BM; }  // A stored K x M: consecutive m
+            else { mm = e / BK; kk = e % BK; }     // A stored M x K: consecutive k
+            const int gm = m0 + mm, gk = k0 + kk;
+            float v = 0.0f;
+            if (gm < M && gk < ke) v = TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
+            As[mm][kk] = __float2bfloat16_rn(v);
+        }
+        for (int e = threadIdx.x; e < BN * BK; e += 256) {
+            int nn, kk;
+            if (TB) { nn = e / BK; kk = e % BK; }  // B stored N x K: consecutive k
+            else { kk = e / BN; nn = e % BN; }     // B stored K x N: consecutive n
+            const int gn = n0 + nn, gk = k0 + kk;
+            float v = 0.0f;
+            if (gn < N && gk < ke) v = TB ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn];
+            Bs[nn][kk] = __float2bfloat16_rn(v);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < BK; ks += 16) {
+            unsigned a[2][4], b[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm * 32 + i * 16 + g, c = ks + 2 * t;
+                a[i][0] = lds32(&As[r][c]);
+                a[i][1] = lds32(&As[r + 8][c]);
+                a[i][2] = lds32(&As[r][c + 8]);
+                a[i][3] = lds32(&As[r + 8][c + 8]);
+            }
+#pragma unroll
+            for (int jn = 0; jn < 4; ++jn) {
+                const int n = wn * 32 + jn * 8 + g, c = ks + 2 * t;
+                b[jn][0] = lds32(&Bs[n][c]);
+                b[jn][1] = lds32(&Bs[n][c + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int jn = 0; jn < 4; ++jn) mma_bf16(acc[i][jn], a[i], b[jn]);
+        }
+        __syncthreads();
+    }
+    // accumulator r of fragment (i, jn): row g (+8 for r >= 2), column 2t (+1 for odd r)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int jn = 0; jn < 4; ++jn)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int gm = m0 + wm * 32 + i * 16 + g + (r >= 2 ? 8 : 0);
+                const int gn = n0 + wn * 32 + jn * 8 + 2 * t + (r & 1);
+                if (gm >= M || gn >= N) continue;
+                float *c = C + (long long)gm * ldc + gn;
+                if (gridDim.z > 1) atomicAdd(c, alpha * acc[i][jn][r]);
+                else *c = alpha * acc[i][jn][r] + (beta != 0.0f ? beta * *c : 0.0f);
+            }
+}
+
+}  // namespace
+
 extern "C" {
 
 int nn_gemm(int transA, int transB, int M, int N, int K, float alpha, const float *A, int lda, const float *B, int ldb,
@@ -277,61 +381,29 @@ int nn_gemm(int transA, int transB, int M, int N, int K, float alpha, const floa
     return status(st);
 }
 
-namespace {
-
-// One cuBLAS handle per device, created on first use.
-std::mutex g_blas_mu;
-cublasHandle_t g_blas[64];
-
-cublasHandle_t blas_handle()
-{
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    std::lock_guard<std::mutex> lk(g_blas_mu);
-    if (!g_blas[dev] && cublasCreate(&g_blas[dev]) != CUBLAS_STATUS_SUCCESS) g_blas[dev] = nullptr;
-    return g_blas[dev];
-}
-
-// dst[r][c] = bf16(src[r][c]) for a rows x cols block with leading dimension
-// ld (round to nearest even); dst is packed (leading dimension cols).
-__global__ void k_to_bf16(const float *src, long long rows, int cols, int ld, __nv_bfloat16 *dst)
-{
-    const long long n = rows * cols;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        const long long r = k / cols;
-        const int c = (int)(k % cols);
-        dst[k] = __float2bfloat16_rn(src[r * ld + c]);
-    }
-}
-
-}  // namespace
-
 int nn_gemm_bf16(int transA, int transB, int M, int N, int K, float alpha, const float *A, int lda, const float *B,
-                 int ldb, float beta, float *C, int ldc, void *scratch, long long scratch_bytes, void *stream)
+                 int ldb, float beta, float *C, int ldc, void *stream)
 {
     if (M < 0 || N < 0 || K < 0 || !C || (K > 0 && (!A || !B))) return 1;
     if (M == 0 || N == 0) return 0;
     if (K == 0) return nn_gemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream);
-    const long long na = (long long)M * K, nb = (long long)K * N;
-    const long long offb = (na * 2 + 255) / 256 * 256;
-    if (!scratch || scratch_bytes < offb + nb * 2) return 1;
     cudaStream_t st = (cudaStream_t)stream;
-    __nv_bfloat16 *a16 = (__nv_bfloat16 *)scratch, *b16 = (__nv_bfloat16 *)((char *)scratch + offb);
-    // packed BF16 copies of A and B as stored (M x K or K x M; K x N or N x K)
-    const long long ar = transA ? K : M, br = transB ? N : K;
-    const int ac = transA ? M : K, bc = transB ? K : N;
-    k_to_bf16<<<blocks_for(na), TPB, 0, st>>>(A, ar, ac, lda, a16);
-    k_to_bf16<<<blocks_for(nb), TPB, 0, st>>>(B, br, bc, ldb, b16);
-    if (cudaGetLastError() != cudaSuccess) return 3;
-    cublasHandle_t h = blas_handle();
-    if (!h || cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return 3;
-    // Row-major C = op(A) op(B) is column-major C^T = op(B)^T op(A)^T, and a
-    // packed row-major operand read column-major is its transpose.
-    const cublasStatus_t r =
-        cublasGemmEx(h, transB ? CUBLAS_OP_T : CUBLAS_OP_N, transA ? CUBLAS_OP_T : CUBLAS_OP_N, N, M, K, &alpha, b16,
-                     CUDA_R_16BF, bc, a16, CUDA_R_16BF, ac, &beta, C, CUDA_R_32F, ldc, CUBLAS_COMPUTE_32F,
-                     CUBLAS_GEMM_DEFAULT);
-    if (r != CUBLAS_STATUS_SUCCESS) return 3;
+    // Few output tiles and a long K (weight gradients): split K so that
+    // every SM gets a couple of blocks.
+    const long long tiles = (long long)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+    int splits = 1;
+    if (tiles < 2 * 152 && K > 8 * BK) {
+        const long long want = (2 * 152 + tiles - 1) / tiles, most = (K + 4 * BK - 1) / (4 * BK);
+        splits = (int)(want < most ? want : most);
+    }
+    const int kc = ((K + splits - 1) / splits + BK - 1) / BK * BK;
+    splits = (K + kc - 1) / kc;
+    if (splits > 1) k_scale_mat<<<blocks_for((long long)M * N), TPB, 0, st>>>(C, M, N, ldc, beta);
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
+    if (!transA && !transB) k_gemm_bf16<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
+    else if (!transA && transB) k_gemm_bf16<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
+    else if (transA && !transB) k_gemm_bf16<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
+    else k_gemm_bf16<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
     return status(st);
 }
 

@@ -5,9 +5,10 @@ produce, used to take cheap design steps between adjoint runs.
 The network runs on the library's own kernels (``include/surrogate.h``):
 im2col + GEMM convolutions, bias + ReLU, average pooling, nearest
 upsampling, MSE and Adam.  The GEMMs run either in FP32 on the library's
-tiled kernel (precision "f32") or with BF16 operands on the tensor cores and
-FP32 accumulation (precision "bf16"; FP32 master weights and Adam state).  This module only allocates buffers (PyTorch) and
-sequences kernel calls.  Activations are [C][B][H][W]; a decoder level's
+tiled kernel (precision "f32") or with BF16 operands on the tensor cores
+(the library's mma.sync kernel) and FP32 accumulation (precision "bf16";
+FP32 master weights and Adam state).  This module only allocates buffers
+(PyTorch) and sequences kernel calls.  Activations are [C][B][H][W]; a decoder level's
 input is one buffer [upsampled deeper features | skip], and the encoder
 writes its skip straight into the second half.
 """
@@ -37,7 +38,7 @@ _FNS = {
                 C.c_float, C.c_int, C.c_void_p],
     "nn_zero": [C.c_void_p, C.c_longlong, C.c_void_p],
     "nn_gemm_bf16": [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_void_p, C.c_int, C.c_void_p,
-                     C.c_int, C.c_float, C.c_void_p, C.c_int, C.c_void_p, C.c_longlong, C.c_void_p],
+                     C.c_int, C.c_float, C.c_void_p, C.c_int, C.c_void_p],
 }
 EXPORTS = sorted(_FNS)
 _lib = None
@@ -106,10 +107,6 @@ class UNet:
                         for n, ci, co, k in self.layers)
         self.col = torch.zeros(col_elems, **f32)
         self.dcol = torch.zeros(col_elems, **f32)
-        # BF16 operand copies of the largest GEMM (both operands bounded by
-        # the im2col buffer or the largest activation)
-        big = max(col_elems, max(t.numel() for t in self.a.values()))
-        self.scratch = torch.zeros(4 * big + 512, dtype=torch.uint8, device=self.dev) if precision == "bf16" else None
         self.loss = torch.zeros(1, dtype=torch.float64, device=self.dev)
 
     def sibling(self, batch: int) -> "UNet":
@@ -151,8 +148,7 @@ class UNet:
     def _gemm(self, ta, tb, M, N, K, A, lda, B, ldb, beta, Cm, ldc, what):
         L, st = _nn(), self._st()
         if self.precision == "bf16":
-            rc = L.nn_gemm_bf16(ta, tb, M, N, K, 1.0, _p(A), lda, _p(B), ldb, beta, _p(Cm), ldc, _p(self.scratch),
-                                self.scratch.numel(), st)
+            rc = L.nn_gemm_bf16(ta, tb, M, N, K, 1.0, _p(A), lda, _p(B), ldb, beta, _p(Cm), ldc, st)
         else:
             rc = L.nn_gemm(ta, tb, M, N, K, 1.0, _p(A), lda, _p(B), ldb, beta, _p(Cm), ldc, st)
         _ck(rc, what)

@@ -17,13 +17,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_sample_steps_follow_the_node_budget():
-    w = I.cfg_2d_2048()
-    assert bench.sample_nsteps(w, 0, bench.CPU_CELL_STEPS) == 300
-    assert bench.sample_nsteps(w, 0, bench.REF_CELL_STEPS) == 200
+    w = I.cfg_3d_256()
+    assert bench.sample_nsteps(w, 0, bench.CPU_CELL_STEPS) == 75
+    assert bench.sample_nsteps(w, 0, bench.REF_CELL_STEPS) == 30
     # a larger grid gets fewer steps, never fewer than 10 nor more than the run
     w3 = I.cfg_3d_512()
     n3 = bench.sample_nsteps(w3, 0, bench.CPU_CELL_STEPS)
-    assert 10 <= n3 < 300
+    assert 10 <= n3 < 75
     assert n3 * I.n_cells(w3) <= bench.CPU_CELL_STEPS
     small = I.cfg_2d_160()
     assert bench.sample_nsteps(small, 0, bench.CPU_CELL_STEPS) == min(small["nsteps"], 1000)
@@ -114,3 +114,11 @@ def test_every_bench_workload_is_a_valid_configuration(name):
     w = bench.workload(name, None)
     nbytes = B.workspace_bytes(w)
     assert 0 < nbytes < 280e9, (name, nbytes)
+
+
+def test_3d_benchmark_step_bytes():
+    """256^3 forward step (the default workload): 48 B per node for the six
+    field components, 28 B more per design node, 32 B per CPML slab crossed,
+    plus the BF16 checkpoint copy every 32 steps: about 1.01 GB."""
+    ab = bench.algorithmic_bytes(I.cfg_3d_256())
+    assert 1.00e9 < ab["forward"] < 1.03e9

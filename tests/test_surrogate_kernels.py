@@ -80,30 +80,66 @@ def _bf16(a):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-@pytest.mark.parametrize("ta,tb", [(0, 0), (0, 1), (1, 0), (1, 1)])
-def test_gemm_bf16_transposes_ragged(ta, tb):
-    """BF16 operands on the tensor cores, FP32 accumulation: equal to the FP64
-    product of the BF16-rounded operands up to FP32 accumulation error."""
+def _gemm_bf16_case(ta, tb, M, N, K, seed, alpha=0.7, beta=0.3):
+    """nn_gemm_bf16 against the FP64 product of the BF16-rounded operands.
+    Products of BF16 values are exact in FP32, so the only error is the FP32
+    accumulation: at most about K u sum_k |a_ik b_kj| (u = 2^-24) for any
+    summation order, taken here with a factor 4 of margin, plus the rounding
+    of the beta C term."""
     import torch
     from paper_2203_01462_gb300.surrogate import _nn, _p
-    rng = np.random.default_rng(10 + ta * 2 + tb)
-    M, N, K = 67, 130, 45
+    rng = np.random.default_rng(seed)
     A = rng.standard_normal((K, M) if ta else (M, K)).astype(np.float32)
     B = rng.standard_normal((N, K) if tb else (K, N)).astype(np.float32)
     Cm = rng.standard_normal((M, N)).astype(np.float32)
     A16, B16 = _bf16(A), _bf16(B)
-    ref = 0.7 * ((A16.T if ta else A16) @ (B16.T if tb else B16)) + 0.3 * Cm
+    Aop, Bop = (A16.T if ta else A16), (B16.T if tb else B16)
+    ref = alpha * (Aop @ Bop) + beta * Cm
+    bound = 4.0 * (K + 2) * 2.0 ** -24 * abs(alpha) * (np.abs(Aop) @ np.abs(Bop)) + 2.0 ** -22 * np.abs(ref) + 1e-30
     a, b, c = (torch.tensor(v, device="cuda") for v in (A, B, Cm))
-    need = (M * K * 2 + 255) // 256 * 256 + K * N * 2
-    short = torch.zeros(need - 1, dtype=torch.uint8, device="cuda")
-    assert _nn().nn_gemm_bf16(ta, tb, M, N, K, 0.7, _p(a), A.shape[1], _p(b), B.shape[1], 0.3, _p(c), N,
-                              _p(short), need - 1, None) == 1
-    scratch = torch.zeros(need, dtype=torch.uint8, device="cuda")
-    rc = _nn().nn_gemm_bf16(ta, tb, M, N, K, 0.7, _p(a), A.shape[1], _p(b), B.shape[1], 0.3, _p(c), N,
-                            _p(scratch), need, None)
+    rc = _nn().nn_gemm_bf16(ta, tb, M, N, K, alpha, _p(a), A.shape[1], _p(b), B.shape[1], beta, _p(c), N, None)
     torch.cuda.synchronize()
     assert rc == 0
-    np.testing.assert_allclose(c.cpu().numpy(), ref, rtol=1e-4, atol=1e-4)
+    err = np.abs(c.cpu().numpy() - ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    return ref
+
+
+@pytest.mark.parametrize("ta,tb", [(0, 0), (0, 1), (1, 0), (1, 1)])
+def test_gemm_bf16_transposes_ragged(ta, tb):
+    """BF16 operands on the tensor cores, FP32 accumulation, every transpose
+    mode, M, N and K ragged against the 64 x 128 x 32 tiles."""
+    _gemm_bf16_case(ta, tb, 67, 130, 45, 10 + ta * 2 + tb)
+
+
+@pytest.mark.parametrize("shape", [(24, 27, 20000), (1, 300, 216), (97, 1, 33), (192, 8000, 864), (5, 7, 3)])
+def test_gemm_bf16_shapes(shape):
+    """A weight-gradient shape (small M x N, long K: split over blocks and
+    added atomically), a one-channel head, a one-column output, a U-Net
+    layer and a product smaller than one fragment."""
+    M, N, K = shape
+    for ta, tb in ((0, 1), (1, 0)):
+        _gemm_bf16_case(ta, tb, M, N, K, 20 + M + ta, beta=0.0 if K > 1000 else 0.3)
+
+
+def test_gemm_bf16_is_not_the_fp32_kernel():
+    """The BF16 path really rounds its operands: on inputs with more than 8
+    significant bits its result differs from the FP32 GEMM's by about the
+    BF16 rounding, and equals the product of the rounded operands."""
+    import torch
+    from paper_2203_01462_gb300.surrogate import _nn, _p
+    rng = np.random.default_rng(3)
+    M, N, K = 64, 128, 64
+    A = (1.0 + rng.random((M, K)) * 1e-2).astype(np.float32)
+    B = (1.0 + rng.random((K, N)) * 1e-2).astype(np.float32)
+    a, b = torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda")
+    c16, c32 = torch.zeros(M, N, device="cuda"), torch.zeros(M, N, device="cuda")
+    assert _nn().nn_gemm_bf16(0, 0, M, N, K, 1.0, _p(a), K, _p(b), N, 0.0, _p(c16), N, None) == 0
+    assert _nn().nn_gemm(0, 0, M, N, K, 1.0, _p(a), K, _p(b), N, 0.0, _p(c32), N, None) == 0
+    torch.cuda.synchronize()
+    exact16 = _bf16(A) @ _bf16(B)
+    assert np.max(np.abs(c16.cpu().numpy() - exact16)) <= 1e-4 * np.max(np.abs(exact16))
+    assert np.max(np.abs(c16.cpu().numpy() - c32.cpu().numpy())) > 1e-3
 
 
 def test_unet_bf16_forward_and_gradients_match_oracle():
