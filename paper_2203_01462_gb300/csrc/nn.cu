@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <stdint.h>
 
 #include "../../include/surrogate.h"
 
@@ -91,15 +92,24 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, float alpha, 
 }
 
 // col[(c*9 + t)][(b*H + y)*W + x] = x[c][b][y + dy_t][x + dx_t] (zero padding).
+// One thread per (c, pixel) writes the pixel's nine taps: the index
+// arithmetic is done once, the nine stores of a warp are each contiguous.
 __global__ void k_im2col3(const float *x, int C, int B, int H, int W, float *col)
 {
-    const long long P = (long long)B * H * W, n = (long long)C * 9 * P;
+    const int HW = H * W;
+    const long long P = (long long)B * HW, n = (long long)C * P;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const long long r = e / P, p = e % P;
-        const int c = (int)(r / 9), t = (int)(r % 9);
-        const int xx = (int)(p % W), yy = (int)((p / W) % H), b = (int)(p / ((long long)W * H));
-        const int sy = yy + t / 3 - 1, sx = xx + t % 3 - 1;
-        col[e] = (sy >= 0 && sy < H && sx >= 0 && sx < W) ? x[(((long long)c * B + b) * H + sy) * W + sx] : 0.0f;
+        const int c = (int)(e / P);
+        const long long p = e - (long long)c * P;
+        const int b = (int)(p / HW), rem = (int)(p - (long long)b * HW);
+        const int yy = rem / W, xx = rem - yy * W;
+        const float *src = x + ((long long)c * B + b) * HW;
+        float *dst = col + (long long)c * 9 * P + p;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int sy = yy + t / 3 - 1, sx = xx + t % 3 - 1;
+            dst[(long long)t * P] = (sy >= 0 && sy < H && sx >= 0 && sx < W) ? src[sy * W + sx] : 0.0f;
+        }
     }
 }
 
@@ -133,18 +143,39 @@ __global__ void k_bias_act(float *y, const float *bias, int Cout, long long P, i
     }
 }
 
-// dy <- dy * (y > 0) where relu, then db[c] = sum over the row (one block per row).
-__global__ void k_relu_bwd_bias(const float *y, float *dy, float *db, long long P, int relu)
+// dy <- dy * (y > 0) where relu, then db[c] = sum over the row: one block
+// of 1024 threads per row, 16-byte accesses when `vec` (P a multiple of 4,
+// both arrays 16-byte aligned), a fixed summation order.
+__global__ void __launch_bounds__(1024) k_relu_bwd_bias(const float *y, float *dy, float *db, long long P, int relu,
+                                                        int vec)
 {
     __shared__ float part[32];
     const int c = blockIdx.x;
     float s = 0.0f;
-    for (long long p = threadIdx.x; p < P; p += blockDim.x) {
-        const long long e = (long long)c * P + p;
-        float g = dy[e];
-        if (relu && !(y[e] > 0.0f)) g = 0.0f;
-        dy[e] = g;
-        s += g;
+    const float *yr = y + (long long)c * P;
+    float *dr = dy + (long long)c * P;
+    if (vec) {
+        const float4 *y4 = reinterpret_cast<const float4 *>(yr);
+        float4 *d4 = reinterpret_cast<float4 *>(dr);
+        for (long long p = threadIdx.x; p < P / 4; p += blockDim.x) {
+            float4 g = d4[p];
+            if (relu) {
+                const float4 v = y4[p];
+                if (!(v.x > 0.0f)) g.x = 0.0f;
+                if (!(v.y > 0.0f)) g.y = 0.0f;
+                if (!(v.z > 0.0f)) g.z = 0.0f;
+                if (!(v.w > 0.0f)) g.w = 0.0f;
+                d4[p] = g;
+            }
+            s += (g.x + g.y) + (g.z + g.w);
+        }
+    } else {
+        for (long long p = threadIdx.x; p < P; p += blockDim.x) {
+            float g = dr[p];
+            if (relu && !(yr[p] > 0.0f)) g = 0.0f;
+            dr[p] = g;
+            s += g;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
@@ -435,7 +466,8 @@ int nn_act_bwd_bias(const float *y, float *dy, float *db, int Cout, long long P,
 {
     if (!y || !dy || !db || Cout <= 0 || P <= 0) return 1;
     cudaStream_t st = (cudaStream_t)stream;
-    k_relu_bwd_bias<<<Cout, TPB, 0, st>>>(y, dy, db, P, relu);
+    const int vec = (P & 3) == 0 && (((uintptr_t)y | (uintptr_t)dy) & 15) == 0;
+    k_relu_bwd_bias<<<Cout, 1024, 0, st>>>(y, dy, db, P, relu, vec);
     return status(st);
 }
 

@@ -1,10 +1,16 @@
 """What the trained surrogate gains over the plain adjoint loop.
 
 On the 256^2-design workload (316^2 grid, 4000 steps), a U-Net pretrained on
-(rho, gradient) pairs from plain optimization trajectories drives the
-surrogate-assisted loop (one full forward + adjoint solve, then four
-surrogate steps, per round).  It must reach the plain loop's final objective
-(within 1 %) in less wall time than the plain loop took."""
+(rho, damping level) -> gradient pairs from plain optimization trajectories
+drives the surrogate-assisted loop (one full forward + adjoint solve, then
+four surrogate steps, per round).  Both loops run the artificial-damping
+continuation (gamma x10 decaying to x1 over the first 20 updates), so the
+network's damping input takes ten levels in training; the compared runs
+start from a half-metal bowtie, outside the random starts of the training
+trajectories.  The surrogate loop must reach the plain loop's final
+objective (within 1 %) in less loop wall time than the plain loop took.
+The pretraining (pair collection + training) is reported beside it, with
+the number of designs that must share one network for it to pay off."""
 
 import numpy as np
 import pytest
@@ -12,6 +18,7 @@ import pytest
 from paper_2203_01462_gb300 import inputs as I
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
 
 def test_surrogate_loop_matches_plain_objective_in_less_time(save_report):
     import time
@@ -21,27 +28,35 @@ def test_surrogate_loop_matches_plain_objective_in_less_time(save_report):
     from paper_2203_01462_gb300.surrogate_loop import Trainer, collect_pairs, surrogate_optimize
     w = I.cfg_2d_316()
     s = Solver(w)
-    rho0s = [I.zero_gap(w, 0.02 * I.rho_uniform(w, 200 + k)) for k in range(4)]
-    pairs = collect_pairs(s, rho0s, iters=15, move=0.05, damping_start=1.0, damping_iters=0)
-    tr = Trainer(256, 256, base=24, batch=8, seed=0, lr=1e-3)
-    tr.fit(pairs, 200)
-    rho_start = I.zero_gap(w, np.zeros(I.design_shape(w)))
+    G0, D, U = 10.0, 20, 40
     torch.cuda.synchronize()
     t = time.perf_counter()
-    _, hp = optimize(s, rho_start, iters=30, move=0.05, zeta_stop=0.0, damping_start=1.0, damping_iters=0,
+    rho0s = [I.zero_gap(w, 0.02 * I.rho_uniform(w, 200 + k)) for k in range(4)]
+    pairs = collect_pairs(s, rho0s, iters=20, move=0.05, damping_start=G0, damping_iters=D)
+    tr = Trainer(256, 256, base=24, batch=8, seed=0, lr=1e-3)
+    tr.fit(pairs, 200)
+    torch.cuda.synchronize()
+    pre_s = time.perf_counter() - t
+    levels = {round(float(x[1, 0, 0, 0].item()), 6) for x in pairs.x}
+    assert len(levels) == D  # the damping channel carries every level of the continuation
+    rho_start = I.zero_gap(w, 0.5 * I.rho_bowtie(w))
+    t = time.perf_counter()
+    _, hp = optimize(s, rho_start, iters=U, move=0.05, zeta_stop=0.0, damping_start=G0, damping_iters=D,
                      move_decay=1.0)
     torch.cuda.synchronize()
     plain_s = time.perf_counter() - t
     target = hp.W[-1]
     t = time.perf_counter()
-    _, hs, st = surrogate_optimize(s, tr, rho_start, updates=90, inner=4, move=0.05, damping_start=1.0,
-                                   damping_iters=0, pairs=pairs, fit_steps=0, target_W=0.99 * target)
+    _, hs, st = surrogate_optimize(s, tr, rho_start, updates=3 * U, inner=4, move=0.05, damping_start=G0,
+                                   damping_iters=D, pairs=pairs, fit_steps=0, target_W=0.99 * target)
     torch.cuda.synchronize()
     sur_s = time.perf_counter() - t
     Ws = [x for x in hs.W if x == x]
-    rep = dict(plain_s=plain_s, plain_updates=30, plain_W=target, sur_s=sur_s, sur_updates=len(hs.W),
-               sur_W=Ws[-1], **st)
+    rep = dict(plain_s=plain_s, plain_updates=U, plain_W=target, sur_s=sur_s, sur_updates=len(hs.W),
+               sur_W=Ws[-1], pretraining_s=pre_s, ratio=sur_s / plain_s,
+               ratio_with_pretraining=(sur_s + pre_s) / plain_s,
+               break_even_designs=pre_s / (plain_s - sur_s) if plain_s > sur_s else None, **st)
     save_report("surrogate_loop.json", rep)
     assert Ws[-1] >= 0.99 * target, rep
     assert sur_s < 0.9 * plain_s, rep
-    assert st["solves"] < 30
+    assert st["solves"] < U
