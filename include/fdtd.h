@@ -61,7 +61,9 @@ typedef enum fdtd_status {
     FDTD_EUNSTABLE = 5,  /* unstable run: a non-finite objective, or a state
                             word non-finite or above the stability-guard
                             bound (fdtd_set_stability_guard)                 */
-    FDTD_ETIMEOUT = 6,   /* reserved: a bounded device wait gave up           */
+    FDTD_ETIMEOUT = 6,   /* a bounded device wait gave up (the in-plane
+                            multi-step launch: a tile waited about a second
+                            for a neighbour)                                 */
     FDTD_ERANGE = 7      /* a design density outside [0, 1]                    */
 } fdtd_status;
 
@@ -239,6 +241,25 @@ fdtd_status fdtd_set_sensitivity_terms(fdtd_ctx *ctx, int terms);
  * settings.  The checks read the state once per `every` steps (0.2 % of the
  * forward traffic at the default) and change no result. */
 fdtd_status fdtd_set_stability_guard(fdtd_ctx *ctx, int every, double max_abs);
+
+/* In-plane 2D contexts (pol = FDTD_POL_INPLANE): time steps per launch
+ * (default 64; 1 = one launch per half step).  With more than one, a run of
+ * steps is one cooperative launch in which each 32 x 32 tile advances as
+ * soon as the neighbouring tiles it reads from have finished the half step
+ * it needs (bounded waits: FDTD_ETIMEOUT from fdtd_sync if one gives up).
+ * Used only when every tile can be resident at once on the device (the
+ * paper's 491^2 geometry: 256 tiles); larger grids keep one launch per half
+ * step.  Such passes are not replayed as CUDA graphs.  Results are identical
+ * either way.  The other modes ignore the setting. */
+fdtd_status fdtd_set_steps_per_launch(fdtd_ctx *ctx, int steps);
+
+/* Self-test of the bounded device wait the multi-step launch uses: one
+ * thread waits on a flag that nothing sets, for limit_cycles clock cycles.
+ * d_words: 16 bytes of caller device memory (16-byte aligned), overwritten.
+ * Returns FDTD_ETIMEOUT when the wait gave up and reported it as it should,
+ * FDTD_OK if the flag was seen set, FDTD_ECUDA / FDTD_EINVAL on errors.
+ * Synchronises `stream` (a cudaStream_t). */
+fdtd_status fdtd_selftest_bounded_wait(void *d_words, long long limit_cycles, void *stream);
 
 /* Forward solve of N steps.  Writes W~ (Eq. 24) to d_W (device, one double;
  * may be NULL) asynchronously.  Requires fdtd_set_design.  Returns

@@ -27,7 +27,8 @@ EXPORTS = ["fdtd_workspace_bytes", "fdtd_create", "fdtd_set_design", "fdtd_set_d
            "fdtd_run_host", "fdtd_get_info", "fdtd_status_string", "fdtd_destroy",
            "fdtd_gradient_static", "fdtd_gap_spectrum", "fdtd_ascent_step", "fdtd_mma_asymptotes", "fdtd_mma_solve",
            "fdtd_mirror_average", "fdtd_fix_design", "fdtd_grayness", "fdtd_threshold", "fdtd_set_graphs",
-           "fdtd_set_l2_residency", "fdtd_set_sensitivity_terms", "fdtd_set_stability_guard"]
+           "fdtd_set_l2_residency", "fdtd_set_sensitivity_terms", "fdtd_set_stability_guard",
+           "fdtd_set_steps_per_launch", "fdtd_selftest_bounded_wait"]
 
 
 TERM_PSI, TERM_EPS, TERM_SIGMA, TERM_ALL = 1, 2, 4, 7
@@ -103,6 +104,8 @@ def load():
             "fdtd_set_l2_residency": [P, C.c_double],
             "fdtd_set_sensitivity_terms": [P, C.c_int],
             "fdtd_set_stability_guard": [P, C.c_int, C.c_double],
+            "fdtd_set_steps_per_launch": [P, C.c_int],
+            "fdtd_selftest_bounded_wait": [P, C.c_longlong, P],
             "fdtd_threshold": [P, P, C.c_size_t, C.c_double],
             "fdtd_gap_history": [P, P, C.c_size_t],
             "fdtd_sync": [P],
@@ -284,6 +287,10 @@ class Solver:
         are not finite or exceed ``max_abs`` (0: the automatic bound)."""
         _check(self.lib.fdtd_set_stability_guard(self.ctx, int(every), float(max_abs)), "fdtd_set_stability_guard")
 
+    def set_steps_per_launch(self, steps: int) -> None:
+        """In-plane 2D mode: time steps per cooperative launch (1: one launch per half step)."""
+        _check(self.lib.fdtd_set_steps_per_launch(self.ctx, int(steps)), "fdtd_set_steps_per_launch")
+
     def set_graphs(self, mode: int) -> None:
         """0: plain launches, 1: replay CUDA graphs of whole passes, 2: automatic by grid size."""
         _check(self.lib.fdtd_set_graphs(self.ctx, int(mode)), "fdtd_set_graphs")
@@ -368,3 +375,13 @@ class Solver:
         self.adjoint()
         g = self.gradient()
         return W, g
+
+
+def selftest_bounded_wait(limit_cycles: int, stream=None) -> int:
+    """Run the library's bounded-wait self-test (a wait on a flag nothing
+    sets, limited to ``limit_cycles`` clock cycles); returns the status."""
+    import torch
+    words = torch.zeros(4, dtype=torch.int32, device="cuda")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return int(load().fdtd_selftest_bounded_wait(C.c_void_p(words.data_ptr()), int(limit_cycles),
+                                                 C.c_void_p(st.cuda_stream)))

@@ -215,6 +215,9 @@ struct fdtd_ctx {
     // polls a mapped host word the kernel writes and stops enqueuing once it
     // sees this pass's tag (not possible while capturing a graph; the error
     // word still reports the instability).
+    // In-plane 2D contexts: time steps per cooperative launch (1: two
+    // launches per step).
+    int multi_steps = 64;
     int guard_every = 256;
     double guard_bound = 0.0;  // 0: automatic, see guard_limit()
     unsigned guard_tag = 0;
@@ -276,6 +279,9 @@ struct fdtd_ctx {
     virtual fdtd_status set_l2(double) { return FDTD_OK; }
     // Blocks of one step launch and how many take the vector path (2D E_z).
     virtual void block_counts(long long *total, long long *vec) const { *total = *vec = 0; }
+    // True when the passes run as few cooperative launches, which are not
+    // captured into graphs.
+    virtual bool plain_launches() const { return false; }
     long long n_free = 0;  // design nodes outside the gap
     virtual void *rho_stage() = 0;
     virtual double *grad_stage() = 0;
@@ -294,7 +300,11 @@ fdtd_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? FDTD_OK : FDTD_EC
 
 constexpr long long GRAPH_AUTO_CELLS = 1LL << 20;
 
-bool use_graphs(const fdtd_ctx *c) { return c->graphs == 1 || (c->graphs == 2 && c->ncells <= GRAPH_AUTO_CELLS); }
+bool use_graphs(const fdtd_ctx *c)
+{
+    if (c->plain_launches()) return false;
+    return c->graphs == 1 || (c->graphs == 2 && c->ncells <= GRAPH_AUTO_CELLS);
+}
 
 // Run `enqueue` (which only enqueues work on c->stream) directly, or through
 // a CUDA graph captured on its first call and replayed afterwards.  The
@@ -915,6 +925,14 @@ struct CtxP final : fdtd_ctx {
     PmlP<R> pm{};
     double *misc = nullptr;
     unsigned *err = nullptr;
+    // Several steps per cooperative launch (k_stepp_multi): one finished-
+    // half-step word per 32 x 32 tile, then the abort word; the pass's count
+    // of half steps so far; whether every tile can be resident at once.
+    unsigned *coop = nullptr;
+    int ntiles = 0;
+    unsigned coop_phase = 0;
+    bool multi_fits = false;
+    static constexpr long long WAIT_CYCLES = 2000000000LL;  // about one second
 
     void *rho_stage() override { return rstage; }
     double *grad_stage() override { return gstage; }
@@ -922,6 +940,40 @@ struct CtxP final : fdtd_ctx {
     unsigned *err_dev() override { return err; }
 
     long long Mdi_all() const { return geo.Mdi[0] + geo.Mdi[1]; }
+    bool multi() const { return multi_fits && multi_steps > 1; }
+    bool plain_launches() const override { return multi(); }
+    // Steps per launch, a divisor of the guard interval so that a launch
+    // ends on every step the guard checks.
+    int chunk() const
+    {
+        int c = multi_steps;
+        if (guard_every > 0) {
+            int a = c, b = guard_every;
+            while (b) {
+                const int t = a % b;
+                a = b;
+                b = t;
+            }
+            c = a;
+        }
+        return c > 1 ? c : 1;
+    }
+    void reset_coop()
+    {
+        launch_zero_bytes(coop, (size_t)(ntiles + 2) * sizeof(unsigned), stream);
+        ++launches;
+        coop_phase = 0;
+    }
+    // Steps [a, b) of one plan (forward: a..b-1; adjoint: m = a down to b+1)
+    // in one cooperative launch.
+    void launch_multi(int mode, const StateP<R> &st, PlanP<R> plan)
+    {
+        const StepP<R> base = step_args();
+        launches += launch_stepp_multi<R>(mode, geo, st, coef_slot, pm, base, plan, coop_phase, coop, coop + ntiles,
+                                          err, WAIT_CYCLES, stream);
+        coop_phase += 2u * (unsigned)plan.count;
+        cell_updates += (long long)plan.count * ncells;
+    }
 
     void carve_state(Carver &cv, StateP<R> &s, char *&base)
     {
@@ -981,6 +1033,8 @@ struct CtxP final : fdtd_ctx {
         pml_tab = cv.take<R>(6 * (size_t)(c.nx + c.ny));
         misc = cv.take<double>(4 + 2 * MMA_BLOCKS);
         err = cv.take<unsigned>(4);
+        ntiles = stepp_multi_tiles(geo);
+        coop = cv.take<unsigned>((size_t)ntiles + 2);
         if (pml_tab) {
             R *t = pml_tab;
             const int nn[2] = {c.nx, c.ny};
@@ -1006,6 +1060,7 @@ struct CtxP final : fdtd_ctx {
         FDTD_TRY(cuda_ok(cudaMemcpyAsync(src_tab, src.data(), src.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
         launch_zero_bytes(err, 4 * sizeof(unsigned), st);
         ++launches;
+        multi_fits = stepp_multi_fits<R>(geo);
         return cuda_ok(cudaStreamSynchronize(st));
     }
 
@@ -1058,6 +1113,28 @@ struct CtxP final : fdtd_ctx {
 
     void advance_forward(int n0, int count, bool gap, R *rec_base)
     {
+        if (multi()) {
+            // runs of steps that end on multiples of chunk(), which divides
+            // the guard interval, so the guard sees every step it checks
+            const int cs = chunk();
+            for (int n = n0; n < n0 + count;) {
+                const int n1 = std::min(n0 + count, (n / cs + 1) * cs);
+                PlanP<R> pl{};
+                pl.src = src_tab;
+                pl.gap = (gap && Mg) ? gap_hist : nullptr;
+                pl.rec = rec_base;
+                pl.rec_step = Mdi_all();
+                pl.Mdi0 = geo.Mdi[0];
+                pl.Mg = (int)Mg;
+                pl.rec0 = n0;
+                pl.n0 = n;
+                pl.count = n1 - n;
+                launch_multi(0, F, pl);
+                n = n1;
+                if (guard_after<R>(n, F_base, state_bytes)) break;
+            }
+            return;
+        }
         StepP<R> a = step_args();
         for (int n = n0; n < n0 + count; ++n) {
             a.src = src_tab + n;
@@ -1073,6 +1150,23 @@ struct CtxP final : fdtd_ctx {
 
     void advance_adjoint(int m_hi, int m_lo, int slot0)
     {
+        if (multi()) {
+            for (int m = m_hi; m > m_lo;) {
+                const int cnt = std::min(multi_steps, m - m_lo);
+                PlanP<R> pl{};
+                pl.gap = Mg ? gap_hist : nullptr;
+                pl.rec = rec;
+                pl.rec_step = Mdi_all();
+                pl.Mdi0 = geo.Mdi[0];
+                pl.Mg = (int)Mg;
+                pl.rec0 = slot0;
+                pl.n0 = m;
+                pl.count = cnt;
+                launch_multi(1, A, pl);
+                m -= cnt;
+            }
+            return;
+        }
         StepP<R> a = step_args();
         a.G[0] = G[0];
         a.G[1] = G[1];
@@ -1093,6 +1187,7 @@ struct CtxP final : fdtd_ctx {
         launch_zero_bytes(F_base, state_bytes, st);
         if (Mg) launch_zero_bytes(gap_hist, Mg * sizeof(R), st);
         launches += 2;
+        if (multi()) reset_coop();
         guarding = true;
         if (K <= 0) {
             advance_forward(0, N, true, rec);
@@ -1121,6 +1216,7 @@ struct CtxP final : fdtd_ctx {
         launch_zero_bytes(G[0], geo.Mdi[0] * sizeof(double), st);
         launch_zero_bytes(G[1], geo.Mdi[1] * sizeof(double), st);
         launches += 3;
+        if (multi()) reset_coop();
         if (K <= 0) {
             advance_adjoint(N, 0, 0);
         } else {
@@ -1625,6 +1721,30 @@ fdtd_status fdtd_set_stability_guard(fdtd_ctx *ctx, int every, double max_abs)
     return FDTD_OK;
 }
 
+fdtd_status fdtd_set_steps_per_launch(fdtd_ctx *ctx, int steps)
+{
+    if (!ctx || steps < 1 || steps > 4096) return FDTD_EINVAL;
+    ctx->multi_steps = steps;
+    ctx->drop_graphs();  // captured passes hold the old launches
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_selftest_bounded_wait(void *d_words, long long limit_cycles, void *stream)
+{
+    if (!d_words || ((uintptr_t)d_words & 15) || !(limit_cycles > 0) || limit_cycles > 10000000000LL)
+        return FDTD_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned *w = (unsigned *)d_words;
+    launch_zero_bytes(w, 4 * sizeof(unsigned), st);
+    launch_wait_selftest(w, limit_cycles, st);
+    FDTD_TRY(cuda_ok(cudaGetLastError()));
+    unsigned h[4] = {0, 0, 0, 0};
+    FDTD_TRY(cuda_ok(cudaMemcpyAsync(h, w, sizeof h, cudaMemcpyDeviceToHost, st)));
+    FDTD_TRY(cuda_ok(cudaStreamSynchronize(st)));
+    if (h[2] & ERR_TIMEOUT) return h[1] ? FDTD_ETIMEOUT : FDTD_ECUDA;
+    return FDTD_OK;
+}
+
 fdtd_status fdtd_set_sensitivity_terms(fdtd_ctx *ctx, int terms)
 {
     if (!ctx || terms < 1 || terms > FDTD_TERM_ALL) return FDTD_EINVAL;
@@ -1816,6 +1936,7 @@ fdtd_status fdtd_sync(fdtd_ctx *ctx)
         ++ctx->launches;
         cudaStreamSynchronize(ctx->stream);
         if (h & ERR_RANGE) return FDTD_ERANGE;
+        if (h & ERR_TIMEOUT) return FDTD_ETIMEOUT;
         return FDTD_EUNSTABLE;
     }
     return FDTD_OK;

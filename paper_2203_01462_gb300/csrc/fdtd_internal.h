@@ -9,7 +9,7 @@
 namespace fdtd {
 
 // Device error word bits (reported by fdtd_sync).
-enum : unsigned { ERR_RANGE = 1u, ERR_NONFINITE = 2u, ERR_UNSTABLE = 4u };
+enum : unsigned { ERR_RANGE = 1u, ERR_NONFINITE = 2u, ERR_UNSTABLE = 4u, ERR_TIMEOUT = 8u };
 
 // Geometry of a 2D TM_z grid: Ez, Hx, Hy on nx x ny nodes with row pitch px
 // (elements).  Hx[j][i] sits at (i, j + 1/2), Hy[j][i] at (i + 1/2, j).
@@ -206,6 +206,39 @@ struct StepP {
 template <typename R>
 int launch_stepp(int mode, const GeoP &g, const StateP<R> &s, int coef_slot, const PmlP<R> &pm,
                  const StepP<R> &a, cudaStream_t st);
+
+// Per-step pointers of a run of `count` in-plane steps in one launch.  Mode
+// 0 (forward / recompute): step n = n0 + t takes src[n], writes gap row n+1
+// of gap (if not null) and the design record slot n - rec0 of rec (if not
+// null).  Mode 1 (adjoint): step t takes m = n0 - t, the gap row m as its
+// source and the forward fields of slot m - 1 - rec0.
+template <typename R>
+struct PlanP {
+    const R *src;
+    R *gap, *rec;
+    long long rec_step, Mdi0;   // elements per record slot; offset of the E_y part
+    int Mg, rec0, n0, count;
+};
+
+// Blocks (32 x 32-node tiles) of the multi-step launch; whether they can
+// all be resident at once on the current device (required: the tiles wait
+// on their neighbours).
+int stepp_multi_tiles(const GeoP &g);
+template <typename R>
+bool stepp_multi_fits(const GeoP &g);
+
+// plan.count steps in one cooperative launch (kernels_2dp.cu).  flags: one
+// word per tile holding its finished half steps, phase0 on entry; a wait
+// longer than `limit` clock cycles sets ERR_TIMEOUT in *err and *abort_word.
+template <typename R>
+int launch_stepp_multi(int mode, const GeoP &g, const StateP<R> &s, int coef_slot, const PmlP<R> &pm,
+                       const StepP<R> &base, const PlanP<R> &plan, unsigned phase0, unsigned *flags,
+                       unsigned *abort_word, unsigned *err, long long limit, cudaStream_t st);
+
+// One bounded wait on words[0] >= 1 (abort word words[1], error word
+// words[2]) that nothing satisfies: it records ERR_TIMEOUT after `limit`
+// clock cycles.
+void launch_wait_selftest(unsigned *words, long long limit, cudaStream_t st);
 
 // H then E half steps of the whole grid, in place (two launches); a forward
 // step with a.tf_inc adds the plane wave's face corrections after each half

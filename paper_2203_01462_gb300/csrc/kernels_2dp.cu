@@ -38,13 +38,12 @@ __device__ __forceinline__ int slabH(int p, int n, int np)
     return p < np ? p : ((p >= n - 1 - np && p < n - 1) ? np + p - (n - 1 - np) : -1);
 }
 
+// H half step of the cell (i, j) (Hz exists on the (nx-1) x (ny-1) cells).
 template <typename R>
-__global__ void __launch_bounds__(BX *BY) k_hp(GeoP g, StateP<R> s, int slot, PmlP<R> pm)
+__device__ __forceinline__ void h_cell(const GeoP &g, const StateP<R> &s, const Coef<R> &c, const PmlP<R> &pm, int i,
+                                       int j)
 {
-    wait_previous_grid();
-    const Coef<R> &c = coef_at<R>(slot);
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    if (i > g.nx - 2 || j > g.ny - 2) return;  // Hz exists on the (nx-1) x (ny-1) cells
+    if (i > g.nx - 2 || j > g.ny - 2) return;
     const long long q = (long long)j * g.px + i;
     const R dEy = s.Ey[q + 1] - s.Ey[q];     // d_x Ey
     const R dEx = s.Ex[q + g.px] - s.Ex[q];  // d_y Ex
@@ -62,6 +61,13 @@ __global__ void __launch_bounds__(BX *BY) k_hp(GeoP g, StateP<R> s, int slot, Pm
         ty += p;
     }
     s.Hz[q] -= c.S * (tx - ty);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(BX *BY) k_hp(GeoP g, StateP<R> s, int slot, PmlP<R> pm)
+{
+    wait_previous_grid();
+    h_cell<R>(g, s, coef_at<R>(slot), pm, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
 }
 
 // Eq. (10a,b) for one edge of component cc at array index (i, j) with the
@@ -112,12 +118,11 @@ __device__ __forceinline__ void e_edge(const GeoP &g, const Coef<R> &c, const St
     if (MODE == 0 && gap && a.gap_rec) a.gap_rec[gidx] = en;
 }
 
+// E half step of the edges Ex(i, j) and Ey(i, j).
 template <typename R, int MODE>
-__global__ void __launch_bounds__(BX *BY) k_ep(GeoP g, StateP<R> s, int slot, PmlP<R> pm, StepP<R> a)
+__device__ __forceinline__ void e_edges(const GeoP &g, const StateP<R> &s, const Coef<R> &c, const PmlP<R> &pm,
+                                        const StepP<R> &a, int i, int j)
 {
-    wait_previous_grid();
-    const Coef<R> &c = coef_at<R>(slot);
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     if (i >= g.nx || j >= g.ny) return;
     const long long q = (long long)j * g.px + i;
     const int np = g.npml;
@@ -157,6 +162,127 @@ __global__ void __launch_bounds__(BX *BY) k_ep(GeoP g, StateP<R> s, int slot, Pm
     }
 }
 
+template <typename R, int MODE>
+__global__ void __launch_bounds__(BX *BY) k_ep(GeoP g, StateP<R> s, int slot, PmlP<R> pm, StepP<R> a)
+{
+    wait_previous_grid();
+    e_edges<R, MODE>(g, s, coef_at<R>(slot), pm, a, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
+}
+
+// ------------------------------------------------ several steps per launch
+//
+// On a small grid (the paper's 491^2 geometry holds 10 MB, resident in L2)
+// each half step is a single partial wave, and the two launches of a step
+// cost about their launch latency.  k_stepp_multi advances `count` steps in
+// one cooperative launch: each block owns a 32 x 32 tile and updates it in
+// place, and instead of a grid-wide barrier it waits only for the tiles it
+// reads from.  The H half step at (i, j) reads E at (i+1, j) and (i, j+1),
+// so it waits until the right and upper tiles have finished the E half of
+// the previous step; the E half step reads H at (i-1, j) and (i, j-1), so it
+// waits until the left and lower tiles have finished this step's H half.
+// The same waits keep every read ahead of the overwrite: a tile overwrites
+// E (H) only after the tiles that read it have published the half step
+// that read it.  Each tile publishes its count of finished half steps (a
+// release store); the waits are acquire loads, bounded by `limit` clock
+// cycles, after which the block records ERR_TIMEOUT and raises the abort
+// word that every waiting block also watches, so the whole grid returns.
+
+__device__ __forceinline__ unsigned load_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void store_release(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait (bounded) until *flag has reached `want` (counts modulo 2^32).
+__device__ bool wait_flag(const unsigned *flag, unsigned want, unsigned *abort_word, unsigned *err, long long limit)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        if ((int)(load_acquire(flag) - want) >= 0) return true;
+        if (load_acquire(abort_word)) return false;
+        if (clock64() - t0 > limit) {
+            atomicOr(err, ERR_TIMEOUT);
+            atomicExch(abort_word, 1u);
+            return false;
+        }
+        __nanosleep(64);
+    }
+}
+
+constexpr int CT = 32, CBY = 8;  // tile of 32 x 32 nodes, 32 x 8 threads, 4 rows each
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(CT *CBY) k_stepp_multi(GeoP g, StateP<R> s, int slot, PmlP<R> pm, StepP<R> base,
+                                                         PlanP<R> plan, unsigned phase0, unsigned *flags,
+                                                         unsigned *abort_word, unsigned *err, long long limit)
+{
+    const Coef<R> &c = coef_at<R>(slot);
+    const int ntx = (g.nx + CT - 1) / CT, nty = (g.ny + CT - 1) / CT;
+    const int tile = blockIdx.x, bx = tile % ntx, by = tile / ntx;
+    const int i = bx * CT + threadIdx.x, j0 = by * CT + threadIdx.y;
+    const bool master = threadIdx.x == 0 && threadIdx.y == 0;
+    const int nR = bx + 1 < ntx ? tile + 1 : -1, nT = by + 1 < nty ? tile + ntx : -1;
+    const int nL = bx > 0 ? tile - 1 : -1, nB = by > 0 ? tile - ntx : -1;
+    __shared__ int go;
+    for (int t = 0; t < plan.count; ++t) {
+        const unsigned ph = phase0 + 2u * (unsigned)t;
+        if (master) {
+            bool ok = nR < 0 || wait_flag(flags + nR, ph, abort_word, err, limit);
+            ok = ok && (nT < 0 || wait_flag(flags + nT, ph, abort_word, err, limit));
+            __threadfence();
+            go = ok;
+        }
+        __syncthreads();
+        if (!go) return;
+#pragma unroll
+        for (int r = 0; r < CT / CBY; ++r) h_cell<R>(g, s, c, pm, i, j0 + r * CBY);
+        __syncthreads();
+        if (master) {
+            __threadfence();
+            store_release(flags + tile, ph + 1);
+            bool ok = nL < 0 || wait_flag(flags + nL, ph + 1, abort_word, err, limit);
+            ok = ok && (nB < 0 || wait_flag(flags + nB, ph + 1, abort_word, err, limit));
+            __threadfence();
+            go = ok;
+        }
+        __syncthreads();
+        if (!go) return;
+        StepP<R> a = base;
+        if (MODE == 0) {
+            const int n = plan.n0 + t;
+            a.src = plan.src + n;
+            a.gap_rec = plan.gap ? plan.gap + (long long)(n + 1) * plan.Mg : nullptr;
+            R *sl = plan.rec ? plan.rec + (long long)(n - plan.rec0) * plan.rec_step : nullptr;
+            a.rec[0] = sl;
+            a.rec[1] = sl ? sl + plan.Mdi0 : nullptr;
+        } else {
+            const int m = plan.n0 - t;
+            a.gap_src = plan.gap ? plan.gap + (long long)m * plan.Mg : nullptr;
+            R *sl = plan.rec + (long long)(m - 1 - plan.rec0) * plan.rec_step;
+            a.rec[0] = sl;
+            a.rec[1] = sl + plan.Mdi0;
+        }
+#pragma unroll
+        for (int r = 0; r < CT / CBY; ++r) e_edges<R, MODE>(g, s, c, pm, a, i, j0 + r * CBY);
+        __syncthreads();
+        if (master) {
+            __threadfence();
+            store_release(flags + tile, ph + 2);
+        }
+    }
+}
+
+// A wait on a flag nothing sets, for the self-test of the bounded wait.
+__global__ void k_wait_selftest(unsigned *words, long long limit)
+{
+    if (threadIdx.x == 0) wait_flag(words, 1u, words + 1, words + 2, limit);
+}
+
 }  // namespace
 
 template <typename R>
@@ -170,6 +296,62 @@ int launch_stepp(int mode, const GeoP &g, const StateP<R> &s, int c, const PmlP<
     return 2;
 }
 
+int stepp_multi_tiles(const GeoP &g) { return ((g.nx + CT - 1) / CT) * ((g.ny + CT - 1) / CT); }
+
+template <typename R>
+bool stepp_multi_fits(const GeoP &g)
+{
+    int dev = 0, sms = 0, per = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
+        cudaGetLastError();
+        return false;
+    }
+    int per1 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_stepp_multi<R, 0>, CT * CBY, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_stepp_multi<R, 1>, CT * CBY, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    per = per < per1 ? per : per1;
+    return (long long)per * sms >= stepp_multi_tiles(g);
+}
+
+template <typename R>
+int launch_stepp_multi(int mode, const GeoP &g, const StateP<R> &s, int c, const PmlP<R> &pm, const StepP<R> &base,
+                       const PlanP<R> &plan, unsigned phase0, unsigned *flags, unsigned *abort_word, unsigned *err,
+                       long long limit, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)stepp_multi_tiles(g));
+    cfg.blockDim = dim3(CT, CBY);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (mode == 0)
+        cudaLaunchKernelEx(&cfg, k_stepp_multi<R, 0>, g, s, c, pm, base, plan, phase0, flags, abort_word, err, limit);
+    else
+        cudaLaunchKernelEx(&cfg, k_stepp_multi<R, 1>, g, s, c, pm, base, plan, phase0, flags, abort_word, err, limit);
+    return 1;
+}
+
+void launch_wait_selftest(unsigned *words, long long limit, cudaStream_t st)
+{
+    k_wait_selftest<<<1, 32, 0, st>>>(words, limit);
+}
+
+template bool stepp_multi_fits<float>(const GeoP &);
+template bool stepp_multi_fits<double>(const GeoP &);
+template int launch_stepp_multi<float>(int, const GeoP &, const StateP<float> &, int, const PmlP<float> &,
+                                       const StepP<float> &, const PlanP<float> &, unsigned, unsigned *, unsigned *,
+                                       unsigned *, long long, cudaStream_t);
+template int launch_stepp_multi<double>(int, const GeoP &, const StateP<double> &, int, const PmlP<double> &,
+                                        const StepP<double> &, const PlanP<double> &, unsigned, unsigned *,
+                                        unsigned *, unsigned *, long long, cudaStream_t);
 template int launch_stepp<float>(int, const GeoP &, const StateP<float> &, int, const PmlP<float> &,
                                  const StepP<float> &, cudaStream_t);
 template int launch_stepp<double>(int, const GeoP &, const StateP<double> &, int,
