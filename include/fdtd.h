@@ -62,8 +62,8 @@ typedef enum fdtd_status {
                             word non-finite or above the stability-guard
                             bound (fdtd_set_stability_guard)                 */
     FDTD_ETIMEOUT = 6,   /* a bounded device wait gave up (the in-plane
-                            multi-step launch: a tile waited about a second
-                            for a neighbour)                                 */
+                            multi-step launch: a block waited about a second
+                            at a grid barrier)                               */
     FDTD_ERANGE = 7      /* a design density outside [0, 1]                    */
 } fdtd_status;
 
@@ -243,14 +243,14 @@ fdtd_status fdtd_set_sensitivity_terms(fdtd_ctx *ctx, int terms);
 fdtd_status fdtd_set_stability_guard(fdtd_ctx *ctx, int every, double max_abs);
 
 /* In-plane 2D contexts (pol = FDTD_POL_INPLANE): time steps per launch
- * (default 64; 1 = one launch per half step).  With more than one, a run of
- * steps is one cooperative launch in which each 32 x 32 tile advances as
- * soon as the neighbouring tiles it reads from have finished the half step
- * it needs (bounded waits: FDTD_ETIMEOUT from fdtd_sync if one gives up).
- * Used only when every tile can be resident at once on the device (the
- * paper's 491^2 geometry: 256 tiles); larger grids keep one launch per half
- * step.  Such passes are not replayed as CUDA graphs.  Results are identical
- * either way.  The other modes ignore the setting. */
+ * (default 1: one launch per half step).  With more than one, a run of
+ * steps is one cooperative launch, one block per SM, whose half steps are
+ * separated by grid-wide barriers with bounded waits (FDTD_ETIMEOUT from
+ * fdtd_sync if one gives up).  Results are bit-identical either way.  On a
+ * GB300 the barrier costs more than the launch boundary it replaces (about
+ * 12 against 6 us per step on the paper's 491^2 geometry), hence the
+ * default.  Such passes are not replayed as CUDA graphs.  The other modes
+ * ignore the setting. */
 fdtd_status fdtd_set_steps_per_launch(fdtd_ctx *ctx, int steps);
 
 /* Self-test of the bounded device wait the multi-step launch uses: one

@@ -215,9 +215,9 @@ struct fdtd_ctx {
     // polls a mapped host word the kernel writes and stops enqueuing once it
     // sees this pass's tag (not possible while capturing a graph; the error
     // word still reports the instability).
-    // In-plane 2D contexts: time steps per cooperative launch (1: two
-    // launches per step).
-    int multi_steps = 64;
+    // In-plane 2D contexts: time steps per cooperative launch (1, the
+    // default: two launches per step).
+    int multi_steps = 1;
     int guard_every = 256;
     double guard_bound = 0.0;  // 0: automatic, see guard_limit()
     unsigned guard_tag = 0;
@@ -925,9 +925,9 @@ struct CtxP final : fdtd_ctx {
     PmlP<R> pm{};
     double *misc = nullptr;
     unsigned *err = nullptr;
-    // Several steps per cooperative launch (k_stepp_multi): one finished-
-    // half-step word per 32 x 32 tile, then the abort word; the pass's count
-    // of half steps so far; whether every tile can be resident at once.
+    // Several steps per cooperative launch (k_stepp_multi): the barrier's
+    // words (arrival count, generation), then the abort word; the pass's
+    // count of half steps so far; whether the launch can be resident.
     unsigned *coop = nullptr;
     int ntiles = 0;
     unsigned coop_phase = 0;
@@ -968,7 +968,11 @@ struct CtxP final : fdtd_ctx {
     // in one cooperative launch.
     void launch_multi(int mode, const StateP<R> &st, PlanP<R> plan)
     {
-        const StepP<R> base = step_args();
+        StepP<R> base = step_args();
+        if (mode == 1) {
+            base.G[0] = G[0];  // the adjoint's sensitivity accumulators
+            base.G[1] = G[1];
+        }
         launches += launch_stepp_multi<R>(mode, geo, st, coef_slot, pm, base, plan, coop_phase, coop, coop + ntiles,
                                           err, WAIT_CYCLES, stream);
         coop_phase += 2u * (unsigned)plan.count;

@@ -220,16 +220,17 @@ struct PlanP {
     int Mg, rec0, n0, count;
 };
 
-// Blocks (32 x 32-node tiles) of the multi-step launch; whether they can
-// all be resident at once on the current device (required: the tiles wait
-// on their neighbours).
+// Words of the multi-step launch's barrier (two); whether
+// its blocks (one per SM) can all be resident at once on the current device
+// (required: they wait on one another).
 int stepp_multi_tiles(const GeoP &g);
 template <typename R>
 bool stepp_multi_fits(const GeoP &g);
 
-// plan.count steps in one cooperative launch (kernels_2dp.cu).  flags: one
-// word per tile holding its finished half steps, phase0 on entry; a wait
-// longer than `limit` clock cycles sets ERR_TIMEOUT in *err and *abort_word.
+// plan.count steps in one cooperative launch (kernels_2dp.cu).  flags: the
+// grid barrier's arrival count and generation (count zero between launches);
+// a wait longer than `limit` clock cycles sets ERR_TIMEOUT in *err and
+// *abort_word.
 template <typename R>
 int launch_stepp_multi(int mode, const GeoP &g, const StateP<R> &s, int coef_slot, const PmlP<R> &pm,
                        const StepP<R> &base, const PlanP<R> &plan, unsigned phase0, unsigned *flags,
