@@ -174,12 +174,12 @@ __device__ __forceinline__ void cpml_curl(const Geo3D &g, R *const (&psi)[3][2],
 // update; the others add the CPML terms (cpml_curl).
 template <typename R>
 __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
-    k_h3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm)
+    k_h3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm, int zrev)
 {
     wait_previous_grid();
     const Coef<R> &c = coef_at<R>(slot);
-    const int i0 = (blockIdx.x * TBX + threadIdx.x) * VX, j = blockIdx.y * TBY + threadIdx.y,
-              k = blockIdx.z * TBZ + threadIdx.z;
+    const int bz = zrev ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
+    const int i0 = (blockIdx.x * TBX + threadIdx.x) * VX, j = blockIdx.y * TBY + threadIdx.y, k = bz * TBZ + threadIdx.z;
     const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
     if (i0 >= n0 || j >= n1 || k >= n2) return;
     const long long q = k * g.PP + (long long)j * g.px + i0;
@@ -261,11 +261,12 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
 //   curl_x = dy Hz - dz Hy,  curl_y = dz Hx - dx Hz,  curl_z = dx Hy - dy Hx
 template <typename R, int MODE>
 __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
-    k_e3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm, Step3D<R> a3)
+    k_e3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm, Step3D<R> a3, int zrev)
 {
     wait_previous_grid();
     const Coef<R> &c = coef_at<R>(slot);
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TBY, z0 = blockIdx.z * TBZ;
+    const int bz = zrev ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TBY, z0 = bz * TBZ;
     const int i0 = x0 + threadIdx.x * VX, j = y0 + threadIdx.y, k = z0 + threadIdx.z;
     const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
     if (i0 >= n0 || j >= n1 || k >= n2) return;
@@ -559,15 +560,20 @@ int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, int c, const Pm
 {
     dim3 vblock(TBX, TBY, TBZ), vgrid((g.n[0] + TX - 1) / TX, (g.n[1] + TBY - 1) / TBY, (g.n[2] + TBZ - 1) / TBZ);
     const bool tf = mode == 0 && a.tf_inc;
-    launch_pdl(k_h3d<R>, vgrid, vblock, st, g, s, c, pm);
+    // The H half step sweeps the planes upwards and the E half step
+    // downwards (blocks start in blockIdx order), so each launch begins where
+    // the previous one ended, on planes whose fields are still in L2.  Each
+    // kernel reads only fields it does not write, so the order changes no
+    // result.
+    launch_pdl(k_h3d<R>, vgrid, vblock, st, g, s, c, pm, 0);
     if (tf) {
         const long long Lx = g.tf_hi[0] - g.tf_lo[0], Ly = g.tf_hi[1] - g.tf_lo[1] + 1,
                         Lz = g.tf_hi[2] - g.tf_lo[2] + 1;
         const long long nh = 2 * Lx * Ly + 2 * Lx * Lz;
         launch_pdl(k_tfsf_h<R>, dim3((unsigned)((nh + 255) / 256)), dim3(256), st, g, s, c, a.tf_inc);
     }
-    if (mode == 0) launch_pdl(k_e3d<R, 0>, vgrid, vblock, st, g, s, c, pm, a);
-    else launch_pdl(k_e3d<R, 1>, vgrid, vblock, st, g, s, c, pm, a);
+    if (mode == 0) launch_pdl(k_e3d<R, 0>, vgrid, vblock, st, g, s, c, pm, a, 1);
+    else launch_pdl(k_e3d<R, 1>, vgrid, vblock, st, g, s, c, pm, a, 1);
     if (tf) {
         const long long Lx = g.tf_hi[0] - g.tf_lo[0], Ly = g.tf_hi[1] - g.tf_lo[1] + 1,
                         Lz = g.tf_hi[2] - g.tf_lo[2] + 1;
