@@ -242,6 +242,14 @@ fdtd_status fdtd_set_sensitivity_terms(fdtd_ctx *ctx, int terms);
  * forward traffic at the default) and change no result. */
 fdtd_status fdtd_set_stability_guard(fdtd_ctx *ctx, int every, double max_abs);
 
+/* Width of the Gaussian design filter (Eq. 26) of a 2D E_z context created
+ * with filter_radius > 0: sigma (cells) replaces cfg->filter_sigma, the
+ * window keeps the create-time radius.  Lets an optimizer continue the
+ * filter (a wide filter first, a narrow one at the end) without a new
+ * context.  Synchronises the stream; the design has to be set again
+ * (FDTD_ESTATE until then).  FDTD_EINVAL for other contexts or sigma <= 0. */
+fdtd_status fdtd_set_filter_width(fdtd_ctx *ctx, double sigma);
+
 /* In-plane 2D contexts (pol = FDTD_POL_INPLANE): time steps per launch
  * (default 1: one launch per half step).  With more than one, a run of
  * steps is one cooperative launch, one block per SM, whose half steps are

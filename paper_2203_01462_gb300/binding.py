@@ -28,7 +28,7 @@ EXPORTS = ["fdtd_workspace_bytes", "fdtd_create", "fdtd_set_design", "fdtd_set_d
            "fdtd_gradient_static", "fdtd_gap_spectrum", "fdtd_ascent_step", "fdtd_mma_asymptotes", "fdtd_mma_solve",
            "fdtd_mirror_average", "fdtd_fix_design", "fdtd_grayness", "fdtd_threshold", "fdtd_set_graphs",
            "fdtd_set_l2_residency", "fdtd_set_sensitivity_terms", "fdtd_set_stability_guard",
-           "fdtd_set_steps_per_launch", "fdtd_selftest_bounded_wait"]
+           "fdtd_set_steps_per_launch", "fdtd_selftest_bounded_wait", "fdtd_set_filter_width"]
 
 
 TERM_PSI, TERM_EPS, TERM_SIGMA, TERM_ALL = 1, 2, 4, 7
@@ -105,6 +105,7 @@ def load():
             "fdtd_set_sensitivity_terms": [P, C.c_int],
             "fdtd_set_stability_guard": [P, C.c_int, C.c_double],
             "fdtd_set_steps_per_launch": [P, C.c_int],
+            "fdtd_set_filter_width": [P, C.c_double],
             "fdtd_selftest_bounded_wait": [P, C.c_longlong, P],
             "fdtd_threshold": [P, P, C.c_size_t, C.c_double],
             "fdtd_gap_history": [P, P, C.c_size_t],
@@ -286,6 +287,12 @@ class Solver:
         """Check the forward state every ``every`` steps (0: off) for words that
         are not finite or exceed ``max_abs`` (0: the automatic bound)."""
         _check(self.lib.fdtd_set_stability_guard(self.ctx, int(every), float(max_abs)), "fdtd_set_stability_guard")
+
+    def set_filter_width(self, sigma: float) -> None:
+        """New width (cells) of the Gaussian design filter; the design has to be set again."""
+        self.generation += 1
+        _check(self.lib.fdtd_set_filter_width(self.ctx, float(sigma)), "fdtd_set_filter_width")
+        self.w["filter_sigma"] = float(sigma)
 
     def set_steps_per_launch(self, steps: int) -> None:
         """In-plane 2D mode: time steps per cooperative launch (1: one launch per half step)."""

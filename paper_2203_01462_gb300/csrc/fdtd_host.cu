@@ -277,6 +277,8 @@ struct fdtd_ctx {
     virtual fdtd_status grayness(double *d_zeta) = 0;
     // L2 residency of the ping-pong state (2D E_z contexts; others ignore it).
     virtual fdtd_status set_l2(double) { return FDTD_OK; }
+    // New width of the design filter (2D E_z contexts with a filter).
+    virtual fdtd_status set_filter_sigma(double) { return FDTD_EINVAL; }
     // Blocks of one step launch and how many take the vector path (2D E_z).
     virtual void block_counts(long long *total, long long *vec) const { *total = *vec = 0; }
     // True when the passes run as few cooperative launches, which are not
@@ -616,9 +618,23 @@ struct Ctx2D final : fdtd_ctx {
         fill_pml<R>(c, c.nx, tab.data());
         fill_pml<R>(c, c.ny, tab.data() + 6 * c.nx);
         std::vector<R> src = source_table<R>(c, dt);
-        const int FR = c.filter_radius;
+        cudaStream_t st = stream;
+        FDTD_TRY(cuda_ok(cudaMemcpyAsync(pml_tab, tab.data(), tab.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
+        FDTD_TRY(cuda_ok(cudaMemcpyAsync(src_tab, src.data(), src.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
+        FDTD_TRY(upload_filter(c.filter_sigma));
+        launch_zero_bytes(err, 4 * sizeof(unsigned), st);
+        ++launches;
+        return cuda_ok(cudaStreamSynchronize(st));
+    }
+
+    // Weights exp(-k^2 / (2 sigma^2)), |k| <= filter_radius, of the Gaussian
+    // design filter (Eq. 26) and the per-row / per-column normalisations of
+    // the truncated window at the box edges, in both precisions.
+    fdtd_status upload_filter(double sigma)
+    {
+        const int FR = cfg.filter_radius;
         std::vector<double> w(2 * FR + 1), nx(geo.dnx), ny(geo.dny);
-        for (int k = -FR; k <= FR; ++k) w[k + FR] = FR ? exp(-(double)k * k / (2.0 * c.filter_sigma * c.filter_sigma)) : 1.0;
+        for (int k = -FR; k <= FR; ++k) w[k + FR] = FR ? exp(-(double)k * k / (2.0 * sigma * sigma)) : 1.0;
         auto norms = [&](std::vector<double> &v, int n) {
             for (int i = 0; i < n; ++i) {
                 double s = 0.0;
@@ -631,17 +647,22 @@ struct Ctx2D final : fdtd_ctx {
         norms(ny, geo.dny);
         std::vector<R> wR(w.begin(), w.end()), nxR(nx.begin(), nx.end()), nyR(ny.begin(), ny.end());
         cudaStream_t st = stream;
-        FDTD_TRY(cuda_ok(cudaMemcpyAsync(pml_tab, tab.data(), tab.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
-        FDTD_TRY(cuda_ok(cudaMemcpyAsync(src_tab, src.data(), src.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
         FDTD_TRY(cuda_ok(cudaMemcpyAsync(fw_R, wR.data(), wR.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
         FDTD_TRY(cuda_ok(cudaMemcpyAsync(fnx_R, nxR.data(), nxR.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
         FDTD_TRY(cuda_ok(cudaMemcpyAsync(fny_R, nyR.data(), nyR.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
         FDTD_TRY(cuda_ok(cudaMemcpyAsync(fw_D, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice, st)));
         FDTD_TRY(cuda_ok(cudaMemcpyAsync(fnx_D, nx.data(), nx.size() * sizeof(double), cudaMemcpyHostToDevice, st)));
         FDTD_TRY(cuda_ok(cudaMemcpyAsync(fny_D, ny.data(), ny.size() * sizeof(double), cudaMemcpyHostToDevice, st)));
-        launch_zero_bytes(err, 4 * sizeof(unsigned), st);
-        ++launches;
+        // the host vectors go out of scope: finish the copies first
         return cuda_ok(cudaStreamSynchronize(st));
+    }
+
+    fdtd_status set_filter_sigma(double sigma) override
+    {
+        if (cfg.filter_radius <= 0) return FDTD_EINVAL;
+        FDTD_TRY(upload_filter(sigma));
+        cfg.filter_sigma = sigma;
+        return FDTD_OK;
     }
 
     Coef<R> coef() const { return make_coef<R>(cfg, dt, sigma_max, gamma_scale, terms); }
@@ -1722,6 +1743,15 @@ fdtd_status fdtd_set_stability_guard(fdtd_ctx *ctx, int every, double max_abs)
     ctx->guard_every = every;
     ctx->guard_bound = max_abs;
     ctx->drop_graphs();  // a captured forward pass holds the old checks
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_set_filter_width(fdtd_ctx *ctx, double sigma)
+{
+    if (!ctx || !(sigma > 0) || !isfinite(sigma)) return FDTD_EINVAL;
+    FDTD_TRY(ctx->set_filter_sigma(sigma));
+    // rho~ = F(rho) changes: the design has to be set again
+    ctx->has_design = ctx->fwd_done = ctx->adj_done = false;
     return FDTD_OK;
 }
 

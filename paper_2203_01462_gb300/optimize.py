@@ -97,6 +97,16 @@ def damping_levels(start: float = 10.0, stages: int = 6) -> list:
     return [start ** (1.0 - j / (stages - 1)) for j in range(stages)]
 
 
+def filter_widths(start_fwhm: float = 5.0, end_fwhm: float = 2.0, stages: int = 6) -> list:
+    """Gaussian widths sigma (cells) of a filter continuation: the full width
+    at half maximum shrinking geometrically from ``start_fwhm`` to
+    ``end_fwhm`` over ``stages`` stages (sigma = FWHM / (2 sqrt(2 ln 2)))."""
+    c = 2.0 * math.sqrt(2.0 * math.log(2.0))
+    if stages <= 1:
+        return [end_fwhm / c]
+    return [start_fwhm * (end_fwhm / start_fwhm) ** (j / (stages - 1)) / c for j in range(stages)]
+
+
 @dataclasses.dataclass
 class GcmmaHistory:
     W: list = dataclasses.field(default_factory=list)          # W~ at each accepted outer iterate
@@ -121,7 +131,7 @@ def optimize_gcmma(s: Solver, rho0=None, max_iters: int = 600, levels=None, sigm
                    move: float = 0.5, min_inner: int = 12, norm_drop: float = 0.7, zeta_stop: float = 0.005,
                    max_inner: int = 10, tol: float = 1e-10, checkpoint: str | None = None,
                    checkpoint_every: int = 1, resume: str | None = None, fixed=None, fixed_value: float = 1.0,
-                   symmetry: int | None = None):
+                   symmetry: int | None = None, widths=None):
     """GCMMA loop of Sec. 3.2 with the damping continuation.
 
     Stage j solves max W~ at damping factor ``levels[j]`` with GCMMA from the
@@ -142,9 +152,19 @@ def optimize_gcmma(s: Solver, rho0=None, max_iters: int = 600, levels=None, sigm
     paper's fixed metal blocks); ``symmetry``: an axis across whose design
     mid-plane the design stays mirror-symmetric (gradients are
     mirror-averaged).  Variables with a zero gradient do not move under MMA,
-    so both constraints hold exactly.  Returns (rho, history)."""
+    so both constraints hold exactly.
+
+    ``widths``: filter continuation, one Gaussian width (cells) per stage
+    (``filter_widths``), set with the damping level at every stage change;
+    None keeps the context's filter.  Returns (rho, history)."""
     t = torch
     levels = list(damping_levels() if levels is None else levels)
+    if widths is not None and len(widths) != len(levels):
+        raise ValueError("one filter width per damping level")
+
+    def set_stage_filter(j):
+        if widths is not None:
+            s.set_filter_width(widths[j])
     n = s.n_design
     h = GcmmaHistory()
     mask = None
@@ -172,6 +192,7 @@ def optimize_gcmma(s: Solver, rho0=None, max_iters: int = 600, levels=None, sigm
         norm0 = float(z["norm0"])
         for f in _FIELDS:
             getattr(h, f).extend(z["h_" + f].tolist())
+        set_stage_filter(stage)
         s.set_design(rho)
         s.set_damping(sigma_max, levels[stage])
     else:
@@ -183,6 +204,7 @@ def optimize_gcmma(s: Solver, rho0=None, max_iters: int = 600, levels=None, sigm
         state = s.mma_state()
         k = kk = stage = it_stage = 0
         norm0 = 0.0
+        set_stage_filter(0)
         W, g = evaluate(rho, levels[0])
     y = t.empty_like(rho)
     while True:
@@ -193,9 +215,11 @@ def optimize_gcmma(s: Solver, rho0=None, max_iters: int = 600, levels=None, sigm
         if it_stage == 0:
             norm0 = norm
         if stage + 1 < len(levels) and it_stage >= min_inner and norm <= (1.0 - norm_drop) * norm0:
-            # subproblem solved: next damping level, a fresh GCMMA run from this design
+            # subproblem solved: next damping level (and filter width), a
+            # fresh GCMMA run from this design
             stage += 1
             it_stage = kk = 0
+            set_stage_filter(stage)
             W, g = evaluate(rho, levels[stage])
             continue
         h.W.append(W)

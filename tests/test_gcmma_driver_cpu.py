@@ -129,3 +129,48 @@ def test_checkpoint_resume_is_exact(tmp_path):
     r_res, h_res = optimize_gcmma(s3, None, max_iters=14, resume=ck, **kw)
     assert np.array_equal(r_full.numpy(), r_res.numpy())
     assert h_full.W == h_res.W and h_full.stage == h_res.stage and h_full.inner == h_res.inner
+
+
+def test_filter_widths_schedule():
+    """FWHM shrinking geometrically from 5 to 2 cells over 4 stages, as
+    Gaussian sigma = FWHM / 2.3548."""
+    from paper_2203_01462_gb300.optimize import filter_widths
+    w = filter_widths(5.0, 2.0, 4)
+    c = 2.0 * np.sqrt(2.0 * np.log(2.0))
+    assert len(w) == 4
+    assert w[0] == pytest.approx(5.0 / c) and w[-1] == pytest.approx(2.0 / c)
+    r = [w[k + 1] / w[k] for k in range(3)]
+    assert np.allclose(r, r[0]) and r[0] < 1.0
+    assert filter_widths(5.0, 2.0, 1) == [pytest.approx(2.0 / c)]
+
+
+def test_filter_continuation_is_set_with_each_stage():
+    """With widths, the driver sets the stage's filter width before the
+    stage's first evaluation, and at resume; the number of widths must match
+    the number of damping levels."""
+    class Recording(ToySolver):
+        def __init__(self):
+            super().__init__()
+            self.widths = []
+            self.events = []
+
+        def set_filter_width(self, sigma):
+            self.widths.append(sigma)
+            self.events.append(("filter", sigma))
+
+        def set_damping(self, sigma_max, gamma_scale):
+            super().set_damping(sigma_max, gamma_scale)
+            self.events.append(("damping", gamma_scale))
+
+    s = Recording()
+    rho, h = optimize_gcmma(s, np.full(40, 0.5), max_iters=60, levels=[4.0, 2.0, 1.0], min_inner=3, norm_drop=0.7,
+                            widths=[2.0, 1.5, 1.0], zeta_stop=0.0)
+    stages = sorted(set(h.stage))
+    assert stages == [0, 1, 2]
+    assert s.widths == [2.0, 1.5, 1.0]
+    # each width comes right before the evaluation at its damping level
+    for sigma, gs in zip([2.0, 1.5, 1.0], [4.0, 2.0, 1.0]):
+        k = s.events.index(("filter", sigma))
+        assert s.events[k + 1] == ("damping", gs)
+    with pytest.raises(ValueError):
+        optimize_gcmma(Recording(), np.full(40, 0.5), max_iters=2, levels=[4.0, 1.0], widths=[1.0])

@@ -129,3 +129,42 @@ def test_gcmma_on_the_device_is_monotone_and_resumes_exactly(tmp_path):
     r_res, h_res = optimize_gcmma(Solver(w), None, max_iters=8, resume=ck, **kw)
     assert np.array_equal(r_full.cpu().numpy(), r_res.cpu().numpy())
     assert h.W == h_res.W and h.inner == h_res.inner
+
+
+def test_filter_width_change_matches_oracle():
+    """fdtd_set_filter_width: after narrowing the filter of a context, W~ and
+    the gradient (F^T with the new width) match the oracle run with that
+    width (FP64); the design has to be set again after the change."""
+    from paper_2203_01462_gb300.binding import FdtdError, Solver
+    w = medium("f64")
+    rho = I.rho_uniform(w, 53)
+    s = Solver(w)
+    s.evaluate(rho, 5e5, 2.0)
+    s.set_filter_width(0.7)
+    with pytest.raises(FdtdError) as e:
+        s.forward()
+    assert e.value.status == 4
+    W, g = s.evaluate(rho, 5e5, 2.0)
+    s.sync()
+    ref = O.gradient(dict(w, filter_sigma=0.7), rho, 5e5, 2.0)
+    assert abs(float(W.item()) - ref["W"]) <= 1e-10 * abs(ref["W"])
+    gg = g.cpu().numpy()
+    assert np.linalg.norm(gg - ref["grad"]) <= 1e-9 * np.linalg.norm(ref["grad"])
+
+
+def test_gcmma_with_filter_continuation_ends_on_the_last_width():
+    """GCMMA through two damping stages with the filter narrowing from FWHM 3
+    to 1.5 cells: the objective the driver reports for its final design is
+    the oracle's W~ of that design with the last filter width and damping."""
+    import torch
+    from paper_2203_01462_gb300.binding import Solver
+    from paper_2203_01462_gb300.optimize import filter_widths, optimize_gcmma
+    w = medium("f64")
+    s = Solver(w)
+    rho0 = I.zero_gap(w, np.full(I.design_shape(w), 0.3))
+    widths = filter_widths(3.0, 1.5, 2)
+    rho, h = optimize_gcmma(s, rho0, max_iters=8, levels=[3.0, 1.0], min_inner=2, norm_drop=-1e9, zeta_stop=0.0,
+                            widths=widths)
+    assert 1 in h.stage
+    ref = O.forward(dict(w, filter_sigma=widths[-1]), rho.cpu().numpy(), 0.0, 1.0)["W"]
+    assert abs(h.W[-1] - ref) <= 1e-9 * abs(ref)
