@@ -1,7 +1,9 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
-Small cases span several 32 x 8 thread tiles with ragged edges; the 160^2
-workload is the full FP64 parity configuration.  Tolerances: FP64 fields
+Small cases are ragged against the kernel's 128 x 4 node tiles (a partial
+tile in x, ten tile rows in y) and so run the scalar edge path; the 160^2
+workload is the full FP64 parity configuration.  Grids large enough for the
+float4 interior path are in test_parity_2d_vector.py.  Tolerances: FP64 fields
 agree with the oracle to round-off (W 1e-10 relative, gradient 1e-9
 L2-relative); FP32 fields within 1e-4 on W and 1e-3 L2-relative on the
 gradient.
@@ -16,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 
 def fast_case(real="f64", **kw):
-    """41 x 37 nodes (ragged against 32 x 8 tiles), 6-cell CPML, coarse dx
+    """41 x 37 nodes (ragged against 128 x 4 tiles), 6-cell CPML, coarse dx
     and a broadband pulse so that a few hundred steps see it."""
     w = I.small_2d(nx=kw.pop("nx", 41), ny=kw.pop("ny", 37), nsteps=kw.pop("nsteps", 400), dx=20e-9,
                    npml=kw.pop("npml", 6), design=kw.pop("design", (17, 15)), real=real, **kw)
