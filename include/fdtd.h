@@ -261,6 +261,22 @@ fdtd_status fdtd_set_filter_width(fdtd_ctx *ctx, double sigma);
  * ignore the setting. */
 fdtd_status fdtd_set_steps_per_launch(fdtd_ctx *ctx, int steps);
 
+/* 3D contexts: time steps per wavefront launch of the leapfrog (Eq. 10,
+ * Sec. 3.2).  steps = 0 runs every step as two launches over the whole
+ * grid, the H half step then the E half step.  steps = 1 .. 8 runs up to
+ * that many steps per persistent cooperative launch (fewer when their L2
+ * window would exceed half the L2): the grid is cut into z slabs of two
+ * planes, and each slab's E half step runs right after the H half steps it
+ * reads, and the next step's H right after the E half steps it reads, while
+ * those fields are still in L2.  Blocks wait on per-slab counters of
+ * finished tiles; a wait that does not end within about a second makes the
+ * pass report FDTD_ETIMEOUT at fdtd_sync.  Every node's arithmetic is that
+ * of the two-launch form, so the results are bit-identical.  Default 0.
+ * Wavefront passes are not replayed as CUDA graphs.  Returns FDTD_EINVAL
+ * for other modes or steps outside 0 .. 8, FDTD_ECUDA when the device
+ * cannot run the cooperative launch. */
+fdtd_status fdtd_set_wavefront(fdtd_ctx *ctx, int steps);
+
 /* Self-test of the bounded device wait the multi-step launch uses: one
  * thread waits on a flag that nothing sets, for limit_cycles clock cycles.
  * d_words: 16 bytes of caller device memory (16-byte aligned), overwritten.

@@ -28,7 +28,8 @@ EXPORTS = ["fdtd_workspace_bytes", "fdtd_create", "fdtd_set_design", "fdtd_set_d
            "fdtd_gradient_static", "fdtd_gap_spectrum", "fdtd_ascent_step", "fdtd_mma_asymptotes", "fdtd_mma_solve",
            "fdtd_mirror_average", "fdtd_fix_design", "fdtd_grayness", "fdtd_threshold", "fdtd_set_graphs",
            "fdtd_set_l2_residency", "fdtd_set_sensitivity_terms", "fdtd_set_stability_guard",
-           "fdtd_set_steps_per_launch", "fdtd_selftest_bounded_wait", "fdtd_set_filter_width"]
+           "fdtd_set_steps_per_launch", "fdtd_selftest_bounded_wait", "fdtd_set_filter_width",
+           "fdtd_set_wavefront"]
 
 
 TERM_PSI, TERM_EPS, TERM_SIGMA, TERM_ALL = 1, 2, 4, 7
@@ -105,6 +106,7 @@ def load():
             "fdtd_set_sensitivity_terms": [P, C.c_int],
             "fdtd_set_stability_guard": [P, C.c_int, C.c_double],
             "fdtd_set_steps_per_launch": [P, C.c_int],
+            "fdtd_set_wavefront": [P, C.c_int],
             "fdtd_set_filter_width": [P, C.c_double],
             "fdtd_selftest_bounded_wait": [P, C.c_longlong, P],
             "fdtd_threshold": [P, P, C.c_size_t, C.c_double],
@@ -297,6 +299,11 @@ class Solver:
     def set_steps_per_launch(self, steps: int) -> None:
         """In-plane 2D mode: time steps per cooperative launch (1: one launch per half step)."""
         _check(self.lib.fdtd_set_steps_per_launch(self.ctx, int(steps)), "fdtd_set_steps_per_launch")
+
+    def set_wavefront(self, steps: int) -> None:
+        """3D: time steps per wavefront launch (0: two launches per step, the H
+        then the E half step over the whole grid); results are bit-identical."""
+        _check(self.lib.fdtd_set_wavefront(self.ctx, int(steps)), "fdtd_set_wavefront")
 
     def set_graphs(self, mode: int) -> None:
         """0: plain launches, 1: replay CUDA graphs of whole passes, 2: automatic by grid size."""

@@ -284,6 +284,9 @@ struct fdtd_ctx {
     // True when the passes run as few cooperative launches, which are not
     // captured into graphs.
     virtual bool plain_launches() const { return false; }
+    // 3D contexts: up to `steps` steps per wavefront launch (0: split half-step
+    // launches).  Returns FDTD_EINVAL for other modes.
+    virtual fdtd_status set_wavefront(int) { return FDTD_EINVAL; }
     long long n_free = 0;  // design nodes outside the gap
     virtual void *rho_stage() = 0;
     virtual double *grad_stage() = 0;
@@ -1315,6 +1318,59 @@ struct Ctx3D final : fdtd_ctx {
     unsigned *err = nullptr;
     R *tf_tab = nullptr, *tf_col = nullptr;  // plane wave: incident table, column state
 
+    // Wavefront launches (k_wave3d): per-slab counters and the job lists of
+    // launches of 1 .. WAVE_MAX steps.
+    static constexpr int WAVE_MAX = 8;
+    static constexpr long long WAIT_CYCLES = 2000000000LL;  // about one second
+    unsigned *wcnt = nullptr;
+    int *wjobs = nullptr;
+    int nslab = 0, wgx = 0, wtpi = 1, wipr = 0, wips = 0;
+    int wave_req = 0;                    // requested steps per launch (0: half-step launches)
+    int wave_blocks[2] = {0, 0};         // resident blocks (forward, adjoint kernel); 0: unavailable
+    int wave_lag[WAVE_MAX + 1] = {};
+    long long wave_off[WAVE_MAX + 1] = {};
+    double l2_budget = 0.0;
+
+    bool wave_on() const { return wave_req > 0 && wave_blocks[0] > 0 && wave_blocks[1] > 0; }
+    bool plain_launches() const override { return wave_on(); }
+    fdtd_status set_wavefront(int steps) override
+    {
+        if (steps < 0 || steps > WAVE_MAX) return FDTD_EINVAL;
+        if (steps > 0 && (wave_blocks[0] <= 0 || wave_blocks[1] <= 0)) return FDTD_ECUDA;
+        wave_req = steps;
+        return FDTD_OK;
+    }
+    // Steps per launch: the largest count up to the request whose L2 window
+    // (the slabs between the leading H and the trailing E job, lag (2c - 1)
+    // + 2 slabs of E and H) fits the budget.
+    int wave_count() const
+    {
+        const double slab = 2.0 * (double)geo.PP * 6.0 * sizeof(R);
+        int best = 1;
+        for (int c = 2; c <= wave_req; ++c)
+            if ((wave_lag[c] * (2.0 * c - 1.0) + 2.0) * slab <= l2_budget) best = c;
+        return best;
+    }
+    Wave3D<R> wave_plan(int count) const
+    {
+        Wave3D<R> w{};
+        w.jobs = wjobs + wave_off[count];
+        w.cnt = wcnt;
+        w.count = count;
+        w.nslab = nslab;
+        w.gx = wgx;
+        w.ipr = wipr;
+        w.ips = wips;
+        w.tpi = wtpi;
+        w.tf_row = tf_tab ? tfsf_row(geo) : 0;
+        return w;
+    }
+    void wave_reset()
+    {
+        launch_zero_bytes(wcnt, (size_t)(2 * nslab + 2) * sizeof(unsigned), stream);
+        ++launches;
+    }
+
     void *rho_stage() override { return rstage; }
     double *grad_stage() override { return gstage; }
     double *W_dev() override { return misc; }
@@ -1398,6 +1454,19 @@ struct Ctx3D final : fdtd_ctx {
             tf_tab = cv.take<R>((size_t)N * tfsf_row(geo));
             tf_col = cv.take<R>(4 * (size_t)c.nz);
         }
+        nslab = (c.nz + WAVE3D_TZ - 1) / WAVE3D_TZ;
+        wgx = (c.nx + WAVE3D_TX - 1) / WAVE3D_TX;
+        wtpi = std::min(4, wgx);
+        wipr = (wgx + wtpi - 1) / wtpi;
+        wips = ((c.ny + WAVE3D_TY - 1) / WAVE3D_TY) * wipr;
+        wcnt = cv.take<unsigned>(2 * (size_t)nslab + 2);
+        long long njobs = 0;
+        for (int k = 1; k <= WAVE_MAX; ++k) {
+            wave_off[k] = njobs;
+            njobs += 2LL * k * nslab;
+        }
+        wjobs = cv.take<int>((size_t)njobs);
+        if (2LL * WAVE_MAX * nslab * wips >= (1LL << 31)) wave_req = 0;  // item index beyond int
         if (pml_tab) {
             R *t = pml_tab;
             for (int a = 0; a < 3; ++a) {
@@ -1423,6 +1492,27 @@ struct Ctx3D final : fdtd_ctx {
         FDTD_TRY(cuda_ok(cudaMemcpyAsync(src_tab, src.data(), src.size() * sizeof(R), cudaMemcpyHostToDevice, st)));
         launch_zero_bytes(err, 4 * sizeof(unsigned), st);
         ++launches;
+        // wavefront job lists: the lag (in slabs) keeps a job's prerequisites
+        // about one wave of blocks (G items) ahead of it
+        wave_blocks[0] = wave3d_blocks<R>(0);
+        wave_blocks[1] = wave3d_blocks<R>(1);
+        {
+            int dev = 0, l2 = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+            l2_budget = 0.5 * (double)l2;
+            const long long G = std::max(1, std::min(wave_blocks[0], wave_blocks[1]));
+            std::vector<int> all;
+            for (int k = 1; k <= WAVE_MAX; ++k) {
+                const long long per_key = 2LL * k * wips;
+                wave_lag[k] = (int)std::max<long long>(2, 1 + (G + per_key - 1) / per_key);
+                const std::vector<int> j = wave3d_jobs(nslab, k, wave_lag[k]);
+                all.insert(all.end(), j.begin(), j.end());
+            }
+            FDTD_TRY(cuda_ok(cudaMemcpyAsync(wjobs, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, st)));
+            launch_zero_bytes(wcnt, (size_t)(2 * nslab + 2) * sizeof(unsigned), st);
+            ++launches;
+        }
         if (c.tfsf) {
             // the incident wave does not depend on rho or the damping: one
             // column run per context, driven by the source plane
@@ -1481,6 +1571,28 @@ struct Ctx3D final : fdtd_ctx {
     {
         Step3D<R> a{};
         a.rho_t = rho_t;
+        if (wave_on()) {
+            // runs end on multiples of the guard interval, so the guard sees
+            // every step it checks
+            const int T = wave_count();
+            for (int n = n0; n < n0 + count;) {
+                int end = n0 + count;
+                if (guarding && guard_every > 0) end = std::min(end, (n / guard_every + 1) * guard_every);
+                const int cnt = std::min(T, end - n);
+                Wave3D<R> w = wave_plan(cnt);
+                w.n0 = n;
+                w.rec0 = n0;
+                w.src = src_tab;
+                w.gap = (gap && Mg) ? gap_hist : nullptr;
+                w.rec = rec_base;
+                w.tf = tf_tab;
+                launches += launch_wave3d<R>(0, geo, F, coef_slot, pm, a, w, wave_blocks[0], err, WAIT_CYCLES, stream);
+                cell_updates += (long long)cnt * ncells;
+                n += cnt;
+                if (guard_after<R>(n, F_base, state_bytes)) break;
+            }
+            return;
+        }
         for (int n = n0; n < n0 + count; ++n) {
             a.src = src_tab + n;
             a.gap_rec = (gap && Mg) ? gap_hist + (size_t)(n + 1) * 3 * Mg : nullptr;
@@ -1497,10 +1609,24 @@ struct Ctx3D final : fdtd_ctx {
         Step3D<R> a{};
         a.rho_t = rho_t;
         a.G = G;
-        for (int m = m_hi; m > m_lo; --m) {
-            a.gap_src = Mg ? gap_hist + (size_t)m * 3 * Mg : nullptr;
-            a.rec = rec + (size_t)(m - 1 - slot0) * 3 * Mdi;
-            launches += launch_step3d<R>(1, geo, A, coef_slot, pm, a, stream);
+        if (wave_on()) {
+            const int T = wave_count();
+            for (int m = m_hi; m > m_lo;) {
+                const int cnt = std::min(T, m - m_lo);
+                Wave3D<R> w = wave_plan(cnt);
+                w.n0 = m;
+                w.rec0 = slot0;
+                w.gap = Mg ? gap_hist : nullptr;
+                w.rec = rec;
+                launches += launch_wave3d<R>(1, geo, A, coef_slot, pm, a, w, wave_blocks[1], err, WAIT_CYCLES, stream);
+                m -= cnt;
+            }
+        } else {
+            for (int m = m_hi; m > m_lo; --m) {
+                a.gap_src = Mg ? gap_hist + (size_t)m * 3 * Mg : nullptr;
+                a.rec = rec + (size_t)(m - 1 - slot0) * 3 * Mdi;
+                launches += launch_step3d<R>(1, geo, A, coef_slot, pm, a, stream);
+            }
         }
         cell_updates += (long long)(m_hi - m_lo) * ncells;
     }
@@ -1512,6 +1638,7 @@ struct Ctx3D final : fdtd_ctx {
         launch_zero_bytes(F_base, state_bytes, st);
         if (Mg) launch_zero_bytes(gap_hist, 3 * Mg * sizeof(R), st);
         launches += 2;
+        if (wave_on()) wave_reset();
         guarding = true;
         if (K <= 0) {
             advance_forward(0, N, true, rec);
@@ -1539,6 +1666,7 @@ struct Ctx3D final : fdtd_ctx {
         launch_zero_bytes(A_base, state_bytes, st);
         launch_zero_bytes(G, Mdi * sizeof(double), st);
         launches += 2;
+        if (wave_on()) wave_reset();
         if (K <= 0) {
             advance_adjoint(N, 0, 0);
         } else {
@@ -1759,6 +1887,14 @@ fdtd_status fdtd_set_steps_per_launch(fdtd_ctx *ctx, int steps)
 {
     if (!ctx || steps < 1 || steps > 4096) return FDTD_EINVAL;
     ctx->multi_steps = steps;
+    ctx->drop_graphs();  // captured passes hold the old launches
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_set_wavefront(fdtd_ctx *ctx, int steps)
+{
+    if (!ctx) return FDTD_EINVAL;
+    FDTD_TRY(ctx->set_wavefront(steps));
     ctx->drop_graphs();  // captured passes hold the old launches
     return FDTD_OK;
 }

@@ -2,6 +2,8 @@
 // the kernel translation units.  Nothing here crosses the C ABI.
 #pragma once
 
+#include <vector>
+
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -247,6 +249,46 @@ void launch_wait_selftest(unsigned *words, long long limit, cudaStream_t st);
 template <typename R>
 int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, int coef_slot, const Pml3D<R> &pm,
                   const Step3D<R> &a, cudaStream_t st);
+
+// Several 3D steps in one persistent launch (kernels_3d.cu, k_wave3d).
+// The grid is cut into z slabs of two planes; an item is up to `tpi`
+// x-adjacent node tiles of one row of one slab, and a job is every item of
+// one half step ("phase": 2t = H of step t, 2t+1 = E of step t) on one slab.
+// jobs[] lists the 2 count nslab jobs (phase << 16 | slab) in an order in
+// which every job comes after the jobs it depends on (E_t(s) on H_t(s),
+// H_t(s-1); H_t(s) on E_{t-1}(s), E_{t-1}(s+1)); blocks take the items in
+// that order, round-robin, and wait (bounded) on per-slab counters of
+// finished items.
+template <typename R>
+struct Wave3D {
+    const int *jobs;
+    unsigned *cnt;  // [nslab] H items done, [nslab] E items done, abort word, finished blocks
+    int count, nslab, gx, ipr, ips, tpi;
+    int n0, rec0;   // forward: steps n0 .. n0+count-1, design record slot n - rec0;
+                    // adjoint: m = n0 down to n0-count+1, record slot m-1-rec0
+    const R *src;   // forward source table (indexed by n)
+    R *gap;         // gap history (forward writes row n+1, adjoint reads row m) or null
+    R *rec;         // design records or null (forward)
+    const R *tf;    // incident table of the plane wave (forward) or null
+    int tf_row;
+};
+
+// Job order of one wavefront launch: job (p, s) has key s + lag p and the
+// jobs are sorted by key, phase ascending within a key.  lag >= 2.
+std::vector<int> wave3d_jobs(int nslab, int count, int lag);
+// Blocks one wavefront launch keeps resident (mode 0 forward, 1 adjoint),
+// or 0 when the device cannot run it as a cooperative launch.
+template <typename R>
+int wave3d_blocks(int mode);
+// One wavefront launch of w.count steps on `blocks` blocks (cooperative).
+// a0 carries rho_t and (adjoint) G; the per-step pointers come from w.
+// A wait longer than `limit` clock cycles sets ERR_TIMEOUT in *err and the
+// abort word; a launch that finds the abort word set does nothing.
+template <typename R>
+int launch_wave3d(int mode, const Geo3D &g, const State3D<R> &s, int coef_slot, const Pml3D<R> &pm,
+                  const Step3D<R> &a0, const Wave3D<R> &w, int blocks, unsigned *err, long long limit,
+                  cudaStream_t st);
+constexpr int WAVE3D_TX = 32, WAVE3D_TY = 8, WAVE3D_TZ = 2;  // nodes of one tile
 
 // The incident plane wave of a tfsf grid: one block steps the 1D column
 // (E_x, H_y, their z-CPML terms in col, 4 nz words, cleared here) for

@@ -22,6 +22,8 @@
 // rho~ at that node (Eq. 5); the adjoint sums the Eq. (25) brackets of the
 // three components into the node's FP64 accumulator.
 
+#include <algorithm>
+
 #include "coef_slots.cuh"
 #include "fdtd_internal.h"
 #include "launch.cuh"
@@ -40,6 +42,7 @@ namespace {
 // registers, no spills) 38.8 / 44.6.
 constexpr int VX = 4, TBX = 8, TBY = 8, TBZ = 2;
 constexpr int TX = TBX * VX;
+static_assert(WAVE3D_TX == TX && WAVE3D_TY == TBY && WAVE3D_TZ == TBZ, "wavefront tiles are the step tiles");
 
 __device__ __forceinline__ bool in_range(int v, int lo, int n) { return (unsigned)(v - lo) < (unsigned)n; }
 
@@ -68,6 +71,45 @@ __device__ __forceinline__ void st4(double *p, const double (&o)[4])
     reinterpret_cast<double2 *>(p)[0] = make_double2(o[0], o[1]);
     reinterpret_cast<double2 *>(p)[1] = make_double2(o[2], o[3]);
 }
+// Loads for the persistent wavefront kernel, which reads fields other blocks
+// of the same launch wrote: plain (coherent) global loads, never the
+// read-only path that `const __restrict__` pointers allow.
+__device__ __forceinline__ void ld4c(const float *p, float (&o)[4])
+{
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void ld4c(const double *p, double (&o)[4])
+{
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+template <bool COH, typename R>
+__device__ __forceinline__ void ldv(const R *p, R (&o)[4])
+{
+    if constexpr (COH) ld4c(p, o);
+    else ld4(p, o);
+}
+
+// Roundings of the plain curl update fixed, so that the half-step kernels
+// and the wavefront kernel (other code around the same arithmetic) give the
+// same bits: the scaled curl is rounded, then subtracted (H) or added with
+// one fused multiply-add by 1/eps (E).
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Plane-wave face corrections with their rounding fixed (one fused
+// multiply-add, the E-face product rounded first), so that the folded and
+// the separate-launch forms give the same bits.
+__device__ __forceinline__ float tf_fma(float a, float b, float x) { return __fmaf_rn(a, b, x); }
+__device__ __forceinline__ double tf_fma(double a, double b, double x) { return __fma_rn(a, b, x); }
+__device__ __forceinline__ float tf_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double tf_mul(double a, double b) { return __dmul_rn(a, b); }
+
 template <typename R>
 __device__ __forceinline__ void zero4(R (&o)[4])
 {
@@ -99,7 +141,7 @@ __device__ __forceinline__ long long pidx(const Geo3D &g, int ax, int s, int i, 
 // k, and the psi arrays of y- and z-slabs are x-contiguous, so psi moves as
 // one vector; along x both are taken per node.  Every psi and coefficient
 // load is issued before any store.
-template <typename R, bool HALF>
+template <typename R, bool HALF, bool COH>
 __device__ __forceinline__ void cpml_curl(const Geo3D &g, R *const (&psi)[3][2], const R *const (&tb)[3],
                                           const R *const (&tc)[3], const R *const (&tk)[3], int i0, int j, int k,
                                           int sy, int sz, R S, const R (&d)[3][2][4], R (&out)[3][4])
@@ -121,9 +163,9 @@ __device__ __forceinline__ void cpml_curl(const Geo3D &g, R *const (&psi)[3][2],
                 for (int v = 0; v < 4; ++v)
                     ps[c][h][v] = sx[v] >= 0 ? psi[c][h][pidx(g, 0, sx[v], i0 + v, j, k)] : R(0);
             } else if (ax == 1) {
-                if (sy >= 0) ld4(psi[c][h] + iy, ps[c][h]);
+                if (sy >= 0) ldv<COH>(psi[c][h] + iy, ps[c][h]);
             } else {
-                if (sz >= 0) ld4(psi[c][h] + iz, ps[c][h]);
+                if (sz >= 0) ldv<COH>(psi[c][h] + iz, ps[c][h]);
             }
         }
     // coefficient tables are read-only: non-coherent loads, free to move past stores
@@ -149,7 +191,7 @@ __device__ __forceinline__ void cpml_curl(const Geo3D &g, R *const (&psi)[3][2],
             }
         }
 #pragma unroll
-        for (int v = 0; v < 4; ++v) out[c][v] = S * (t[0][v] - t[1][v]);
+        for (int v = 0; v < 4; ++v) out[c][v] = rn_mul(S, t[0][v] - t[1][v]);
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -172,40 +214,40 @@ __device__ __forceinline__ void cpml_curl(const Geo3D &g, R *const (&psi)[3][2],
 //   Hx -= S (dy Ez - dz Ey),  Hy -= S (dz Ex - dx Ez),  Hz -= S (dx Ey - dy Ex)
 // (forward differences).  Threads clear of every CPML slab run the plain
 // update; the others add the CPML terms (cpml_curl).
-template <typename R>
-__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
-    k_h3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm, int zrev)
+// One tile (bx, by, bz) of the H half step.  COH: loads for the wavefront
+// kernel; FOLD: inc (may then be null) is the plane wave's incident row of
+// this step, whose face corrections are added before the stores.
+template <typename R, bool COH, bool FOLD>
+__device__ __forceinline__ void h_tile(const Geo3D &g, const State3D<R> &s, const Coef<R> &c, const Pml3D<R> &pm,
+                                       int bx, int by, int bz, const R *inc)
 {
-    wait_previous_grid();
-    const Coef<R> &c = coef_at<R>(slot);
-    const int bz = zrev ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
-    const int i0 = (blockIdx.x * TBX + threadIdx.x) * VX, j = blockIdx.y * TBY + threadIdx.y, k = bz * TBZ + threadIdx.z;
+    const int i0 = (bx * TBX + threadIdx.x) * VX, j = by * TBY + threadIdx.y, k = bz * TBZ + threadIdx.z;
     const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
     if (i0 >= n0 || j >= n1 || k >= n2) return;
     const long long q = k * g.PP + (long long)j * g.px + i0;
     const long long P = g.px, PP = g.PP;
     const bool yin = j <= n1 - 2, zin = k <= n2 - 2, xin = i0 + VX <= n0 - 1;  // next row / plane / node exist
     R ex[4], exN[4], exU[4], ey[4], eyU[4], ez[4], ezN[4], hx[4], hy[4], hz[4];
-    ld4(s.E[0] + q, ex);
-    ld4(s.E[1] + q, ey);
-    ld4(s.E[2] + q, ez);
+    ldv<COH>(s.E[0] + q, ex);
+    ldv<COH>(s.E[1] + q, ey);
+    ldv<COH>(s.E[2] + q, ez);
     if (yin) {
-        ld4(s.E[0] + q + P, exN);
-        ld4(s.E[2] + q + P, ezN);
+        ldv<COH>(s.E[0] + q + P, exN);
+        ldv<COH>(s.E[2] + q + P, ezN);
     } else {
         zero4(exN);
         zero4(ezN);
     }
     if (zin) {
-        ld4(s.E[0] + q + PP, exU);
-        ld4(s.E[1] + q + PP, eyU);
+        ldv<COH>(s.E[0] + q + PP, exU);
+        ldv<COH>(s.E[1] + q + PP, eyU);
     } else {
         zero4(exU);
         zero4(eyU);
     }
-    ld4(s.H[0] + q, hx);
-    ld4(s.H[1] + q, hy);
-    ld4(s.H[2] + q, hz);
+    ldv<COH>(s.H[0] + q, hx);
+    ldv<COH>(s.H[1] + q, hy);
+    ldv<COH>(s.H[2] + q, hz);
     const R eyE = xin ? s.E[1][q + VX] : R(0), ezE = xin ? s.E[2][q + VX] : R(0);
     const R S = c.S;
     const int np = g.npml;
@@ -216,9 +258,9 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const R ezx = v < 3 ? ez[v + 1] : ezE, eyx = v < 3 ? ey[v + 1] : eyE;
-            cu[0][v] = S * ((ezN[v] - ez[v]) - (eyU[v] - ey[v]));
-            cu[1][v] = S * ((exU[v] - ex[v]) - (ezx - ez[v]));
-            cu[2][v] = S * ((eyx - ey[v]) - (exN[v] - ex[v]));
+            cu[0][v] = rn_mul(S, (ezN[v] - ez[v]) - (eyU[v] - ey[v]));
+            cu[1][v] = rn_mul(S, (exU[v] - ex[v]) - (ezx - ez[v]));
+            cu[2][v] = rn_mul(S, (eyx - ey[v]) - (exN[v] - ex[v]));
         }
     } else {
         R d[3][2][4];  // d[c][0]: along c+1, d[c][1]: along c+2 (forward differences of E)
@@ -231,14 +273,14 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
             d[2][0][v] = (v < 3 ? ey[v + 1] : eyE) - ey[v];      // d_x Ey
             d[2][1][v] = exN[v] - ex[v];                         // d_y Ex
         }
-        cpml_curl<R, true>(g, s.ph, pm.bH, pm.cH, pm.kiH, i0, j, k, sy, sz, S, d, cu);
+        cpml_curl<R, true, COH>(g, s.ph, pm.bH, pm.cH, pm.kiH, i0, j, k, sy, sz, S, d, cu);
     }
     if (xin && yin && zin) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            hx[v] -= cu[0][v];
-            hy[v] -= cu[1][v];
-            hz[v] -= cu[2][v];
+            hx[v] = rn_sub(hx[v], cu[0][v]);
+            hy[v] = rn_sub(hy[v], cu[1][v]);
+            hz[v] = rn_sub(hz[v], cu[2][v]);
         }
     } else {
         // last row / plane / node: H_x exists where j, k <= n-2, H_y where
@@ -246,9 +288,28 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int i = i0 + v;
-            if (yin && zin && i < n0) hx[v] -= cu[0][v];
-            if (zin && i <= n0 - 2) hy[v] -= cu[1][v];
-            if (yin && i <= n0 - 2) hz[v] -= cu[2][v];
+            if (yin && zin && i < n0) hx[v] = rn_sub(hx[v], cu[0][v]);
+            if (zin && i <= n0 - 2) hy[v] = rn_sub(hy[v], cu[1][v]);
+            if (yin && i <= n0 - 2) hz[v] = rn_sub(hz[v], cu[2][v]);
+        }
+    }
+    if constexpr (FOLD) {
+        if (inc) {
+            // the corrections k_tfsf_h adds after a separate H launch
+            const int lx = g.tf_lo[0], ly = g.tf_lo[1], lz = g.tf_lo[2];
+            const int ux = g.tf_hi[0], uy = g.tf_hi[1], uz = g.tf_hi[2];
+            if ((k == lz - 1 || k == uz) && j >= ly && j <= uy) {
+                const R a = k == uz ? -S : S, e = k == uz ? inc[uz - lz] : inc[0];
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    if (i0 + v >= lx && i0 + v < ux) hy[v] = tf_fma(a, e, hy[v]);
+            }
+            if ((j == ly - 1 || j == uy) && k >= lz && k <= uz) {
+                const R a = j == uy ? S : -S, e = inc[k - lz];
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    if (i0 + v >= lx && i0 + v < ux) hz[v] = tf_fma(a, e, hz[v]);
+            }
         }
     }
     st4(s.H[0] + q, hx);
@@ -256,36 +317,46 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
     st4(s.H[2] + q, hz);
 }
 
+// The H half step of the whole grid, bottom up or (zrev) top down.
+template <typename R>
+__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
+    k_h3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm, int zrev)
+{
+    wait_previous_grid();
+    const int bz = zrev ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
+    h_tile<R, false, false>(g, s, coef_at<R>(slot), pm, blockIdx.x, blockIdx.y, bz, nullptr);
+}
+
 // E half step: curl H with backward differences (CPML terms as in the H
 // kernel); per component the Drude update of Eq. (10a,b) in the design box.
 //   curl_x = dy Hz - dz Hy,  curl_y = dz Hx - dx Hz,  curl_z = dx Hy - dy Hx
-template <typename R, int MODE>
-__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
-    k_e3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm, Step3D<R> a3, int zrev)
+// One tile (bx, by, bz) of the E half step.  COH: loads for the wavefront
+// kernel; FOLD (forward): the plane wave's face corrections of row
+// a3.tf_inc (when set) added before the stores.
+template <typename R, int MODE, bool COH, bool FOLD>
+__device__ __forceinline__ void e_tile(const Geo3D &g, const State3D<R> &s, const Coef<R> &c, const Pml3D<R> &pm,
+                                       const Step3D<R> &a3, int bx, int by, int bz)
 {
-    wait_previous_grid();
-    const Coef<R> &c = coef_at<R>(slot);
-    const int bz = zrev ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TBY, z0 = bz * TBZ;
+    const int x0 = bx * TX, y0 = by * TBY, z0 = bz * TBZ;
     const int i0 = x0 + threadIdx.x * VX, j = y0 + threadIdx.y, k = z0 + threadIdx.z;
     const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
     if (i0 >= n0 || j >= n1 || k >= n2) return;
     const long long q = k * g.PP + (long long)j * g.px + i0;
     const long long P = g.px, PP = g.PP;
     R hx[4], hxS[4], hxD[4], hy[4], hyD[4], hz[4], hzS[4], e[3][4];
-    ld4(s.H[0] + q, hx);
-    ld4(s.H[1] + q, hy);
-    ld4(s.H[2] + q, hz);
+    ldv<COH>(s.H[0] + q, hx);
+    ldv<COH>(s.H[1] + q, hy);
+    ldv<COH>(s.H[2] + q, hz);
     if (j >= 1) {
-        ld4(s.H[0] + q - P, hxS);
-        ld4(s.H[2] + q - P, hzS);
+        ldv<COH>(s.H[0] + q - P, hxS);
+        ldv<COH>(s.H[2] + q - P, hzS);
     } else {
         zero4(hxS);
         zero4(hzS);
     }
     if (k >= 1) {
-        ld4(s.H[0] + q - PP, hxD);
-        ld4(s.H[1] + q - PP, hyD);
+        ldv<COH>(s.H[0] + q - PP, hxD);
+        ldv<COH>(s.H[1] + q - PP, hyD);
     } else {
         zero4(hxD);
         zero4(hyD);
@@ -293,9 +364,9 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
     const R hyW = i0 >= 1 ? s.H[1][q - 1] : R(0), hzW = i0 >= 1 ? s.H[2][q - 1] : R(0);
     // all E loads before any store (the compiler cannot reorder them past
     // stores through other field pointers)
-    ld4(s.E[0] + q, e[0]);
-    ld4(s.E[1] + q, e[1]);
-    ld4(s.E[2] + q, e[2]);
+    ldv<COH>(s.E[0] + q, e[0]);
+    ldv<COH>(s.E[1] + q, e[1]);
+    ldv<COH>(s.E[2] + q, e[2]);
     R curl[3][4];
     const int np = g.npml;
     const int sy = slabE(j, n1, np), sz = slabE(k, n2, np);
@@ -304,9 +375,9 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const R hyx = v > 0 ? hy[v - 1] : hyW, hzx = v > 0 ? hz[v - 1] : hzW;
-            curl[0][v] = c.S * ((hz[v] - hzS[v]) - (hy[v] - hyD[v]));
-            curl[1][v] = c.S * ((hx[v] - hxD[v]) - (hz[v] - hzx));
-            curl[2][v] = c.S * ((hy[v] - hyx) - (hx[v] - hxS[v]));
+            curl[0][v] = rn_mul(c.S, (hz[v] - hzS[v]) - (hy[v] - hyD[v]));
+            curl[1][v] = rn_mul(c.S, (hx[v] - hxD[v]) - (hz[v] - hzx));
+            curl[2][v] = rn_mul(c.S, (hy[v] - hyx) - (hx[v] - hxS[v]));
         }
     } else {
         R d[3][2][4];  // backward differences of H
@@ -319,7 +390,7 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
             d[2][0][v] = hy[v] - (v > 0 ? hy[v - 1] : hyW);      // d_x Hy
             d[2][1][v] = hx[v] - hxS[v];                         // d_y Hx
         }
-        cpml_curl<R, false>(g, s.pe, pm.bE, pm.cE, pm.kiE, i0, j, k, sy, sz, c.S, d, curl);
+        cpml_curl<R, false, COH>(g, s.pe, pm.bE, pm.cE, pm.kiE, i0, j, k, sy, sz, c.S, d, curl);
     }
     // E_c is updated where p <= n-2 along c and 1 <= p <= n-2 across; a
     // component that is not updated keeps its value (zero on the walls).
@@ -337,12 +408,35 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
                          (MODE == 0 && x0 < g.s1[0] && x0 + TX > g.s0[0] && y0 < g.s1[1] && y0 + TBY > g.s0[1] &&
                           z0 < g.s1[2] && z0 + TBZ > g.s0[2]);
     const R inv_bg = rcp(k < g.sub_hi ? c.eps_sub : c.eps_s);
+    // the corrections k_tfsf_e adds after a separate E launch (wavefront
+    // kernel only; the faces lie in background material)
+    auto tf_fix = [&](int cc, R(&x)[4]) {
+        if constexpr (FOLD && MODE == 0) {
+            if (!a3.tf_inc) return;
+            const int lx = g.tf_lo[0], ly = g.tf_lo[1], lz = g.tf_lo[2];
+            const int ux = g.tf_hi[0], uy = g.tf_hi[1], uz = g.tf_hi[2];
+            const R *hi = a3.tf_inc + (uz - lz + 1);
+            if (cc == 0 && (k == lz || k == uz) && j >= ly && j <= uy) {
+                const R m = tf_mul(k == uz ? -c.S : c.S, k == uz ? hi[uz - lz + 1] : hi[0]);
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    if (i0 + v >= lx && i0 + v < ux) x[v] = tf_fma(m, inv_bg, x[v]);
+            }
+            if (cc == 2 && j >= ly && j <= uy && k >= lz && k < uz) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    if (i0 + v == lx || i0 + v == ux)
+                        x[v] = tf_fma(tf_mul(i0 + v == ux ? c.S : -c.S, hi[k - lz + 1]), inv_bg, x[v]);
+            }
+        }
+    };
     if (!touches) {
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
 #pragma unroll
             for (int v = 0; v < 4; ++v)
-                if (full || upd(cc, v)) e[cc][v] += curl[cc][v] * inv_bg;
+                if (full || upd(cc, v)) e[cc][v] = rn_fma(curl[cc][v], inv_bg, e[cc][v]);
+            tf_fix(cc, e[cc]);
             st4(s.E[cc] + q, e[cc]);
         }
         return;
@@ -364,10 +458,10 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
         ld4(a3.rho_t + d0, rt4);
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
-            ld4(s.J[cc] + d0, J4[cc]);
-            if (MODE == 1) ld4(a3.rec + cc * g.Mdi + d0, em4[cc]);
+            ldv<COH>(s.J[cc] + d0, J4[cc]);
+            if (MODE == 1) ldv<COH>(a3.rec + cc * g.Mdi + d0, em4[cc]);
         }
-        if (MODE == 1) ld4(a3.G + d0, G4);
+        if (MODE == 1) ldv<COH>(a3.G + d0, G4);
     }
     const R src_fwd = (MODE == 0 && rsrc) ? *a3.src : R(0);
 #pragma unroll
@@ -406,11 +500,12 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
                     gadd[v] += (double)em4[cc][v] * (double)term;
                 }
             } else {
-                en[v] = e[cc][v] + (curl[cc][v] - src) * (gap ? rcp(c.eps_g) : inv_bg);
+                en[v] = rn_fma(curl[cc][v] - src, gap ? rcp(c.eps_g) : inv_bg, e[cc][v]);
             }
             if (MODE == 0 && gap && a3.gap_rec && (full || upd(cc, v)))
                 a3.gap_rec[(long long)cc * g.Mg + gidx] = en[v];
         }
+        tf_fix(cc, en);
         st4(s.E[cc] + q, en);
         if (vdes) {
             st4(s.J[cc] + d0, jn4);
@@ -422,6 +517,15 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
         for (int v = 0; v < 4; ++v) G4[v] += gadd[v];
         st4(a3.G + d0, G4);
     }
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
+    k_e3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm, Step3D<R> a3, int zrev)
+{
+    wait_previous_grid();
+    const int bz = zrev ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
+    e_tile<R, MODE, false, false>(g, s, coef_at<R>(slot), pm, a3, blockIdx.x, blockIdx.y, bz);
 }
 
 // ------------------------------------------------ plane wave (TFSF)
@@ -456,14 +560,14 @@ __global__ void __launch_bounds__(256) k_tfsf_h(Geo3D g, State3D<R> s, int slot,
         const long long r = t - top * zf;
         const int i = lx + (int)(r % Lx), j = ly + (int)(r / Lx), k = top ? g.tf_hi[2] : lz - 1;
         R *h = s.H[1] + k * g.PP + (long long)j * g.px + i;
-        *h += top ? -S * inc[Lz - 1] : S * inc[0];
+        *h = tf_fma(top ? -S : S, top ? inc[Lz - 1] : inc[0], *h);
     } else if (t < 2 * zf + 2 * yf) {
         const long long u = t - 2 * zf;
         const int far = u >= yf;
         const long long r = u - far * yf;
         const int i = lx + (int)(r % Lx), k = lz + (int)(r / Lx), j = far ? g.tf_hi[1] : ly - 1;
         R *h = s.H[2] + k * g.PP + (long long)j * g.px + i;
-        *h += far ? S * inc[k - lz] : -S * inc[k - lz];
+        *h = tf_fma(far ? S : -S, inc[k - lz], *h);
     }
 }
 
@@ -484,7 +588,7 @@ __global__ void __launch_bounds__(256) k_tfsf_e(Geo3D g, State3D<R> s, int slot,
         const int i = lx + (int)(r % Lx), j = ly + (int)(r / Lx), k = top ? g.tf_hi[2] : lz;
         const R inv = rcp(k < g.sub_hi ? c.eps_sub : c.eps_s);
         R *e = s.E[0] + k * g.PP + (long long)j * g.px + i;
-        *e += top ? -S * hi[Lz] * inv : S * hi[0] * inv;
+        *e = tf_fma(tf_mul(top ? -S : S, top ? hi[Lz] : hi[0]), inv, *e);
     } else if (t < 2 * zf + 2 * xf) {
         const long long u = t - 2 * zf;
         const int far = u >= xf;
@@ -492,7 +596,7 @@ __global__ void __launch_bounds__(256) k_tfsf_e(Geo3D g, State3D<R> s, int slot,
         const int j = ly + (int)(r % Ly), k = lz + (int)(r / Ly), i = far ? g.tf_hi[0] : lx;
         const R inv = rcp(k < g.sub_hi ? c.eps_sub : c.eps_s);
         R *e = s.E[2] + k * g.PP + (long long)j * g.px + i;
-        *e += far ? S * hi[k - lz + 1] * inv : -S * hi[k - lz + 1] * inv;
+        *e = tf_fma(tf_mul(far ? S : -S, hi[k - lz + 1]), inv, *e);
     }
 }
 
@@ -540,6 +644,134 @@ __global__ void __launch_bounds__(256) k_tfsf_column(Geo3D g, Pml3D<R> pm, R S, 
     }
 }
 
+// ------------------------------------------------ wavefront: several steps per launch
+//
+// k_wave3d runs `count` steps in one persistent launch whose blocks are all
+// resident (cooperative launch).  The half steps are cut into jobs (one
+// phase on one z slab of two planes) and items (up to tpi x-adjacent tiles
+// of one row of a job); block b takes items b, b + G, b + 2G, ... of the
+// job list (G blocks), whose order puts every job after the jobs it
+// depends on:
+//   E_t(s) reads H_t of slabs s and s-1 (backward differences) and
+//          overwrites E that H_t(s), H_t(s-1) read;
+//   H_t(s) reads E_{t-1} of slabs s and s+1 (forward differences) and
+//          overwrites H that E_{t-1}(s), E_{t-1}(s+1) read.
+// Before an item, one thread waits (acquire loads, bounded) until the
+// per-slab counters of finished items show those jobs complete; after it,
+// the block's stores are fenced and the slab's counter incremented.  Since a
+// block only ever waits for items earlier in the list, and the earliest
+// unfinished item's block is running it, the launch always progresses.
+// Each node sees exactly the arithmetic of the split launches (the plane
+// wave's face corrections are added before the stores, with the same
+// rounding), so the results are bit-identical; what changes is that the E
+// half step of a slab runs while the H it reads is still in L2, and with
+// count > 1 the next steps re-use the slab before it leaves L2.
+
+#ifndef WAVE_MINB
+#define WAVE_MINB 4
+#endif
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded wait until *p >= want (counts modulo 2^32).
+__device__ bool wait_count(const unsigned *p, unsigned want, unsigned *abort_word, unsigned *err, long long limit)
+{
+    if ((int)(ld_acquire(p) - want) >= 0) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        __nanosleep(32);
+        if ((int)(ld_acquire(p) - want) >= 0) return true;
+        if (ld_acquire(abort_word)) return false;
+        if (clock64() - t0 > limit) {
+            atomicOr(err, ERR_TIMEOUT);
+            atomicExch(abort_word, 1u);
+            return false;
+        }
+    }
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? WAVE_MINB : 1)
+    k_wave3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm, Step3D<R> a0, Wave3D<R> w, unsigned *err,
+             long long limit)
+{
+    const Coef<R> &c = coef_at<R>(slot);
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0;
+    __shared__ int go;
+    if (lead) go = ld_acquire(w.cnt + 2 * w.nslab) == 0u;
+    __syncthreads();
+    if (!go) return;
+    const int nitems = 2 * w.count * w.nslab * w.ips;  // below 2^31 (checked by the host)
+#pragma unroll 1
+    for (int q = blockIdx.x; q < nitems; q += gridDim.x) {
+        const int job = q / w.ips, r = q - job * w.ips;
+        const int code = __ldg(w.jobs + job);
+        const int p = code >> 16, sl = code & 0xffff, t = p >> 1;
+        const bool isE = (p & 1) != 0;
+        if (lead) {
+            unsigned *cH = w.cnt, *cE = w.cnt + w.nslab, *abort_word = w.cnt + 2 * w.nslab;
+            bool ok = true;
+            if (isE) {
+                const unsigned want = (unsigned)(t + 1) * (unsigned)w.ips;
+                ok = wait_count(cH + sl, want, abort_word, err, limit) &&
+                     (sl == 0 || wait_count(cH + sl - 1, want, abort_word, err, limit));
+            } else if (t > 0) {
+                const unsigned want = (unsigned)t * (unsigned)w.ips;
+                ok = wait_count(cE + sl, want, abort_word, err, limit) &&
+                     (sl + 1 == w.nslab || wait_count(cE + sl + 1, want, abort_word, err, limit));
+            }
+            go = ok;
+        }
+        __syncthreads();
+        if (!go) return;
+        const int by = r / w.ipr, bx0 = (r - by * w.ipr) * w.tpi, bx1 = min(w.gx, bx0 + w.tpi);
+        if (!isE) {
+            const R *inc = (MODE == 0 && w.tf) ? w.tf + (long long)(w.n0 + t) * w.tf_row : nullptr;
+#pragma unroll 1
+            for (int bx = bx0; bx < bx1; ++bx) h_tile<R, true, true>(g, s, c, pm, bx, by, sl, inc);
+        } else {
+            Step3D<R> a = a0;
+            if (MODE == 0) {
+                const int n = w.n0 + t;
+                a.src = w.src + n;
+                a.gap_rec = w.gap ? w.gap + (long long)(n + 1) * 3 * g.Mg : nullptr;
+                a.rec = w.rec ? w.rec + (long long)(n - w.rec0) * 3 * g.Mdi : nullptr;
+                a.tf_inc = w.tf ? w.tf + (long long)n * w.tf_row : nullptr;
+            } else {
+                const int m = w.n0 - t;
+                a.gap_src = w.gap ? w.gap + (long long)m * 3 * g.Mg : nullptr;
+                a.rec = w.rec + (long long)(m - 1 - w.rec0) * 3 * g.Mdi;
+            }
+#pragma unroll 1
+            for (int bx = bx0; bx < bx1; ++bx) e_tile<R, MODE, true, true>(g, s, c, pm, a, bx, by, sl);
+        }
+        __syncthreads();
+        // E items of the last step have no reader in this launch
+        if (lead && (!isE || t + 1 < w.count)) {
+            __threadfence();
+            atomicAdd(w.cnt + (isE ? w.nslab : 0) + sl, 1u);
+        }
+    }
+    // The last block to finish clears the counters for the next launch.
+    __shared__ int last;
+    if (lead) {
+        __threadfence();
+        last = atomicAdd(w.cnt + 2 * w.nslab + 1, 1u) + 1 == gridDim.x;
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        const int nt = TBX * TBY * TBZ, tid = threadIdx.x + TBX * (threadIdx.y + TBY * threadIdx.z);
+        for (int i = tid; i < 2 * w.nslab; i += nt) w.cnt[i] = 0u;
+        if (lead) w.cnt[2 * w.nslab + 1] = 0u;
+    }
+}
+
 }  // namespace
 
 template <typename R>
@@ -560,6 +792,7 @@ int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, int c, const Pm
 {
     dim3 vblock(TBX, TBY, TBZ), vgrid((g.n[0] + TX - 1) / TX, (g.n[1] + TBY - 1) / TBY, (g.n[2] + TBZ - 1) / TBZ);
     const bool tf = mode == 0 && a.tf_inc;
+    const long long Lx = g.tf_hi[0] - g.tf_lo[0], Ly = g.tf_hi[1] - g.tf_lo[1] + 1, Lz = g.tf_hi[2] - g.tf_lo[2] + 1;
     // The H half step sweeps the planes upwards and the E half step
     // downwards (blocks start in blockIdx order), so each launch begins where
     // the previous one ended, on planes whose fields are still in L2.  Each
@@ -567,22 +800,79 @@ int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, int c, const Pm
     // result.
     launch_pdl(k_h3d<R>, vgrid, vblock, st, g, s, c, pm, 0);
     if (tf) {
-        const long long Lx = g.tf_hi[0] - g.tf_lo[0], Ly = g.tf_hi[1] - g.tf_lo[1] + 1,
-                        Lz = g.tf_hi[2] - g.tf_lo[2] + 1;
         const long long nh = 2 * Lx * Ly + 2 * Lx * Lz;
         launch_pdl(k_tfsf_h<R>, dim3((unsigned)((nh + 255) / 256)), dim3(256), st, g, s, c, a.tf_inc);
     }
     if (mode == 0) launch_pdl(k_e3d<R, 0>, vgrid, vblock, st, g, s, c, pm, a, 1);
     else launch_pdl(k_e3d<R, 1>, vgrid, vblock, st, g, s, c, pm, a, 1);
     if (tf) {
-        const long long Lx = g.tf_hi[0] - g.tf_lo[0], Ly = g.tf_hi[1] - g.tf_lo[1] + 1,
-                        Lz = g.tf_hi[2] - g.tf_lo[2] + 1;
         const long long ne = 2 * Lx * Ly + 2 * Ly * (Lz - 1);
         launch_pdl(k_tfsf_e<R>, dim3((unsigned)((ne + 255) / 256)), dim3(256), st, g, s, c, a.tf_inc);
         return 4;
     }
     return 2;
 }
+
+
+std::vector<int> wave3d_jobs(int nslab, int count, int lag)
+{
+    std::vector<int> jobs;
+    const int phases = 2 * count;
+    jobs.reserve((size_t)phases * nslab);
+    for (int key = 0; key < nslab + lag * (phases - 1); ++key)
+        for (int p = 0; p < phases; ++p) {
+            const int sl = key - lag * p;
+            if (sl >= 0 && sl < nslab) jobs.push_back(p << 16 | sl);
+        }
+    return jobs;
+}
+
+template <typename R>
+int wave3d_blocks(int mode)
+{
+    int dev = 0, sms = 0, coop = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
+        cudaGetLastError();
+        return 0;
+    }
+    const cudaError_t e = mode == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wave3d<R, 0>, TBX * TBY * TBZ, 0)
+                                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wave3d<R, 1>, TBX * TBY * TBZ, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per * sms;
+}
+
+template <typename R>
+int launch_wave3d(int mode, const Geo3D &g, const State3D<R> &s, int c, const Pml3D<R> &pm, const Step3D<R> &a0,
+                  const Wave3D<R> &w, int blocks, unsigned *err, long long limit, cudaStream_t st)
+{
+    const long long nitems = 2LL * w.count * w.nslab * w.ips;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::min<long long>(blocks, nitems));
+    cfg.blockDim = dim3(TBX, TBY, TBZ);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (mode == 0) cudaLaunchKernelEx(&cfg, k_wave3d<R, 0>, g, s, c, pm, a0, w, err, limit);
+    else cudaLaunchKernelEx(&cfg, k_wave3d<R, 1>, g, s, c, pm, a0, w, err, limit);
+    return 1;
+}
+
+template int wave3d_blocks<float>(int);
+template int wave3d_blocks<double>(int);
+template int launch_wave3d<float>(int, const Geo3D &, const State3D<float> &, int, const Pml3D<float> &,
+                                  const Step3D<float> &, const Wave3D<float> &, int, unsigned *, long long,
+                                  cudaStream_t);
+template int launch_wave3d<double>(int, const Geo3D &, const State3D<double> &, int, const Pml3D<double> &,
+                                   const Step3D<double> &, const Wave3D<double> &, int, unsigned *, long long,
+                                   cudaStream_t);
 
 template int launch_step3d<float>(int, const Geo3D &, const State3D<float> &, int,
                                   const Pml3D<float> &, const Step3D<float> &, cudaStream_t);
