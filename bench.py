@@ -227,14 +227,15 @@ def run_surrogate(args) -> None:
     import torch
     from paper_2203_01462_gb300.binding import Solver
     from paper_2203_01462_gb300.optimize import optimize
-    from paper_2203_01462_gb300.surrogate_loop import Trainer, collect_pairs, surrogate_optimize
+    from paper_2203_01462_gb300.surrogate_loop import Trainer, collect_pairs_concurrent, surrogate_optimize
     w = I.cfg_2d_316()
     s = Solver(w)
     U, D, g0 = args.sur_updates, args.sur_damping_iters, args.sur_damping
     t = time.perf_counter()
     rho0s = [I.zero_gap(w, 0.02 * I.rho_uniform(w, 300 + k)) for k in range(args.sur_trajectories)]
-    pairs = collect_pairs(s, rho0s, iters=args.sur_pairs_per_trajectory, move=0.05, damping_start=g0,
-                          damping_iters=D)
+    # the training trajectories are independent: they run side by side
+    pairs = collect_pairs_concurrent(w, rho0s, iters=args.sur_pairs_per_trajectory, move=0.05, damping_start=g0,
+                                     damping_iters=D, width=args.sur_trajectories)
     torch.cuda.synchronize()
     collect_s = time.perf_counter() - t
     tr = Trainer(256, 256, base=24, batch=8, seed=0, lr=1e-3)
@@ -273,6 +274,8 @@ def run_surrogate(args) -> None:
                 wall_time_ratio_amortised=dict(designs=R, ratio=(sur_s + pre / R) / plain_s),
                 break_even_designs=(pre / (plain_s - sur_s)) if plain_s > sur_s else None,
                 pretraining=dict(pairs=len(pairs), damping_levels_in_pairs=len(levels), collect_s=collect_s,
+                                 collect="%d trajectories side by side, one solver and CUDA stream each"
+                                 % args.sur_trajectories,
                                  train_steps=args.sur_train_steps, train_s=train_s, final_loss=loss))
     print(json.dumps(line), flush=True)
 

@@ -46,8 +46,10 @@ def net_input(rho_map: torch.Tensor, gamma_scale: float) -> torch.Tensor:
 
 
 def normalised(g: torch.Tensor) -> torch.Tensor:
+    """g over its largest magnitude (g itself when it is zero), without a host
+    synchronisation."""
     m = g.abs().max()
-    return (g / m if m > 0 else g).float()
+    return (g / torch.where(m > 0, m, torch.ones_like(m))).float()
 
 
 @dataclasses.dataclass
@@ -76,6 +78,41 @@ def collect_pairs(s: Solver, rho0_list, iters: int, move: float = 0.05, sigma_ma
             m = design_map(s, rho)
             pairs.add(net_input(m, gs), normalised(design_map(s, g)).unsqueeze(0).unsqueeze(0).contiguous())
             s.ascent_step(rho, g, move)
+    return pairs
+
+
+def collect_pairs_concurrent(w: dict, rho0_list, iters: int, move: float = 0.05, sigma_max: float = 0.0,
+                             damping_start: float = 10.0, damping_iters: int = 50, pairs: Pairs | None = None,
+                             width: int = 16) -> Pairs:
+    """collect_pairs with the trajectories run side by side: up to ``width``
+    solvers of workload ``w``, each on its own CUDA stream, take one design
+    step each per round, so that the launches of several small-grid
+    trajectories (one partial wave of blocks each) share the GPU.  Every
+    trajectory computes exactly what collect_pairs computes (same kernels,
+    same inputs); the pairs are kept in trajectory order."""
+    pairs = pairs or Pairs()
+    for b0 in range(0, len(rho0_list), width):
+        group = list(rho0_list[b0:b0 + width])
+        solvers = [Solver(w, stream=torch.cuda.Stream()) for _ in group]
+        per = [Pairs() for _ in group]
+        rhos = []
+        for s, rho0 in zip(solvers, group):
+            with torch.cuda.stream(s.stream):
+                rhos.append(torch.as_tensor(rho0, device=s.device).to(s.real).contiguous().clone())
+        for k in range(iters):
+            gs = damping_schedule(k, damping_start, damping_iters)
+            for s, rho, pp in zip(solvers, rhos, per):
+                with torch.cuda.stream(s.stream):
+                    W, g = s.evaluate(rho, sigma_max, gs)
+                    m = design_map(s, rho)
+                    pp.add(net_input(m, gs), normalised(design_map(s, g)).unsqueeze(0).unsqueeze(0).contiguous())
+                    s.ascent_step(rho, g, move)
+        torch.cuda.synchronize()
+        for pp in per:
+            pairs.x += pp.x
+            pairs.t += pp.t
+        for s in solvers:
+            s.close()
     return pairs
 
 

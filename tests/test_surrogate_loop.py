@@ -25,14 +25,14 @@ def test_surrogate_loop_matches_plain_objective_in_less_time(save_report):
     import torch
     from paper_2203_01462_gb300.binding import Solver
     from paper_2203_01462_gb300.optimize import optimize
-    from paper_2203_01462_gb300.surrogate_loop import Trainer, collect_pairs, surrogate_optimize
+    from paper_2203_01462_gb300.surrogate_loop import Trainer, collect_pairs_concurrent, surrogate_optimize
     w = I.cfg_2d_316()
     s = Solver(w)
     G0, D, U = 10.0, 20, 40
     torch.cuda.synchronize()
     t = time.perf_counter()
     rho0s = [I.zero_gap(w, 0.02 * I.rho_uniform(w, 200 + k)) for k in range(4)]
-    pairs = collect_pairs(s, rho0s, iters=20, move=0.05, damping_start=G0, damping_iters=D)
+    pairs = collect_pairs_concurrent(w, rho0s, iters=20, move=0.05, damping_start=G0, damping_iters=D)
     tr = Trainer(256, 256, base=24, batch=8, seed=0, lr=1e-3)
     tr.fit(pairs, 200)
     torch.cuda.synchronize()
@@ -60,3 +60,20 @@ def test_surrogate_loop_matches_plain_objective_in_less_time(save_report):
     assert Ws[-1] >= 0.99 * target, rep
     assert sur_s < 0.9 * plain_s, rep
     assert st["solves"] < U
+
+
+def test_concurrent_collection_gives_the_sequential_pairs():
+    """Three trajectories side by side on their own streams give bit for bit
+    the pairs one solver makes one trajectory after another."""
+    import torch
+    from paper_2203_01462_gb300.binding import Solver
+    from paper_2203_01462_gb300.surrogate_loop import collect_pairs, collect_pairs_concurrent
+    w = I.cfg_2d_316(nsteps=600)
+    rho0s = [I.zero_gap(w, 0.02 * I.rho_uniform(w, 210 + k)) for k in range(3)]
+    seq = collect_pairs(Solver(w), rho0s, iters=3, move=0.05, damping_start=10.0, damping_iters=2)
+    con = collect_pairs_concurrent(w, rho0s, iters=3, move=0.05, damping_start=10.0, damping_iters=2, width=2)
+    torch.cuda.synchronize()
+    assert len(seq) == len(con) == 9
+    for a, b in zip(seq.x + seq.t, con.x + con.t):
+        assert torch.equal(a, b)
+
