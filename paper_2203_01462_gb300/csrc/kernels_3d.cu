@@ -139,35 +139,44 @@ __device__ __forceinline__ long long pidx(const Geo3D &g, int ax, int s, int i, 
 // the slab of its axis, plus psi <- b psi + c d; out[c] = S (t_a - t_b).
 // Along y and z the slab index and coefficients are those of row j / plane
 // k, and the psi arrays of y- and z-slabs are x-contiguous, so psi moves as
-// one vector; along x both are taken per node.  Every psi and coefficient
-// load is issued before any store.
+// one vector; along x both are taken per node.  In two parts: cpml_load
+// issues the psi loads (the kernels call it before their field loads, so
+// that both round trips overlap), cpml_apply updates psi, stores it and
+// forms the curl.
 template <typename R, bool HALF, bool COH>
-__device__ __forceinline__ void cpml_curl(const Geo3D &g, R *const (&psi)[3][2], const R *const (&tb)[3],
-                                          const R *const (&tc)[3], const R *const (&tk)[3], int i0, int j, int k,
-                                          int sy, int sz, R S, const R (&d)[3][2][4], R (&out)[3][4])
+__device__ __forceinline__ void cpml_load(const Geo3D &g, R *const (&psi)[3][2], int i0, int j, int k, int sy, int sz,
+                                          int (&sx)[4], R (&ps)[3][2][4])
 {
     const int np = g.npml;
-    int sx[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v)  // nodes past the last one are row padding: no slab
         sx[v] = i0 + v >= g.n[0] ? -1 : (HALF ? slabH(i0 + v, g.n[0], np) : slabE(i0 + v, g.n[0], np));
     const long long iy = pidx(g, 1, sy, i0, j, k), iz = pidx(g, 2, sz, i0, j, k);
-    R ps[3][2][4];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int ax = (c + 1 + h) % 3;
+            zero4(ps[c][h]);
             if (ax == 0) {
 #pragma unroll
                 for (int v = 0; v < 4; ++v)
-                    ps[c][h][v] = sx[v] >= 0 ? psi[c][h][pidx(g, 0, sx[v], i0 + v, j, k)] : R(0);
+                    if (sx[v] >= 0) ps[c][h][v] = psi[c][h][pidx(g, 0, sx[v], i0 + v, j, k)];
             } else if (ax == 1) {
                 if (sy >= 0) ldv<COH>(psi[c][h] + iy, ps[c][h]);
             } else {
                 if (sz >= 0) ldv<COH>(psi[c][h] + iz, ps[c][h]);
             }
         }
+}
+
+template <typename R>
+__device__ __forceinline__ void cpml_apply(const Geo3D &g, R *const (&psi)[3][2], const R *const (&tb)[3],
+                                           const R *const (&tc)[3], const R *const (&tk)[3], int i0, int j, int k,
+                                           int sy, int sz, R S, const R (&d)[3][2][4], const int (&sx)[4],
+                                           R (&ps)[3][2][4], R (&out)[3][4])
+{
+    const long long iy = pidx(g, 1, sy, i0, j, k), iz = pidx(g, 2, sz, i0, j, k);
     // coefficient tables are read-only: non-coherent loads, free to move past stores
     const R by = __ldg(tb[1] + j), cy = __ldg(tc[1] + j), ky = __ldg(tk[1] + j);
     const R bz = __ldg(tb[2] + k), cz = __ldg(tc[2] + k), kz = __ldg(tk[2] + k);
@@ -227,6 +236,13 @@ __device__ __forceinline__ void h_tile(const Geo3D &g, const State3D<R> &s, cons
     const long long q = k * g.PP + (long long)j * g.px + i0;
     const long long P = g.px, PP = g.PP;
     const bool yin = j <= n1 - 2, zin = k <= n2 - 2, xin = i0 + VX <= n0 - 1;  // next row / plane / node exist
+    const int np = g.npml;
+    const int sy = slabH(j, n1, np), sz = slabH(k, n2, np);
+    const bool xslab = i0 < np || i0 + VX - 1 >= n0 - 1 - np;
+    const bool pml = xslab || sy >= 0 || sz >= 0;
+    int sx[4];
+    R ps[3][2][4];
+    if (pml) cpml_load<R, true, COH>(g, s.ph, i0, j, k, sy, sz, sx, ps);
     R ex[4], exN[4], exU[4], ey[4], eyU[4], ez[4], ezN[4], hx[4], hy[4], hz[4];
     ldv<COH>(s.E[0] + q, ex);
     ldv<COH>(s.E[1] + q, ey);
@@ -250,11 +266,8 @@ __device__ __forceinline__ void h_tile(const Geo3D &g, const State3D<R> &s, cons
     ldv<COH>(s.H[2] + q, hz);
     const R eyE = xin ? s.E[1][q + VX] : R(0), ezE = xin ? s.E[2][q + VX] : R(0);
     const R S = c.S;
-    const int np = g.npml;
-    const int sy = slabH(j, n1, np), sz = slabH(k, n2, np);
-    const bool xslab = i0 < np || i0 + VX - 1 >= n0 - 1 - np;
     R cu[3][4];
-    if (!xslab && sy < 0 && sz < 0) {
+    if (!pml) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const R ezx = v < 3 ? ez[v + 1] : ezE, eyx = v < 3 ? ey[v + 1] : eyE;
@@ -273,7 +286,7 @@ __device__ __forceinline__ void h_tile(const Geo3D &g, const State3D<R> &s, cons
             d[2][0][v] = (v < 3 ? ey[v + 1] : eyE) - ey[v];      // d_x Ey
             d[2][1][v] = exN[v] - ex[v];                         // d_y Ex
         }
-        cpml_curl<R, true, COH>(g, s.ph, pm.bH, pm.cH, pm.kiH, i0, j, k, sy, sz, S, d, cu);
+        cpml_apply<R>(g, s.ph, pm.bH, pm.cH, pm.kiH, i0, j, k, sy, sz, S, d, sx, ps, cu);
     }
     if (xin && yin && zin) {
 #pragma unroll
@@ -343,6 +356,13 @@ __device__ __forceinline__ void e_tile(const Geo3D &g, const State3D<R> &s, cons
     if (i0 >= n0 || j >= n1 || k >= n2) return;
     const long long q = k * g.PP + (long long)j * g.px + i0;
     const long long P = g.px, PP = g.PP;
+    const int np = g.npml;
+    const int sy = slabE(j, n1, np), sz = slabE(k, n2, np);
+    const bool xslab = i0 < np || i0 + VX - 1 >= n0 - np;
+    const bool pml = xslab || sy >= 0 || sz >= 0;
+    int sx[4];
+    R ps[3][2][4];
+    if (pml) cpml_load<R, false, COH>(g, s.pe, i0, j, k, sy, sz, sx, ps);
     R hx[4], hxS[4], hxD[4], hy[4], hyD[4], hz[4], hzS[4], e[3][4];
     ldv<COH>(s.H[0] + q, hx);
     ldv<COH>(s.H[1] + q, hy);
@@ -368,10 +388,7 @@ __device__ __forceinline__ void e_tile(const Geo3D &g, const State3D<R> &s, cons
     ldv<COH>(s.E[1] + q, e[1]);
     ldv<COH>(s.E[2] + q, e[2]);
     R curl[3][4];
-    const int np = g.npml;
-    const int sy = slabE(j, n1, np), sz = slabE(k, n2, np);
-    const bool xslab = i0 < np || i0 + VX - 1 >= n0 - np;
-    if (!xslab && sy < 0 && sz < 0) {
+    if (!pml) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const R hyx = v > 0 ? hy[v - 1] : hyW, hzx = v > 0 ? hz[v - 1] : hzW;
@@ -390,7 +407,7 @@ __device__ __forceinline__ void e_tile(const Geo3D &g, const State3D<R> &s, cons
             d[2][0][v] = hy[v] - (v > 0 ? hy[v - 1] : hyW);      // d_x Hy
             d[2][1][v] = hx[v] - hxS[v];                         // d_y Hx
         }
-        cpml_curl<R, false, COH>(g, s.pe, pm.bE, pm.cE, pm.kiE, i0, j, k, sy, sz, c.S, d, curl);
+        cpml_apply<R>(g, s.pe, pm.bE, pm.cE, pm.kiE, i0, j, k, sy, sz, c.S, d, sx, ps, curl);
     }
     // E_c is updated where p <= n-2 along c and 1 <= p <= n-2 across; a
     // component that is not updated keeps its value (zero on the walls).
