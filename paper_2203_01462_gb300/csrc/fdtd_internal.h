@@ -244,8 +244,8 @@ int launch_stepp_multi(int mode, const GeoP &g, const StateP<R> &s, int coef_slo
 void launch_wait_selftest(unsigned *words, long long limit, cudaStream_t st);
 
 // H then E half steps of the whole grid, in place (two launches); a forward
-// step with a.tf_inc adds the plane wave's face corrections after each half
-// step (four launches).  Returns the launch count.
+// step with a.tf_inc adds the plane wave's face corrections inside them.
+// Returns the launch count.
 template <typename R>
 int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, int coef_slot, const Pml3D<R> &pm,
                   const Step3D<R> &a, cudaStream_t st);

@@ -103,8 +103,8 @@ __device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fm
 __device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Plane-wave face corrections with their rounding fixed (one fused
-// multiply-add, the E-face product rounded first), so that the folded and
-// the separate-launch forms give the same bits.
+// multiply-add, the E-face product rounded first), so that the half-step
+// kernels and the wavefront kernel give the same bits.
 __device__ __forceinline__ float tf_fma(float a, float b, float x) { return __fmaf_rn(a, b, x); }
 __device__ __forceinline__ double tf_fma(double a, double b, double x) { return __fma_rn(a, b, x); }
 __device__ __forceinline__ float tf_mul(float a, float b) { return __fmul_rn(a, b); }
@@ -308,7 +308,7 @@ __device__ __forceinline__ void h_tile(const Geo3D &g, const State3D<R> &s, cons
     }
     if constexpr (FOLD) {
         if (inc) {
-            // the corrections k_tfsf_h adds after a separate H launch
+            // the H-face corrections of the plane wave (see the TFSF notes)
             const int lx = g.tf_lo[0], ly = g.tf_lo[1], lz = g.tf_lo[2];
             const int ux = g.tf_hi[0], uy = g.tf_hi[1], uz = g.tf_hi[2];
             if ((k == lz - 1 || k == uz) && j >= ly && j <= uy) {
@@ -330,14 +330,15 @@ __device__ __forceinline__ void h_tile(const Geo3D &g, const State3D<R> &s, cons
     st4(s.H[2] + q, hz);
 }
 
-// The H half step of the whole grid, bottom up or (zrev) top down.
-template <typename R>
+// The H half step of the whole grid, bottom up or (zrev) top down; FOLD:
+// with the plane wave's H-face corrections of incident row inc.
+template <typename R, bool FOLD>
 __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
-    k_h3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm, int zrev)
+    k_h3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm, int zrev, const R *inc)
 {
     wait_previous_grid();
     const int bz = zrev ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
-    h_tile<R, false, false>(g, s, coef_at<R>(slot), pm, blockIdx.x, blockIdx.y, bz, nullptr);
+    h_tile<R, false, FOLD>(g, s, coef_at<R>(slot), pm, blockIdx.x, blockIdx.y, bz, inc);
 }
 
 // E half step: curl H with backward differences (CPML terms as in the H
@@ -425,8 +426,8 @@ __device__ __forceinline__ void e_tile(const Geo3D &g, const State3D<R> &s, cons
                          (MODE == 0 && x0 < g.s1[0] && x0 + TX > g.s0[0] && y0 < g.s1[1] && y0 + TBY > g.s0[1] &&
                           z0 < g.s1[2] && z0 + TBZ > g.s0[2]);
     const R inv_bg = rcp(k < g.sub_hi ? c.eps_sub : c.eps_s);
-    // the corrections k_tfsf_e adds after a separate E launch (wavefront
-    // kernel only; the faces lie in background material)
+    // the E-face corrections of the plane wave (see the TFSF notes; the
+    // faces lie in background material)
     auto tf_fix = [&](int cc, R(&x)[4]) {
         if constexpr (FOLD && MODE == 0) {
             if (!a3.tf_inc) return;
@@ -536,16 +537,16 @@ __device__ __forceinline__ void e_tile(const Geo3D &g, const State3D<R> &s, cons
     }
 }
 
-template <typename R, int MODE>
+template <typename R, int MODE, bool FOLD>
 __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
     k_e3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm, Step3D<R> a3, int zrev)
 {
     wait_previous_grid();
     const int bz = zrev ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
-    e_tile<R, MODE, false, false>(g, s, coef_at<R>(slot), pm, a3, blockIdx.x, blockIdx.y, bz);
+    e_tile<R, MODE, false, FOLD>(g, s, coef_at<R>(slot), pm, a3, blockIdx.x, blockIdx.y, bz);
 }
 
-// ------------------------------------------------ plane wave (TFSF)
+// ------------------------------------------------ plane wave (TFSF notes)
 //
 // An x-polarised plane wave along +z enters through the faces of the
 // total-field box: components whose Yee position lies in the closed box
@@ -554,7 +555,8 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
 // component on the other side; only E_x and H_y carry one.  The faces lie in
 // background material (the box encloses the design box, away from the
 // CPML), where each half step is E += S curl / eps or H -= S curl, so the
-// correction is added after the main launch:
+// half-step kernels add the correction to the updated value before storing
+// it (h_tile / e_tile with FOLD):
 //   H_y(i, j, lo_z - 1) += S Ei(lo_z)     H_y(i, j, hi_z) -= S Ei(hi_z)
 //   H_z(i, lo_y - 1, k) -= S Ei(k)        H_z(i, hi_y, k) += S Ei(k)
 //   E_x(i, j, lo_z) += S Hi(lo_z - 1) / eps(lo_z)
@@ -562,60 +564,6 @@ __global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
 //   E_z(lo_x, j, k) -= S Hi(k) / eps(k)   E_z(hi_x, j, k) += S Hi(k) / eps(k)
 // with i in [lo_x, hi_x), j in [lo_y, hi_y], k in [lo_z, hi_z] (H_z) or
 // [lo_z, hi_z) (E_z).  Ei = E_x^n and Hi = H_y^{n+1/2} of the incident column.
-
-template <typename R>
-__global__ void __launch_bounds__(256) k_tfsf_h(Geo3D g, State3D<R> s, int slot, const R *__restrict__ inc)
-{
-    wait_previous_grid();
-    const R S = coef_at<R>(slot).S;
-    const int lx = g.tf_lo[0], ly = g.tf_lo[1], lz = g.tf_lo[2];
-    const int Lx = g.tf_hi[0] - lx, Ly = g.tf_hi[1] - ly + 1, Lz = g.tf_hi[2] - lz + 1;
-    const long long zf = (long long)Lx * Ly, yf = (long long)Lx * Lz;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < 2 * zf) {
-        const int top = t >= zf;
-        const long long r = t - top * zf;
-        const int i = lx + (int)(r % Lx), j = ly + (int)(r / Lx), k = top ? g.tf_hi[2] : lz - 1;
-        R *h = s.H[1] + k * g.PP + (long long)j * g.px + i;
-        *h = tf_fma(top ? -S : S, top ? inc[Lz - 1] : inc[0], *h);
-    } else if (t < 2 * zf + 2 * yf) {
-        const long long u = t - 2 * zf;
-        const int far = u >= yf;
-        const long long r = u - far * yf;
-        const int i = lx + (int)(r % Lx), k = lz + (int)(r / Lx), j = far ? g.tf_hi[1] : ly - 1;
-        R *h = s.H[2] + k * g.PP + (long long)j * g.px + i;
-        *h = tf_fma(far ? S : -S, inc[k - lz], *h);
-    }
-}
-
-template <typename R>
-__global__ void __launch_bounds__(256) k_tfsf_e(Geo3D g, State3D<R> s, int slot, const R *__restrict__ inc)
-{
-    wait_previous_grid();
-    const Coef<R> &c = coef_at<R>(slot);
-    const R S = c.S;
-    const int lx = g.tf_lo[0], ly = g.tf_lo[1], lz = g.tf_lo[2];
-    const int Lx = g.tf_hi[0] - lx, Ly = g.tf_hi[1] - ly + 1, Lz = g.tf_hi[2] - lz + 1;
-    const R *hi = inc + Lz;  // H_y^{n+1/2} at k = lz - 1 + q
-    const long long zf = (long long)Lx * Ly, xf = (long long)Ly * (Lz - 1);
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < 2 * zf) {
-        const int top = t >= zf;
-        const long long r = t - top * zf;
-        const int i = lx + (int)(r % Lx), j = ly + (int)(r / Lx), k = top ? g.tf_hi[2] : lz;
-        const R inv = rcp(k < g.sub_hi ? c.eps_sub : c.eps_s);
-        R *e = s.E[0] + k * g.PP + (long long)j * g.px + i;
-        *e = tf_fma(tf_mul(top ? -S : S, top ? hi[Lz] : hi[0]), inv, *e);
-    } else if (t < 2 * zf + 2 * xf) {
-        const long long u = t - 2 * zf;
-        const int far = u >= xf;
-        const long long r = u - far * xf;
-        const int j = ly + (int)(r % Ly), k = lz + (int)(r / Ly), i = far ? g.tf_hi[0] : lx;
-        const R inv = rcp(k < g.sub_hi ? c.eps_sub : c.eps_s);
-        R *e = s.E[2] + k * g.PP + (long long)j * g.px + i;
-        *e = tf_fma(tf_mul(far ? S : -S, hi[k - lz + 1]), inv, *e);
-    }
-}
 
 // The incident column: E_x(k) at z = k and H_y(k) at z = k + 1/2 of a
 // laterally uniform field, updated exactly as the 3D kernels update those
@@ -808,24 +756,19 @@ int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, int c, const Pm
                   const Step3D<R> &a, cudaStream_t st)
 {
     dim3 vblock(TBX, TBY, TBZ), vgrid((g.n[0] + TX - 1) / TX, (g.n[1] + TBY - 1) / TBY, (g.n[2] + TBZ - 1) / TBZ);
-    const bool tf = mode == 0 && a.tf_inc;
-    const long long Lx = g.tf_hi[0] - g.tf_lo[0], Ly = g.tf_hi[1] - g.tf_lo[1] + 1, Lz = g.tf_hi[2] - g.tf_lo[2] + 1;
     // The H half step sweeps the planes upwards and the E half step
     // downwards (blocks start in blockIdx order), so each launch begins where
     // the previous one ended, on planes whose fields are still in L2.  Each
     // kernel reads only fields it does not write, so the order changes no
-    // result.
-    launch_pdl(k_h3d<R>, vgrid, vblock, st, g, s, c, pm, 0);
-    if (tf) {
-        const long long nh = 2 * Lx * Ly + 2 * Lx * Lz;
-        launch_pdl(k_tfsf_h<R>, dim3((unsigned)((nh + 255) / 256)), dim3(256), st, g, s, c, a.tf_inc);
-    }
-    if (mode == 0) launch_pdl(k_e3d<R, 0>, vgrid, vblock, st, g, s, c, pm, a, 1);
-    else launch_pdl(k_e3d<R, 1>, vgrid, vblock, st, g, s, c, pm, a, 1);
-    if (tf) {
-        const long long ne = 2 * Lx * Ly + 2 * Ly * (Lz - 1);
-        launch_pdl(k_tfsf_e<R>, dim3((unsigned)((ne + 255) / 256)), dim3(256), st, g, s, c, a.tf_inc);
-        return 4;
+    // result.  A forward step of a plane wave adds the face corrections
+    // inside the same launches.
+    if (mode == 0 && a.tf_inc) {
+        launch_pdl(k_h3d<R, true>, vgrid, vblock, st, g, s, c, pm, 0, a.tf_inc);
+        launch_pdl(k_e3d<R, 0, true>, vgrid, vblock, st, g, s, c, pm, a, 1);
+    } else {
+        launch_pdl(k_h3d<R, false>, vgrid, vblock, st, g, s, c, pm, 0, (const R *)nullptr);
+        if (mode == 0) launch_pdl(k_e3d<R, 0, false>, vgrid, vblock, st, g, s, c, pm, a, 1);
+        else launch_pdl(k_e3d<R, 1, false>, vgrid, vblock, st, g, s, c, pm, a, 1);
     }
     return 2;
 }
