@@ -24,17 +24,23 @@ extern "C" {
 
 /* C[M][N] = alpha op(A) op(B) + beta C (row-major).  op(A) = A (M x K, lda)
  * or A^T (A stored K x M) when transA; op(B) = B (K x N, ldb) or B^T (B
- * stored N x K) when transB. */
+ * stored N x K) when transB.  work: caller device scratch of work_elems
+ * floats (may be NULL with work_elems = 0).  When the product has few output
+ * tiles and a long K (weight gradients) it is split into K slices, as many
+ * as the scratch holds at M x N floats each; each slice writes its partial
+ * product there and the slices are summed in a fixed order, so results are
+ * deterministic whatever the split.  Without scratch the product runs
+ * unsplit (slower for weight gradients, same precision class). */
 int nn_gemm(int transA, int transB, int M, int N, int K, float alpha, const float *A, int lda, const float *B, int ldb,
-            float beta, float *C, int ldc, void *stream);
+            float beta, float *C, int ldc, float *work, long long work_elems, void *stream);
 
 /* The same product with BF16 operands on the tensor cores and FP32
  * accumulation and output: each tile of A and B (FP32 in memory) is rounded
  * to BF16 (nearest even) as it is staged in shared memory, then C = alpha
  * op(A16) op(B16) + beta C with mma.sync (m16n8k16) and FP32 accumulators.
- * Needs no scratch memory. */
+ * K splitting and the scratch as for nn_gemm. */
 int nn_gemm_bf16(int transA, int transB, int M, int N, int K, float alpha, const float *A, int lda, const float *B,
-                 int ldb, float beta, float *C, int ldc, void *stream);
+                 int ldb, float beta, float *C, int ldc, float *work, long long work_elems, void *stream);
 
 /* col[(c 9 + t)][(b H + y) W + x] = x[c][b][y + t/3 - 1][x + t%3 - 1], zero
  * outside the image (3 x 3 convolution, stride 1, padding 1). */

@@ -30,12 +30,13 @@ inline int blocks_for(long long n, int cap = 152 * 16)
 constexpr int GT = 64, GK = 16;
 
 // Split K: blockIdx.z takes the K slice [z kc, (z + 1) kc); with more than
-// one slice the partial tiles are added to C atomically (C scaled by beta
-// beforehand).
+// one slice each slice writes alpha times its partial tile to part[z] (M x N,
+// row-major) and k_splitk_sum adds the slices in order, so the result does
+// not depend on which block finishes first.
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, float alpha, const float *__restrict__ A, int lda,
                                               const float *__restrict__ B, int ldb, float beta, float *C, int ldc,
-                                              int kc)
+                                              int kc, float *part)
 {
     __shared__ float As[GK][GT + 4];
     __shared__ float Bs[GK][GT + 4];
@@ -84,10 +85,25 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, float alpha, 
         for (int j = 0; j < 4; ++j) {
             const int gn = n0 + tx + 16 * j;
             if (gn >= N) continue;
-            float *c = C + (long long)gm * ldc + gn;
-            if (gridDim.z > 1) atomicAdd(c, alpha * acc[i][j]);
-            else *c = alpha * acc[i][j] + (beta != 0.0f ? beta * *c : 0.0f);
+            if (gridDim.z > 1) {
+                part[((long long)blockIdx.z * M + gm) * N + gn] = alpha * acc[i][j];
+            } else {
+                float *c = C + (long long)gm * ldc + gn;
+                *c = alpha * acc[i][j] + (beta != 0.0f ? beta * *c : 0.0f);
+            }
         }
+    }
+}
+
+// C = sum over s = 0 .. S-1 of part[s] (in that order) + beta C.
+__global__ void k_splitk_sum(float *C, int ldc, const float *__restrict__ part, int M, int N, int S, float beta)
+{
+    const long long n = (long long)M * N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        float acc = part[e];
+        for (int z = 1; z < S; ++z) acc += part[z * n + e];
+        float *c = C + (e / N) * ldc + e % N;
+        *c = acc + (beta != 0.0f ? beta * *c : 0.0f);
     }
 }
 
@@ -262,15 +278,6 @@ __global__ void k_adam(float *p, const float *g, float *m, float *v, long long n
     }
 }
 
-__global__ void k_scale_mat(float *C, int M, int N, int ldc, float beta)
-{
-    const long long n = (long long)M * N;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        float *c = C + (e / N) * ldc + e % N;
-        *c = beta != 0.0f ? beta * *c : 0.0f;
-    }
-}
-
 __global__ void k_zero_f(float *x, long long n)
 {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
@@ -307,7 +314,7 @@ __device__ __forceinline__ unsigned lds32(const __nv_bfloat16 *p) { return *rein
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) k_gemm_bf16(int M, int N, int K, float alpha, const float *__restrict__ A,
                                                    int lda, const float *__restrict__ B, int ldb, float beta,
-                                                   float *C, int ldc, int kc)
+                                                   float *C, int ldc, int kc, float *part)
 {
     __shared__ __align__(16) __nv_bfloat16 As[BM][BKP];
     __shared__ __align__(16) __nv_bfloat16 Bs[BN][BKP];
@@ -377,9 +384,12 @@ __global__ void __launch_bounds__(256) k_gemm_bf16(int M, int N, int K, float al
                 const int gm = m0 + wm * 32 + i * 16 + g + (r >= 2 ? 8 : 0);
                 const int gn = n0 + wn * 32 + jn * 8 + 2 * t + (r & 1);
                 if (gm >= M || gn >= N) continue;
-                float *c = C + (long long)gm * ldc + gn;
-                if (gridDim.z > 1) atomicAdd(c, alpha * acc[i][jn][r]);
-                else *c = alpha * acc[i][jn][r] + (beta != 0.0f ? beta * *c : 0.0f);
+                if (gridDim.z > 1) {
+                    part[((long long)blockIdx.z * M + gm) * N + gn] = alpha * acc[i][jn][r];
+                } else {
+                    float *c = C + (long long)gm * ldc + gn;
+                    *c = alpha * acc[i][jn][r] + (beta != 0.0f ? beta * *c : 0.0f);
+                }
             }
 }
 
@@ -387,54 +397,57 @@ __global__ void __launch_bounds__(256) k_gemm_bf16(int M, int N, int K, float al
 
 extern "C" {
 
-int nn_gemm(int transA, int transB, int M, int N, int K, float alpha, const float *A, int lda, const float *B, int ldb,
-            float beta, float *C, int ldc, void *stream)
+// K slices of one product: with few output tiles and a long K (weight
+// gradients), enough slices to give every SM a couple of blocks, as many as
+// the scratch (work_elems floats, M x N per slice) holds; kc receives the
+// slice depth (a multiple of `step`).
+static int splitk(int M, int N, int K, long long tiles, int step, long long work_elems, int *kc)
 {
-    if (M < 0 || N < 0 || K < 0 || !C || (K > 0 && (!A || !B))) return 1;
+    long long splits = 1;
+    if (tiles < 2 * 152 && K > 8 * step) {
+        const long long want = (2 * 152 + tiles - 1) / tiles, most = (K + 4 * step - 1) / (4 * step);
+        splits = want < most ? want : most;
+    }
+    const long long fit = work_elems / ((long long)M * N);
+    if (splits > fit) splits = fit > 1 ? fit : 1;
+    *kc = (int)(((K + splits - 1) / splits + step - 1) / step * step);
+    return (K + *kc - 1) / *kc;
+}
+
+int nn_gemm(int transA, int transB, int M, int N, int K, float alpha, const float *A, int lda, const float *B, int ldb,
+            float beta, float *C, int ldc, float *work, long long work_elems, void *stream)
+{
+    if (M < 0 || N < 0 || K < 0 || !C || (K > 0 && (!A || !B)) || work_elems < 0 || (work_elems > 0 && !work))
+        return 1;
     if (M == 0 || N == 0) return 0;
     cudaStream_t st = (cudaStream_t)stream;
-    // Few output tiles and a long K (weight gradients): split K over enough
-    // slices to give every SM a couple of blocks.
-    const long long tiles = (long long)((N + GT - 1) / GT) * ((M + GT - 1) / GT);
-    int splits = 1;
-    if (tiles < 2 * 152 && K > 8 * GK) {
-        const long long want = (2 * 152 + tiles - 1) / tiles, most = (K + 4 * GK - 1) / (4 * GK);
-        splits = (int)(want < most ? want : most);
-    }
-    const int kc = ((K + splits - 1) / splits + GK - 1) / GK * GK;
-    splits = (K + kc - 1) / kc;
-    if (splits > 1) k_scale_mat<<<blocks_for((long long)M * N), TPB, 0, st>>>(C, M, N, ldc, beta);
+    int kc = 0;
+    const int splits = splitk(M, N, K, (long long)((N + GT - 1) / GT) * ((M + GT - 1) / GT), GK, work_elems, &kc);
     dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT, splits);
-    if (!transA && !transB) k_gemm<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
-    else if (!transA && transB) k_gemm<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
-    else if (transA && !transB) k_gemm<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
-    else k_gemm<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
+    if (!transA && !transB) k_gemm<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc, work);
+    else if (!transA && transB) k_gemm<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc, work);
+    else if (transA && !transB) k_gemm<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc, work);
+    else k_gemm<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc, work);
+    if (splits > 1) k_splitk_sum<<<blocks_for((long long)M * N), TPB, 0, st>>>(C, ldc, work, M, N, splits, beta);
     return status(st);
 }
 
 int nn_gemm_bf16(int transA, int transB, int M, int N, int K, float alpha, const float *A, int lda, const float *B,
-                 int ldb, float beta, float *C, int ldc, void *stream)
+                 int ldb, float beta, float *C, int ldc, float *work, long long work_elems, void *stream)
 {
-    if (M < 0 || N < 0 || K < 0 || !C || (K > 0 && (!A || !B))) return 1;
+    if (M < 0 || N < 0 || K < 0 || !C || (K > 0 && (!A || !B)) || work_elems < 0 || (work_elems > 0 && !work))
+        return 1;
     if (M == 0 || N == 0) return 0;
-    if (K == 0) return nn_gemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream);
+    if (K == 0) return nn_gemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, work, work_elems, stream);
     cudaStream_t st = (cudaStream_t)stream;
-    // Few output tiles and a long K (weight gradients): split K so that
-    // every SM gets a couple of blocks.
-    const long long tiles = (long long)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
-    int splits = 1;
-    if (tiles < 2 * 152 && K > 8 * BK) {
-        const long long want = (2 * 152 + tiles - 1) / tiles, most = (K + 4 * BK - 1) / (4 * BK);
-        splits = (int)(want < most ? want : most);
-    }
-    const int kc = ((K + splits - 1) / splits + BK - 1) / BK * BK;
-    splits = (K + kc - 1) / kc;
-    if (splits > 1) k_scale_mat<<<blocks_for((long long)M * N), TPB, 0, st>>>(C, M, N, ldc, beta);
+    int kc = 0;
+    const int splits = splitk(M, N, K, (long long)((N + BN - 1) / BN) * ((M + BM - 1) / BM), BK, work_elems, &kc);
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
-    if (!transA && !transB) k_gemm_bf16<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
-    else if (!transA && transB) k_gemm_bf16<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
-    else if (transA && !transB) k_gemm_bf16<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
-    else k_gemm_bf16<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc);
+    if (!transA && !transB) k_gemm_bf16<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc, work);
+    else if (!transA && transB) k_gemm_bf16<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc, work);
+    else if (transA && !transB) k_gemm_bf16<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc, work);
+    else k_gemm_bf16<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kc, work);
+    if (splits > 1) k_splitk_sum<<<blocks_for((long long)M * N), TPB, 0, st>>>(C, ldc, work, M, N, splits, beta);
     return status(st);
 }
 

@@ -24,7 +24,7 @@ from .binding import load
 
 _FNS = {
     "nn_gemm": [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
-                C.c_float, C.c_void_p, C.c_int, C.c_void_p],
+                C.c_float, C.c_void_p, C.c_int, C.c_void_p, C.c_longlong, C.c_void_p],
     "nn_im2col3": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
     "nn_col2im3_add": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
     "nn_bias_act": [C.c_void_p, C.c_void_p, C.c_int, C.c_longlong, C.c_int, C.c_void_p],
@@ -38,7 +38,7 @@ _FNS = {
                 C.c_float, C.c_int, C.c_void_p],
     "nn_zero": [C.c_void_p, C.c_longlong, C.c_void_p],
     "nn_gemm_bf16": [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_void_p, C.c_int, C.c_void_p,
-                     C.c_int, C.c_float, C.c_void_p, C.c_int, C.c_void_p],
+                     C.c_int, C.c_float, C.c_void_p, C.c_int, C.c_void_p, C.c_longlong, C.c_void_p],
 }
 EXPORTS = sorted(_FNS)
 _lib = None
@@ -107,6 +107,9 @@ class UNet:
                         for n, ci, co, k in self.layers)
         self.col = torch.zeros(col_elems, **f32)
         self.dcol = torch.zeros(col_elems, **f32)
+        # split-K scratch of the GEMMs (partial products summed in a fixed
+        # order): room for 16 slices of the largest weight matrix
+        self.gemm_work = torch.zeros(max(1 << 20, 16 * max(co * ci * k * k for n, ci, co, k in self.layers)), **f32)
         self.loss = torch.zeros(1, dtype=torch.float64, device=self.dev)
 
     def sibling(self, batch: int) -> "UNet":
@@ -147,10 +150,11 @@ class UNet:
 
     def _gemm(self, ta, tb, M, N, K, A, lda, B, ldb, beta, Cm, ldc, what):
         L, st = _nn(), self._st()
+        wk, nw = _p(self.gemm_work), self.gemm_work.numel()
         if self.precision == "bf16":
-            rc = L.nn_gemm_bf16(ta, tb, M, N, K, 1.0, _p(A), lda, _p(B), ldb, beta, _p(Cm), ldc, st)
+            rc = L.nn_gemm_bf16(ta, tb, M, N, K, 1.0, _p(A), lda, _p(B), ldb, beta, _p(Cm), ldc, wk, nw, st)
         else:
-            rc = L.nn_gemm(ta, tb, M, N, K, 1.0, _p(A), lda, _p(B), ldb, beta, _p(Cm), ldc, st)
+            rc = L.nn_gemm(ta, tb, M, N, K, 1.0, _p(A), lda, _p(B), ldb, beta, _p(Cm), ldc, wk, nw, st)
         _ck(rc, what)
 
     def _conv_fwd(self, name, ci, co, k, x, y, relu):

@@ -21,7 +21,7 @@ def test_gemm_transposes_ragged(ta, tb):
     Cm = rng.standard_normal((M, N)).astype(np.float32)
     ref = 0.7 * ((A.T if ta else A).astype(np.float64) @ (B.T if tb else B).astype(np.float64)) + 0.3 * Cm
     a, b, c = (torch.tensor(v, device="cuda") for v in (A, B, Cm))
-    rc = _nn().nn_gemm(ta, tb, M, N, K, 0.7, _p(a), A.shape[1], _p(b), B.shape[1], 0.3, _p(c), N, None)
+    rc = _nn().nn_gemm(ta, tb, M, N, K, 0.7, _p(a), A.shape[1], _p(b), B.shape[1], 0.3, _p(c), N, None, 0, None)
     torch.cuda.synchronize()
     assert rc == 0
     np.testing.assert_allclose(c.cpu().numpy(), ref, rtol=1e-4, atol=1e-4)
@@ -80,12 +80,13 @@ def _bf16(a):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def _gemm_bf16_case(ta, tb, M, N, K, seed, alpha=0.7, beta=0.3):
+def _gemm_bf16_case(ta, tb, M, N, K, seed, alpha=0.7, beta=0.3, slices=16):
     """nn_gemm_bf16 against the FP64 product of the BF16-rounded operands.
     Products of BF16 values are exact in FP32, so the only error is the FP32
     accumulation: at most about K u sum_k |a_ik b_kj| (u = 2^-24) for any
     summation order, taken here with a factor 4 of margin, plus the rounding
-    of the beta C term."""
+    of the beta C term.  The scratch holds `slices` partial products, so a
+    long K is split."""
     import torch
     from paper_2203_01462_gb300.surrogate import _nn, _p
     rng = np.random.default_rng(seed)
@@ -97,7 +98,9 @@ def _gemm_bf16_case(ta, tb, M, N, K, seed, alpha=0.7, beta=0.3):
     ref = alpha * (Aop @ Bop) + beta * Cm
     bound = 4.0 * (K + 2) * 2.0 ** -24 * abs(alpha) * (np.abs(Aop) @ np.abs(Bop)) + 2.0 ** -22 * np.abs(ref) + 1e-30
     a, b, c = (torch.tensor(v, device="cuda") for v in (A, B, Cm))
-    rc = _nn().nn_gemm_bf16(ta, tb, M, N, K, alpha, _p(a), A.shape[1], _p(b), B.shape[1], beta, _p(c), N, None)
+    work = torch.empty(max(1, slices * M * N), device="cuda")
+    rc = _nn().nn_gemm_bf16(ta, tb, M, N, K, alpha, _p(a), A.shape[1], _p(b), B.shape[1], beta, _p(c), N,
+                            _p(work), slices * M * N, None)
     torch.cuda.synchronize()
     assert rc == 0
     err = np.abs(c.cpu().numpy() - ref)
@@ -114,12 +117,38 @@ def test_gemm_bf16_transposes_ragged(ta, tb):
 
 @pytest.mark.parametrize("shape", [(24, 27, 20000), (1, 300, 216), (97, 1, 33), (192, 8000, 864), (5, 7, 3)])
 def test_gemm_bf16_shapes(shape):
-    """A weight-gradient shape (small M x N, long K: split over blocks and
-    added atomically), a one-channel head, a one-column output, a U-Net
-    layer and a product smaller than one fragment."""
+    """A weight-gradient shape (small M x N, long K: split into K slices
+    whose partial products are summed in order), a one-channel head, a
+    one-column output, a U-Net layer and a product smaller than one
+    fragment."""
     M, N, K = shape
     for ta, tb in ((0, 1), (1, 0)):
         _gemm_bf16_case(ta, tb, M, N, K, 20 + M + ta, beta=0.0 if K > 1000 else 0.3)
+
+
+@pytest.mark.parametrize("bf16", [0, 1])
+def test_split_k_is_deterministic(bf16):
+    """A weight-gradient product split into K slices (scratch for 16) gives
+    the same bits on every call, and agrees with the unsplit product (no
+    scratch) to FP32 accumulation accuracy."""
+    import torch
+    from paper_2203_01462_gb300.surrogate import _nn, _p
+    rng = np.random.default_rng(4)
+    M, N, K = 48, 216, 131072
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    B = rng.standard_normal((N, K)).astype(np.float32)
+    a, b = torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda")
+    work = torch.empty(16 * M * N, device="cuda")
+    f = _nn().nn_gemm_bf16 if bf16 else _nn().nn_gemm
+    outs = []
+    for nw in (16 * M * N, 16 * M * N, 0):
+        c = torch.full((M, N), 3.0, device="cuda")
+        assert f(0, 1, M, N, K, 1.0, _p(a), K, _p(b), K, 0.5, _p(c), N, _p(work) if nw else None, nw, None) == 0
+        outs.append(c.cpu().numpy())
+    torch.cuda.synchronize()
+    assert np.array_equal(outs[0], outs[1])
+    scale = np.abs(A) @ np.abs(B).T
+    assert np.all(np.abs(outs[0] - outs[2]) <= 8.0 * K * 2.0 ** -24 * scale + 1e-6)
 
 
 def test_gemm_bf16_is_not_the_fp32_kernel():
@@ -134,8 +163,8 @@ def test_gemm_bf16_is_not_the_fp32_kernel():
     B = (1.0 + rng.random((K, N)) * 1e-2).astype(np.float32)
     a, b = torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda")
     c16, c32 = torch.zeros(M, N, device="cuda"), torch.zeros(M, N, device="cuda")
-    assert _nn().nn_gemm_bf16(0, 0, M, N, K, 1.0, _p(a), K, _p(b), N, 0.0, _p(c16), N, None) == 0
-    assert _nn().nn_gemm(0, 0, M, N, K, 1.0, _p(a), K, _p(b), N, 0.0, _p(c32), N, None) == 0
+    assert _nn().nn_gemm_bf16(0, 0, M, N, K, 1.0, _p(a), K, _p(b), N, 0.0, _p(c16), N, None, 0, None) == 0
+    assert _nn().nn_gemm(0, 0, M, N, K, 1.0, _p(a), K, _p(b), N, 0.0, _p(c32), N, None, 0, None) == 0
     torch.cuda.synchronize()
     exact16 = _bf16(A) @ _bf16(B)
     assert np.max(np.abs(c16.cpu().numpy() - exact16)) <= 1e-4 * np.max(np.abs(exact16))

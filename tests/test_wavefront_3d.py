@@ -100,7 +100,6 @@ def test_wavefront_setting_is_validated():
         solver(w2).set_wavefront(2)
 
 
-
 def test_wavefront_with_the_stability_guard():
     """Guard every 20 steps: runs end on multiples of 20 (launches of up to 8
     steps) and the result is still bit-identical; a bound below the fields
