@@ -1426,6 +1426,7 @@ struct Ctx3D final : fdtd_ctx {
         geo.Mg = (int)Mg;
         geo.src_comp = c.src_comp;
         geo.sub_hi = c.sub_hi;
+        geo.kappa1 = c.pml_kappa_max == 1.0;
         geo.tfsf = c.tfsf;
         for (int a = 0; a < 3; ++a) {
             geo.tf_lo[a] = c.tf_lo[a];

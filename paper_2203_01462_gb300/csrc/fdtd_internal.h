@@ -132,6 +132,7 @@ struct Geo3D {
     // plane wave by total-field / scattered-field injection (tfsf = 1): the
     // closed total-field box of positions [tf_lo, tf_hi] (node units)
     int tfsf, tf_lo[3], tf_hi[3];
+    int kappa1;  // every CPML kappa is 1 (pml_kappa_max = 1): the 1/kappa tables are all ones
 };
 
 // Incident-table row of one step of the plane wave: E_x^n at k = tf_lo[2] ..

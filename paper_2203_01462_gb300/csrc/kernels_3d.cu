@@ -178,8 +178,11 @@ __device__ __forceinline__ void cpml_apply(const Geo3D &g, R *const (&psi)[3][2]
 {
     const long long iy = pidx(g, 1, sy, i0, j, k), iz = pidx(g, 2, sz, i0, j, k);
     // coefficient tables are read-only: non-coherent loads, free to move past stores
-    const R by = __ldg(tb[1] + j), cy = __ldg(tc[1] + j), ky = __ldg(tk[1] + j);
-    const R bz = __ldg(tb[2] + k), cz = __ldg(tc[2] + k), kz = __ldg(tk[2] + k);
+    // with kappa = 1 everywhere the 1/kappa tables are not read (the product
+    // by 1 below is exact, so the result is the same)
+    const bool k1 = g.kappa1 != 0;
+    const R by = __ldg(tb[1] + j), cy = __ldg(tc[1] + j), ky = k1 ? R(1) : __ldg(tk[1] + j);
+    const R bz = __ldg(tb[2] + k), cz = __ldg(tc[2] + k), kz = k1 ? R(1) : __ldg(tk[2] + k);
     R t[2][4];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -189,7 +192,7 @@ __device__ __forceinline__ void cpml_apply(const Geo3D &g, R *const (&psi)[3][2]
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 const bool in = ax == 0 ? sx[v] >= 0 : (ax == 1 ? sy >= 0 : sz >= 0);
-                const R kk = ax == 0 ? (i0 + v < g.n[0] ? __ldg(tk[0] + i0 + v) : R(1)) : (ax == 1 ? ky : kz);
+                const R kk = ax == 0 ? ((!k1 && i0 + v < g.n[0]) ? __ldg(tk[0] + i0 + v) : R(1)) : (ax == 1 ? ky : kz);
                 t[h][v] = d[c][h][v] * kk;
                 if (in) {
                     const R bb = ax == 0 ? __ldg(tb[0] + i0 + v) : (ax == 1 ? by : bz);
