@@ -297,7 +297,9 @@ class Solver:
         self.w["filter_sigma"] = float(sigma)
 
     def set_steps_per_launch(self, steps: int) -> None:
-        """In-plane 2D mode: time steps per cooperative launch (1: one launch per half step)."""
+        """Time steps per launch (1: one launch per step): in-plane 2D mode, a
+        cooperative launch with grid barriers; 2D E_z, temporal blocking on
+        32 x 32 tiles with a halo in shared memory (up to 8 steps)."""
         _check(self.lib.fdtd_set_steps_per_launch(self.ctx, int(steps)), "fdtd_set_steps_per_launch")
 
     def set_wavefront(self, steps: int) -> None:

@@ -251,6 +251,34 @@ template <typename R>
 int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, int coef_slot, const Pml3D<R> &pm,
                   const Step3D<R> &a, cudaStream_t st);
 
+// Temporally blocked 2D E_z steps (kernels_tb2d.cu): a block owns a 32 x 32
+// tile and advances count <= TB_MAX steps on it and a halo of count nodes in
+// shared memory, reading state `in` and writing its tile into `out`.
+// Forward: steps n0 .. n0+count-1 (source row n, gap row n+1, design record
+// slot n - rec0); adjoint: m = n0 down to n0-count+1 (gap row m, record slot
+// m-1-rec0), G the accumulator.
+constexpr int TB_MAX = 8;
+template <typename R>
+struct Tb2D {
+    int count, n0, rec0;
+    long long Mdi;
+    const R *src;
+    R *gap;
+    R *rec;
+    const R *rho_t;
+    double *G;
+};
+size_t tb2d_smem_bytes(int esz, int T);
+// The most steps per launch whose region fits a block's shared memory (and
+// the kernels' shared-memory limit raised to it), or 0.
+template <typename R>
+int tb2d_max_steps();
+template <typename R>
+int launch_tb2d(int mode, const Geo2D &g, const State2D<R> &in, const State2D<R> &out, int coef_slot,
+                const Pml1D<R> &px, const Pml1D<R> &py, const Tb2D<R> &w, cudaStream_t st);
+template <typename R>
+cudaError_t upload_coef_tb2d(int slot, const Coef<R> &c, cudaStream_t st);
+
 // Several 3D steps in one persistent launch (kernels_3d.cu, k_wave3d).
 // The grid is cut into z slabs of two planes; an item is up to `tpi`
 // x-adjacent node tiles of one row of one slab, and a job is every item of

@@ -1,0 +1,356 @@
+// Temporally blocked 2D TM_z leapfrog (Ez, Hx, Hy, Jz + CPML) for small
+// grids, for sm_103a.
+//
+// On a small grid (the surrogate workload's 316^2, the 160^2 parity case)
+// each launch-per-step kernel is a single partial wave, so a step costs a
+// few launch and memory latencies (about 7 us) whatever its work.  Here a
+// block (48 x 16 threads: one per column of the region, its rows in
+// passes) owns a 32 x 32 node tile; one launch advances T steps (T <=
+// TB_MAX) at once.  The block loads its tile with a halo of T
+// nodes on every side into shared memory (fields, J and the Drude
+// coefficients of rho~ on design nodes, the CPML terms on slab nodes), runs the T steps there (an H half
+// step and an E half step per step, each over the whole region, separated
+// by block barriers), and writes back only its own tile, from one buffer of
+// the ping-pong pair into the other.  Each half step invalidates one layer
+// of the region from the outside (H reads Ez one node up and right, E reads
+// H one node down and left), so after T steps the tile itself is still exact
+// and no block ever waits for another.  Records (the gap history, the
+// design-box history), the source and, in the adjoint, the forward record
+// and the FP64 sensitivity accumulator are read and written for the tile's
+// own nodes only; the adjoint's records of all T steps are loaded with the
+// tile, so no global load waits inside the step loop.
+//
+// Per node the arithmetic is that of the launch-per-step kernel's generic
+// (border) path: H -= S t / H += S t with t the CPML-corrected difference,
+// E from the curl S (c_x - c_y) through the same Drude, gap and source
+// update.
+
+#include <algorithm>
+
+#include "coef_slots.cuh"
+#include "fdtd_internal.h"
+
+namespace fdtd {
+
+namespace {
+
+constexpr int TBT = 32;                  // tile side (nodes)
+constexpr int TBX = TBT + 2 * TB_MAX;    // threads along x: one per region column
+constexpr int TBY = 16;                  // threads along y (region rows in passes of TBY)
+constexpr int TBN = TBX * TBY;
+
+__device__ __forceinline__ bool in_range(int v, int lo, int n) { return (unsigned)(v - lo) < (unsigned)n; }
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+
+// Slab indices of the CPML arrays: x-slab columns [ny][2 np] and y-slab rows
+// [2 np][px], for E (node positions) and H (half positions); -1 outside.
+__device__ __forceinline__ int slab_e(int p, int n, int np) { return p < np ? p : (p >= n - np ? p - (n - 2 * np) : -1); }
+__device__ __forceinline__ int slab_h(int p, int n, int np)
+{
+    return p < np ? p : ((p >= n - 1 - np && p < n - 1) ? np + p - (n - 1 - np) : -1);
+}
+
+// Shared-memory arrays of one block, each [RH][RW] (R) but the adjoint's
+// accumulator [TBT][TBT] (double) and records [T][TBT][TBT] (R).  On
+// design nodes ca, cb, bJ (and, for the adjoint's sensitivity bracket, a1,
+// a2) are the Drude update's coefficients, worked out from rho~ once per
+// launch exactly as the step kernel's drude() works them out every step.
+constexpr int RARR = 13;  // [RH][RW] arrays
+template <typename R>
+struct Region {
+    R *ez, *hx, *hy, *J, *ca, *cb, *bJ, *a1, *a2, *pezx, *phyx, *pezy, *phxy, *rec;
+    double *G;
+};
+
+template <typename R>
+__device__ __forceinline__ Region<R> carve_region(char *base, int cells, int T)
+{
+    Region<R> r;
+    R *p = (R *)base;
+    R **arr[RARR] = {&r.ez, &r.hx, &r.hy, &r.J, &r.ca, &r.cb, &r.bJ, &r.a1, &r.a2, &r.pezx, &r.phyx, &r.pezy, &r.phxy};
+#pragma unroll
+    for (int k = 0; k < RARR; ++k) *arr[k] = p + k * cells;
+    r.rec = p + RARR * cells;
+    // the accumulator after the T record planes, 16-byte aligned
+    size_t off = (size_t)(RARR * cells + T * TBT * TBT) * sizeof(R);
+    off = (off + 15) & ~(size_t)15;
+    r.G = (double *)(base + off);
+    return r;
+}
+
+}  // namespace
+
+// Shared memory of one block for steps of at most T per launch.
+size_t tb2d_smem_bytes(int esz, int T)
+{
+    const int side = TBT + 2 * T;
+    size_t off = (size_t)(RARR * side * side + T * TBT * TBT) * esz;
+    off = (off + 15) & ~(size_t)15;
+    return off + (size_t)TBT * TBT * sizeof(double);
+}
+
+namespace {
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(TBN, 1)
+    k_tb2d(const __grid_constant__ Geo2D g, const __grid_constant__ State2D<R> in,
+           const __grid_constant__ State2D<R> out, int slot, const __grid_constant__ Pml1D<R> px,
+           const __grid_constant__ Pml1D<R> py, const __grid_constant__ Tb2D<R> w)
+{
+    extern __shared__ __align__(16) char smem[];
+    const int T = w.count, side = TBT + 2 * T, cells = side * side;
+    const Region<R> r = carve_region<R>(smem, cells, T);
+    const Coef<R> &c = coef_at<R>(slot);
+    const int nx = g.nx, ny = g.ny, np = g.npml, P = g.px, np2 = 2 * np;
+    const int x0 = blockIdx.x * TBT - T, y0 = blockIdx.y * TBT - T;  // region origin (global)
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const R S = c.S;
+    const int Mg = g.gnx * g.gny;
+    // the source amplitudes of the launch's steps, loaded with the tile
+    __shared__ R src_s[TB_MAX];
+    if (MODE == 0 && threadIdx.y == 0 && threadIdx.x < T) src_s[threadIdx.x] = w.src[w.n0 + threadIdx.x];
+
+    // ---- load the region (zeros outside the grid and outside the boxes)
+    for (int rj = ty; rj < side; rj += TBY)
+        for (int ri = tx; ri < side; ri += TBX) {
+            const int i = x0 + ri, j = y0 + rj, q = rj * side + ri;
+            R ez = R(0), hx = R(0), hy = R(0), J = R(0), a = R(0), b = R(0), cc = R(0), d = R(0);
+            R ca = R(0), cb = R(0), bJ = R(0), a1 = R(0), a2 = R(0);
+            if ((unsigned)i < (unsigned)nx && (unsigned)j < (unsigned)ny) {
+                const long long gq = (long long)j * P + i;
+                ez = in.Ez[gq];
+                hx = in.Hx[gq];
+                hy = in.Hy[gq];
+                if (in_range(i, g.dx0, g.dnx) && in_range(j, g.dy0, g.dny)) {
+                    const long long dg = (long long)(j - g.dy0) * g.dp + (i - g.dxa);
+                    J = in.J[dg];
+                    // the coefficients of drude(), in its order of operations
+                    const R rt = w.rho_t[dg];
+                    const R eps = c.eps_s + rt * c.d_eps;
+                    const R psi = c.psi_s + rt * (c.psi - c.psi_s);
+                    const R sig = c.sig_max * rt * (R(1) - rt);
+                    bJ = R(0.5) * psi * c.inv1g;
+                    const R hs = R(0.5) * (sig + bJ);
+                    cb = rcp(eps + hs);
+                    ca = (eps - hs) * cb;
+                    if (MODE == 1) {
+                        a1 = c.t_sig * (R(1) - R(2) * rt) * R(0.5);
+                        a2 = c.t_dpsi * rcp(psi) * R(0.5);
+                    }
+                }
+                if (np > 0) {
+                    const int se = slab_e(i, nx, np), sh = slab_h(i, nx, np);
+                    const int te = slab_e(j, ny, np), th = slab_h(j, ny, np);
+                    if (se >= 0) a = in.pezx[(long long)j * np2 + se];
+                    if (sh >= 0) b = in.phyx[(long long)j * np2 + sh];
+                    if (te >= 0) cc = in.pezy[(long long)te * P + i];
+                    if (th >= 0) d = in.phxy[(long long)th * P + i];
+                }
+            }
+            r.ez[q] = ez;
+            r.hx[q] = hx;
+            r.hy[q] = hy;
+            r.J[q] = J;
+            r.ca[q] = ca;
+            r.cb[q] = cb;
+            r.bJ[q] = bJ;
+            r.a1[q] = a1;
+            r.a2[q] = a2;
+            r.pezx[q] = a;
+            r.phyx[q] = b;
+            r.pezy[q] = cc;
+            r.phxy[q] = d;
+        }
+    // (adjoint) the accumulator of the tile's own nodes and their forward
+    // records of all T steps
+    const int flat = ty * TBX + tx;
+    if (MODE == 1)
+        for (int o = flat; o < TBT * TBT; o += TBN) {
+            const int oi = blockIdx.x * TBT + (o & (TBT - 1)), oj = blockIdx.y * TBT + o / TBT;
+            const bool des = oi < nx && oj < ny && in_range(oi, g.dx0, g.dnx) && in_range(oj, g.dy0, g.dny);
+            const long long dg = (long long)(oj - g.dy0) * g.dp + (oi - g.dxa);
+            r.G[o] = des ? w.G[dg] : 0.0;
+            for (int t = 0; t < T; ++t)
+                r.rec[t * TBT * TBT + o] = des ? w.rec[(long long)(w.n0 - t - 1 - w.rec0) * w.Mdi + dg] : R(0);
+        }
+    __syncthreads();
+
+    for (int t = 0; t < T; ++t) {
+        // ---- H half step over the region (reads Ez, writes Hx, Hy, psi_H)
+        for (int rj = ty; rj < side; rj += TBY)
+            for (int ri = tx; ri < side; ri += TBX) {
+                const int i = x0 + ri, j = y0 + rj, q = rj * side + ri;
+                if ((unsigned)i >= (unsigned)nx || (unsigned)j >= (unsigned)ny) continue;
+                const R ez = r.ez[q];
+                if (j + 1 < ny && rj + 1 < side) {
+                    const R dd = r.ez[q + side] - ez;
+                    R tt = dd;
+                    if (np > 0 && (j < np || j >= ny - 1 - np)) {
+                        const R p = py.bH[j] * r.phxy[q] + py.cH[j] * dd;
+                        r.phxy[q] = p;
+                        tt = dd * py.kiH[j] + p;
+                    }
+                    r.hx[q] = r.hx[q] - S * tt;
+                }
+                if (i + 1 < nx && ri + 1 < side) {
+                    const R dd = r.ez[q + 1] - ez;
+                    R tt = dd;
+                    if (np > 0 && (i < np || i >= nx - 1 - np)) {
+                        const R p = px.bH[i] * r.phyx[q] + px.cH[i] * dd;
+                        r.phyx[q] = p;
+                        tt = dd * px.kiH[i] + p;
+                    }
+                    r.hy[q] = r.hy[q] + S * tt;
+                }
+            }
+        __syncthreads();
+        // ---- E half step over the region (reads Hx, Hy, writes Ez, J, psi_E)
+        R src_v = R(0);
+        const R *gsrc = nullptr;
+        R *gap_rec = nullptr, *rec = nullptr;
+        if (MODE == 0) {
+            const int n = w.n0 + t;
+            src_v = src_s[t];
+            gap_rec = w.gap ? w.gap + (long long)(n + 1) * Mg : nullptr;
+            rec = w.rec ? w.rec + (long long)(n - w.rec0) * w.Mdi : nullptr;
+        } else {
+            gsrc = w.gap ? w.gap + (long long)(w.n0 - t) * Mg : nullptr;
+        }
+        for (int rj = ty; rj < side; rj += TBY)
+            for (int ri = tx; ri < side; ri += TBX) {
+                const int i = x0 + ri, j = y0 + rj, q = rj * side + ri;
+                if (i < 1 || i > nx - 2 || j < 1 || j > ny - 2 || ri < 1 || rj < 1) continue;
+                const R ez = r.ez[q];
+                const R dHy = r.hy[q] - r.hy[q - 1];
+                const R dHx = r.hx[q] - r.hx[q - side];
+                R cx = dHy, cy = dHx;
+                if (np > 0 && (i < np || i >= nx - np)) {
+                    const R p = px.bE[i] * r.pezx[q] + px.cE[i] * dHy;
+                    r.pezx[q] = p;
+                    cx = dHy * px.kiE[i] + p;
+                }
+                if (np > 0 && (j < np || j >= ny - np)) {
+                    const R p = py.bE[j] * r.pezy[q] + py.cE[j] * dHx;
+                    r.pezy[q] = p;
+                    cy = dHx * py.kiE[j] + p;
+                }
+                const R curl = S * (cx - cy);
+                // the step kernel's e_update; records for the tile's own nodes
+                const bool own = ri >= T && ri < T + TBT && rj >= T && rj < T + TBT;
+                const bool gap = in_range(i, g.gx0, g.gnx) && in_range(j, g.gy0, g.gny);
+                const int gidx = (j - g.gy0) * g.gnx + (i - g.gx0);
+                R src = R(0);
+                if (MODE == 0) {
+                    if (in_range(i, g.sx0, g.sx1 - g.sx0) && in_range(j, g.sy0, g.sy1 - g.sy0)) src = src_v;
+                } else if (gap) {
+                    src = -c.eps_g * gsrc[gidx];
+                }
+                const bool des = in_range(i, g.dx0, g.dnx) && in_range(j, g.dy0, g.dny);
+                const long long dg = (long long)(j - g.dy0) * g.dp + (i - g.dxa);
+                R en;
+                if (des && !gap) {
+                    // drude() with its rho~-only coefficients precomputed
+                    const R jo = r.J[q];
+                    en = r.ca[q] * ez + r.cb[q] * (curl - c.half1pkJ * jo - src);
+                    const R jn = c.kJ * jo + r.bJ[q] * (en + ez);
+                    R term = R(0);
+                    if (MODE == 1) term = -c.t_eps * (en - ez) - r.a1[q] * (en + ez) - r.a2[q] * (jn + jo);
+                    r.J[q] = jn;
+                    if (own) {
+                        const int o = (rj - T) * TBT + (ri - T);
+                        if (MODE == 0) {
+                            if (rec) rec[dg] = en;
+                        } else {
+                            r.G[o] += (double)r.rec[t * TBT * TBT + o] * (double)term;
+                        }
+                    }
+                } else {
+                    en = ez + (curl - src) * (gap ? c.inv_eps_g : c.inv_eps_s);
+                    if (MODE == 0 && own && des && rec) rec[dg] = en;
+                }
+                if (MODE == 0 && own && gap && gap_rec) gap_rec[gidx] = en;
+                r.ez[q] = en;
+            }
+        __syncthreads();
+    }
+
+    // ---- store the tile's own nodes into the other buffer of the pair
+    for (int o = flat; o < TBT * TBT; o += TBN) {
+        const int ox = o & (TBT - 1), oy = o / TBT;
+        const int oi = blockIdx.x * TBT + ox, oj = blockIdx.y * TBT + oy;
+        if (oi >= nx || oj >= ny) continue;
+        const int q = (oy + T) * side + (ox + T);
+        const long long gq = (long long)oj * P + oi;
+        out.Ez[gq] = r.ez[q];
+        out.Hx[gq] = r.hx[q];
+        out.Hy[gq] = r.hy[q];
+        if (in_range(oi, g.dx0, g.dnx) && in_range(oj, g.dy0, g.dny)) {
+            const long long dg = (long long)(oj - g.dy0) * g.dp + (oi - g.dxa);
+            out.J[dg] = r.J[q];
+            if (MODE == 1) w.G[dg] = r.G[o];
+        }
+        if (np > 0) {
+            const int se = slab_e(oi, nx, np), sh = slab_h(oi, nx, np);
+            const int te = slab_e(oj, ny, np), th = slab_h(oj, ny, np);
+            if (se >= 0) out.pezx[(long long)oj * np2 + se] = r.pezx[q];
+            if (sh >= 0) out.phyx[(long long)oj * np2 + sh] = r.phyx[q];
+            if (te >= 0) out.pezy[(long long)te * P + oi] = r.pezy[q];
+            if (th >= 0) out.phxy[(long long)th * P + oi] = r.phxy[q];
+        }
+    }
+}
+
+}  // namespace
+
+template <typename R>
+int tb2d_max_steps()
+{
+    int dev = 0, smem = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    for (int T = TB_MAX; T >= 1; --T) {
+        const size_t b = tb2d_smem_bytes((int)sizeof(R), T);
+        if (b > (size_t)smem) continue;
+        if (cudaFuncSetAttribute(k_tb2d<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b) != cudaSuccess ||
+            cudaFuncSetAttribute(k_tb2d<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return T;
+    }
+    return 0;
+}
+
+template <typename R>
+int launch_tb2d(int mode, const Geo2D &g, const State2D<R> &in, const State2D<R> &out, int coef_slot,
+                const Pml1D<R> &px, const Pml1D<R> &py, const Tb2D<R> &w, cudaStream_t st)
+{
+    const dim3 block(TBX, TBY), grid((g.nx + TBT - 1) / TBT, (g.ny + TBT - 1) / TBT);
+    const size_t smem = tb2d_smem_bytes((int)sizeof(R), w.count);
+    if (mode == 0) k_tb2d<R, 0><<<grid, block, smem, st>>>(g, in, out, coef_slot, px, py, w);
+    else k_tb2d<R, 1><<<grid, block, smem, st>>>(g, in, out, coef_slot, px, py, w);
+    return 1;
+}
+
+// This translation unit's copy of the coefficient slots (constant memory is
+// per translation unit).
+template <typename R>
+cudaError_t upload_coef_tb2d(int slot, const Coef<R> &c, cudaStream_t st)
+{
+    return write_coef_slot(slot, c, st);
+}
+
+template int tb2d_max_steps<float>();
+template int tb2d_max_steps<double>();
+template int launch_tb2d<float>(int, const Geo2D &, const State2D<float> &, const State2D<float> &, int,
+                                const Pml1D<float> &, const Pml1D<float> &, const Tb2D<float> &, cudaStream_t);
+template int launch_tb2d<double>(int, const Geo2D &, const State2D<double> &, const State2D<double> &, int,
+                                 const Pml1D<double> &, const Pml1D<double> &, const Tb2D<double> &, cudaStream_t);
+template cudaError_t upload_coef_tb2d<float>(int, const Coef<float> &, cudaStream_t);
+template cudaError_t upload_coef_tb2d<double>(int, const Coef<double> &, cudaStream_t);
+
+}  // namespace fdtd

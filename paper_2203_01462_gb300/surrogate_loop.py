@@ -83,17 +83,23 @@ def collect_pairs(s: Solver, rho0_list, iters: int, move: float = 0.05, sigma_ma
 
 def collect_pairs_concurrent(w: dict, rho0_list, iters: int, move: float = 0.05, sigma_max: float = 0.0,
                              damping_start: float = 10.0, damping_iters: int = 50, pairs: Pairs | None = None,
-                             width: int = 16) -> Pairs:
+                             width: int = 16, steps_per_launch: int | None = None) -> Pairs:
     """collect_pairs with the trajectories run side by side: up to ``width``
     solvers of workload ``w``, each on its own CUDA stream, take one design
     step each per round, so that the launches of several small-grid
     trajectories (one partial wave of blocks each) share the GPU.  Every
     trajectory computes exactly what collect_pairs computes (same kernels,
-    same inputs); the pairs are kept in trajectory order."""
+    same inputs); the pairs are kept in trajectory order.  steps_per_launch
+    (None: the library's default) sets the solvers' steps per launch: side
+    by side, one launch per step shares the GPU better than temporally
+    blocked launches, which each hold about a hundred SMs."""
     pairs = pairs or Pairs()
     for b0 in range(0, len(rho0_list), width):
         group = list(rho0_list[b0:b0 + width])
         solvers = [Solver(w, stream=torch.cuda.Stream()) for _ in group]
+        if steps_per_launch is not None:
+            for s in solvers:
+                s.set_steps_per_launch(steps_per_launch)
         per = [Pairs() for _ in group]
         rhos = []
         for s, rho0 in zip(solvers, group):
