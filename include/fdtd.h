@@ -265,7 +265,7 @@ fdtd_status fdtd_set_filter_width(fdtd_ctx *ctx, double sigma);
  * of that many nodes into shared memory, advances all the steps there and
  * writes back its tile, so no block waits for another.  Small grids, whose
  * launch-per-step kernels are single partial waves, gain: the default is 8
- * for FP32 grids of at most one 32 x 32 tile per SM (316^2: 7.1 -> 4.4 us
+ * for FP32 grids of at most one 32 x 32 tile per SM (316^2: 7.1 -> 3.4 us
  * per forward step) and 1 otherwise (a 640^2 grid or an FP64 one runs
  * slower blocked).  Results agree with the launch-per-step path to rounding
  * (the per-node arithmetic of its generic path).

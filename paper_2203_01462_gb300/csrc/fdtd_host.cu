@@ -643,7 +643,7 @@ struct Ctx2D final : fdtd_ctx {
         tb_max = tb2d_max_steps<R>();
         // Default: temporal blocking on FP32 grids of at most one 32 x 32 tile
         // per SM, where the launch-per-step kernels are single partial waves
-        // (measured: 316^2, 7.1 -> 4.4 us per step); larger or FP64 grids run
+        // (measured: 316^2, 7.1 -> 3.4 us per forward step); larger or FP64 grids run
         // faster one launch per step.
         {
             int dev = 0, sms = 0;

@@ -38,6 +38,7 @@ constexpr int TBT = 32;                  // tile side (nodes)
 constexpr int TBX = TBT + 2 * TB_MAX;    // threads along x: one per region column
 constexpr int TBY = 16;                  // threads along y (region rows in passes of TBY)
 constexpr int TBN = TBX * TBY;
+constexpr int NK = (TBX + TBY - 1) / TBY;  // region rows per thread
 
 __device__ __forceinline__ bool in_range(int v, int lo, int n) { return (unsigned)(v - lo) < (unsigned)n; }
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
@@ -176,34 +177,57 @@ __global__ void __launch_bounds__(TBN, 1)
         }
     __syncthreads();
 
+    // Each thread owns column ri = tx of the region and its rows ty + k TBY,
+    // k < NK; every half step loads the inputs of all its rows before it
+    // computes any of them (the loads of different rows then overlap).
+    const int ri = tx, i = x0 + ri;
+    const bool col_in = ri < side && (unsigned)i < (unsigned)nx;
     for (int t = 0; t < T; ++t) {
         // ---- H half step over the region (reads Ez, writes Hx, Hy, psi_H)
-        for (int rj = ty; rj < side; rj += TBY)
-            for (int ri = tx; ri < side; ri += TBX) {
-                const int i = x0 + ri, j = y0 + rj, q = rj * side + ri;
-                if ((unsigned)i >= (unsigned)nx || (unsigned)j >= (unsigned)ny) continue;
-                const R ez = r.ez[q];
+        {
+            R ez[NK], ezU[NK], ezR[NK], hxo[NK], hyo[NK], pxy[NK], pyx[NK];
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                const int rj = ty + k * TBY, j = y0 + rj, q = rj * side + ri;
+                ez[k] = ezU[k] = ezR[k] = hxo[k] = hyo[k] = pxy[k] = pyx[k] = R(0);
+                if (col_in && rj < side && (unsigned)j < (unsigned)ny) {
+                    ez[k] = r.ez[q];
+                    hxo[k] = r.hx[q];
+                    hyo[k] = r.hy[q];
+                    if (j + 1 < ny && rj + 1 < side) ezU[k] = r.ez[q + side];
+                    if (i + 1 < nx && ri + 1 < side) ezR[k] = r.ez[q + 1];
+                    if (np > 0) {
+                        pxy[k] = r.phxy[q];
+                        pyx[k] = r.phyx[q];
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                const int rj = ty + k * TBY, j = y0 + rj, q = rj * side + ri;
+                if (!(col_in && rj < side && (unsigned)j < (unsigned)ny)) continue;
                 if (j + 1 < ny && rj + 1 < side) {
-                    const R dd = r.ez[q + side] - ez;
+                    const R dd = ezU[k] - ez[k];
                     R tt = dd;
                     if (np > 0 && (j < np || j >= ny - 1 - np)) {
-                        const R p = py.bH[j] * r.phxy[q] + py.cH[j] * dd;
+                        const R p = py.bH[j] * pxy[k] + py.cH[j] * dd;
                         r.phxy[q] = p;
                         tt = dd * py.kiH[j] + p;
                     }
-                    r.hx[q] = r.hx[q] - S * tt;
+                    r.hx[q] = hxo[k] - S * tt;
                 }
                 if (i + 1 < nx && ri + 1 < side) {
-                    const R dd = r.ez[q + 1] - ez;
+                    const R dd = ezR[k] - ez[k];
                     R tt = dd;
                     if (np > 0 && (i < np || i >= nx - 1 - np)) {
-                        const R p = px.bH[i] * r.phyx[q] + px.cH[i] * dd;
+                        const R p = px.bH[i] * pyx[k] + px.cH[i] * dd;
                         r.phyx[q] = p;
                         tt = dd * px.kiH[i] + p;
                     }
-                    r.hy[q] = r.hy[q] + S * tt;
+                    r.hy[q] = hyo[k] + S * tt;
                 }
             }
+        }
         __syncthreads();
         // ---- E half step over the region (reads Hx, Hy, writes Ez, J, psi_E)
         R src_v = R(0);
@@ -217,21 +241,49 @@ __global__ void __launch_bounds__(TBN, 1)
         } else {
             gsrc = w.gap ? w.gap + (long long)(w.n0 - t) * Mg : nullptr;
         }
-        for (int rj = ty; rj < side; rj += TBY)
-            for (int ri = tx; ri < side; ri += TBX) {
-                const int i = x0 + ri, j = y0 + rj, q = rj * side + ri;
-                if (i < 1 || i > nx - 2 || j < 1 || j > ny - 2 || ri < 1 || rj < 1) continue;
-                const R ez = r.ez[q];
-                const R dHy = r.hy[q] - r.hy[q - 1];
-                const R dHx = r.hx[q] - r.hx[q - side];
+        {
+            R ez[NK], hy[NK], hyL[NK], hx[NK], hxD[NK], pex[NK], pey[NK], jo[NK], ca[NK], cb[NK], bj[NK], a1[NK],
+                a2[NK];
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                const int rj = ty + k * TBY, j = y0 + rj, q = rj * side + ri;
+                ez[k] = hy[k] = hyL[k] = hx[k] = hxD[k] = pex[k] = pey[k] = R(0);
+                jo[k] = ca[k] = cb[k] = bj[k] = a1[k] = a2[k] = R(0);
+                if (col_in && rj < side && i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && ri >= 1 && rj >= 1) {
+                    ez[k] = r.ez[q];
+                    hy[k] = r.hy[q];
+                    hyL[k] = r.hy[q - 1];
+                    hx[k] = r.hx[q];
+                    hxD[k] = r.hx[q - side];
+                    if (np > 0) {
+                        pex[k] = r.pezx[q];
+                        pey[k] = r.pezy[q];
+                    }
+                    jo[k] = r.J[q];
+                    ca[k] = r.ca[q];
+                    cb[k] = r.cb[q];
+                    bj[k] = r.bJ[q];
+                    if (MODE == 1) {
+                        a1[k] = r.a1[q];
+                        a2[k] = r.a2[q];
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                const int rj = ty + k * TBY, j = y0 + rj, q = rj * side + ri;
+                if (!(col_in && rj < side && i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && ri >= 1 && rj >= 1))
+                    continue;
+                const R dHy = hy[k] - hyL[k];
+                const R dHx = hx[k] - hxD[k];
                 R cx = dHy, cy = dHx;
                 if (np > 0 && (i < np || i >= nx - np)) {
-                    const R p = px.bE[i] * r.pezx[q] + px.cE[i] * dHy;
+                    const R p = px.bE[i] * pex[k] + px.cE[i] * dHy;
                     r.pezx[q] = p;
                     cx = dHy * px.kiE[i] + p;
                 }
                 if (np > 0 && (j < np || j >= ny - np)) {
-                    const R p = py.bE[j] * r.pezy[q] + py.cE[j] * dHx;
+                    const R p = py.bE[j] * pey[k] + py.cE[j] * dHx;
                     r.pezy[q] = p;
                     cy = dHx * py.kiE[j] + p;
                 }
@@ -251,11 +303,10 @@ __global__ void __launch_bounds__(TBN, 1)
                 R en;
                 if (des && !gap) {
                     // drude() with its rho~-only coefficients precomputed
-                    const R jo = r.J[q];
-                    en = r.ca[q] * ez + r.cb[q] * (curl - c.half1pkJ * jo - src);
-                    const R jn = c.kJ * jo + r.bJ[q] * (en + ez);
+                    en = ca[k] * ez[k] + cb[k] * (curl - c.half1pkJ * jo[k] - src);
+                    const R jn = c.kJ * jo[k] + bj[k] * (en + ez[k]);
                     R term = R(0);
-                    if (MODE == 1) term = -c.t_eps * (en - ez) - r.a1[q] * (en + ez) - r.a2[q] * (jn + jo);
+                    if (MODE == 1) term = -c.t_eps * (en - ez[k]) - a1[k] * (en + ez[k]) - a2[k] * (jn + jo[k]);
                     r.J[q] = jn;
                     if (own) {
                         const int o = (rj - T) * TBT + (ri - T);
@@ -266,12 +317,13 @@ __global__ void __launch_bounds__(TBN, 1)
                         }
                     }
                 } else {
-                    en = ez + (curl - src) * (gap ? c.inv_eps_g : c.inv_eps_s);
+                    en = ez[k] + (curl - src) * (gap ? c.inv_eps_g : c.inv_eps_s);
                     if (MODE == 0 && own && des && rec) rec[dg] = en;
                 }
                 if (MODE == 0 && own && gap && gap_rec) gap_rec[gidx] = en;
                 r.ez[q] = en;
             }
+        }
         __syncthreads();
     }
 
