@@ -33,13 +33,16 @@ namespace fdtd {
 namespace {
 
 // Tiles: 8 x 8 x 2 threads, four x-adjacent nodes each, i.e.
-// 32 x 8 x 2 nodes (a warp reads 128 contiguous bytes per row), up to 5
-// blocks per SM in FP32.  Shapes (at 768 threads per SM): 8x8x4 at 3 /
-// 8x8x2 at 6 / 4x8x4 at 6 / 8x4x2 at 12 per SM; 8x8x2 and 4x8x4 were
-// fastest, by 3-5 %.  Occupancy against register spills (8x8x2; 256^3 and
-// 512x512x384 Gcell/s): 6 blocks (80 registers, 100-260 B of spill stores)
-// 39.2 / 45.9, 5 blocks (102 registers, 28-80 B) 39.5 / 46.6, 4 blocks (128
-// registers, no spills) 38.8 / 44.6.
+// 32 x 8 x 2 nodes (a warp reads 128 contiguous bytes per row).  Shapes
+// (at 768 threads per SM): 8x8x4 at 3 / 8x8x2 at 6 / 4x8x4 at 6 / 8x4x2 at
+// 12 per SM; 8x8x2 and 4x8x4 were fastest, by 3-5 %.  Blocks per SM in
+// FP32 (the register budget): H 6 (80 registers), forward E 7 (72), adjoint
+// E 6 (80).  With the CPML terms taken one axis at a time the kernels need
+// about 100 registers unbounded (128-136 with all six psi pairs held), so
+// these bounds spill little (16-44 B; 148 B in the adjoint E).  256^3
+// forward step: 5 blocks everywhere 242.6 us, 6 everywhere 229.3, H and
+// forward E at 7 227.4, everything at 7 227.4 (adjoint 465 against 457 at
+// 6), H at 7 with E at 6 231.7.
 constexpr int VX = 4, TBX = 8, TBY = 8, TBZ = 2;
 constexpr int TX = TBX * VX;
 static_assert(WAVE3D_TX == TX && WAVE3D_TY == TBY && WAVE3D_TZ == TBZ, "wavefront tiles are the step tiles");
@@ -133,93 +136,140 @@ __device__ __forceinline__ long long pidx(const Geo3D &g, int ax, int s, int i, 
     return ((long long)s * g.n[1] + j) * g.px + i;
 }
 
-// CPML-corrected curl of four x-adjacent nodes (i0 .. i0+3, row j, plane k)
-// for all three components: component c takes the derivative d[c][0] along
-// a = c+1 and d[c][1] along b = c+2 (cyclic), each divided by kappa and, in
-// the slab of its axis, plus psi <- b psi + c d; out[c] = S (t_a - t_b).
-// Along y and z the slab index and coefficients are those of row j / plane
-// k, and the psi arrays of y- and z-slabs are x-contiguous, so psi moves as
-// one vector; along x both are taken per node.  In two parts: cpml_load
-// issues the psi loads (the kernels call it before their field loads, so
-// that both round trips overlap), cpml_apply updates psi, stores it and
-// forms the curl.
-template <typename R, bool HALF, bool COH>
-__device__ __forceinline__ void cpml_load(const Geo3D &g, R *const (&psi)[3][2], int i0, int j, int k, int sy, int sz,
-                                          int (&sx)[4], R (&ps)[3][2][4])
+// CPML-corrected curl of four x-adjacent nodes (i0 .. i0+3, row j, plane k),
+// one axis at a time.  Component c takes the derivative d[c][0] along
+// a = c+1 and d[c][1] along b = c+2 (cyclic), so the two terms along axis
+// ax are (c, h) = ((ax+2) % 3, 0) and ((ax+1) % 3, 1).  Each term becomes
+// t = d / kappa, plus, in the slab of its axis, psi <- b psi + c d and
+// t += psi; the caller forms S (t_a - t_b).  Along y and z the slab index
+// and coefficients are those of row j / plane k, and the psi arrays of y-
+// and z-slabs are x-contiguous, so psi moves as one vector; along x both
+// are taken per node.  The kernels load the psi pair of one axis (the
+// first slab axis in the order z, y, x: the only one on a face of the
+// absorbing shell) before their field loads, so that both round trips
+// overlap; the pairs of further axes (edges and corners of the shell) are
+// loaded where they are used.  Only one pair is held across the field
+// loads, not all six.
+template <bool HALF>
+__device__ __forceinline__ void slab_x(const Geo3D &g, int i0, int (&sx)[4])
 {
-    const int np = g.npml;
 #pragma unroll
     for (int v = 0; v < 4; ++v)  // nodes past the last one are row padding: no slab
-        sx[v] = i0 + v >= g.n[0] ? -1 : (HALF ? slabH(i0 + v, g.n[0], np) : slabE(i0 + v, g.n[0], np));
-    const long long iy = pidx(g, 1, sy, i0, j, k), iz = pidx(g, 2, sz, i0, j, k);
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int ax = (c + 1 + h) % 3;
-            zero4(ps[c][h]);
-            if (ax == 0) {
-#pragma unroll
-                for (int v = 0; v < 4; ++v)
-                    if (sx[v] >= 0) ps[c][h][v] = psi[c][h][pidx(g, 0, sx[v], i0 + v, j, k)];
-            } else if (ax == 1) {
-                if (sy >= 0) ldv<COH>(psi[c][h] + iy, ps[c][h]);
-            } else {
-                if (sz >= 0) ldv<COH>(psi[c][h] + iz, ps[c][h]);
-            }
-        }
+        sx[v] = i0 + v >= g.n[0] ? -1 : (HALF ? slabH(i0 + v, g.n[0], g.npml) : slabE(i0 + v, g.n[0], g.npml));
 }
 
-template <typename R>
-__device__ __forceinline__ void cpml_apply(const Geo3D &g, R *const (&psi)[3][2], const R *const (&tb)[3],
-                                           const R *const (&tc)[3], const R *const (&tk)[3], int i0, int j, int k,
-                                           int sy, int sz, R S, const R (&d)[3][2][4], const int (&sx)[4],
-                                           R (&ps)[3][2][4], R (&out)[3][4])
+template <typename R, bool COH, int AX>
+__device__ __forceinline__ void cpml_load_axis(const Geo3D &g, R *const (&psi)[3][2], int i0, int j, int k, int sy,
+                                               int sz, const int (&sx)[4], R (&p)[2][4])
 {
-    const long long iy = pidx(g, 1, sy, i0, j, k), iz = pidx(g, 2, sz, i0, j, k);
-    // coefficient tables are read-only: non-coherent loads, free to move past stores
-    // with kappa = 1 everywhere the 1/kappa tables are not read (the product
-    // by 1 below is exact, so the result is the same)
-    const bool k1 = g.kappa1 != 0;
-    const R by = __ldg(tb[1] + j), cy = __ldg(tc[1] + j), ky = k1 ? R(1) : __ldg(tk[1] + j);
-    const R bz = __ldg(tb[2] + k), cz = __ldg(tc[2] + k), kz = k1 ? R(1) : __ldg(tk[2] + k);
-    R t[2][4];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int h = 0; h < 2; ++h) {
+        const int c = (AX + 2 - h) % 3;
+        zero4(p[h]);
+        if (AX == 0) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int ax = (c + 1 + h) % 3;
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const bool in = ax == 0 ? sx[v] >= 0 : (ax == 1 ? sy >= 0 : sz >= 0);
-                const R kk = ax == 0 ? ((!k1 && i0 + v < g.n[0]) ? __ldg(tk[0] + i0 + v) : R(1)) : (ax == 1 ? ky : kz);
-                t[h][v] = d[c][h][v] * kk;
-                if (in) {
-                    const R bb = ax == 0 ? __ldg(tb[0] + i0 + v) : (ax == 1 ? by : bz);
-                    const R cc = ax == 0 ? __ldg(tc[0] + i0 + v) : (ax == 1 ? cy : cz);
-                    ps[c][h][v] = bb * ps[c][h][v] + cc * d[c][h][v];
-                    t[h][v] += ps[c][h][v];
-                }
-            }
+            for (int v = 0; v < 4; ++v)
+                if (sx[v] >= 0) p[h][v] = psi[c][h][pidx(g, 0, sx[v], i0 + v, j, k)];
+        } else if (AX == 1) {
+            if (sy >= 0) ldv<COH>(psi[c][h] + pidx(g, 1, sy, i0, j, k), p[h]);
+        } else {
+            if (sz >= 0) ldv<COH>(psi[c][h] + pidx(g, 2, sz, i0, j, k), p[h]);
         }
-#pragma unroll
-        for (int v = 0; v < 4; ++v) out[c][v] = rn_mul(S, t[0][v] - t[1][v]);
     }
+}
+
+// The early load: the pair of axis pa (2, 1 or 0).
+template <typename R, bool COH>
+__device__ __forceinline__ void cpml_preload(const Geo3D &g, R *const (&psi)[3][2], int pa, int i0, int j, int k,
+                                             int sy, int sz, const int (&sx)[4], R (&p)[2][4])
+{
+    if (pa == 2) cpml_load_axis<R, COH, 2>(g, psi, i0, j, k, sy, sz, sx, p);
+    else if (pa == 1) cpml_load_axis<R, COH, 1>(g, psi, i0, j, k, sy, sz, sx, p);
+    else cpml_load_axis<R, COH, 0>(g, psi, i0, j, k, sy, sz, sx, p);
+}
+
+// Axis AX: d[c][h] <- d / kappa (+ the updated psi in the slab of AX) for
+// its two terms, psi stored back.  pre: the pair loaded early when pa == AX.
+template <typename R, bool COH, int AX>
+__device__ __forceinline__ void cpml_axis(const Geo3D &g, R *const (&psi)[3][2], const R *const (&tb)[3],
+                                          const R *const (&tc)[3], const R *const (&tk)[3], int i0, int j, int k,
+                                          int sy, int sz, const int (&sx)[4], int pa, const R (&pre)[2][4],
+                                          R (&d)[3][2][4])
+{
+    // with kappa = 1 everywhere the 1/kappa tables are not read (the product
+    // by 1 is exact, so the result is the same); coefficient tables are
+    // read-only: non-coherent loads, free to move past stores
+    const bool k1 = g.kappa1 != 0;
+    R kk[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+        kk[v] = AX == 0 ? ((!k1 && i0 + v < g.n[0]) ? __ldg(tk[0] + i0 + v) : R(1))
+                        : (k1 ? R(1) : __ldg(tk[AX] + (AX == 1 ? j : k)));
+    const bool any = AX == 0 ? (sx[0] >= 0 || sx[1] >= 0 || sx[2] >= 0 || sx[3] >= 0) : (AX == 1 ? sy >= 0 : sz >= 0);
+    if (!any) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) d[(AX + 2 - h) % 3][h][v] = d[(AX + 2 - h) % 3][h][v] * kk[v];
+        return;
+    }
+    R ps[2][4];
+    if (pa == AX) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) ps[h][v] = pre[h][v];
+    } else {
+        cpml_load_axis<R, COH, AX>(g, psi, i0, j, k, sy, sz, sx, ps);
+    }
+    R bb[4], cc[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        if (AX == 0) {
+            bb[v] = sx[v] >= 0 ? __ldg(tb[0] + i0 + v) : R(0);
+            cc[v] = sx[v] >= 0 ? __ldg(tc[0] + i0 + v) : R(0);
+        } else {
+            bb[v] = __ldg(tb[AX] + (AX == 1 ? j : k));
+            cc[v] = __ldg(tc[AX] + (AX == 1 ? j : k));
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int c = (AX + 2 - h) % 3;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const R dd = d[c][h][v];
+            R t = dd * kk[v];
+            if (AX != 0 || sx[v] >= 0) {
+                ps[h][v] = bb[v] * ps[h][v] + cc[v] * dd;
+                t += ps[h][v];
+            }
+            d[c][h][v] = t;
+        }
+        if (AX == 0) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+                if (sx[v] >= 0) psi[c][h][pidx(g, 0, sx[v], i0 + v, j, k)] = ps[h][v];
+        } else {
+            st4(psi[c][h] + pidx(g, AX, AX == 1 ? sy : sz, i0, j, k), ps[h]);
+        }
+    }
+}
+
+// All three axes (z, y, x), then out[c] = S (t_a - t_b).
+template <typename R, bool COH>
+__device__ __forceinline__ void cpml_curl(const Geo3D &g, R *const (&psi)[3][2], const R *const (&tb)[3],
+                                          const R *const (&tc)[3], const R *const (&tk)[3], int i0, int j, int k,
+                                          int sy, int sz, const int (&sx)[4], int pa, const R (&pre)[2][4], R S,
+                                          R (&d)[3][2][4], R (&out)[3][4])
+{
+    cpml_axis<R, COH, 2>(g, psi, tb, tc, tk, i0, j, k, sy, sz, sx, pa, pre, d);
+    cpml_axis<R, COH, 1>(g, psi, tb, tc, tk, i0, j, k, sy, sz, sx, pa, pre, d);
+    cpml_axis<R, COH, 0>(g, psi, tb, tc, tk, i0, j, k, sy, sz, sx, pa, pre, d);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int ax = (c + 1 + h) % 3;
-            if (ax == 0) {
-#pragma unroll
-                for (int v = 0; v < 4; ++v)
-                    if (sx[v] >= 0) psi[c][h][pidx(g, 0, sx[v], i0 + v, j, k)] = ps[c][h][v];
-            } else if (ax == 1) {
-                if (sy >= 0) st4(psi[c][h] + iy, ps[c][h]);
-            } else {
-                if (sz >= 0) st4(psi[c][h] + iz, ps[c][h]);
-            }
-        }
+        for (int v = 0; v < 4; ++v) out[c][v] = rn_mul(S, d[c][0][v] - d[c][1][v]);
 }
 
 // H half step, four x-adjacent nodes per thread:
@@ -243,9 +293,13 @@ __device__ __forceinline__ void h_tile(const Geo3D &g, const State3D<R> &s, cons
     const int sy = slabH(j, n1, np), sz = slabH(k, n2, np);
     const bool xslab = i0 < np || i0 + VX - 1 >= n0 - 1 - np;
     const bool pml = xslab || sy >= 0 || sz >= 0;
-    int sx[4];
-    R ps[3][2][4];
-    if (pml) cpml_load<R, true, COH>(g, s.ph, i0, j, k, sy, sz, sx, ps);
+    int sx[4], pa = 0;
+    R pre[2][4];
+    if (pml) {
+        slab_x<true>(g, i0, sx);
+        pa = sz >= 0 ? 2 : (sy >= 0 ? 1 : 0);
+        cpml_preload<R, COH>(g, s.ph, pa, i0, j, k, sy, sz, sx, pre);
+    }
     R ex[4], exN[4], exU[4], ey[4], eyU[4], ez[4], ezN[4], hx[4], hy[4], hz[4];
     ldv<COH>(s.E[0] + q, ex);
     ldv<COH>(s.E[1] + q, ey);
@@ -289,7 +343,7 @@ __device__ __forceinline__ void h_tile(const Geo3D &g, const State3D<R> &s, cons
             d[2][0][v] = (v < 3 ? ey[v + 1] : eyE) - ey[v];      // d_x Ey
             d[2][1][v] = exN[v] - ex[v];                         // d_y Ex
         }
-        cpml_apply<R>(g, s.ph, pm.bH, pm.cH, pm.kiH, i0, j, k, sy, sz, S, d, sx, ps, cu);
+        cpml_curl<R, COH>(g, s.ph, pm.bH, pm.cH, pm.kiH, i0, j, k, sy, sz, sx, pa, pre, S, d, cu);
     }
     if (xin && yin && zin) {
 #pragma unroll
@@ -336,7 +390,7 @@ __device__ __forceinline__ void h_tile(const Geo3D &g, const State3D<R> &s, cons
 // The H half step of the whole grid, bottom up or (zrev) top down; FOLD:
 // with the plane wave's H-face corrections of incident row inc.
 template <typename R, bool FOLD>
-__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
+__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 6 : 1)
     k_h3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm, int zrev, const R *inc)
 {
     wait_previous_grid();
@@ -364,9 +418,13 @@ __device__ __forceinline__ void e_tile(const Geo3D &g, const State3D<R> &s, cons
     const int sy = slabE(j, n1, np), sz = slabE(k, n2, np);
     const bool xslab = i0 < np || i0 + VX - 1 >= n0 - np;
     const bool pml = xslab || sy >= 0 || sz >= 0;
-    int sx[4];
-    R ps[3][2][4];
-    if (pml) cpml_load<R, false, COH>(g, s.pe, i0, j, k, sy, sz, sx, ps);
+    int sx[4], pa = 0;
+    R pre[2][4];
+    if (pml) {
+        slab_x<false>(g, i0, sx);
+        pa = sz >= 0 ? 2 : (sy >= 0 ? 1 : 0);
+        cpml_preload<R, COH>(g, s.pe, pa, i0, j, k, sy, sz, sx, pre);
+    }
     R hx[4], hxS[4], hxD[4], hy[4], hyD[4], hz[4], hzS[4], e[3][4];
     ldv<COH>(s.H[0] + q, hx);
     ldv<COH>(s.H[1] + q, hy);
@@ -411,7 +469,7 @@ __device__ __forceinline__ void e_tile(const Geo3D &g, const State3D<R> &s, cons
             d[2][0][v] = hy[v] - (v > 0 ? hy[v - 1] : hyW);      // d_x Hy
             d[2][1][v] = hx[v] - hxS[v];                         // d_y Hx
         }
-        cpml_apply<R>(g, s.pe, pm.bE, pm.cE, pm.kiE, i0, j, k, sy, sz, c.S, d, sx, ps, curl);
+        cpml_curl<R, COH>(g, s.pe, pm.bE, pm.cE, pm.kiE, i0, j, k, sy, sz, sx, pa, pre, c.S, d, curl);
     }
     // E_c is updated where p <= n-2 along c and 1 <= p <= n-2 across; a
     // component that is not updated keeps its value (zero on the walls).
@@ -541,7 +599,7 @@ __device__ __forceinline__ void e_tile(const Geo3D &g, const State3D<R> &s, cons
 }
 
 template <typename R, int MODE, bool FOLD>
-__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? 5 : 1)
+__global__ void __launch_bounds__(TBX *TBY *TBZ, sizeof(R) == 4 ? (MODE == 1 ? 6 : 7) : 1)
     k_e3d(Geo3D g, State3D<R> s, int slot, Pml3D<R> pm, Step3D<R> a3, int zrev)
 {
     wait_previous_grid();
