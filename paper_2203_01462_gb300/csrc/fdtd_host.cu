@@ -520,7 +520,7 @@ struct Ctx2D final : fdtd_ctx {
     // Temporal blocking (kernels_tb2d.cu): with multi_steps > 1 the forward
     // and the full-history adjoint advance up to min(multi_steps, tb_max)
     // steps per launch.
-    int tb_max = 0;
+    int tb_max = 0, tb_tile = 32;
     int tb_steps() const { return (multi_steps > 1 && tb_max > 0) ? std::min(multi_steps, tb_max) : 0; }
     // Steps of the next run from step n (forward): at most T, ending on the
     // guard's multiples while the forward is guarded.
@@ -643,13 +643,15 @@ struct Ctx2D final : fdtd_ctx {
         tb_max = tb2d_max_steps<R>();
         // Default: temporal blocking on FP32 grids of at most one 32 x 32 tile
         // per SM, where the launch-per-step kernels are single partial waves
-        // (measured: 316^2, 7.1 -> 3.4 us per forward step); larger or FP64 grids run
-        // faster one launch per step.
+        // (measured: 316^2, 7.1 -> 3.4 us per forward step with 32 x 32
+        // tiles); larger or FP64 grids run faster one launch per step.  The
+        // tile side is the smallest whose tiles still fit one wave.
         {
             int dev = 0, sms = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const long long tiles = (long long)((c.nx + 31) / 32) * ((c.ny + 31) / 32);
+            tb_tile = tb2d_tile(c.nx, c.ny, sms);
+            const long long tiles = (long long)((c.nx + tb_tile - 1) / tb_tile) * ((c.ny + tb_tile - 1) / tb_tile);
             if (sizeof(R) == 4 && tb_max > 0 && tiles <= sms) multi_steps = TB_MAX;
         }
         return cuda_ok(cudaStreamSynchronize(st));
@@ -755,6 +757,7 @@ struct Ctx2D final : fdtd_ctx {
             for (int n = n0; n < n0 + count;) {
                 Tb2D<R> w{};
                 w.count = tb_run(n, n0 + count, T);
+                w.tile = tb_tile;
                 w.n0 = n;
                 w.rec0 = n0;
                 w.Mdi = Mdi;
@@ -792,6 +795,7 @@ struct Ctx2D final : fdtd_ctx {
             for (int m = m_hi; m > m_lo;) {
                 Tb2D<R> w{};
                 w.count = std::min(T, m - m_lo);
+                w.tile = tb_tile;
                 w.n0 = m;
                 w.rec0 = slot0;
                 w.Mdi = Mdi;

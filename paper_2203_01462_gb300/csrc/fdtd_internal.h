@@ -251,16 +251,17 @@ template <typename R>
 int launch_step3d(int mode, const Geo3D &g, const State3D<R> &s, int coef_slot, const Pml3D<R> &pm,
                   const Step3D<R> &a, cudaStream_t st);
 
-// Temporally blocked 2D E_z steps (kernels_tb2d.cu): a block owns a 32 x 32
-// tile and advances count <= TB_MAX steps on it and a halo of count nodes in
-// shared memory, reading state `in` and writing its tile into `out`.
+// Temporally blocked 2D E_z steps (kernels_tb2d.cu): a block owns a square
+// tile (`tile` nodes a side, tb2d_tile) and advances count <= TB_MAX steps
+// on it and a halo of count nodes in shared memory, reading state `in` and
+// writing its tile into `out`.
 // Forward: steps n0 .. n0+count-1 (source row n, gap row n+1, design record
 // slot n - rec0); adjoint: m = n0 down to n0-count+1 (gap row m, record slot
 // m-1-rec0), G the accumulator.
 constexpr int TB_MAX = 8;
 template <typename R>
 struct Tb2D {
-    int count, n0, rec0;
+    int count, n0, rec0, tile;
     long long Mdi;
     const R *src;
     R *gap;
@@ -269,6 +270,8 @@ struct Tb2D {
     double *G;
 };
 size_t tb2d_smem_bytes(int esz, int T);
+// Tile side of the blocked kernel for an nx x ny grid on `sms` SMs.
+int tb2d_tile(int nx, int ny, int sms);
 // The most steps per launch whose region fits a block's shared memory (and
 // the kernels' shared-memory limit raised to it), or 0.
 template <typename R>
