@@ -3,7 +3,7 @@
  * surrogate: a small convolutional U-Net that maps a design rho and the
  * damping level to an estimate of the sensitivity map dW~/drho, so that an
  * optimizer can take cheap intermediate design steps between full
- * forward + adjoint runs (which stay the reference and judge the steps).
+ * forward + adjoint runs (which stay the reference and check the steps).
  * The paper has no such component; its Sec. 1 notes that learned models need
  * large data sets, which the adjoint runs themselves provide here.
  *
