@@ -260,13 +260,14 @@ fdtd_status fdtd_set_filter_width(fdtd_ctx *ctx, double sigma);
  * default.  Such passes are not replayed as CUDA graphs.
  *
  * 2D E_z contexts: with steps > 1 the forward (and recompute) and the
- * full-history adjoint advance up to min(steps, 8) steps per launch by
- * temporal blocking: a block owns a 32 x 32 node tile, loads it with a halo
- * of that many nodes into shared memory, advances all the steps there and
- * writes back its tile, so no block waits for another.  Small grids, whose
- * launch-per-step kernels are single partial waves, gain: the default is 8
- * for FP32 grids of at most one 32 x 32 tile per SM (316^2: 7.1 -> 3.4 us
- * per forward step) and 1 otherwise (a 640^2 grid or an FP64 one runs
+ * full-history adjoint advance up to min(steps, 8) steps per launch (4 in
+ * FP64) by temporal blocking: a block owns a square tile (16 to 32 nodes a
+ * side, the smallest whose tiles fit one wave of blocks), loads it with a
+ * halo of that many nodes into shared memory, advances all the steps there
+ * and writes back its tile, so no block waits for another.  Small grids,
+ * whose launch-per-step kernels are single partial waves, gain: the default
+ * is 8 for FP32 grids of at most one 32 x 32 tile per SM (316^2: 7.1 -> 2.9
+ * us per forward step) and 1 otherwise (a 640^2 grid or an FP64 one runs
  * slower blocked).  Results agree with the launch-per-step path to rounding
  * (the per-node arithmetic of its generic path).
  *

@@ -299,7 +299,8 @@ class Solver:
     def set_steps_per_launch(self, steps: int) -> None:
         """Time steps per launch (1: one launch per step): in-plane 2D mode, a
         cooperative launch with grid barriers; 2D E_z, temporal blocking on
-        32 x 32 tiles with a halo in shared memory (up to 8 steps)."""
+        square tiles (16 to 32 nodes a side) with a halo in shared memory (up
+        to 8 steps, 4 in FP64)."""
         _check(self.lib.fdtd_set_steps_per_launch(self.ctx, int(steps)), "fdtd_set_steps_per_launch")
 
     def set_wavefront(self, steps: int) -> None:
